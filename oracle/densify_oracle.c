@@ -1,0 +1,356 @@
+/*
+ * densify_oracle.c - plain, slow FP64 CPU oracle of the LiDAR densification
+ * path (Murasaki et al., "Real-Time LiDAR Point Cloud Densification for
+ * Low-Latency Spatial Data Transmission").
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this code. The product path (the CUDA
+ * library) never calls it, and it shares no code, header, table or constant
+ * with the CUDA path.
+ *
+ * Every function is the definition written out as loops, in FP64, with no
+ * blocking, fusion or reordering beyond what the definition states:
+ *
+ *   oracle_compose        calibration: world<-camera inverse times LiDAR pose
+ *                         (Sec. 2, "calibrated in advance")
+ *   oracle_project        merged scans -> nearest-depth z-buffer (Sec. 2;
+ *                         the depth image D and mask B of Algorithm 1).
+ *                         The pixel index and stored depth are decided in the
+ *                         kernel's precision (FP32), emulated exactly here.
+ *   oracle_project_fp64   the same projection in pure FP64 (informational)
+ *   oracle_pool           1/3 pooling of depth, mask and guide (Sec. 5,
+ *                         two-stage filtering)
+ *   oracle_jbf_gather     Eq. (1)-(4), gather form, plain or shifted exponent
+ *   oracle_jbf_scatter    Algorithm 1 (colour weights, Gaussian, Hadamard
+ *                         with the spatial Gaussian, transpose-convolution
+ *                         scatter, normalisation)
+ *   oracle_upsample       restore of the stage-1 result to full resolution
+ *                         (Sec. 5, two-stage filtering)
+ *   oracle_backproject    dense depth -> coloured 3D points (Sec. 2, Sec. 5)
+ *
+ * Parity pins: all functions above are pinned by the CPU tests (closed forms,
+ * brute force, invariants). The exact pooling / restore semantics of the
+ * two-stage filter are a documented reading of Sec. 5, which only says
+ * "pooling" and "restoring".
+ *
+ * Build with -ffp-contract=off: the FP32 emulation relies on every product
+ * and sum being rounded separately.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------------ */
+/* FP32 emulation: an FP64 operation on two FP32 values, rounded once to FP32,
+ * equals the correctly rounded FP32 operation (53 >= 2*24 + 2). */
+static float r32(double x) { return (float)x; }
+static float mul32(float a, float b) { return r32((double)a * (double)b); }
+static float add32(float a, float b) { return r32((double)a + (double)b); }
+static float div32(float a, float b) { return r32((double)a / (double)b); }
+
+static uint32_t f32_bits(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
+static float bits_f32(uint32_t u) { float f; memcpy(&f, &u, 4); return f; }
+
+#define ZBUF_EMPTY 0x7F800000u /* bit pattern of +inf */
+
+/* ------------------------------------------------------------------------ */
+/* Calibration (Sec. 2). M = inverse(cam_to_world) * lidar_to_world, with the
+ * rigid inverse [R^T, -R^T t]. Inputs are row-major 4x4 rigid transforms;
+ * the output is the top 3x4 block, row-major, in FP64 and rounded once to
+ * FP32. The operation order is fixed: every dot product is summed left to
+ * right over k = 0, 1, 2 and the translation is added last. */
+void oracle_compose(const double cam_to_world[16], const double lidar_to_world[16],
+                    double out64[12], float out32[12])
+{
+    double Rinv[3][3], tinv[3];
+    for (int i = 0; i < 3; ++i)
+        for (int k = 0; k < 3; ++k)
+            Rinv[i][k] = cam_to_world[k * 4 + i];          /* R^T */
+    for (int i = 0; i < 3; ++i) {
+        double s = Rinv[i][0] * cam_to_world[0 * 4 + 3];
+        s = s + Rinv[i][1] * cam_to_world[1 * 4 + 3];
+        s = s + Rinv[i][2] * cam_to_world[2 * 4 + 3];
+        tinv[i] = -s;                                       /* -R^T t */
+    }
+    for (int i = 0; i < 3; ++i) {
+        for (int j = 0; j < 4; ++j) {
+            double s = Rinv[i][0] * lidar_to_world[0 * 4 + j];
+            s = s + Rinv[i][1] * lidar_to_world[1 * 4 + j];
+            s = s + Rinv[i][2] * lidar_to_world[2 * 4 + j];
+            if (j == 3) s = s + tinv[i];
+            out64[i * 4 + j] = s;
+            out32[i * 4 + j] = (float)s;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Projection and nearest-depth z-buffer (Sec. 2: "merged and projected into
+ * the camera view to form a single depth image"; Algorithm 1 input D, B).
+ *
+ * For each point p = (x, y, z) of a scan with FP32 matrix M (3x4):
+ *   xc = ((m00 x + m01 y) + m02 z) + m03, likewise yc, zc   (FP32, each op rounded)
+ *   u  = fx (xc / zc) + cx,  v = fy (yc / zc) + cy           (FP32, each op rounded)
+ * The point is kept iff zc > 0, zc finite, 0 <= u < W and 0 <= v < H; it
+ * lands on pixel (floor u, floor v). The z-buffer keeps the smallest camera
+ * depth zc, stored as its FP32 bit pattern (order-preserving for positive
+ * values); an empty pixel holds the bit pattern of +inf.
+ *
+ * zbuf must be cleared to ZBUF_EMPTY by the caller (scans are merged into
+ * one buffer). Points are read with a stride of stride_floats floats.
+ * Returns the number of points that landed inside the image. */
+int64_t oracle_project(const float M[12], const float *xyz, int64_t n, int64_t stride_floats,
+                       int W, int H, float fx, float fy, float cx, float cy, uint32_t *zbuf)
+{
+    int64_t kept = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        const float x = xyz[k * stride_floats + 0];
+        const float y = xyz[k * stride_floats + 1];
+        const float z = xyz[k * stride_floats + 2];
+        float c[3];
+        for (int i = 0; i < 3; ++i) {
+            float s = mul32(M[i * 4 + 0], x);
+            s = add32(s, mul32(M[i * 4 + 1], y));
+            s = add32(s, mul32(M[i * 4 + 2], z));
+            s = add32(s, M[i * 4 + 3]);
+            c[i] = s;
+        }
+        if (!(c[2] > 0.0f) || !(c[2] < INFINITY)) continue;
+        const float u = add32(mul32(fx, div32(c[0], c[2])), cx);
+        const float v = add32(mul32(fy, div32(c[1], c[2])), cy);
+        if (!(u >= 0.0f && u < (float)W && v >= 0.0f && v < (float)H)) continue;
+        const int i = (int)floor((double)u);
+        const int j = (int)floor((double)v);
+        const uint32_t b = f32_bits(c[2]);
+        uint32_t *cell = &zbuf[(int64_t)j * W + i];
+        if (b < *cell) *cell = b;
+        ++kept;
+    }
+    return kept;
+}
+
+/* Pure FP64 projection of the same points (informational: it shows how many
+ * pixels an FP64 pipeline would assign differently). depth must be cleared to
+ * +inf by the caller; it keeps the nearest FP64 camera depth per pixel. */
+int64_t oracle_project_fp64(const double M[12], const float *xyz, int64_t n, int64_t stride_floats,
+                            int W, int H, double fx, double fy, double cx, double cy, double *depth)
+{
+    int64_t kept = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        const double p[3] = {xyz[k * stride_floats], xyz[k * stride_floats + 1], xyz[k * stride_floats + 2]};
+        double c[3];
+        for (int i = 0; i < 3; ++i)
+            c[i] = M[i * 4] * p[0] + M[i * 4 + 1] * p[1] + M[i * 4 + 2] * p[2] + M[i * 4 + 3];
+        if (!(c[2] > 0.0) || !isfinite(c[2])) continue;
+        const double u = fx * (c[0] / c[2]) + cx, v = fy * (c[1] / c[2]) + cy;
+        if (!(u >= 0.0 && u < W && v >= 0.0 && v < H)) continue;
+        double *cell = &depth[(int64_t)floor(v) * W + (int64_t)floor(u)];
+        if (c[2] < *cell) *cell = c[2];
+        ++kept;
+    }
+    return kept;
+}
+
+/* Depth image D and mask B from the z-buffer (Algorithm 1 input). */
+void oracle_zbuf_to_depth(const uint32_t *zbuf, int64_t npix, double *D, double *B)
+{
+    for (int64_t k = 0; k < npix; ++k) {
+        if (zbuf[k] != ZBUF_EMPTY) { D[k] = (double)bits_f32(zbuf[k]); B[k] = 1.0; }
+        else { D[k] = 0.0; B[k] = 0.0; }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Pooling to 1/f resolution (Sec. 5, first stage: "reduced to 1/3 ... using
+ * pooling"). Coarse pixel (I, J) covers the full-resolution block
+ * [fI, fI+f) x [fJ, fJ+f) clipped to the image (ceil mode). Reading: average
+ * pooling of D*B and of B as in a CNN; the uniform divisor cancels in the
+ * filter's ratio, so the outputs are the block sums
+ *   ssum(I,J) = sum of D over observed pixels,  cnt(I,J) = number observed,
+ * and the coarse guide is the mean RGB over the block's in-image pixels.
+ * guide is Hc x Wc x 3 (channel fastest); Hc = ceil(H/f), Wc = ceil(W/f). */
+void oracle_pool(const uint32_t *zbuf, const uint8_t *rgb, int64_t rgb_pitch, int W, int H, int f,
+                 double *ssum, double *cnt, double *guide)
+{
+    const int Wc = (W + f - 1) / f, Hc = (H + f - 1) / f;
+    for (int J = 0; J < Hc; ++J) {
+        for (int I = 0; I < Wc; ++I) {
+            double s = 0.0, c = 0.0, g[3] = {0.0, 0.0, 0.0}, npx = 0.0;
+            for (int y = J * f; y < J * f + f && y < H; ++y) {
+                for (int x = I * f; x < I * f + f && x < W; ++x) {
+                    const uint32_t z = zbuf[(int64_t)y * W + x];
+                    if (z != ZBUF_EMPTY) { s += (double)bits_f32(z); c += 1.0; }
+                    for (int ch = 0; ch < 3; ++ch) g[ch] += rgb[(int64_t)y * rgb_pitch + 3 * x + ch];
+                    npx += 1.0;
+                }
+            }
+            const int64_t o = (int64_t)J * Wc + I;
+            ssum[o] = s;
+            cnt[o] = c;
+            for (int ch = 0; ch < 3; ++ch) guide[o * 3 + ch] = g[ch] / npx;
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Joint bilateral filter, Eq. (1)-(4), gather form.
+ *
+ * For output pixel p and every in-image pixel q with max(|qx-px|,|qy-py|) <= r:
+ *   e(p,q) = ||I(q) - I(p)||^2 / (2 sigma_c^2) + ((qx-px)^2 + (qy-py)^2) / (2 sigma_p^2)
+ *   out(p) = sum_q beta_d(q) exp(-e) / sum_q beta(q) exp(-e)
+ * beta(q) is the observation weight (the mask B at a single stage, the block
+ * count after pooling) and beta_d(q) the matching depth sum (B*D, or the
+ * block depth sum). Only q with beta(q) > 0 are in the neighbour set eps(x)
+ * of Eq. (1). valid(p) = 1 iff that set is non-empty; an invalid output is 0.
+ *
+ * guide is H x W x 3 (channel fastest), on the 0-255 scale.
+ * shifted = 0: the plain form. shifted = 1: exp(-(e - e_min)) with e_min the
+ * smallest e over the neighbour set; the common factor exp(-e_min) cancels,
+ * so both forms are the same number up to rounding. */
+void oracle_jbf_gather(const double *guide, const double *beta, const double *beta_d,
+                       int W, int H, int r, double sigma_p, double sigma_c, int shifted,
+                       double *out, uint8_t *valid)
+{
+    const double kc = 1.0 / (2.0 * sigma_c * sigma_c);
+    const double kp = 1.0 / (2.0 * sigma_p * sigma_p);
+    for (int py = 0; py < H; ++py) {
+        for (int px = 0; px < W; ++px) {
+            const double *Ip = &guide[((int64_t)py * W + px) * 3];
+            double emin = INFINITY;
+            int any = 0;
+            if (shifted) {
+                for (int qy = py - r; qy <= py + r; ++qy) {
+                    for (int qx = px - r; qx <= px + r; ++qx) {
+                        if (qx < 0 || qx >= W || qy < 0 || qy >= H) continue;
+                        const int64_t q = (int64_t)qy * W + qx;
+                        if (!(beta[q] > 0.0)) continue;
+                        const double *Iq = &guide[q * 3];
+                        const double dc = (Iq[0] - Ip[0]) * (Iq[0] - Ip[0]) + (Iq[1] - Ip[1]) * (Iq[1] - Ip[1]) +
+                                          (Iq[2] - Ip[2]) * (Iq[2] - Ip[2]);
+                        const double ds = (double)(qx - px) * (qx - px) + (double)(qy - py) * (qy - py);
+                        const double e = dc * kc + ds * kp;
+                        if (e < emin) emin = e;
+                    }
+                }
+            } else {
+                emin = 0.0;
+            }
+            double num = 0.0, den = 0.0;
+            for (int qy = py - r; qy <= py + r; ++qy) {
+                for (int qx = px - r; qx <= px + r; ++qx) {
+                    if (qx < 0 || qx >= W || qy < 0 || qy >= H) continue;
+                    const int64_t q = (int64_t)qy * W + qx;
+                    if (!(beta[q] > 0.0)) continue;
+                    const double *Iq = &guide[q * 3];
+                    const double dc = (Iq[0] - Ip[0]) * (Iq[0] - Ip[0]) + (Iq[1] - Ip[1]) * (Iq[1] - Ip[1]) +
+                                      (Iq[2] - Ip[2]) * (Iq[2] - Ip[2]);
+                    const double ds = (double)(qx - px) * (qx - px) + (double)(qy - py) * (qy - py);
+                    const double w = exp(-(dc * kc + ds * kp - emin));  /* w_c * w_p, Eq. (2), (3) */
+                    num += beta_d[q] * w;                                  /* Eq. (1) numerator */
+                    den += beta[q] * w;                                    /* Eq. (4) */
+                    any = 1;
+                }
+            }
+            const int64_t o = (int64_t)py * W + px;
+            valid[o] = (uint8_t)any;
+            out[o] = any ? num / den : 0.0;
+        }
+    }
+}
+
+/* Joint bilateral filter as Algorithm 1 (scatter form).
+ * Step 1-3: for every source pixel (x, y) and offset (a, b) in [-r, r]^2, the
+ *   weight w = exp(-||I(x,y) - I(x+a,y+b)||^2 / (2 sigma_c^2))
+ *            * exp(-(a^2 + b^2) / (2 sigma_p^2)).
+ * Step 4: spread beta_d(x,y) w into num(x+a, y+b) and beta(x,y) w into
+ *   den(x+a, y+b) (transpose convolution; targets outside the image drop).
+ * Step 5: out = num / den where den > 0; valid = (den > 0).
+ * num and den are caller-provided scratch arrays of H x W doubles. */
+void oracle_jbf_scatter(const double *guide, const double *beta, const double *beta_d,
+                        int W, int H, int r, double sigma_p, double sigma_c,
+                        double *num, double *den, double *out, uint8_t *valid)
+{
+    const int64_t npix = (int64_t)W * H;
+    for (int64_t k = 0; k < npix; ++k) { num[k] = 0.0; den[k] = 0.0; }
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            const int64_t s = (int64_t)y * W + x;
+            if (!(beta[s] > 0.0)) continue;      /* D = B = 0 adds nothing */
+            const double *Is = &guide[s * 3];
+            for (int a = -r; a <= r; ++a) {          /* a along x, b along y */
+                for (int b = -r; b <= r; ++b) {
+                    const int tx = x + a, ty = y + b;
+                    if (tx < 0 || tx >= W || ty < 0 || ty >= H) continue;
+                    const int64_t t = (int64_t)ty * W + tx;
+                    const double *It = &guide[t * 3];
+                    double d2 = 0.0;
+                    for (int ch = 0; ch < 3; ++ch) d2 += (Is[ch] - It[ch]) * (Is[ch] - It[ch]);
+                    double w = exp(-d2 / (2.0 * sigma_c * sigma_c));                    /* step 2 */
+                    w = w * exp(-((double)a * a + (double)b * b) / (2.0 * sigma_p * sigma_p)); /* step 3 */
+                    num[t] += beta_d[s] * w;                                           /* step 4 */
+                    den[t] += beta[s] * w;
+                }
+            }
+        }
+    }
+    for (int64_t k = 0; k < npix; ++k) {                                               /* step 5 */
+        valid[k] = den[k] > 0.0;
+        out[k] = den[k] > 0.0 ? num[k] / den[k] : 0.0;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Restore to full resolution (Sec. 5, second stage: "the depth map after
+ * restoring it to the original resolution"). Nearest restore: full pixel
+ * (x, y) takes coarse pixel (x / f, y / f). Literal reading (override = 0):
+ * the stage-2 input is the restored stage-1 result, beta = restored valid,
+ * beta_d = restored depth. With override = 1, pixels observed in the full
+ * z-buffer keep their own depth instead (an alternative reading). */
+void oracle_upsample(const double *d1, const uint8_t *v1, int Wc, int Hc, int f, int W, int H,
+                     const uint32_t *zbuf, int override, double *beta, double *beta_d)
+{
+    (void)Hc;
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            const int64_t o = (int64_t)y * W + x;
+            const int64_t c = (int64_t)(y / f) * Wc + (x / f);
+            if (override && zbuf && zbuf[o] != ZBUF_EMPTY) {
+                beta[o] = 1.0;
+                beta_d[o] = (double)bits_f32(zbuf[o]);
+            } else {
+                beta[o] = v1[c] ? 1.0 : 0.0;
+                beta_d[o] = v1[c] ? d1[c] : 0.0;
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Back-projection to coloured points (Sec. 2: coloured point clouds in a
+ * common frame). For every valid pixel (x, y) in row-major order:
+ *   Z = depth, X = (x + 1/2 - cx) Z / fx, Y = (y + 1/2 - cy) Z / fy,
+ *   world = R (X, Y, Z) + t from cam_to_world, colour = RGB(x, y).
+ * out_xyz receives n x 3 doubles, out_rgba n packed colours
+ * (r | g << 8 | b << 16 | 255 << 24). Returns n. */
+int64_t oracle_backproject(const double *depth, const uint8_t *valid, const uint8_t *rgb, int64_t rgb_pitch,
+                           int W, int H, double fx, double fy, double cx, double cy,
+                           const double cam_to_world[16], double *out_xyz, uint32_t *out_rgba)
+{
+    int64_t n = 0;
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            const int64_t o = (int64_t)y * W + x;
+            if (!valid[o]) continue;
+            const double Z = depth[o];
+            const double X = ((double)x + 0.5 - cx) * Z / fx;
+            const double Y = ((double)y + 0.5 - cy) * Z / fy;
+            for (int i = 0; i < 3; ++i)
+                out_xyz[n * 3 + i] = cam_to_world[i * 4 + 0] * X + cam_to_world[i * 4 + 1] * Y +
+                                     cam_to_world[i * 4 + 2] * Z + cam_to_world[i * 4 + 3];
+            const uint8_t *c = &rgb[(int64_t)y * rgb_pitch + 3 * x];
+            out_rgba[n] = (uint32_t)c[0] | ((uint32_t)c[1] << 8) | ((uint32_t)c[2] << 16) | (255u << 24);
+            ++n;
+        }
+    }
+    return n;
+}
