@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark of the densification path on GB300.
+
+Workload (one step): a batch of B distinct 1920x1080 viewpoints, each with
+three staggered 128x1024 LiDAR sweeps (about 124k points each after 5%
+dropout, about 373k merged), projected with the nearest-depth z-buffer,
+densified with the two-stage joint bilateral filter (r=4 at 1/3 resolution,
+r=2 at full resolution, sigma_p 5 px, sigma_c 20) and back-projected to
+coloured points. Inputs are seeded synthetic scenes (the paper's capture data
+is not available). Metric: dense 1080p frames per second.
+
+  value   device time: inputs resident in HBM, L2 flushed (256 MiB write)
+          before every step, CUDA events on the launching stream around the
+          step's work, summed over K steps.
+  e2e     the same frames through the C ABI with pinned HOST buffers:
+          host->device copies of points and RGB and device->host copies of
+          depth, mask and points inside the timed region (wall clock).
+
+--impl reference times the FP64 CPU oracle (the method's plain definition)
+on the host cores, on a bounded sample of the same workload.
+
+Multi-GPU (torchrun): viewpoints are independent (no exchange between
+viewpoints in the paper's system), so each rank runs its own batch of views:
+weak scaling, no collective on the data path; rank 0 prints the total.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "1080p dense-depth frames/s (3 merged LiDAR scans, two-stage JBF r=4@1/3 + r=2, coloured points)"
+UNIT = "frames/s"
+STAGES = ((4, 5.0, 20.0), (2, 5.0, 20.0))
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--batch", type=int, default=8, help="viewpoints per step")
+    ap.add_argument("--views", type=int, default=8, help="distinct synthetic views generated")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-frames", type=int, default=4, help="frames in the oracle's timed sample")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# inputs
+# ---------------------------------------------------------------------------
+def _gen(args):
+    import scene
+    seed, idx, n = args
+    v = scene.make_view(seed, res="1080p", scene_kind="room", n_scans=3, beams=128, az_steps=1024,
+                        view_index=idx, n_views=n)
+    return v
+
+
+def make_views(n, seed0):
+    """Distinct 1080p three-scan viewpoints, generated in a spawn pool."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    jobs = [(seed0 + i, i % 7, 7) for i in range(n)]
+    workers = max(1, min(n, (os.cpu_count() or 2) - 1, 12))
+    if workers == 1:
+        return [_gen(j) for j in jobs]
+    with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_gen, jobs))
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for n, val in zip(names, p[5:9]):
+                if val.lower() == "active":
+                    reasons.add(n)
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+def cpu_oracle_rate(views, frames):
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    for i in range(frames):
+        oracle.densify_view(views[i % len(views)], num_stages=2, stages=STAGES)
+    dt = time.perf_counter() - t0
+    return frames / dt, dt
+
+
+def reference_arm(a, rank, world):
+    if rank != 0:
+        return
+    views = make_views(max(1, min(a.views, a.cpu_frames)), 1001)
+    import oracle
+    oracle.build()
+    for _ in range(min(a.warmup, 1)):
+        oracle.densify_view(views[0], num_stages=2, stages=STAGES)
+    per = max(1, a.cpu_frames // max(1, a.steps))
+    t0 = time.perf_counter()
+    n = 0
+    for s in range(a.steps):
+        for i in range(per):
+            oracle.densify_view(views[(s * per + i) % len(views)], num_stages=2, stages=STAGES)
+            n += 1
+    dt = time.perf_counter() - t0
+    rate = n / dt
+    sample = f"{n} frames of the 1080p three-scan workload, {per} per step, single thread FP64"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": 1000.0 * dt / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "1080p_3scan_two_stage", "frames_per_step": per, "resolution": "1920x1080",
+                   "scans": 3, "sweep": "128x1024", "stages": "r4@1/3 + r2", "parallelism": "host cores"},
+        "cpu_baseline": {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+def valid_taps_stage2(coarse_valid, W, H, pool=3, r=2):
+    """(output pixel, observed tap) pairs of the full-resolution filter."""
+    import numpy as np
+    from scipy.ndimage import correlate
+    b2 = np.kron(coarse_valid.astype(np.float64), np.ones((pool, pool)))[:H, :W]
+    return int(correlate(b2, np.ones((2 * r + 1, 2 * r + 1)), mode="constant").sum())
+
+
+def valid_taps_stage1(cnt_pos, r=4):
+    import numpy as np
+    from scipy.ndimage import correlate
+    return int(correlate(cnt_pos.astype(np.float64), np.ones((2 * r + 1, 2 * r + 1)), mode="constant").sum())
+
+
+def ours_arm(a, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2601_01210_gb300 import Densifier, build
+    from paper_2601_01210_gb300.densify import DENSIFY_MEM_HOST
+    from paper_2601_01210_gb300.frames import FrameBuffers
+
+    views = make_views(a.views, 1001 + 1000 * rank)   # before any CUDA call (spawn pool)
+    build.build()
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    B = a.batch
+    def fb(i, **kw):
+        v = views[i % len(views)]
+        return FrameBuffers(v.camera, v.rgb, [(s.xyz, s.lidar_to_world) for s in v.scans], device=dev, **kw)
+
+    bufs = [fb(i) for i in range(B)]
+    params = dict(num_stages=2, stages=STAGES, max_batch=B, max_inflight=max(B, 16), launch_policy=1, timing=1,
+                  batches_in_flight=1, hbm_budget_bytes=max(2 << 30, B * 48 << 20))
+    flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
+    with Densifier(params, device=local_rank, stream=stream.cuda_stream) as d:
+        def step():
+            ts = [d.submit(b.frame) for b in bufs]
+            return ts
+
+        for _ in range(max(3, a.warmup)):
+            for t in step():
+                d.poll(t, -1)
+        torch.cuda.synchronize()
+        # algorithmic work of the dominant kernel: observed taps of the full-resolution filter,
+        # counted from each distinct view's first-stage mask (outside the timed region)
+        probe = [fb(i, debug=True) for i in range(len(views))]
+        for t in [d.submit(b.frame) for b in probe]:
+            d.poll(t, -1)
+        torch.cuda.synchronize()
+        taps_view = [valid_taps_stage2(b.coarse_valid.cpu().numpy(), b.W, b.H) for b in probe]
+        taps2 = sum(taps_view[i % len(views)] for i in range(B))
+        del probe
+        d.reset_kernel_times()
+        if world > 1:
+            torch.distributed.barrier()
+        clocks = ClockSampler(local_rank)
+        clocks.start()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+        step_tickets = []
+        for k in range(a.steps):
+            flush_buf.fill_(k)                      # evict L2 between steps
+            ev[k][0].record(stream)
+            ts = step()
+            ev[k][1].record(stream)
+            step_tickets.append(ts)
+            for t in ts:
+                d.poll(t, -1)
+        torch.cuda.synchronize()
+        ck = clocks.stop()
+        step_ms = [s.elapsed_time(e) for s, e in ev]
+        total_ms = sum(step_ms)
+        times = d.kernel_times()
+        n_launch = sum(n for _, n in times.values())
+        gpu_launches = n_launch
+        total_t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        if world > 1:
+            torch.distributed.all_reduce(total_t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(total_t.item())
+        value = world * B * a.steps / (total_ms / 1000.0)
+
+        # e2e: host buffers through the C ABI
+        e2e = None
+        if not a.no_e2e:
+            hb = [fb(i, memory=DENSIFY_MEM_HOST) for i in range(B)]
+            for _ in range(2):
+                for t in [d.submit(b.frame) for b in hb]:
+                    d.poll(t, -1)
+            torch.cuda.synchronize()
+            h2d = sum(sum(x.numel() * 4 for x, _ in b.scans) + b.rgb.numel() for b in hb)
+            t0 = time.perf_counter()
+            for _ in range(a.steps):
+                for t in [d.submit(b.frame) for b in hb]:
+                    d.poll(t, -1)
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            d2h = sum(b.W * b.H * 5 + 8 + b.n_points() * 16 for b in hb)
+            e2e = {"value": B * a.steps / dt * world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+                   "d2h_bytes_per_step": int(d2h)}
+    if rank != 0:
+        return
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    # ALU peak of the filter: 152 SMs x 4 SMSPs x 32 lanes issue one instruction per clock; a tap needs
+    # 10 (3 sub, 3 mul/fma for the colour distance, 1 fma for the exponent, 1 ex2, 2 fma accumulate).
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak_gtap = sms * 128 / 10.0 * sm_max * 1e6 / 1e9
+    s2 = times.get("jbf_stage2", (0.0, 1))
+    avg_us = s2[0] / max(1, s2[1])
+    achieved = taps2 / (avg_us * 1e-6) / 1e9 if avg_us > 0 else 0.0
+    ktable = {k: {"total_us": round(v[0], 2), "launches": v[1], "avg_us": round(v[0] / max(1, v[1]), 3)}
+              for k, v in times.items()}
+    cpu = None
+    if not a.no_cpu_baseline:
+        rate, dt = cpu_oracle_rate(views, a.cpu_frames)
+        cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"{a.cpu_frames} frames of the same workload, single thread FP64 ({dt:.1f} s)"}
+    sorted_ms = sorted(step_ms)
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+        "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded room scenes, 3 LiDAR sweeps per view)",
+        "config": {"workload": "1080p_3scan_two_stage", "frames_per_step": B, "distinct_views": len(views),
+                   "resolution": "1920x1080", "scans": 3, "sweep": "128x1024", "stages": "r4@1/3 + r2",
+                   "sigma_p": 5.0, "sigma_c": 20.0, "precision": "fp32", "parallelism": f"replicas x{world}",
+                   "l2": "flushed (256 MiB write) before every step", "launch": "batched CUDA graph"},
+        "latency_ms_per_step": {"p50": sorted_ms[len(sorted_ms) // 2],
+                                "p99": sorted_ms[min(len(sorted_ms) - 1, int(0.99 * len(sorted_ms)))]},
+        "roofline": {"kernel": "jbf_stage2", "bound": "alu", "achieved": achieved, "peak": peak_gtap,
+                     "unit": "Gtap/s", "frac": achieved / peak_gtap if peak_gtap else None, "traffic": None,
+                     "peak_basis": f"{sms} SMs x 128 lanes / 10 instructions per tap x {sm_max:.0f} MHz",
+                     "taps_per_launch": taps2, "avg_launch_us": avg_us},
+        "kernels": ktable,
+        "clocks": ck,
+        "gpu_launches": gpu_launches,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    a = parse()
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local_rank = int(os.environ.get("LOCAL_RANK", 0))
+    if a.impl == "reference":
+        reference_arm(a, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        # views are generated before the first CUDA call (spawn pool), then the group starts
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    ours_arm(a, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

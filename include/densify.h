@@ -1,0 +1,259 @@
+/*
+ * densify.h - C ABI of the GB300 LiDAR densification library (libdensify.so).
+ *
+ * The library implements the per-viewpoint hot path of Murasaki et al.,
+ * "Real-Time LiDAR Point Cloud Densification for Low-Latency Spatial Data
+ * Transmission":
+ *
+ *   1. merge the three staggered LiDAR scans of a viewpoint and project them
+ *      into the camera view as one depth image (Sec. 2, System Overview),
+ *      keeping the nearest depth per pixel;
+ *   2. densify that sparse depth with the RGB-guided joint bilateral filter of
+ *      Eq. (1)-(4) (Sec. 4.2; Algorithm 1 gives the same filter as a
+ *      convolution / transpose-convolution pipeline), run in the two-stage
+ *      form of Sec. 5: radius 4 on a depth map pooled to 1/3 resolution, then
+ *      radius 2 at full resolution after restoring the first result;
+ *   3. back-project the dense depth to coloured 3D points in the common frame
+ *      (Sec. 2: coloured point clouds of all viewpoints are overlaid).
+ *
+ * Every step runs in hand-written CUDA kernels for sm_103a. The host side
+ * admits frames against a device-memory budget, batches the frames waiting
+ * for the GPU into one launch sequence (replayed as a CUDA graph), and hands
+ * results back through tickets.
+ *
+ * Conventions
+ *   - Matrices are row-major 4x4 rigid transforms in FP64 (*_to_world).
+ *   - Camera frame: x right, y down, z forward; pixel (i, j) covers
+ *     [i, i+1) x [j, j+1), so its centre is (i + 1/2, j + 1/2).
+ *   - Depth is the camera z coordinate in the units of the point clouds.
+ *   - RGB frames are H x W x 3 uint8, row pitch in bytes (>= 3 W, multiple
+ *     of 16).
+ *   - Unless a function says otherwise, pointers inside densify_frame are
+ *     DEVICE pointers (memory = DENSIFY_MEM_DEVICE) owned by the caller; with
+ *     memory = DENSIFY_MEM_HOST they are host pointers (page-locked for
+ *     asynchronous copies) and the library copies inputs in and results out.
+ *   - Every call returns a status; nothing throws across the ABI. Invalid
+ *     point values (NaN, z <= 0 in the camera, outside the image) are not
+ *     errors: such points are skipped.
+ *   - A context is not thread-safe: use one context per host thread, or
+ *     serialise the calls on it.
+ */
+#ifndef DENSIFY_H
+#define DENSIFY_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define DENSIFY_API __attribute__((visibility("default")))
+#else
+#define DENSIFY_API
+#endif
+
+#define DENSIFY_ABI_VERSION 1
+#define DENSIFY_MAX_SCANS 3     /* three LiDARs per viewpoint (Sec. 2) */
+#define DENSIFY_MAX_BATCH 64    /* frames in one batched launch */
+
+typedef struct densify_ctx densify_ctx; /* opaque */
+
+typedef enum densify_status {
+    DENSIFY_OK = 0,
+    DENSIFY_PENDING = 1,      /* submitted, not finished yet */
+    DENSIFY_E_INVALID = -1,   /* bad argument; see densify_last_error() */
+    DENSIFY_E_NOMEM = -2,     /* can never fit the device-memory budget */
+    DENSIFY_E_AGAIN = -3,     /* no free slot / budget now: poll, then retry */
+    DENSIFY_E_CUDA = -4,      /* a CUDA call failed; context is unusable */
+    DENSIFY_E_TIMEOUT = -5,   /* poll timed out; the frame is still pending */
+    DENSIFY_E_TICKET = -6     /* unknown or already-collected ticket */
+} densify_status;
+
+typedef enum densify_precision {
+    DENSIFY_FP32 = 0,         /* FP32 guide, weights and accumulation */
+    DENSIFY_FP16 = 1          /* FP16 guide and weights, FP32 accumulation */
+} densify_precision;
+
+typedef enum densify_memory {
+    DENSIFY_MEM_DEVICE = 0,
+    DENSIFY_MEM_HOST = 1
+} densify_memory;
+
+/* One joint bilateral filter stage (Eq. (1)-(4)): square window of
+ * (2 radius + 1)^2 pixels (Algorithm 1: offsets a, b in [-r, r]), spatial
+ * Gaussian sigma_p in the stage's own pixel units (Eq. (3)), colour Gaussian
+ * sigma_c on the 0-255 RGB scale (Eq. (2)). */
+typedef struct densify_stage {
+    int32_t radius;
+    float sigma_p;
+    float sigma_c;
+} densify_stage;
+
+/* Context parameters. Fill with densify_default_params() and override.
+ *   num_stages    1: one JBF at full resolution on the projected depth.
+ *                 2: the two-stage filter of Sec. 5 (stage[0] on the map
+ *                 pooled by `pool`, stage[1] at full resolution on the
+ *                 restored result).
+ *   stage         radii and sigmas. Supported radii: single stage 1-7,
+ *                 coarse stage 1-7, full-resolution second stage 1-3.
+ *   pool          pooling factor of the two-stage form (Sec. 5 uses 3).
+ *   stage2_input  0: the second stage filters the restored first-stage result
+ *                 only (the literal reading of Sec. 5); 1: pixels with a
+ *                 LiDAR depth keep it instead of the restored value.
+ *   precision     DENSIFY_FP32 or DENSIFY_FP16.
+ *   emit_points   1: back-project to coloured points; 0: depth only.
+ *   max_inflight  frames admitted at once (submitted and not yet collected).
+ *   max_batch     frames per batched launch (<= DENSIFY_MAX_BATCH).
+ *   batches_in_flight  launches allowed on the GPU at once; frames that
+ *                 arrive while they run wait and go out together in the next
+ *                 launch (continuous batching).
+ *   hbm_budget_bytes   device memory the context may use for per-frame
+ *                 scratch (z-buffers, coarse maps, staging of host frames);
+ *                 admission fails with DENSIFY_E_AGAIN when it is full.
+ *   use_graphs    1: replay each batch slot's launch sequence as a CUDA graph.
+ *   timing        1: record CUDA events around every kernel of every batch and
+ *                 accumulate per-kernel device time (densify_kernel_times).
+ *   launch_policy 0 (eager): a queued frame goes to the GPU as soon as a
+ *                 launch slot is free; frames that arrive while every slot is
+ *                 busy are launched together when one frees (continuous
+ *                 batching). 1 (batch): frames wait until max_batch are
+ *                 queued, or until densify_flush() / densify_poll().
+ */
+typedef struct densify_params {
+    int32_t num_stages;
+    densify_stage stage[2];
+    int32_t pool;
+    int32_t stage2_input;
+    int32_t precision;
+    int32_t emit_points;
+    int32_t max_inflight;
+    int32_t max_batch;
+    int32_t batches_in_flight;
+    int32_t use_graphs;
+    uint64_t hbm_budget_bytes;
+    int32_t timing;
+    int32_t launch_policy;
+    int32_t reserved[6];
+} densify_params;
+
+/* Pinhole intrinsics of the camera (Sec. 2: calibrated in advance). */
+typedef struct densify_intrinsics {
+    int32_t width, height;
+    float fx, fy, cx, cy;
+} densify_intrinsics;
+
+/* One LiDAR scan: `count` points of float32 (x, y, z) in the LiDAR frame,
+ * `stride_bytes` apart (12: packed xyz, 16: xyzw). The base address must be
+ * 16-byte aligned. lidar_to_world is the scan's calibrated extrinsic. */
+typedef struct densify_scan {
+    const float *xyz;
+    int64_t count;
+    int32_t stride_bytes;
+    int32_t reserved;
+    double lidar_to_world[16];
+} densify_scan;
+
+/* One frame of one viewpoint.
+ * Inputs: intrinsics, camera pose, 0..3 scans, the RGB frame.
+ * Outputs (caller-owned, written when the frame completes):
+ *   out_depth  H x W float, densified depth, 0 where invalid (may be NULL)
+ *   out_valid  H x W uint8, 1 where the filter window held an observation
+ *   out_points up to out_points_cap points of 4 floats
+ *              (x, y, z in the world frame, then the colour packed as
+ *              r | g << 8 | b << 16 | 255 << 24 in the bits of the 4th float),
+ *              in row-major pixel order of the valid pixels;
+ *   out_points_n  one int64: the number of valid pixels. Points past the
+ *              capacity are dropped, so n > cap means the buffer was short.
+ * Optional debug outputs (NULL to skip; device memory like the rest):
+ *   out_zbuf     H x W uint32: the nearest-depth z-buffer (bit patterns of
+ *                FP32 depths, 0x7F800000 where empty)
+ *   out_coarse   ceil(H/pool) x ceil(W/pool) float: first-stage depth
+ *   out_coarse_valid  same size, uint8: first-stage validity
+ * memory says whether every pointer above is a device or a host pointer. */
+typedef struct densify_frame {
+    densify_intrinsics K;
+    double cam_to_world[16];
+    int32_t num_scans;
+    int32_t memory;
+    densify_scan scans[DENSIFY_MAX_SCANS];
+    const uint8_t *rgb;
+    int64_t rgb_pitch;
+    float *out_depth;
+    uint8_t *out_valid;
+    float *out_points;
+    int64_t out_points_cap;
+    int64_t *out_points_n;
+    uint32_t *out_zbuf;
+    float *out_coarse;
+    uint8_t *out_coarse_valid;
+} densify_frame;
+
+/* Fill *p with the paper's two-stage configuration (Sec. 5: pool 3, radius 4
+ * then radius 2; sigma_p = 5 px and sigma_c = 20 in both stages, since the
+ * paper sets the sigmas empirically without printing them), FP32, points on,
+ * 16 frames in flight, batches of up to 16, one batch on the GPU at a time,
+ * a 2 GiB budget and CUDA graphs on. */
+DENSIFY_API void densify_default_params(densify_params *p);
+
+/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+ * (a cudaStream_t; NULL: the context creates its own non-blocking stream).
+ * Allocates the scratch arena (hbm_budget_bytes) and per-batch descriptors
+ * up front; nothing is allocated per frame afterwards.
+ * Errors: E_INVALID (bad params), E_NOMEM, E_CUDA. *out is NULL on error. */
+DENSIFY_API densify_status densify_create(const densify_params *params, int device, void *cuda_stream,
+                              densify_ctx **out);
+
+/* Admit one frame (non-blocking). Validates it, reserves its scratch in the
+ * arena and queues it; the frame goes to the GPU at once if a launch slot
+ * is free, else with the next batch. The caller keeps every buffer alive and
+ * unmodified until densify_poll() returns DENSIFY_OK (or an error) for the
+ * ticket. Errors: E_INVALID (bad frame), E_AGAIN (max_inflight frames
+ * admitted or no scratch free right now: collect results, then retry),
+ * E_NOMEM (the frame can never fit the budget), E_CUDA. */
+DENSIFY_API densify_status densify_submit(densify_ctx *ctx, const densify_frame *frame, uint64_t *ticket);
+
+/* Send every queued frame to the GPU now, waiting (bounded by timeout_ns,
+ * <0: no bound) for a launch slot if all are busy. */
+DENSIFY_API densify_status densify_flush(densify_ctx *ctx, int64_t timeout_ns);
+
+/* Wait up to timeout_ns (0: just check; <0: no bound) for a ticket.
+ * Returns OK (results written; the ticket is collected and its scratch
+ * freed), PENDING (timeout_ns == 0 and not done), E_TIMEOUT, E_TICKET or
+ * E_CUDA. Polling also launches frames that were waiting for a slot. */
+DENSIFY_API densify_status densify_poll(densify_ctx *ctx, uint64_t ticket, int64_t timeout_ns);
+
+/* Wait (bounded: at most timeout_ns per outstanding batch, 10 s if <0) for
+ * in-flight work, then free every resource of the context. */
+DENSIFY_API densify_status densify_destroy(densify_ctx *ctx);
+
+/* Static string naming a status. */
+DENSIFY_API const char *densify_status_str(densify_status s);
+
+/* The last error message of a context (empty if none). Valid until the next
+ * call on the context. ctx may be NULL: the last error of a failed create. */
+DENSIFY_API const char *densify_last_error(const densify_ctx *ctx);
+
+/* Device bytes one frame of this shape reserves from the arena. */
+DENSIFY_API uint64_t densify_frame_scratch_bytes(const densify_params *params, const densify_frame *frame);
+
+/* Per-kernel device time accumulated since the last reset, when the context
+ * was created with timing = 1: for each kernel, its static name, the summed
+ * CUDA-event duration in microseconds over all completed batches and the
+ * number of launches. Times are read when batches are collected, so call
+ * after the tickets of interest returned OK. Returns the number of kernels
+ * written (<= cap). */
+DENSIFY_API int32_t densify_kernel_times(densify_ctx *ctx, const char **names, double *total_us,
+                             int64_t *launches, int32_t cap);
+
+/* Zero the accumulated kernel times. */
+DENSIFY_API void densify_reset_kernel_times(densify_ctx *ctx);
+
+/* ABI version of the loaded library (DENSIFY_ABI_VERSION). */
+DENSIFY_API int32_t densify_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DENSIFY_H */

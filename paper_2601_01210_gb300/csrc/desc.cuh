@@ -1,0 +1,125 @@
+// Device-side descriptors shared by the host runtime and the kernels.
+//
+// One batched launch processes up to kMaxBatch frames (viewpoints) of uneven
+// resolution and point count. The host writes a BatchDev table into a fixed
+// device buffer per batch slot; every kernel is a persistent grid-stride loop
+// over work items (point chunks, z-buffer chunks, coarse pixels, filter
+// tiles, compaction chunks) whose per-frame prefix sums sit in the table, so
+// the launch sequence of a slot never changes and can be replayed as a CUDA
+// graph.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace dz {
+
+constexpr int kMaxBatch = 64;
+constexpr int kMaxScans = 3;
+constexpr uint32_t kEmpty = 0x7F800000u;   // z-buffer cell with no depth (+inf)
+
+// Work-item granularity of the non-filter kernels.
+constexpr int kThreads = 256;
+constexpr int kPtsPerThread = 4;
+constexpr int kPtsPerChunk = kThreads * kPtsPerThread;        // 1024 points
+constexpr int kZbWordsPerChunk = 8192;                        // z-buffer clear
+constexpr int kPoolPerChunk = kThreads;                       // coarse pixels
+constexpr int kBpChunk = 4096;                                // compaction: 8 warps x 512 px
+
+struct ScanDev {
+    const float *xyz;
+    int64_t count;
+    int32_t stride_floats;   // 3 or 4
+    int32_t pad;
+    double l2w[16];          // lidar_to_world, row-major
+    float M[12];             // camera <- LiDAR, composed on the GPU in FP64
+};
+
+struct FrameDev {
+    int32_t W, H, Wc, Hc;    // full and coarse (ceil(H/pool) x ceil(W/pool)) grids
+    float fx, fy, cx, cy;
+    double c2w[16];          // cam_to_world, row-major
+    float c2w32[12];         // written by the prep kernel (FP64 -> FP32 once)
+    int32_t num_scans;
+    int32_t n_bp_chunks;
+    ScanDev scans[kMaxScans];
+    const uint8_t *rgb;      // H x W x 3, rgb_pitch bytes per row
+    int64_t rgb_pitch;
+    // scratch (context arena)
+    uint32_t *zbuf;          // W*H nearest-depth bit patterns
+    float4 *cguide;          // Wc*Hc: pooled mean r, g, b and observation count
+    float *cssum;            // Wc*Hc: pooled depth sum
+    float2 *s1;              // Wc*Hc: first-stage depth and validity (0/1)
+    uint32_t *chunk_cnt;     // n_bp_chunks valid-pixel counts
+    // outputs (caller memory, or arena staging for host frames)
+    float *out_depth;
+    uint8_t *out_valid;
+    float4 *out_points;
+    int64_t points_cap;
+    int64_t *points_n;
+    float *out_coarse;       // optional first-stage depth copy
+    uint8_t *out_coarse_valid;
+};
+
+struct BatchDev {
+    int32_t n_frames;
+    int32_t pad;
+    int32_t zb_pre[kMaxBatch + 1];                 // z-buffer clear chunks
+    int32_t pt_pre[kMaxBatch * kMaxScans + 1];     // point chunks per (frame, scan)
+    int32_t pool_pre[kMaxBatch + 1];               // pooling chunks
+    int32_t t1_pre[kMaxBatch + 1];                 // tiles of the first (or only) filter
+    int32_t t2_pre[kMaxBatch + 1];                 // tiles of the full-resolution second filter
+    int32_t bp_pre[kMaxBatch + 1];                 // compaction chunks
+    FrameDev f[kMaxBatch];
+};
+
+// Per-context filter constants for one stage (by value in kernel parameters,
+// so the per-tap spatial terms are constant-bank operands).
+constexpr int kMaxR = 7;
+struct StageArgs {
+    float kc;                // log2(e) / (2 sigma_c^2)
+    float kp;                // log2(e) / (2 sigma_p^2)
+    int32_t pool;            // restore factor of the second stage
+    int32_t override_sparse; // second stage: LiDAR depths replace the restored value
+    float sp[(2 * kMaxR + 1) * (2 * kMaxR + 1)];   // -(dx^2 + dy^2) kp, row-major over (dy, dx)
+};
+
+// Largest i with pre[i] <= item (pre is non-decreasing, pre[0] = 0).
+__device__ __forceinline__ int find_segment(const int32_t *pre, int n, int item) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (pre[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// Kernel launchers. Grids are persistent: a multiple of the SM count.
+enum KernelId {
+    K_PREP = 0, K_PROJECT, K_POOL, K_JBF1, K_JBF2, K_BP_COUNT, K_BP_WRITE, K_COUNT
+};
+
+cudaError_t launch_prep(const BatchDev *b, int grid, cudaStream_t s);
+cudaError_t launch_project(const BatchDev *b, int grid, cudaStream_t s);
+cudaError_t launch_pool(const BatchDev *b, int pool, int grid, cudaStream_t s);
+cudaError_t launch_bp_count(const BatchDev *b, int grid, cudaStream_t s);
+cudaError_t launch_bp_write(const BatchDev *b, int grid, cudaStream_t s);
+int occupancy_points(KernelId k);
+int occupancy_pool_bp(KernelId k);
+
+// Joint bilateral filter, one entry per stage kind:
+//   single: full resolution, z-buffer input (radii 1-7)
+//   coarse: pooled grid, first of the two stages (radii 1-7)
+//   up:     full resolution on the restored first-stage result (radii 1-3)
+// Tiles are 32 x (8 * kp) output pixels.
+cudaError_t launch_jbf_single(int radius, const BatchDev *b, const StageArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_jbf_coarse(int radius, const BatchDev *b, const StageArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_jbf_up(int radius, const BatchDev *b, const StageArgs &a, int grid, cudaStream_t s);
+int occupancy_jbf_single(int radius);
+int occupancy_jbf_coarse(int radius);
+int occupancy_jbf_up(int radius);
+int kp_jbf_single(int radius);
+int kp_jbf_coarse(int radius);
+int kp_jbf_up(int radius);
+
+}  // namespace dz

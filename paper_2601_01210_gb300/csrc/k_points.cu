@@ -1,0 +1,143 @@
+// Calibration compose, z-buffer clear and LiDAR projection (Sec. 2: the three
+// scans of a viewpoint are merged and projected into the camera view to form
+// one depth image; the depth image D and mask B of Algorithm 1).
+//
+// Arithmetic contract (bit-exact z-buffer):
+//   * M_s = inverse(cam_to_world) * lidar_to_world in FP64 with the rigid
+//     inverse [R^T, -R^T t]; each entry summed left to right over k = 0..2,
+//     translation added last; rounded once to FP32.
+//   * per point, FP32 with every product, sum and quotient rounded on its own
+//     (no contraction): xc = ((m00 x + m01 y) + m02 z) + m03 (likewise yc, zc),
+//     u = fx (xc / zc) + cx, v = fy (yc / zc) + cy;
+//   * kept iff zc > 0 and finite, 0 <= u < W, 0 <= v < H; pixel (floor u,
+//     floor v); the z-buffer keeps the smallest zc as its FP32 bit pattern
+//     (atomicMin on uint32 is order-preserving for positive floats).
+#include "desc.cuh"
+
+namespace dz {
+
+// ---------------------------------------------------------------------------
+// prep: one work item per z-buffer chunk; the first chunk of each frame also
+// composes the frame's calibration (the only FP64 arithmetic on the GPU).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double compose_entry(const double *c2w, const double *l2w, int i, int j) {
+    // Rinv[i][k] = R[k][i]
+    const double r0 = c2w[0 * 4 + i], r1 = c2w[1 * 4 + i], r2 = c2w[2 * 4 + i];
+    double s = __dmul_rn(r0, l2w[0 * 4 + j]);
+    s = __dadd_rn(s, __dmul_rn(r1, l2w[1 * 4 + j]));
+    s = __dadd_rn(s, __dmul_rn(r2, l2w[2 * 4 + j]));
+    if (j == 3) {
+        double t = __dmul_rn(r0, c2w[0 * 4 + 3]);
+        t = __dadd_rn(t, __dmul_rn(r1, c2w[1 * 4 + 3]));
+        t = __dadd_rn(t, __dmul_rn(r2, c2w[2 * 4 + 3]));
+        s = __dadd_rn(s, -t);
+    }
+    return s;
+}
+
+__global__ void __launch_bounds__(kThreads) prep_kernel(BatchDev *__restrict__ B) {
+    const int nf = B->n_frames;
+    const int total = B->zb_pre[nf];
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int f = find_segment(B->zb_pre, nf, item);
+        FrameDev &F = B->f[f];
+        const int c = item - B->zb_pre[f];
+        if (c == 0) {
+            const int t = threadIdx.x;
+            if (t < F.num_scans * 12) {
+                const int s = t / 12, e = t % 12;
+                F.scans[s].M[e] = __double2float_rn(compose_entry(F.c2w, F.scans[s].l2w, e / 4, e % 4));
+            } else if (t >= 64 && t < 76) {
+                const int e = t - 64;
+                F.c2w32[e] = __double2float_rn(F.c2w[(e / 4) * 4 + (e % 4)]);
+            }
+        }
+        const int64_t n = (int64_t)F.W * F.H;
+        const int64_t w0 = (int64_t)c * kZbWordsPerChunk;
+        const int64_t w1 = min(n, w0 + kZbWordsPerChunk);
+        uint32_t *z = F.zbuf;
+        // arena buffers are 256-byte aligned and w0 is a multiple of 4
+        const int64_t v1 = w0 + ((w1 - w0) & ~int64_t(3));
+        const uint4 e4 = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+        for (int64_t w = w0 + 4 * threadIdx.x; w < v1; w += 4 * kThreads)
+            *reinterpret_cast<uint4 *>(z + w) = e4;
+        for (int64_t w = v1 + threadIdx.x; w < w1; w += kThreads) z[w] = kEmpty;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// project: one work item = 1024 consecutive points of one (frame, scan);
+// each thread takes 4 points with 16-byte vector loads.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void project_one(const float (&M)[12], float x, float y, float z, const FrameDev &F,
+                                            uint32_t *zbuf) {
+    const float xc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[0], x), __fmul_rn(M[1], y)), __fmul_rn(M[2], z)), M[3]);
+    const float yc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[4], x), __fmul_rn(M[5], y)), __fmul_rn(M[6], z)), M[7]);
+    const float zc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[8], x), __fmul_rn(M[9], y)), __fmul_rn(M[10], z)), M[11]);
+    if (!(zc > 0.0f) || !(zc < __int_as_float(0x7F800000))) return;
+    const float u = __fadd_rn(__fmul_rn(F.fx, __fdiv_rn(xc, zc)), F.cx);
+    const float v = __fadd_rn(__fmul_rn(F.fy, __fdiv_rn(yc, zc)), F.cy);
+    if (!(u >= 0.0f && u < (float)F.W && v >= 0.0f && v < (float)F.H)) return;
+    const int i = __float2int_rz(u);   // u >= 0: truncation is floor
+    const int j = __float2int_rz(v);
+    atomicMin(zbuf + (int64_t)j * F.W + i, __float_as_uint(zc));
+}
+
+__global__ void __launch_bounds__(kThreads) project_kernel(const BatchDev *__restrict__ B) {
+    const int nseg = B->n_frames * kMaxScans;
+    const int total = B->pt_pre[nseg];
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int seg = find_segment(B->pt_pre, nseg, item);
+        const FrameDev &F = B->f[seg / kMaxScans];
+        const ScanDev &S = F.scans[seg % kMaxScans];
+        float M[12];
+#pragma unroll
+        for (int e = 0; e < 12; ++e) M[e] = S.M[e];
+        const int64_t p0 = (int64_t)(item - B->pt_pre[seg]) * kPtsPerChunk + (int64_t)threadIdx.x * kPtsPerThread;
+        if (p0 >= S.count) continue;
+        uint32_t *zbuf = F.zbuf;
+        if (S.stride_floats == 3) {
+            if (p0 + 4 <= S.count) {
+                // 4 packed points = 48 bytes = 3 aligned float4 (base 16-byte aligned, p0 % 4 == 0)
+                const float4 *q = reinterpret_cast<const float4 *>(S.xyz + p0 * 3);
+                const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
+                project_one(M, a.x, a.y, a.z, F, zbuf);
+                project_one(M, a.w, b.x, b.y, F, zbuf);
+                project_one(M, b.z, b.w, c.x, F, zbuf);
+                project_one(M, c.y, c.z, c.w, F, zbuf);
+            } else {
+                for (int64_t p = p0; p < S.count; ++p)
+                    project_one(M, __ldg(S.xyz + 3 * p), __ldg(S.xyz + 3 * p + 1), __ldg(S.xyz + 3 * p + 2), F, zbuf);
+            }
+        } else {
+            const float4 *q = reinterpret_cast<const float4 *>(S.xyz) + p0;
+            const int n = (int)(S.count - p0 < 4 ? S.count - p0 : 4);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                if (k < n) {
+                    const float4 a = __ldg(q + k);
+                    project_one(M, a.x, a.y, a.z, F, zbuf);
+                }
+            }
+        }
+    }
+}
+
+cudaError_t launch_prep(const BatchDev *b, int grid, cudaStream_t s) {
+    prep_kernel<<<grid, kThreads, 0, s>>>(const_cast<BatchDev *>(b));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_project(const BatchDev *b, int grid, cudaStream_t s) {
+    project_kernel<<<grid, kThreads, 0, s>>>(b);
+    return cudaGetLastError();
+}
+
+int occupancy_points(KernelId k) {
+    int n = 0;
+    if (k == K_PREP) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, prep_kernel, kThreads, 0);
+    else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, project_kernel, kThreads, 0);
+    return n > 0 ? n : 1;
+}
+
+}  // namespace dz

@@ -1,0 +1,820 @@
+// Host runtime behind the C ABI (include/densify.h).
+//
+// * Admission: every frame reserves its scratch (z-buffer, coarse maps,
+//   compaction counts, staging of host frames) from one device arena that is
+//   allocated when the context is created; a frame that does not fit now
+//   gets DENSIFY_E_AGAIN, one that never fits DENSIFY_E_NOMEM. Nothing is
+//   allocated per frame.
+// * Batching: admitted frames queue on the host. A batch slot takes up to
+//   max_batch of them, writes their descriptors into its device table and
+//   runs the fixed kernel sequence (prep, project, [pool, coarse filter],
+//   filter, compaction count, compaction write) on the context stream,
+//   replayed from a CUDA graph captured the first time the slot is used.
+//   Frames that arrive while every slot is busy go out together as soon as a
+//   slot frees (continuous batching).
+// * Completion: each slot records an event; densify_poll() queries events
+//   (bounded waits only), finishes host-frame copies, frees scratch.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/densify.h"
+#include "desc.cuh"
+
+using namespace dz;
+
+namespace {
+
+const char *const kKernelNames[K_COUNT] = {"prep_compose_clear", "project_zbuf", "pool3", "jbf_stage1",
+                                           "jbf_stage2",          "bp_count",     "bp_write"};
+
+constexpr uint64_t kAlign = 256;
+uint64_t align_up(uint64_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
+
+thread_local std::string g_create_error;
+
+// First-fit allocator over offsets of the device arena.
+class Arena {
+public:
+    void init(uint64_t size) {
+        size_ = size;
+        free_.clear();
+        if (size) free_[0] = size;
+    }
+    bool alloc(uint64_t n, uint64_t *off) {
+        n = align_up(n ? n : 1);
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= n) {
+                *off = it->first;
+                const uint64_t rest = it->second - n;
+                const uint64_t at = it->first + n;
+                free_.erase(it);
+                if (rest) free_[at] = rest;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(uint64_t off, uint64_t n) {
+        n = align_up(n ? n : 1);
+        auto it = free_.emplace(off, n).first;
+        if (it != free_.begin()) {
+            auto prev = std::prev(it);
+            if (prev->first + prev->second == it->first) {
+                prev->second += it->second;
+                free_.erase(it);
+                it = prev;
+            }
+        }
+        auto next = std::next(it);
+        if (next != free_.end() && it->first + it->second == next->first) {
+            it->second += next->second;
+            free_.erase(next);
+        }
+    }
+    uint64_t size() const { return size_; }
+
+private:
+    uint64_t size_ = 0;
+    std::map<uint64_t, uint64_t> free_;
+};
+
+// Scratch layout of one frame inside its arena block.
+struct Layout {
+    uint64_t zbuf = 0, cguide = 0, cssum = 0, s1 = 0, chunk = 0, depth = 0, valid = 0;
+    uint64_t pts[kMaxScans] = {0, 0, 0}, rgb = 0, points = 0, npts = 0, coarse = 0, coarse_valid = 0;
+    uint64_t total = 0;
+    bool own_depth = false, own_valid = false;
+};
+
+struct FrameRec {
+    densify_frame fr;
+    Layout L;
+    uint64_t off = 0;
+    int state = 0;   // 0 queued, 1 on the GPU, 2 finished
+    int slot = -1;
+    FrameDev dev;
+    int64_t host_npts = 0;   // points count copied back for host frames
+};
+
+struct Slot {
+    BatchDev *d = nullptr;       // device table
+    BatchDev *h = nullptr;       // pinned host mirror
+    cudaEvent_t done = nullptr;
+    cudaEvent_t kev[K_COUNT + 1] = {};
+    bool ktimed[K_COUNT] = {};
+    cudaGraphExec_t exec = nullptr;
+    bool busy = false;
+    std::vector<uint64_t> tickets;
+};
+
+int64_t now_ns() {
+    return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+}  // namespace
+
+struct densify_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    cudaStream_t cap_stream = nullptr;   // private stream for graph capture
+    cudaStream_t d2h_stream = nullptr;   // exact-size point copies of host frames
+    densify_params p{};
+    StageArgs sa[2]{};
+    void *arena_base = nullptr;
+    Arena arena;
+    std::vector<Slot> slots;
+    std::deque<uint64_t> queue;
+    std::map<uint64_t, FrameRec> frames;
+    uint64_t next_ticket = 1;
+    int admitted = 0;
+    int grid[K_COUNT] = {};
+    std::string err;
+    bool dead = false;
+    double t_us[K_COUNT] = {};
+    int64_t t_n[K_COUNT] = {};
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+densify_status fail(densify_ctx *c, densify_status s, const std::string &msg) {
+    if (c) c->err = msg;
+    else g_create_error = msg;
+    return s;
+}
+
+densify_status cuda_fail(densify_ctx *c, cudaError_t e, const char *what) {
+    c->dead = true;
+    c->err = std::string(what) + ": " + cudaGetErrorString(e);
+    return DENSIFY_E_CUDA;
+}
+
+#define CU(call, what)                                   \
+    do {                                                 \
+        cudaError_t e_ = (call);                         \
+        if (e_ != cudaSuccess) return cuda_fail(c, e_, what); \
+    } while (0)
+
+int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+bool stage_supported(int kind, int r) {
+    if (r < 1) return false;
+    if (kind == 2) return r <= 3;
+    return r <= kMaxR;
+}
+
+int tile_h(const densify_params &p, int kind, int r) {
+    const int kp = kind == 0 ? kp_jbf_single(r) : kind == 1 ? kp_jbf_coarse(r) : kp_jbf_up(r);
+    return 8 * kp;
+}
+
+void fill_stage(StageArgs &a, const densify_stage &st, int pool, int override_sparse) {
+    const double log2e = 1.4426950408889634;
+    a.kc = (float)(log2e / (2.0 * (double)st.sigma_c * (double)st.sigma_c));
+    a.kp = (float)(log2e / (2.0 * (double)st.sigma_p * (double)st.sigma_p));
+    a.pool = pool;
+    a.override_sparse = override_sparse;
+    const int R = st.radius;
+    for (int dy = 0; dy < 2 * kMaxR + 1; ++dy)
+        for (int dx = 0; dx < 2 * kMaxR + 1; ++dx) {
+            const double d2 = (double)((dx - R) * (dx - R) + (dy - R) * (dy - R));
+            a.sp[dy * (2 * kMaxR + 1) + dx] = (float)(-d2 * log2e / (2.0 * (double)st.sigma_p * (double)st.sigma_p));
+        }
+}
+
+std::string validate_params(const densify_params &p) {
+    if (p.num_stages != 1 && p.num_stages != 2) return "num_stages must be 1 or 2";
+    for (int s = 0; s < p.num_stages; ++s) {
+        const int kind = p.num_stages == 1 ? 0 : (s == 0 ? 1 : 2);
+        if (!stage_supported(kind, p.stage[s].radius)) return "unsupported radius for stage " + std::to_string(s);
+        if (!(p.stage[s].sigma_p > 0.0f) || !(p.stage[s].sigma_c > 0.0f) || !std::isfinite(p.stage[s].sigma_p) ||
+            !std::isfinite(p.stage[s].sigma_c))
+            return "sigmas must be positive and finite";
+    }
+    if (p.num_stages == 2 && (p.pool < 1 || p.pool > 8)) return "pool must be in 1..8";
+    if (p.precision != DENSIFY_FP32) return "only DENSIFY_FP32 is built in this library";
+    if (p.max_inflight < 1) return "max_inflight must be >= 1";
+    if (p.max_batch < 1 || p.max_batch > kMaxBatch) return "max_batch must be in 1..64";
+    if (p.batches_in_flight < 1 || p.batches_in_flight > 8) return "batches_in_flight must be in 1..8";
+    if (p.hbm_budget_bytes < (1u << 20)) return "hbm_budget_bytes must be >= 1 MiB";
+    if (p.launch_policy != 0 && p.launch_policy != 1) return "launch_policy must be 0 or 1";
+    return "";
+}
+
+std::string validate_frame(const densify_ctx *c, const densify_frame *f) {
+    if (!f) return "frame is NULL";
+    const int W = f->K.width, H = f->K.height;
+    if (W < 1 || H < 1 || W > 16384 || H > 16384) return "image size must be in 1..16384";
+    if (!std::isfinite(f->K.fx) || !std::isfinite(f->K.fy) || f->K.fx == 0.0f || f->K.fy == 0.0f ||
+        !std::isfinite(f->K.cx) || !std::isfinite(f->K.cy))
+        return "intrinsics must be finite with nonzero focal lengths";
+    if (f->num_scans < 0 || f->num_scans > kMaxScans) return "num_scans must be in 0..3";
+    if (f->memory != DENSIFY_MEM_DEVICE && f->memory != DENSIFY_MEM_HOST) return "memory must be DEVICE or HOST";
+    for (int s = 0; s < f->num_scans; ++s) {
+        const densify_scan &S = f->scans[s];
+        if (S.count < 0 || S.count > (int64_t)1 << 30) return "scan count must be in 0..2^30";
+        if (S.stride_bytes != 12 && S.stride_bytes != 16) return "scan stride_bytes must be 12 or 16";
+        if (S.count > 0 && !S.xyz) return "scan xyz is NULL";
+        if (S.count > 0 && f->memory == DENSIFY_MEM_DEVICE && ((uintptr_t)S.xyz & 15u))
+            return "scan xyz must be 16-byte aligned";
+    }
+    if (!f->rgb) return "rgb is NULL";
+    if (f->rgb_pitch < 3 * (int64_t)W) return "rgb_pitch must be >= 3 * width";
+    if (c->p.emit_points) {
+        if (!f->out_points_n) return "out_points_n is NULL while points are on";
+        if (f->out_points_cap < 0) return "out_points_cap must be >= 0";
+        if (f->out_points_cap > 0 && !f->out_points) return "out_points is NULL with a nonzero capacity";
+        if (f->out_points && ((uintptr_t)f->out_points & 15u)) return "out_points must be 16-byte aligned";
+    }
+    if (f->memory == DENSIFY_MEM_DEVICE && f->out_zbuf && ((uintptr_t)f->out_zbuf & 15u))
+        return "out_zbuf must be 16-byte aligned";
+    return "";
+}
+
+Layout layout_of(const densify_params &p, const densify_frame *f) {
+    Layout L;
+    const int64_t W = f->K.width, H = f->K.height, npx = W * H;
+    const bool host = f->memory == DENSIFY_MEM_HOST;
+    uint64_t o = 0;
+    auto take = [&](uint64_t bytes) {
+        const uint64_t at = o;
+        o += align_up(bytes ? bytes : 1);
+        return at;
+    };
+    L.zbuf = take(npx * 4);
+    if (p.num_stages == 2) {
+        const int64_t Wc = (W + p.pool - 1) / p.pool, Hc = (H + p.pool - 1) / p.pool;
+        L.cguide = take(Wc * Hc * 16);
+        L.cssum = take(Wc * Hc * 4);
+        L.s1 = take(Wc * Hc * 8);
+        if (host && f->out_coarse) L.coarse = take(Wc * Hc * 4);
+        if (host && f->out_coarse_valid) L.coarse_valid = take(Wc * Hc);
+    }
+    L.chunk = take(((npx + kBpChunk - 1) / kBpChunk) * 4);
+    L.own_depth = host || !f->out_depth;
+    L.own_valid = host || !f->out_valid;
+    if (L.own_depth) L.depth = take(npx * 4);
+    if (L.own_valid) L.valid = take(npx);
+    if (host) {
+        for (int s = 0; s < f->num_scans; ++s) L.pts[s] = take((uint64_t)f->scans[s].count * f->scans[s].stride_bytes);
+        L.rgb = take((uint64_t)H * W * 3);
+        if (p.emit_points) {
+            L.points = take((uint64_t)f->out_points_cap * 16);
+            L.npts = take(8);
+        }
+    } else if (p.emit_points) {
+        L.npts = 0;
+    }
+    L.total = o;
+    return L;
+}
+
+void build_frame_dev(densify_ctx *c, FrameRec &r) {
+    const densify_frame *f = &r.fr;
+    const Layout &L = r.L;
+    char *base = (char *)c->arena_base + r.off;
+    const bool host = f->memory == DENSIFY_MEM_HOST;
+    FrameDev &d = r.dev;
+    std::memset(&d, 0, sizeof(d));
+    d.W = f->K.width;
+    d.H = f->K.height;
+    const int pool = c->p.num_stages == 2 ? c->p.pool : 1;
+    d.Wc = (d.W + pool - 1) / pool;
+    d.Hc = (d.H + pool - 1) / pool;
+    d.fx = f->K.fx; d.fy = f->K.fy; d.cx = f->K.cx; d.cy = f->K.cy;
+    std::memcpy(d.c2w, f->cam_to_world, sizeof(d.c2w));
+    d.num_scans = f->num_scans;
+    d.n_bp_chunks = ceil_div((int64_t)d.W * d.H, kBpChunk);
+    for (int s = 0; s < kMaxScans; ++s) {
+        ScanDev &S = d.scans[s];
+        if (s < f->num_scans) {
+            S.xyz = host ? (const float *)(base + L.pts[s]) : f->scans[s].xyz;
+            S.count = f->scans[s].count;
+            S.stride_floats = f->scans[s].stride_bytes / 4;
+            std::memcpy(S.l2w, f->scans[s].lidar_to_world, sizeof(S.l2w));
+        } else {
+            S.count = 0;
+            S.stride_floats = 3;
+        }
+    }
+    d.rgb = host ? (const uint8_t *)(base + L.rgb) : f->rgb;
+    d.rgb_pitch = host ? (int64_t)d.W * 3 : f->rgb_pitch;
+    d.zbuf = (!host && f->out_zbuf) ? f->out_zbuf : (uint32_t *)(base + L.zbuf);
+    if (c->p.num_stages == 2) {
+        d.cguide = (float4 *)(base + L.cguide);
+        d.cssum = (float *)(base + L.cssum);
+        d.s1 = (float2 *)(base + L.s1);
+        d.out_coarse = host ? (f->out_coarse ? (float *)(base + L.coarse) : nullptr) : f->out_coarse;
+        d.out_coarse_valid =
+            host ? (f->out_coarse_valid ? (uint8_t *)(base + L.coarse_valid) : nullptr) : f->out_coarse_valid;
+    }
+    d.chunk_cnt = (uint32_t *)(base + L.chunk);
+    d.out_depth = L.own_depth ? (float *)(base + L.depth) : f->out_depth;
+    d.out_valid = L.own_valid ? (uint8_t *)(base + L.valid) : f->out_valid;
+    if (c->p.emit_points) {
+        d.out_points = host ? (float4 *)(base + L.points) : (float4 *)f->out_points;
+        d.points_cap = f->out_points_cap;
+        d.points_n = host ? (int64_t *)(base + L.npts) : f->out_points_n;
+    }
+}
+
+void fill_batch(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &tk) {
+    BatchDev &b = *sl.h;
+    const int n = (int)tk.size();
+    b.n_frames = n;
+    b.zb_pre[0] = b.pt_pre[0] = b.pool_pre[0] = b.t1_pre[0] = b.t2_pre[0] = b.bp_pre[0] = 0;
+    const int nst = c->p.num_stages;
+    const int r1 = c->p.stage[0].radius, r2 = nst == 2 ? c->p.stage[1].radius : 0;
+    const int th1 = tile_h(c->p, nst == 1 ? 0 : 1, r1);
+    const int th2 = nst == 2 ? tile_h(c->p, 2, r2) : 1;
+    for (int i = 0; i < n; ++i) {
+        FrameRec &r = c->frames[tk[i]];
+        const FrameDev &d = r.dev;
+        b.f[i] = d;
+        const int64_t npx = (int64_t)d.W * d.H;
+        b.zb_pre[i + 1] = b.zb_pre[i] + ceil_div(npx, kZbWordsPerChunk);
+        for (int s = 0; s < kMaxScans; ++s) {
+            const int k = i * kMaxScans + s;
+            b.pt_pre[k + 1] = b.pt_pre[k] + ceil_div(d.scans[s].count, kPtsPerChunk);
+        }
+        b.pool_pre[i + 1] = b.pool_pre[i] + (nst == 2 ? ceil_div((int64_t)d.Wc * d.Hc, kPoolPerChunk) : 0);
+        const int g1w = nst == 2 ? d.Wc : d.W, g1h = nst == 2 ? d.Hc : d.H;
+        b.t1_pre[i + 1] = b.t1_pre[i] + ceil_div(g1w, 32) * ceil_div(g1h, th1);
+        b.t2_pre[i + 1] = b.t2_pre[i] + (nst == 2 ? ceil_div(d.W, 32) * ceil_div(d.H, th2) : 0);
+        b.bp_pre[i + 1] = b.bp_pre[i] + (c->p.emit_points ? d.n_bp_chunks : 0);
+    }
+}
+
+// The fixed kernel sequence of one batch (captured into a graph or issued directly).
+densify_status issue_kernels(densify_ctx *c, Slot &sl, cudaStream_t s, bool record_events) {
+    const BatchDev *b = sl.d;
+    const int nst = c->p.num_stages;
+    int ev = 0;
+    auto mark = [&](int k) -> cudaError_t {
+        if (!record_events) return cudaSuccess;
+        if (k >= 0) sl.ktimed[k] = true;
+        return cudaEventRecordWithFlags(sl.kev[ev++], s, s == c->cap_stream ? cudaEventRecordExternal : 0);
+    };
+    for (int k = 0; k < K_COUNT; ++k) sl.ktimed[k] = false;
+    CU(mark(-1), "event");
+    CU(launch_prep(b, c->grid[K_PREP], s), "prep launch");
+    CU(mark(K_PREP), "event");
+    CU(launch_project(b, c->grid[K_PROJECT], s), "project launch");
+    CU(mark(K_PROJECT), "event");
+    if (nst == 2) {
+        CU(launch_pool(b, c->p.pool, c->grid[K_POOL], s), "pool launch");
+        CU(mark(K_POOL), "event");
+        CU(launch_jbf_coarse(c->p.stage[0].radius, b, c->sa[0], c->grid[K_JBF1], s), "stage-1 filter launch");
+        CU(mark(K_JBF1), "event");
+        CU(launch_jbf_up(c->p.stage[1].radius, b, c->sa[1], c->grid[K_JBF2], s), "stage-2 filter launch");
+        CU(mark(K_JBF2), "event");
+    } else {
+        CU(launch_jbf_single(c->p.stage[0].radius, b, c->sa[0], c->grid[K_JBF1], s), "filter launch");
+        CU(mark(K_JBF1), "event");
+    }
+    if (c->p.emit_points) {
+        CU(launch_bp_count(b, c->grid[K_BP_COUNT], s), "compaction count launch");
+        CU(mark(K_BP_COUNT), "event");
+        CU(launch_bp_write(b, c->grid[K_BP_WRITE], s), "compaction write launch");
+        CU(mark(K_BP_WRITE), "event");
+    }
+    return DENSIFY_OK;
+}
+
+densify_status launch_batch(densify_ctx *c, int si) {
+    Slot &sl = c->slots[si];
+    std::vector<uint64_t> tk;
+    while (!c->queue.empty() && (int)tk.size() < c->p.max_batch) {
+        tk.push_back(c->queue.front());
+        c->queue.pop_front();
+    }
+    if (tk.empty()) return DENSIFY_OK;
+    for (uint64_t t : tk) build_frame_dev(c, c->frames[t]);
+    fill_batch(c, sl, tk);
+    const size_t bytes = offsetof(BatchDev, f) + sizeof(FrameDev) * tk.size();
+    CU(cudaMemcpyAsync(sl.d, sl.h, bytes, cudaMemcpyHostToDevice, c->stream), "descriptor upload");
+    // host frames: inputs in
+    for (uint64_t t : tk) {
+        FrameRec &r = c->frames[t];
+        if (r.fr.memory != DENSIFY_MEM_HOST) continue;
+        for (int s = 0; s < r.fr.num_scans; ++s)
+            if (r.fr.scans[s].count > 0)
+                CU(cudaMemcpyAsync((void *)r.dev.scans[s].xyz, r.fr.scans[s].xyz,
+                                   (size_t)r.fr.scans[s].count * r.fr.scans[s].stride_bytes, cudaMemcpyHostToDevice,
+                                   c->stream),
+                   "points upload");
+        CU(cudaMemcpy2DAsync((void *)r.dev.rgb, (size_t)r.dev.rgb_pitch, r.fr.rgb, (size_t)r.fr.rgb_pitch,
+                             (size_t)r.fr.K.width * 3, (size_t)r.fr.K.height, cudaMemcpyHostToDevice, c->stream),
+           "rgb upload");
+    }
+    if (c->p.use_graphs) {
+        if (!sl.exec) {
+            CU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+            densify_status st = issue_kernels(c, sl, c->cap_stream, c->p.timing != 0);
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+            if (st != DENSIFY_OK) {
+                if (g) cudaGraphDestroy(g);
+                return st;
+            }
+            if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+            e = cudaGraphInstantiate(&sl.exec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+        }
+        CU(cudaGraphLaunch(sl.exec, c->stream), "graph launch");
+    } else {
+        densify_status st = issue_kernels(c, sl, c->stream, c->p.timing != 0);
+        if (st != DENSIFY_OK) return st;
+    }
+    // host frames: results out (points are copied at poll time, exactly n of them)
+    for (uint64_t t : tk) {
+        FrameRec &r = c->frames[t];
+        if (r.fr.memory != DENSIFY_MEM_HOST) continue;
+        const size_t npx = (size_t)r.fr.K.width * r.fr.K.height;
+        if (r.fr.out_depth)
+            CU(cudaMemcpyAsync(r.fr.out_depth, r.dev.out_depth, npx * 4, cudaMemcpyDeviceToHost, c->stream), "depth copy");
+        if (r.fr.out_valid)
+            CU(cudaMemcpyAsync(r.fr.out_valid, r.dev.out_valid, npx, cudaMemcpyDeviceToHost, c->stream), "valid copy");
+        if (r.fr.out_zbuf)
+            CU(cudaMemcpyAsync(r.fr.out_zbuf, r.dev.zbuf, npx * 4, cudaMemcpyDeviceToHost, c->stream), "zbuf copy");
+        if (c->p.num_stages == 2) {
+            const size_t nc = (size_t)r.dev.Wc * r.dev.Hc;
+            if (r.fr.out_coarse)
+                CU(cudaMemcpyAsync(r.fr.out_coarse, r.dev.out_coarse, nc * 4, cudaMemcpyDeviceToHost, c->stream),
+                   "coarse copy");
+            if (r.fr.out_coarse_valid)
+                CU(cudaMemcpyAsync(r.fr.out_coarse_valid, r.dev.out_coarse_valid, nc, cudaMemcpyDeviceToHost,
+                                   c->stream),
+                   "coarse valid copy");
+        }
+        if (c->p.emit_points)
+            CU(cudaMemcpyAsync(r.fr.out_points_n, r.dev.points_n, 8, cudaMemcpyDeviceToHost, c->stream), "count copy");
+    }
+    CU(cudaEventRecord(sl.done, c->stream), "event record");
+    for (uint64_t t : tk) {
+        FrameRec &r = c->frames[t];
+        r.state = 1;
+        r.slot = si;
+    }
+    sl.tickets = tk;
+    sl.busy = true;
+    return DENSIFY_OK;
+}
+
+densify_status complete_slot(densify_ctx *c, Slot &sl) {
+    if (c->p.timing) {
+        int ev = 1;
+        for (int k = 0; k < K_COUNT; ++k) {
+            if (!sl.ktimed[k]) continue;
+            float ms = 0.0f;
+            CU(cudaEventElapsedTime(&ms, sl.kev[ev - 1], sl.kev[ev]), "elapsed time");
+            c->t_us[k] += 1000.0 * ms;
+            c->t_n[k] += 1;
+            ++ev;
+        }
+    }
+    for (uint64_t t : sl.tickets) {
+        auto it = c->frames.find(t);
+        if (it != c->frames.end()) it->second.state = 2;
+    }
+    sl.tickets.clear();
+    sl.busy = false;
+    return DENSIFY_OK;
+}
+
+densify_status progress(densify_ctx *c, bool launch) {
+    if (c->dead) return DENSIFY_E_CUDA;
+    for (auto &sl : c->slots) {
+        if (!sl.busy) continue;
+        cudaError_t q = cudaEventQuery(sl.done);
+        if (q == cudaSuccess) {
+            densify_status st = complete_slot(c, sl);
+            if (st != DENSIFY_OK) return st;
+        } else if (q != cudaErrorNotReady) {
+            return cuda_fail(c, q, "batch failed");
+        }
+    }
+    if (launch) {
+        for (int si = 0; si < (int)c->slots.size() && !c->queue.empty(); ++si) {
+            if (c->slots[si].busy) continue;
+            densify_status st = launch_batch(c, si);
+            if (st != DENSIFY_OK) return st;
+        }
+    }
+    return DENSIFY_OK;
+}
+
+bool any_busy(const densify_ctx *c) {
+    for (const auto &sl : c->slots)
+        if (sl.busy) return true;
+    return false;
+}
+
+// Bounded wait for some busy slot to finish: spin on the event with a yield.
+densify_status wait_some(densify_ctx *c, int64_t deadline_ns) {
+    while (true) {
+        for (auto &sl : c->slots) {
+            if (!sl.busy) continue;
+            cudaError_t q = cudaEventQuery(sl.done);
+            if (q == cudaSuccess) return DENSIFY_OK;
+            if (q != cudaErrorNotReady) return cuda_fail(c, q, "batch failed");
+        }
+        if (deadline_ns >= 0 && now_ns() >= deadline_ns) return DENSIFY_E_TIMEOUT;
+        std::this_thread::yield();
+    }
+}
+
+densify_status finalize(densify_ctx *c, FrameRec &r) {
+    if (r.fr.memory == DENSIFY_MEM_HOST && c->p.emit_points && r.fr.out_points && r.fr.out_points_cap > 0) {
+        const int64_t n = std::min<int64_t>(*r.fr.out_points_n, r.fr.out_points_cap);
+        if (n > 0) {
+            CU(cudaMemcpyAsync(r.fr.out_points, r.dev.out_points, (size_t)n * 16, cudaMemcpyDeviceToHost,
+                               c->d2h_stream),
+               "points copy");
+            CU(cudaStreamSynchronize(c->d2h_stream), "points copy sync");
+        }
+    }
+    return DENSIFY_OK;
+}
+
+void destroy_resources(densify_ctx *c) {
+    for (auto &sl : c->slots) {
+        if (sl.exec) cudaGraphExecDestroy(sl.exec);
+        if (sl.done) cudaEventDestroy(sl.done);
+        for (auto &e : sl.kev)
+            if (e) cudaEventDestroy(e);
+        if (sl.d) cudaFree(sl.d);
+        if (sl.h) cudaFreeHost(sl.h);
+    }
+    c->slots.clear();
+    if (c->arena_base) cudaFree(c->arena_base);
+    c->arena_base = nullptr;
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->d2h_stream) cudaStreamDestroy(c->d2h_stream);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+int32_t densify_abi_version(void) { return DENSIFY_ABI_VERSION; }
+
+const char *densify_status_str(densify_status s) {
+    switch (s) {
+    case DENSIFY_OK: return "DENSIFY_OK";
+    case DENSIFY_PENDING: return "DENSIFY_PENDING";
+    case DENSIFY_E_INVALID: return "DENSIFY_E_INVALID";
+    case DENSIFY_E_NOMEM: return "DENSIFY_E_NOMEM";
+    case DENSIFY_E_AGAIN: return "DENSIFY_E_AGAIN";
+    case DENSIFY_E_CUDA: return "DENSIFY_E_CUDA";
+    case DENSIFY_E_TIMEOUT: return "DENSIFY_E_TIMEOUT";
+    case DENSIFY_E_TICKET: return "DENSIFY_E_TICKET";
+    }
+    return "DENSIFY_UNKNOWN";
+}
+
+const char *densify_last_error(const densify_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+void densify_default_params(densify_params *p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof(*p));
+    p->num_stages = 2;
+    p->stage[0] = densify_stage{4, 5.0f, 20.0f};
+    p->stage[1] = densify_stage{2, 5.0f, 20.0f};
+    p->pool = 3;
+    p->stage2_input = 0;
+    p->precision = DENSIFY_FP32;
+    p->emit_points = 1;
+    p->max_inflight = 16;
+    p->max_batch = 16;
+    p->batches_in_flight = 1;
+    p->use_graphs = 1;
+    p->hbm_budget_bytes = (uint64_t)2 << 30;
+    p->timing = 0;
+    p->launch_policy = 0;
+}
+
+uint64_t densify_frame_scratch_bytes(const densify_params *params, const densify_frame *frame) {
+    if (!params || !frame) return 0;
+    return layout_of(*params, frame).total;
+}
+
+densify_status densify_create(const densify_params *params, int device, void *cuda_stream, densify_ctx **out) {
+    if (!out) return fail(nullptr, DENSIFY_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (!params) return fail(nullptr, DENSIFY_E_INVALID, "params is NULL");
+    const std::string perr = validate_params(*params);
+    if (!perr.empty()) return fail(nullptr, DENSIFY_E_INVALID, perr);
+    int ndev = 0;
+    cudaError_t e = cudaGetDeviceCount(&ndev);
+    if (e != cudaSuccess) return fail(nullptr, DENSIFY_E_CUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+    if (device < 0 || device >= ndev) return fail(nullptr, DENSIFY_E_INVALID, "device out of range");
+    DeviceGuard guard(device);
+    densify_ctx *c = new densify_ctx();
+    c->device = device;
+    c->p = *params;
+    auto bail = [&](densify_status s, const std::string &m) {
+        g_create_error = m + (c->err.empty() ? "" : (": " + c->err));
+        destroy_resources(c);
+        delete c;
+        return s;
+    };
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if ((e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return bail(DENSIFY_E_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+        c->own_stream = true;
+    }
+    if ((e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
+        (e = cudaStreamCreateWithFlags(&c->d2h_stream, cudaStreamNonBlocking)) != cudaSuccess)
+        return bail(DENSIFY_E_CUDA, std::string("stream: ") + cudaGetErrorString(e));
+    if ((e = cudaMalloc(&c->arena_base, params->hbm_budget_bytes)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(DENSIFY_E_NOMEM, std::string("arena: ") + cudaGetErrorString(e));
+    }
+    c->arena.init(params->hbm_budget_bytes);
+    c->slots.resize(params->batches_in_flight);
+    for (auto &sl : c->slots) {
+        if ((e = cudaMalloc(&sl.d, sizeof(BatchDev))) != cudaSuccess ||
+            (e = cudaMallocHost(&sl.h, sizeof(BatchDev))) != cudaSuccess ||
+            (e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming)) != cudaSuccess)
+            return bail(DENSIFY_E_CUDA, std::string("slot: ") + cudaGetErrorString(e));
+        if (params->timing)
+            for (auto &ev : sl.kev)
+                if ((e = cudaEventCreate(&ev)) != cudaSuccess)
+                    return bail(DENSIFY_E_CUDA, std::string("event: ") + cudaGetErrorString(e));
+    }
+    // stage constants
+    if (params->num_stages == 1) {
+        fill_stage(c->sa[0], params->stage[0], 1, 0);
+    } else {
+        fill_stage(c->sa[0], params->stage[0], params->pool, 0);
+        fill_stage(c->sa[1], params->stage[1], params->pool, params->stage2_input);
+    }
+    // persistent grids: SM count x resident blocks
+    int sms = 0;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess)
+        return bail(DENSIFY_E_CUDA, std::string("attribute: ") + cudaGetErrorString(e));
+    c->grid[K_PREP] = sms * occupancy_points(K_PREP);
+    c->grid[K_PROJECT] = sms * occupancy_points(K_PROJECT);
+    c->grid[K_POOL] = sms * occupancy_pool_bp(K_POOL);
+    c->grid[K_BP_COUNT] = sms * occupancy_pool_bp(K_BP_COUNT);
+    c->grid[K_BP_WRITE] = sms * occupancy_pool_bp(K_BP_WRITE);
+    if (params->num_stages == 1) {
+        c->grid[K_JBF1] = sms * occupancy_jbf_single(params->stage[0].radius);
+    } else {
+        c->grid[K_JBF1] = sms * occupancy_jbf_coarse(params->stage[0].radius);
+        c->grid[K_JBF2] = sms * occupancy_jbf_up(params->stage[1].radius);
+    }
+    if ((e = cudaGetLastError()) != cudaSuccess)
+        return bail(DENSIFY_E_CUDA, std::string("setup: ") + cudaGetErrorString(e));
+    *out = c;
+    return DENSIFY_OK;
+}
+
+densify_status densify_submit(densify_ctx *c, const densify_frame *frame, uint64_t *ticket) {
+    if (!c) return fail(nullptr, DENSIFY_E_INVALID, "ctx is NULL");
+    if (!ticket) return fail(c, DENSIFY_E_INVALID, "ticket is NULL");
+    *ticket = 0;
+    if (c->dead) return DENSIFY_E_CUDA;
+    const std::string ferr = validate_frame(c, frame);
+    if (!ferr.empty()) return fail(c, DENSIFY_E_INVALID, ferr);
+    DeviceGuard guard(c->device);
+    densify_status st = progress(c, false);
+    if (st != DENSIFY_OK) return st;
+    if (c->admitted >= c->p.max_inflight) return fail(c, DENSIFY_E_AGAIN, "max_inflight frames admitted");
+    FrameRec r;
+    r.fr = *frame;
+    r.L = layout_of(c->p, frame);
+    if (r.L.total > c->arena.size()) return fail(c, DENSIFY_E_NOMEM, "frame scratch exceeds hbm_budget_bytes");
+    if (!c->arena.alloc(r.L.total, &r.off)) return fail(c, DENSIFY_E_AGAIN, "scratch arena full");
+    const uint64_t t = c->next_ticket++;
+    c->frames.emplace(t, r);
+    c->queue.push_back(t);
+    c->admitted++;
+    *ticket = t;
+    const bool eager = c->p.launch_policy == 0;
+    if (eager || (int)c->queue.size() >= c->p.max_batch) return progress(c, true);
+    return DENSIFY_OK;
+}
+
+densify_status densify_flush(densify_ctx *c, int64_t timeout_ns) {
+    if (!c) return fail(nullptr, DENSIFY_E_INVALID, "ctx is NULL");
+    DeviceGuard guard(c->device);
+    const int64_t deadline = timeout_ns < 0 ? -1 : now_ns() + timeout_ns;
+    while (true) {
+        densify_status st = progress(c, true);
+        if (st != DENSIFY_OK) return st;
+        if (c->queue.empty()) return DENSIFY_OK;
+        if (timeout_ns == 0) return DENSIFY_PENDING;
+        st = wait_some(c, deadline);
+        if (st != DENSIFY_OK) return st;
+    }
+}
+
+densify_status densify_poll(densify_ctx *c, uint64_t ticket, int64_t timeout_ns) {
+    if (!c) return fail(nullptr, DENSIFY_E_INVALID, "ctx is NULL");
+    auto it = c->frames.find(ticket);
+    if (it == c->frames.end()) return fail(c, DENSIFY_E_TICKET, "unknown ticket");
+    DeviceGuard guard(c->device);
+    const int64_t deadline = timeout_ns < 0 ? -1 : now_ns() + timeout_ns;
+    while (true) {
+        densify_status st = progress(c, true);
+        if (st != DENSIFY_OK) return st;
+        FrameRec &r = c->frames[ticket];
+        if (r.state == 2) {
+            st = finalize(c, r);
+            c->arena.release(r.off, r.L.total);
+            c->frames.erase(ticket);
+            c->admitted--;
+            return st;
+        }
+        if (timeout_ns == 0) return DENSIFY_PENDING;
+        if (deadline >= 0 && now_ns() >= deadline) return fail(c, DENSIFY_E_TIMEOUT, "poll timed out");
+        if (r.state == 1 && timeout_ns < 0) {
+            cudaError_t e = cudaEventSynchronize(c->slots[r.slot].done);
+            if (e != cudaSuccess) return cuda_fail(c, e, "batch failed");
+            continue;
+        }
+        if (!any_busy(c) && r.state == 0) continue;   // a slot is free: the next progress launches it
+        st = wait_some(c, deadline);
+        if (st == DENSIFY_E_TIMEOUT) return fail(c, st, "poll timed out");
+        if (st != DENSIFY_OK) return st;
+    }
+}
+
+densify_status densify_destroy(densify_ctx *c) {
+    if (!c) return DENSIFY_E_INVALID;
+    densify_status ret = DENSIFY_OK;
+    {
+        DeviceGuard guard(c->device);
+        const int64_t per = 10ll * 1000 * 1000 * 1000;
+        for (auto &sl : c->slots) {
+            if (!sl.busy) continue;
+            const int64_t deadline = now_ns() + per;
+            while (true) {
+                cudaError_t q = cudaEventQuery(sl.done);
+                if (q == cudaSuccess) break;
+                if (q != cudaErrorNotReady) { ret = DENSIFY_E_CUDA; break; }
+                if (now_ns() >= deadline) { ret = DENSIFY_E_TIMEOUT; break; }
+                std::this_thread::yield();
+            }
+        }
+        if (ret == DENSIFY_OK) destroy_resources(c);
+    }
+    if (ret == DENSIFY_OK) delete c;
+    return ret;
+}
+
+int32_t densify_kernel_times(densify_ctx *c, const char **names, double *total_us, int64_t *launches, int32_t cap) {
+    if (!c) return 0;
+    DeviceGuard guard(c->device);
+    progress(c, false);
+    int32_t n = 0;
+    for (int k = 0; k < K_COUNT && n < cap; ++k) {
+        if (c->t_n[k] == 0) continue;
+        if (names) names[n] = kKernelNames[k];
+        if (total_us) total_us[n] = c->t_us[k];
+        if (launches) launches[n] = c->t_n[k];
+        ++n;
+    }
+    return n;
+}
+
+void densify_reset_kernel_times(densify_ctx *c) {
+    if (!c) return;
+    for (int k = 0; k < K_COUNT; ++k) {
+        c->t_us[k] = 0.0;
+        c->t_n[k] = 0;
+    }
+}
+
+}  // extern "C"
