@@ -119,6 +119,12 @@ typedef struct densify_stage {
  *                 busy are launched together when one frees (continuous
  *                 batching). 1 (batch): frames wait until max_batch are
  *                 queued, or until densify_flush() / densify_poll().
+ *   kernel_variant 0: filter kernels whose tiles are staged by TMA where the
+ *                 stage has one (radius 1-3 second stage with pool 3 and
+ *                 stage2_input 0; radius 2 or 4 first stage; radius 2, 4 or 7
+ *                 single stage), the plain shared-memory kernels elsewhere.
+ *                 1: the plain kernels everywhere (same results, for
+ *                 comparison).
  */
 typedef struct densify_params {
     int32_t num_stages;
@@ -134,7 +140,8 @@ typedef struct densify_params {
     uint64_t hbm_budget_bytes;
     int32_t timing;
     int32_t launch_policy;
-    int32_t reserved[6];
+    int32_t kernel_variant;
+    int32_t reserved[5];
 } densify_params;
 
 /* Pinhole intrinsics of the camera (Sec. 2: calibrated in advance). */

@@ -10,6 +10,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda.h>          // CUtensorMap (type only; maps are encoded through the runtime's driver entry point)
 #include <cuda_runtime.h>
 
 namespace dz {
@@ -35,8 +36,16 @@ struct ScanDev {
     float M[12];             // camera <- LiDAR, composed on the GPU in FP64
 };
 
-struct FrameDev {
+// Tensor maps of a frame (TMA descriptors, encoded on the host per batch).
+enum { TM_RGB = 0, TM_S1 = 1, TM_CGUIDE = 2, TM_CSSUM = 3, TM_ZBUF = 4, TM_COUNT = 5 };
+
+struct alignas(64) FrameDev {
+    CUtensorMap tm[TM_COUNT];
     int32_t W, H, Wc, Hc;    // full and coarse (ceil(H/pool) x ceil(W/pool)) grids
+    int32_t cpitch;          // row pitch of the coarse arrays in elements (multiple of 4)
+    int32_t zpitch;          // row pitch of the z-buffer in elements (multiple of 4)
+    int32_t pad0;
+    int32_t tma;             // tensor maps valid
     float fx, fy, cx, cy;
     double c2w[16];          // cam_to_world, row-major
     float c2w32[12];         // written by the prep kernel (FP64 -> FP32 once)
@@ -46,10 +55,10 @@ struct FrameDev {
     const uint8_t *rgb;      // H x W x 3, rgb_pitch bytes per row
     int64_t rgb_pitch;
     // scratch (context arena)
-    uint32_t *zbuf;          // W*H nearest-depth bit patterns
-    float4 *cguide;          // Wc*Hc: pooled mean r, g, b and observation count
-    float *cssum;            // Wc*Hc: pooled depth sum
-    float2 *s1;              // Wc*Hc: first-stage depth and validity (0/1)
+    uint32_t *zbuf;          // H x zpitch nearest-depth bit patterns
+    float4 *cguide;          // Hc x cpitch: pooled mean r, g, b and observation count
+    float *cssum;            // Hc x cpitch: pooled depth sum
+    float2 *s1;              // Hc x cpitch: first-stage depth and validity (0/1)
     uint32_t *chunk_cnt;     // n_bp_chunks valid-pixel counts
     // outputs (caller memory, or arena staging for host frames)
     float *out_depth;
@@ -64,6 +73,7 @@ struct FrameDev {
 struct BatchDev {
     int32_t n_frames;
     int32_t pad;
+    int32_t *status;                               // device word: nonzero after a bounded wait gave up
     int32_t zb_pre[kMaxBatch + 1];                 // z-buffer clear chunks
     int32_t pt_pre[kMaxBatch * kMaxScans + 1];     // point chunks per (frame, scan)
     int32_t pool_pre[kMaxBatch + 1];               // pooling chunks

@@ -48,22 +48,22 @@ __device__ __forceinline__ void grid_size(const FrameDev &F, int &gw, int &gh) {
 template <int STAGE>
 __device__ __forceinline__ void load_src(const FrameDev &F, const StageArgs &a, int gx, int gy, float4 &g, float &bd) {
     if (STAGE == JBF_COARSE) {
-        const int64_t o = (int64_t)gy * F.Wc + gx;
+        const int64_t o = (int64_t)gy * F.cpitch + gx;
         g = F.cguide[o];                      // mean r, g, b and count
         bd = F.cssum[o];
     } else {
         const uint8_t *c = F.rgb + (int64_t)gy * F.rgb_pitch + 3 * gx;
         g.x = (float)c[0]; g.y = (float)c[1]; g.z = (float)c[2];
         if (STAGE == JBF_SINGLE) {
-            const uint32_t z = F.zbuf[(int64_t)gy * F.W + gx];
+            const uint32_t z = F.zbuf[(int64_t)gy * F.zpitch + gx];
             g.w = z != kEmpty ? 1.0f : 0.0f;
             bd = z != kEmpty ? __uint_as_float(z) : 0.0f;
         } else {
-            const float2 s = F.s1[(int64_t)(gy / a.pool) * F.Wc + gx / a.pool];
+            const float2 s = F.s1[(int64_t)(gy / a.pool) * F.cpitch + gx / a.pool];
             g.w = s.y;
             bd = s.y > 0.0f ? s.x : 0.0f;
             if (a.override_sparse) {
-                const uint32_t z = F.zbuf[(int64_t)gy * F.W + gx];
+                const uint32_t z = F.zbuf[(int64_t)gy * F.zpitch + gx];
                 if (z != kEmpty) { g.w = 1.0f; bd = __uint_as_float(z); }
             }
         }
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(256) jbf_kernel(const BatchDev *__restrict__ B
             if (x < gw && y < gh) {
                 const int64_t o = (int64_t)y * gw + x;
                 if (STAGE == JBF_COARSE) {
-                    F.s1[o] = make_float2(out, val[k] ? 1.0f : 0.0f);
+                    F.s1[(int64_t)y * F.cpitch + x] = make_float2(out, val[k] ? 1.0f : 0.0f);
                     if (F.out_coarse) F.out_coarse[o] = out;
                     if (F.out_coarse_valid) F.out_coarse_valid[o] = val[k];
                 } else {

@@ -1,0 +1,390 @@
+// Joint bilateral filter (Eq. (1)-(4)), gather form, with the input tiles
+// staged by TMA.
+//
+// Same arithmetic as jbf_core.cuh; what changes is how a tile reaches shared
+// memory. The kernel is persistent (a multiple of the SM count of CTAs, each
+// walking tiles t = blockIdx.x + i * gridDim.x across all frames of the
+// batch). Thread 0 issues the 2-D bulk tensor copies (cp.async.bulk.tensor,
+// no multicast) of tile i+1 into the second of two raw buffers while the CTA
+// filters tile i, so global-memory latency is hidden behind the ALU work.
+//
+// Sources:
+//   SRC_UP     second stage: raw RGB bytes of the full-resolution tile + halo,
+//              and the first-stage result (float2 depth, validity) on the
+//              coarse grid; restored by nearest-neighbour indexing (x / 3).
+//   SRC_ZBUF   single stage: raw RGB bytes and the z-buffer tile.
+//   SRC_COARSE first stage: pooled guide (float4 r, g, b, count) and pooled
+//              depth sums (float); used in place, no conversion.
+// For SRC_UP / SRC_ZBUF a conversion pass writes each staged neighbour as one
+// float4 (r, g, b, depth); an unobserved neighbour gets the colour 1e18, so
+// its weight 2^(-kc * 1e36 ...) is exactly 0 and the weight sum needs no mask
+// multiply. The centre colour of each output pixel is read from the raw bytes.
+//
+// Bounded waits: every mbarrier wait gives up after kWaitCycles SM clocks
+// (about 2 s); the CTA then sets bit 0 of the batch status word, waits (again
+// bounded) for its own copies in flight and leaves. The host reports the
+// status as a CUDA error of the batch.
+#pragma once
+
+#include "jbf_core.cuh"
+
+namespace dz {
+
+constexpr long long kWaitCycles = 4000000000LL;
+constexpr float kSentinel = 1.0e18f;
+
+enum { SRC_UP = 0, SRC_ZBUF = 1, SRC_COARSE = 2 };
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity))
+        if (clock64() - t0 > kWaitCycles) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tmap_acquire(const CUtensorMap *m) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)m) : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *m, int x, int y, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+            "r"(smem_u32(dst)),
+        "l"((uint64_t)m), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ int floor_div3(int a) { return a >= 0 ? a / 3 : -((2 - a) / 3); }
+
+constexpr int ceil_to(int x, int m) { return (x + m - 1) / m * m; }
+
+// Tile geometry shared by the kernel and the host (tensor-map boxes).
+template <int SRC, int R, int KP>
+struct TmaGeom {
+    static constexpr int TW = 32, NW = 8, TH = NW * KP, SW = TW + 2 * R, SH = TH + 2 * R;
+    // RGB bytes: box starts at byte 3*x0 - RGB_LEAD (x0 is a multiple of 32, so 3*x0 of 16)
+    static constexpr int RGB_LEAD = ceil_to(3 * R, 16);
+    static constexpr int RGB_BX = ceil_to(3 * TW + 3 * R + RGB_LEAD, 16);
+    static constexpr int RGB_BY = SH;
+    // first-stage result (float2) on the pooled grid, pool 3: rows floor((y0-R)/3) ..
+    // floor((y0+TH-1+R)/3); columns from floor((x0-R)/3) rounded down to even
+    static constexpr int C_BX = ceil_to(2 + (SW + 1) / 3, 2);
+    static constexpr int C_BY = 1 + (SH + 1) / 3;
+    // z-buffer (uint32): box starts at x0 - Z_LEAD
+    static constexpr int Z_LEAD = ceil_to(R, 4);
+    static constexpr int Z_BX = ceil_to(TW + R + Z_LEAD, 4);
+    static constexpr int Z_BY = SH;
+    // pooled guide (float4, as 4 floats per element) and pooled sums (float, starts at x0 - S_LEAD)
+    static constexpr int G_BX = 4 * SW;
+    static constexpr int G_BY = SH;
+    static constexpr int S_LEAD = ceil_to(R, 4);
+    static constexpr int S_BX = ceil_to(TW + R + S_LEAD, 4);
+    static constexpr int S_BY = SH;
+
+    // raw buffer bytes (each rounded to 128 for TMA destination alignment)
+    static constexpr int RAW_A = SRC == SRC_COARSE ? ceil_to(G_BX * G_BY * 4, 128) : ceil_to(RGB_BX * RGB_BY, 128);
+    static constexpr int RAW_B = SRC == SRC_UP     ? ceil_to(C_BX * C_BY * 8, 128)
+                                 : SRC == SRC_ZBUF ? ceil_to(Z_BX * Z_BY * 4, 128)
+                                                   : ceil_to(S_BX * S_BY * 4, 128);
+    static constexpr int TX_BYTES = SRC == SRC_COARSE ? G_BX * G_BY * 4 + S_BX * S_BY * 4
+                                    : SRC == SRC_UP   ? RGB_BX * RGB_BY + C_BX * C_BY * 8
+                                                      : RGB_BX * RGB_BY + Z_BX * Z_BY * 4;
+    static constexpr int STAGED = SRC == SRC_COARSE ? 0 : SH * SW * 16;
+    static constexpr int OBS = SRC == SRC_COARSE ? 0 : ceil_to(SH * SW, 16);
+    static constexpr int HOR = ceil_to(SH * TW, 16);
+    static constexpr int OFF_RAW = 0;
+    static constexpr int OFF_STAGED = OFF_RAW + 2 * (RAW_A + RAW_B);
+    static constexpr int OFF_OBS = OFF_STAGED + STAGED;
+    static constexpr int OFF_HOR = OFF_OBS + OBS;
+    static constexpr int OFF_BAR = ceil_to(OFF_HOR + HOR, 16);
+    static constexpr int SMEM = OFF_BAR + 16;
+};
+
+// Shifted recomputation of one output pixel (rare: every observed neighbour
+// far in colour, so the plain weight sum fell below 2^-60). The exponents are
+// shifted by their maximum over the window; the quotient is unchanged.
+template <int SRC, int R, int SW, int S_BX, int S_LEAD>
+__device__ __noinline__ float jbf_tma_shifted(const float4 *q4, const float *cs, int row0, int col0, float cr, float cg,
+                                              float cb, float kc, float kp) {
+    constexpr int T = 2 * R + 1;
+    float amax = -__int_as_float(0x7F800000);
+    for (int dy = 0; dy < T; ++dy)
+        for (int dx = 0; dx < T; ++dx) {
+            const float4 q = q4[(row0 + dy) * SW + col0 + dx];
+            const bool seen = SRC == SRC_COARSE ? q.w > 0.0f : q.x < 1.0e17f;
+            if (seen) {
+                const float dr = q.x - cr, dg = q.y - cg, db = q.z - cb;
+                const float n2 = fmaf(dr, dr, fmaf(dg, dg, db * db));
+                const float s2 = (float)((dx - R) * (dx - R) + (dy - R) * (dy - R));
+                amax = fmaxf(amax, fmaf(n2, -kc, -s2 * kp));
+            }
+        }
+    float nn = 0.0f, dd = 0.0f;
+    for (int dy = 0; dy < T; ++dy)
+        for (int dx = 0; dx < T; ++dx) {
+            const float4 q = q4[(row0 + dy) * SW + col0 + dx];
+            const bool seen = SRC == SRC_COARSE ? q.w > 0.0f : q.x < 1.0e17f;
+            if (seen) {
+                const float dr = q.x - cr, dg = q.y - cg, db = q.z - cb;
+                const float n2 = fmaf(dr, dr, fmaf(dg, dg, db * db));
+                const float s2 = (float)((dx - R) * (dx - R) + (dy - R) * (dy - R));
+                const float w = ex2_approx(fmaf(n2, -kc, -s2 * kp) - amax);
+                if (SRC == SRC_COARSE) {
+                    nn = fmaf(w, cs[(row0 + dy) * S_BX + col0 + dx - R + S_LEAD], nn);
+                    dd = fmaf(w, q.w, dd);
+                } else {
+                    nn = fmaf(w, q.w, nn);
+                    dd += w;
+                }
+            }
+        }
+    return nn / dd;
+}
+
+template <int SRC, int R, int KP>
+__global__ void __launch_bounds__(256, 2) jbf_tma_kernel(const BatchDev *__restrict__ B, const StageArgs a) {
+    using G = TmaGeom<SRC, R, KP>;
+    constexpr int TW = G::TW, TH = G::TH, SW = G::SW, SH = G::SH, T = 2 * R + 1;
+    extern __shared__ __align__(128) uint8_t smem[];
+    // raw buffer b: A part at smem + b * (RAW_A + RAW_B), B part right after it
+    auto rawA = [&](int b) { return smem + G::OFF_RAW + b * (G::RAW_A + G::RAW_B); };
+    auto rawB = [&](int b) { return smem + G::OFF_RAW + b * (G::RAW_A + G::RAW_B) + G::RAW_A; };
+    float4 *staged = reinterpret_cast<float4 *>(smem + G::OFF_STAGED);
+    uint8_t *obs = smem + G::OFF_OBS;
+    uint8_t *hor = smem + G::OFF_HOR;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + G::OFF_BAR);
+
+    const int32_t *pre = SRC == SRC_UP ? B->t2_pre : B->t1_pre;
+    const int nf = B->n_frames;
+    const int total = pre[nf];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+
+    // tile -> (frame, x0, y0)
+    auto locate = [&](int item, int &fi, int &x0, int &y0) {
+        fi = find_segment(pre, nf, item);
+        const FrameDev &F = B->f[fi];
+        const int gw = SRC == SRC_COARSE ? F.Wc : F.W;
+        const int tiles_x = (gw + TW - 1) / TW;
+        const int t = item - pre[fi];
+        x0 = (t % tiles_x) * TW;
+        y0 = (t / tiles_x) * TH;
+    };
+    auto issue = [&](int item, int buf) {
+        int fi, x0, y0;
+        locate(item, fi, x0, y0);
+        const FrameDev &F = B->f[fi];
+        mbar_expect_tx(&bar[buf], G::TX_BYTES);
+        if (SRC == SRC_COARSE) {
+            tmap_acquire(&F.tm[TM_CGUIDE]);
+            tmap_acquire(&F.tm[TM_CSSUM]);
+            tma_load_2d(rawA(buf), &F.tm[TM_CGUIDE], 4 * (x0 - R), y0 - R, &bar[buf]);
+            tma_load_2d(rawB(buf), &F.tm[TM_CSSUM], x0 - G::S_LEAD, y0 - R, &bar[buf]);
+        } else {
+            tmap_acquire(&F.tm[TM_RGB]);
+            tma_load_2d(rawA(buf), &F.tm[TM_RGB], 3 * x0 - G::RGB_LEAD, y0 - R, &bar[buf]);
+            if (SRC == SRC_UP) {
+                tmap_acquire(&F.tm[TM_S1]);
+                tma_load_2d(rawB(buf), &F.tm[TM_S1], floor_div3(x0 - R) & ~1, floor_div3(y0 - R), &bar[buf]);
+            } else {
+                tmap_acquire(&F.tm[TM_ZBUF]);
+                tma_load_2d(rawB(buf), &F.tm[TM_ZBUF], x0 - G::Z_LEAD, y0 - R, &bar[buf]);
+            }
+        }
+    };
+
+    if (threadIdx.x == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    uint32_t inflight = 0u;   // bit b: thread 0 issued copies into buffer b not yet consumed
+    uint32_t phase = 0u;      // bit b: parity of buffer b's barrier
+    if (threadIdx.x == 0 && (int)blockIdx.x < total) {
+        issue(blockIdx.x, 0);
+        inflight |= 1u;
+    }
+    int it = 0;
+    for (int item = blockIdx.x; item < total; item += gridDim.x, ++it) {
+        const int buf = it & 1;
+        const int next = item + gridDim.x;
+        if (threadIdx.x == 0 && next < total) {   // the other buffer was released by the last barrier
+            issue(next, buf ^ 1);
+            inflight |= 1u << (buf ^ 1);
+        }
+        const bool ok = mbar_wait_bounded(&bar[buf], (phase >> buf) & 1u);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicOr(B->status, 1);
+                for (int b = 0; b < 2; ++b)
+                    if ((inflight >> b) & 1u) mbar_wait_bounded(&bar[b], (phase >> b) & 1u);
+            }
+            return;
+        }
+        phase ^= 1u << buf;
+        inflight &= ~(1u << buf);
+
+        int fi, x0, y0;
+        locate(item, fi, x0, y0);
+        const FrameDev &F = B->f[fi];
+        const int gw = SRC == SRC_COARSE ? F.Wc : F.W;
+        const int gh = SRC == SRC_COARSE ? F.Hc : F.H;
+        const uint8_t *rgbraw = rawA(buf);
+        const float4 *cg = reinterpret_cast<const float4 *>(rawA(buf));
+        const float *cs = reinterpret_cast<const float *>(rawB(buf));
+
+        // ---- conversion (SRC_UP / SRC_ZBUF) and observation map
+        if (SRC != SRC_COARSE) {
+            const int cx0 = floor_div3(x0 - R) & ~1, cy0 = floor_div3(y0 - R);
+            const float2 *craw = reinterpret_cast<const float2 *>(rawB(buf));
+            const uint32_t *zraw = reinterpret_cast<const uint32_t *>(rawB(buf));
+            for (int i = threadIdx.x; i < SH * SW; i += 256) {
+                const int sy = i / SW, sx = i - sy * SW;
+                const int gx = x0 - R + sx, gy = y0 - R + sy;
+                float4 v = make_float4(kSentinel, 0.0f, 0.0f, 0.0f);
+                uint8_t o = 0;
+                if (gx >= 0 && gx < gw && gy >= 0 && gy < gh) {
+                    const uint8_t *p = rgbraw + sy * G::RGB_BX + 3 * sx - 3 * R + G::RGB_LEAD;
+                    float d = 0.0f;
+                    if (SRC == SRC_UP) {
+                        const float2 c = craw[(gy / 3 - cy0) * G::C_BX + (gx / 3 - cx0)];
+                        o = c.y > 0.0f;
+                        d = c.x;
+                    } else {
+                        const uint32_t z = zraw[sy * G::Z_BX + sx - R + G::Z_LEAD];
+                        o = z != kEmpty;
+                        d = __uint_as_float(z);
+                    }
+                    if (o) v = make_float4((float)p[0], (float)p[1], (float)p[2], d);
+                }
+                staged[i] = v;
+                obs[i] = o;
+            }
+            __syncthreads();
+            for (int i = threadIdx.x; i < SH * TW; i += 256) {
+                const int sy = i / TW, sx = i - sy * TW;
+                uint32_t any = 0;
+#pragma unroll
+                for (int dx = 0; dx < T; ++dx) any |= obs[sy * SW + sx + dx];
+                hor[i] = any != 0;
+            }
+        } else {
+            for (int i = threadIdx.x; i < SH * TW; i += 256) {
+                const int sy = i / TW, sx = i - sy * TW;
+                bool any = false;
+#pragma unroll
+                for (int dx = 0; dx < T; ++dx) any |= cg[sy * SW + sx + dx].w > 0.0f;
+                hor[i] = any;
+            }
+        }
+        __syncthreads();
+
+        // ---- filter: thread owns column lane, rows rbase .. rbase + KP - 1 of the tile
+        const int rbase = warp * KP;
+        float cr[KP], cgr[KP], cb[KP], num[KP], den[KP];
+        bool val[KP];
+        bool any_val = false;
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            if (SRC == SRC_COARSE) {
+                const float4 c = cg[(rbase + k + R) * SW + lane + R];
+                cr[k] = c.x; cgr[k] = c.y; cb[k] = c.z;
+            } else {
+                const uint8_t *p = rgbraw + (rbase + k + R) * G::RGB_BX + 3 * lane + G::RGB_LEAD;
+                cr[k] = (float)p[0]; cgr[k] = (float)p[1]; cb[k] = (float)p[2];
+            }
+            num[k] = 0.0f;
+            den[k] = 0.0f;
+            bool v = false;
+#pragma unroll
+            for (int dy = 0; dy < T; ++dy) v |= hor[(rbase + k + dy) * TW + lane] != 0;
+            val[k] = v;
+            any_val |= v;
+        }
+        if (__any_sync(0xffffffffu, any_val)) {
+            const float kc = a.kc;
+#pragma unroll
+            for (int iy = 0; iy < KP + 2 * R; ++iy) {
+#pragma unroll
+                for (int dx = 0; dx < T; ++dx) {
+                    float4 q;
+                    float qs = 0.0f;
+                    if (SRC == SRC_COARSE) {
+                        q = cg[(rbase + iy) * SW + lane + dx];
+                        qs = cs[(rbase + iy) * G::S_BX + lane + dx - R + G::S_LEAD];
+                    } else {
+                        q = staged[(rbase + iy) * SW + lane + dx];
+                    }
+#pragma unroll
+                    for (int k = 0; k < KP; ++k) {
+                        const int dy = iy - k;
+                        if (dy >= 0 && dy < T) {
+                            const float dr = q.x - cr[k], dg = q.y - cgr[k], db = q.z - cb[k];
+                            const float n2 = fmaf(dr, dr, fmaf(dg, dg, db * db));
+                            const float w = ex2_approx(fmaf(n2, -kc, a.sp[dy * (2 * kMaxR + 1) + dx]));
+                            if (SRC == SRC_COARSE) {
+                                num[k] = fmaf(w, qs, num[k]);
+                                den[k] = fmaf(w, q.w, den[k]);
+                            } else {
+                                num[k] = fmaf(w, q.w, num[k]);
+                                den[k] += w;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        const int x = x0 + lane;
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            const int y = y0 + rbase + k;
+            float out = 0.0f;
+            if (val[k]) {
+                if (den[k] >= 0x1p-60f) {
+                    out = num[k] / den[k];
+                } else {
+                    out = jbf_tma_shifted<SRC, R, SW, G::S_BX, G::S_LEAD>(
+                        SRC == SRC_COARSE ? cg : staged, cs, rbase + k, lane, cr[k], cgr[k], cb[k], a.kc, a.kp);
+                }
+            }
+            if (x < gw && y < gh) {
+                const int64_t o = (int64_t)y * gw + x;
+                if (SRC == SRC_COARSE) {
+                    F.s1[(int64_t)y * F.cpitch + x] = make_float2(out, val[k] ? 1.0f : 0.0f);
+                    if (F.out_coarse) F.out_coarse[o] = out;
+                    if (F.out_coarse_valid) F.out_coarse_valid[o] = val[k];
+                } else {
+                    F.out_depth[o] = out;
+                    F.out_valid[o] = val[k];
+                }
+            }
+        }
+        __syncthreads();   // staged / raw[buf] / hor are reused by the next tile
+    }
+}
+
+}  // namespace dz

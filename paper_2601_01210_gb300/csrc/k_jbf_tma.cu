@@ -1,0 +1,95 @@
+// Instantiations of the TMA-staged joint bilateral filter and the host-side
+// description of their tiles (tensor-map boxes, shared memory, rows per tile).
+#include "jbf_tma.cuh"
+#include "tma_info.h"
+
+namespace dz {
+
+namespace {
+
+template <int SRC, int R, int KP>
+void fill_info(TmaKernelInfo *o) {
+    using G = TmaGeom<SRC, R, KP>;
+    o->supported = 1;
+    o->kp = KP;
+    o->tile_w = G::TW;
+    o->tile_h = G::TH;
+    o->smem = G::SMEM;
+    o->rgb_box[0] = G::RGB_BX; o->rgb_box[1] = G::RGB_BY;
+    o->s1_box[0] = G::C_BX;    o->s1_box[1] = G::C_BY;
+    o->zbuf_box[0] = G::Z_BX;  o->zbuf_box[1] = G::Z_BY;
+    o->cguide_box[0] = G::G_BX; o->cguide_box[1] = G::G_BY;
+    o->cssum_box[0] = G::S_BX; o->cssum_box[1] = G::S_BY;
+}
+
+template <int SRC, int R, int KP>
+cudaError_t prep() {
+    return cudaFuncSetAttribute(jbf_tma_kernel<SRC, R, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TmaGeom<SRC, R, KP>::SMEM);
+}
+
+template <int SRC, int R, int KP>
+cudaError_t go(const BatchDev *b, const StageArgs &a, int grid, cudaStream_t s) {
+    jbf_tma_kernel<SRC, R, KP><<<grid, 256, TmaGeom<SRC, R, KP>::SMEM, s>>>(b, a);
+    return cudaGetLastError();
+}
+
+template <int SRC, int R, int KP>
+int occ() {
+    int n = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, jbf_tma_kernel<SRC, R, KP>, 256, TmaGeom<SRC, R, KP>::SMEM);
+    return n > 0 ? n : 1;
+}
+
+// (source, radius) -> rows per thread; 0: no TMA variant
+constexpr int kp_of(int src, int r) {
+    return src == SRC_UP ? (r == 1 || r == 2 ? 8 : r == 3 ? 4 : 0)
+         : src == SRC_COARSE ? (r == 2 || r == 4 ? 4 : 0)
+         : src == SRC_ZBUF ? (r == 2 || r == 4 ? 8 : r == 7 ? 4 : 0)
+         : 0;
+}
+
+#define DZ_TMA_CASES(X)           \
+    X(SRC_UP, 1, 8)               \
+    X(SRC_UP, 2, 8)               \
+    X(SRC_UP, 3, 4)               \
+    X(SRC_COARSE, 2, 4)           \
+    X(SRC_COARSE, 4, 4)           \
+    X(SRC_ZBUF, 2, 8)             \
+    X(SRC_ZBUF, 4, 8)             \
+    X(SRC_ZBUF, 7, 4)
+
+}  // namespace
+
+bool jbf_tma_info(int src, int r, TmaKernelInfo *out) {
+    *out = TmaKernelInfo{};
+#define X(S, RR, K) if (src == S && r == RR) { fill_info<S, RR, K>(out); return true; }
+    DZ_TMA_CASES(X)
+#undef X
+    return false;
+}
+
+cudaError_t jbf_tma_prepare(int src, int r) {
+#define X(S, RR, K) if (src == S && r == RR) return prep<S, RR, K>();
+    DZ_TMA_CASES(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_jbf_tma(int src, int r, const BatchDev *b, const StageArgs &a, int grid, cudaStream_t s) {
+#define X(S, RR, K) if (src == S && r == RR) return go<S, RR, K>(b, a, grid, s);
+    DZ_TMA_CASES(X)
+#undef X
+    return cudaErrorInvalidValue;
+}
+
+int occupancy_jbf_tma(int src, int r) {
+#define X(S, RR, K) if (src == S && r == RR) return occ<S, RR, K>();
+    DZ_TMA_CASES(X)
+#undef X
+    return 1;
+}
+
+static_assert(kp_of(SRC_UP, 2) == 8, "paper second stage has a TMA variant");
+
+}  // namespace dz

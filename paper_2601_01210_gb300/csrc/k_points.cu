@@ -52,7 +52,7 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(BatchDev *__restrict__ B
                 F.c2w32[e] = __double2float_rn(F.c2w[(e / 4) * 4 + (e % 4)]);
             }
         }
-        const int64_t n = (int64_t)F.W * F.H;
+        const int64_t n = (int64_t)F.zpitch * F.H;
         const int64_t w0 = (int64_t)c * kZbWordsPerChunk;
         const int64_t w1 = min(n, w0 + kZbWordsPerChunk);
         uint32_t *z = F.zbuf;
@@ -80,7 +80,7 @@ __device__ __forceinline__ void project_one(const float (&M)[12], float x, float
     if (!(u >= 0.0f && u < (float)F.W && v >= 0.0f && v < (float)F.H)) return;
     const int i = __float2int_rz(u);   // u >= 0: truncation is floor
     const int j = __float2int_rz(v);
-    atomicMin(zbuf + (int64_t)j * F.W + i, __float_as_uint(zc));
+    atomicMin(zbuf + (int64_t)j * F.zpitch + i, __float_as_uint(zc));
 }
 
 __global__ void __launch_bounds__(kThreads) project_kernel(const BatchDev *__restrict__ B) {

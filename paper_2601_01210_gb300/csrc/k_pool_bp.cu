@@ -25,7 +25,7 @@ __global__ void __launch_bounds__(kThreads) pool_kernel(const BatchDev *__restri
         const int x1 = min(x0 + f, F.W), y1 = min(y0 + f, F.H);
         float s = 0.0f, cnt = 0.0f, r = 0.0f, g = 0.0f, b = 0.0f;
         for (int y = y0; y < y1; ++y) {
-            const uint32_t *zr = F.zbuf + (int64_t)y * F.W;
+            const uint32_t *zr = F.zbuf + (int64_t)y * F.zpitch;
             const uint8_t *cr = F.rgb + (int64_t)y * F.rgb_pitch;
             for (int x = x0; x < x1; ++x) {
                 const uint32_t z = zr[x];
@@ -39,8 +39,9 @@ __global__ void __launch_bounds__(kThreads) pool_kernel(const BatchDev *__restri
             }
         }
         const float npx = (float)((x1 - x0) * (y1 - y0));
-        F.cguide[idx] = make_float4(__fdiv_rn(r, npx), __fdiv_rn(g, npx), __fdiv_rn(b, npx), cnt);
-        F.cssum[idx] = s;
+        const int64_t o = (int64_t)J * F.cpitch + I;
+        F.cguide[o] = make_float4(__fdiv_rn(r, npx), __fdiv_rn(g, npx), __fdiv_rn(b, npx), cnt);
+        F.cssum[o] = s;
     }
 }
 

@@ -22,12 +22,16 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "../../include/densify.h"
 #include "desc.cuh"
+#include "tma_info.h"
 
 using namespace dz;
 
@@ -91,6 +95,7 @@ private:
 struct Layout {
     uint64_t zbuf = 0, cguide = 0, cssum = 0, s1 = 0, chunk = 0, depth = 0, valid = 0;
     uint64_t pts[kMaxScans] = {0, 0, 0}, rgb = 0, points = 0, npts = 0, coarse = 0, coarse_valid = 0;
+    int64_t rgb_pitch = 0;   // pitch of the staged RGB copy (0: the caller's frame is used in place)
     uint64_t total = 0;
     bool own_depth = false, own_valid = false;
 };
@@ -108,6 +113,8 @@ struct FrameRec {
 struct Slot {
     BatchDev *d = nullptr;       // device table
     BatchDev *h = nullptr;       // pinned host mirror
+    int32_t *d_status = nullptr; // device status word (bounded waits that gave up)
+    int32_t *h_status = nullptr; // pinned copy, written at the end of every batch
     cudaEvent_t done = nullptr;
     cudaEvent_t kev[K_COUNT + 1] = {};
     bool ktimed[K_COUNT] = {};
@@ -115,6 +122,43 @@ struct Slot {
     bool busy = false;
     std::vector<uint64_t> tickets;
 };
+
+// One filter launch: which kernel runs it and its tile height.
+struct FilterSel {
+    int kind = 0;        // 0 single, 1 coarse, 2 restored full resolution
+    int radius = 0;
+    bool tma = false;
+    int src = 0;         // TMA source kind
+    int tile_h = 0;
+    TmaKernelInfo info{};
+};
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+bool tensor_map_encoder() {
+    std::call_once(g_encode_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+        cudaGetLastError();
+    });
+    return g_encode != nullptr;
+}
+
+bool encode2d(CUtensorMap *m, CUtensorMapDataType dt, const void *base, uint64_t d0, uint64_t d1, uint64_t stride,
+              int b0, int b1) {
+    const cuuint64_t dims[2] = {d0, d1};
+    const cuuint64_t strides[1] = {stride};
+    const cuuint32_t box[2] = {(cuuint32_t)b0, (cuuint32_t)b1};
+    const cuuint32_t es[2] = {1, 1};
+    return g_encode(m, dt, 2, const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 int64_t now_ns() {
     return std::chrono::duration_cast<std::chrono::nanoseconds>(std::chrono::steady_clock::now().time_since_epoch())
@@ -139,6 +183,7 @@ struct densify_ctx {
     uint64_t next_ticket = 1;
     int admitted = 0;
     int grid[K_COUNT] = {};
+    FilterSel sel[2];                    // first (or only) and second filter
     std::string err;
     bool dead = false;
     double t_us[K_COUNT] = {};
@@ -185,9 +230,21 @@ bool stage_supported(int kind, int r) {
     return r <= kMaxR;
 }
 
-int tile_h(const densify_params &p, int kind, int r) {
-    const int kp = kind == 0 ? kp_jbf_single(r) : kind == 1 ? kp_jbf_coarse(r) : kp_jbf_up(r);
-    return 8 * kp;
+FilterSel select_filter(const densify_params &p, int kind, int r) {
+    FilterSel s;
+    s.kind = kind;
+    s.radius = r;
+    const int src = kind == 0 ? TMA_SRC_ZBUF : kind == 1 ? TMA_SRC_COARSE : TMA_SRC_UP;
+    const bool allowed = p.kernel_variant == 0 && (kind != 2 || (p.pool == 3 && p.stage2_input == 0));
+    if (allowed && jbf_tma_info(src, r, &s.info)) {
+        s.tma = true;
+        s.src = src;
+        s.tile_h = s.info.tile_h;
+    } else {
+        const int kp = kind == 0 ? kp_jbf_single(r) : kind == 1 ? kp_jbf_coarse(r) : kp_jbf_up(r);
+        s.tile_h = 8 * kp;
+    }
+    return s;
 }
 
 void fill_stage(StageArgs &a, const densify_stage &st, int pool, int override_sparse) {
@@ -220,6 +277,7 @@ std::string validate_params(const densify_params &p) {
     if (p.batches_in_flight < 1 || p.batches_in_flight > 8) return "batches_in_flight must be in 1..8";
     if (p.hbm_budget_bytes < (1u << 20)) return "hbm_budget_bytes must be >= 1 MiB";
     if (p.launch_policy != 0 && p.launch_policy != 1) return "launch_policy must be 0 or 1";
+    if (p.kernel_variant != 0 && p.kernel_variant != 1) return "kernel_variant must be 0 or 1";
     return "";
 }
 
@@ -248,8 +306,6 @@ std::string validate_frame(const densify_ctx *c, const densify_frame *f) {
         if (f->out_points_cap > 0 && !f->out_points) return "out_points is NULL with a nonzero capacity";
         if (f->out_points && ((uintptr_t)f->out_points & 15u)) return "out_points must be 16-byte aligned";
     }
-    if (f->memory == DENSIFY_MEM_DEVICE && f->out_zbuf && ((uintptr_t)f->out_zbuf & 15u))
-        return "out_zbuf must be 16-byte aligned";
     return "";
 }
 
@@ -263,12 +319,14 @@ Layout layout_of(const densify_params &p, const densify_frame *f) {
         o += align_up(bytes ? bytes : 1);
         return at;
     };
-    L.zbuf = take(npx * 4);
+    const int64_t zp = (W + 3) & ~int64_t(3);
+    L.zbuf = take(zp * H * 4);
     if (p.num_stages == 2) {
         const int64_t Wc = (W + p.pool - 1) / p.pool, Hc = (H + p.pool - 1) / p.pool;
-        L.cguide = take(Wc * Hc * 16);
-        L.cssum = take(Wc * Hc * 4);
-        L.s1 = take(Wc * Hc * 8);
+        const int64_t cp = (Wc + 3) & ~int64_t(3);
+        L.cguide = take(cp * Hc * 16);
+        L.cssum = take(cp * Hc * 4);
+        L.s1 = take(cp * Hc * 8);
         if (host && f->out_coarse) L.coarse = take(Wc * Hc * 4);
         if (host && f->out_coarse_valid) L.coarse_valid = take(Wc * Hc);
     }
@@ -279,13 +337,18 @@ Layout layout_of(const densify_params &p, const densify_frame *f) {
     if (L.own_valid) L.valid = take(npx);
     if (host) {
         for (int s = 0; s < f->num_scans; ++s) L.pts[s] = take((uint64_t)f->scans[s].count * f->scans[s].stride_bytes);
-        L.rgb = take((uint64_t)H * W * 3);
         if (p.emit_points) {
             L.points = take((uint64_t)f->out_points_cap * 16);
             L.npts = take(8);
         }
     } else if (p.emit_points) {
         L.npts = 0;
+    }
+    // RGB goes to the kernels through TMA, which needs a 16-byte aligned base and
+    // pitch: host frames and unaligned device frames are staged with pitch ceil16(3W)
+    if (host || ((uintptr_t)f->rgb & 15u) || (f->rgb_pitch & 15)) {
+        L.rgb_pitch = (3 * W + 15) & ~int64_t(15);
+        L.rgb = take((uint64_t)L.rgb_pitch * H);
     }
     L.total = o;
     return L;
@@ -303,6 +366,7 @@ void build_frame_dev(densify_ctx *c, FrameRec &r) {
     const int pool = c->p.num_stages == 2 ? c->p.pool : 1;
     d.Wc = (d.W + pool - 1) / pool;
     d.Hc = (d.H + pool - 1) / pool;
+    d.cpitch = (d.Wc + 3) & ~3;
     d.fx = f->K.fx; d.fy = f->K.fy; d.cx = f->K.cx; d.cy = f->K.cy;
     std::memcpy(d.c2w, f->cam_to_world, sizeof(d.c2w));
     d.num_scans = f->num_scans;
@@ -319,9 +383,10 @@ void build_frame_dev(densify_ctx *c, FrameRec &r) {
             S.stride_floats = 3;
         }
     }
-    d.rgb = host ? (const uint8_t *)(base + L.rgb) : f->rgb;
-    d.rgb_pitch = host ? (int64_t)d.W * 3 : f->rgb_pitch;
-    d.zbuf = (!host && f->out_zbuf) ? f->out_zbuf : (uint32_t *)(base + L.zbuf);
+    d.rgb = L.rgb_pitch ? (const uint8_t *)(base + L.rgb) : f->rgb;
+    d.rgb_pitch = L.rgb_pitch ? L.rgb_pitch : f->rgb_pitch;
+    d.zpitch = (d.W + 3) & ~3;
+    d.zbuf = (uint32_t *)(base + L.zbuf);
     if (c->p.num_stages == 2) {
         d.cguide = (float4 *)(base + L.cguide);
         d.cssum = (float *)(base + L.cssum);
@@ -344,17 +409,19 @@ void fill_batch(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &tk) {
     BatchDev &b = *sl.h;
     const int n = (int)tk.size();
     b.n_frames = n;
+    b.status = sl.d_status;
     b.zb_pre[0] = b.pt_pre[0] = b.pool_pre[0] = b.t1_pre[0] = b.t2_pre[0] = b.bp_pre[0] = 0;
     const int nst = c->p.num_stages;
     const int r1 = c->p.stage[0].radius, r2 = nst == 2 ? c->p.stage[1].radius : 0;
-    const int th1 = tile_h(c->p, nst == 1 ? 0 : 1, r1);
-    const int th2 = nst == 2 ? tile_h(c->p, 2, r2) : 1;
+    (void)r1;
+    (void)r2;
+    const int th1 = c->sel[0].tile_h;
+    const int th2 = nst == 2 ? c->sel[1].tile_h : 1;
     for (int i = 0; i < n; ++i) {
         FrameRec &r = c->frames[tk[i]];
         const FrameDev &d = r.dev;
         b.f[i] = d;
-        const int64_t npx = (int64_t)d.W * d.H;
-        b.zb_pre[i + 1] = b.zb_pre[i] + ceil_div(npx, kZbWordsPerChunk);
+        b.zb_pre[i + 1] = b.zb_pre[i] + ceil_div((int64_t)d.zpitch * d.H, kZbWordsPerChunk);
         for (int s = 0; s < kMaxScans; ++s) {
             const int k = i * kMaxScans + s;
             b.pt_pre[k + 1] = b.pt_pre[k] + ceil_div(d.scans[s].count, kPtsPerChunk);
@@ -365,6 +432,48 @@ void fill_batch(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &tk) {
         b.t2_pre[i + 1] = b.t2_pre[i] + (nst == 2 ? ceil_div(d.W, 32) * ceil_div(d.H, th2) : 0);
         b.bp_pre[i + 1] = b.bp_pre[i] + (c->p.emit_points ? d.n_bp_chunks : 0);
     }
+}
+
+cudaError_t launch_filter(densify_ctx *c, int i, const BatchDev *b, cudaStream_t s) {
+    const FilterSel &f = c->sel[i];
+    const int k = i == 0 ? K_JBF1 : K_JBF2;
+    if (f.tma) return launch_jbf_tma(f.src, f.radius, b, c->sa[i], c->grid[k], s);
+    if (f.kind == 0) return launch_jbf_single(f.radius, b, c->sa[i], c->grid[k], s);
+    if (f.kind == 1) return launch_jbf_coarse(f.radius, b, c->sa[i], c->grid[k], s);
+    return launch_jbf_up(f.radius, b, c->sa[i], c->grid[k], s);
+}
+
+// Tensor maps of one frame for the TMA filter kernels of the context.
+std::string encode_maps(densify_ctx *c, FrameDev &d) {
+    d.tma = 0;
+    bool need = false;
+    for (int i = 0; i < c->p.num_stages; ++i) need |= c->sel[i].tma;
+    if (!need) return "";
+    if (!tensor_map_encoder()) return "cuTensorMapEncodeTiled is not available";
+    for (int i = 0; i < c->p.num_stages; ++i) {
+        const FilterSel &f = c->sel[i];
+        if (!f.tma) continue;
+        const TmaKernelInfo &I = f.info;
+        bool ok = true;
+        if (f.src == TMA_SRC_UP || f.src == TMA_SRC_ZBUF)
+            ok &= encode2d(&d.tm[TM_RGB], CU_TENSOR_MAP_DATA_TYPE_UINT8, d.rgb, (uint64_t)d.W * 3, d.H,
+                           (uint64_t)d.rgb_pitch, I.rgb_box[0], I.rgb_box[1]);
+        if (f.src == TMA_SRC_UP)
+            ok &= encode2d(&d.tm[TM_S1], CU_TENSOR_MAP_DATA_TYPE_UINT64, d.s1, d.Wc, d.Hc, (uint64_t)d.cpitch * 8,
+                           I.s1_box[0], I.s1_box[1]);
+        if (f.src == TMA_SRC_ZBUF)
+            ok &= encode2d(&d.tm[TM_ZBUF], CU_TENSOR_MAP_DATA_TYPE_UINT32, d.zbuf, d.W, d.H, (uint64_t)d.zpitch * 4,
+                           I.zbuf_box[0], I.zbuf_box[1]);
+        if (f.src == TMA_SRC_COARSE) {
+            ok &= encode2d(&d.tm[TM_CGUIDE], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, d.cguide, (uint64_t)d.Wc * 4, d.Hc,
+                           (uint64_t)d.cpitch * 16, I.cguide_box[0], I.cguide_box[1]);
+            ok &= encode2d(&d.tm[TM_CSSUM], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, d.cssum, d.Wc, d.Hc,
+                           (uint64_t)d.cpitch * 4, I.cssum_box[0], I.cssum_box[1]);
+        }
+        if (!ok) return "tensor map encoding failed";
+    }
+    d.tma = 1;
+    return "";
 }
 
 // The fixed kernel sequence of one batch (captured into a graph or issued directly).
@@ -386,12 +495,12 @@ densify_status issue_kernels(densify_ctx *c, Slot &sl, cudaStream_t s, bool reco
     if (nst == 2) {
         CU(launch_pool(b, c->p.pool, c->grid[K_POOL], s), "pool launch");
         CU(mark(K_POOL), "event");
-        CU(launch_jbf_coarse(c->p.stage[0].radius, b, c->sa[0], c->grid[K_JBF1], s), "stage-1 filter launch");
+        CU(launch_filter(c, 0, b, s), "stage-1 filter launch");
         CU(mark(K_JBF1), "event");
-        CU(launch_jbf_up(c->p.stage[1].radius, b, c->sa[1], c->grid[K_JBF2], s), "stage-2 filter launch");
+        CU(launch_filter(c, 1, b, s), "stage-2 filter launch");
         CU(mark(K_JBF2), "event");
     } else {
-        CU(launch_jbf_single(c->p.stage[0].radius, b, c->sa[0], c->grid[K_JBF1], s), "filter launch");
+        CU(launch_filter(c, 0, b, s), "filter launch");
         CU(mark(K_JBF1), "event");
     }
     if (c->p.emit_points) {
@@ -411,7 +520,15 @@ densify_status launch_batch(densify_ctx *c, int si) {
         c->queue.pop_front();
     }
     if (tk.empty()) return DENSIFY_OK;
-    for (uint64_t t : tk) build_frame_dev(c, c->frames[t]);
+    for (uint64_t t : tk) {
+        build_frame_dev(c, c->frames[t]);
+        const std::string e = encode_maps(c, c->frames[t].dev);
+        if (!e.empty()) {
+            c->dead = true;
+            c->err = e;
+            return DENSIFY_E_CUDA;
+        }
+    }
     fill_batch(c, sl, tk);
     const size_t bytes = offsetof(BatchDev, f) + sizeof(FrameDev) * tk.size();
     CU(cudaMemcpyAsync(sl.d, sl.h, bytes, cudaMemcpyHostToDevice, c->stream), "descriptor upload");
@@ -425,9 +542,16 @@ densify_status launch_batch(densify_ctx *c, int si) {
                                    (size_t)r.fr.scans[s].count * r.fr.scans[s].stride_bytes, cudaMemcpyHostToDevice,
                                    c->stream),
                    "points upload");
+    }
+    // RGB staging (host frames, and device frames whose base or pitch is not 16-byte aligned)
+    for (uint64_t t : tk) {
+        FrameRec &r = c->frames[t];
+        if (!r.L.rgb_pitch) continue;
         CU(cudaMemcpy2DAsync((void *)r.dev.rgb, (size_t)r.dev.rgb_pitch, r.fr.rgb, (size_t)r.fr.rgb_pitch,
-                             (size_t)r.fr.K.width * 3, (size_t)r.fr.K.height, cudaMemcpyHostToDevice, c->stream),
-           "rgb upload");
+                             (size_t)r.fr.K.width * 3, (size_t)r.fr.K.height,
+                             r.fr.memory == DENSIFY_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
+                             c->stream),
+           "rgb staging");
     }
     if (c->p.use_graphs) {
         if (!sl.exec) {
@@ -449,6 +573,16 @@ densify_status launch_batch(densify_ctx *c, int si) {
         densify_status st = issue_kernels(c, sl, c->stream, c->p.timing != 0);
         if (st != DENSIFY_OK) return st;
     }
+    // debug z-buffer out (row pitch W), both memory kinds
+    for (uint64_t t : tk) {
+        FrameRec &r = c->frames[t];
+        if (!r.fr.out_zbuf) continue;
+        CU(cudaMemcpy2DAsync(r.fr.out_zbuf, (size_t)r.fr.K.width * 4, r.dev.zbuf, (size_t)r.dev.zpitch * 4,
+                             (size_t)r.fr.K.width * 4, (size_t)r.fr.K.height,
+                             r.fr.memory == DENSIFY_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                             c->stream),
+           "zbuf copy");
+    }
     // host frames: results out (points are copied at poll time, exactly n of them)
     for (uint64_t t : tk) {
         FrameRec &r = c->frames[t];
@@ -458,8 +592,6 @@ densify_status launch_batch(densify_ctx *c, int si) {
             CU(cudaMemcpyAsync(r.fr.out_depth, r.dev.out_depth, npx * 4, cudaMemcpyDeviceToHost, c->stream), "depth copy");
         if (r.fr.out_valid)
             CU(cudaMemcpyAsync(r.fr.out_valid, r.dev.out_valid, npx, cudaMemcpyDeviceToHost, c->stream), "valid copy");
-        if (r.fr.out_zbuf)
-            CU(cudaMemcpyAsync(r.fr.out_zbuf, r.dev.zbuf, npx * 4, cudaMemcpyDeviceToHost, c->stream), "zbuf copy");
         if (c->p.num_stages == 2) {
             const size_t nc = (size_t)r.dev.Wc * r.dev.Hc;
             if (r.fr.out_coarse)
@@ -473,6 +605,7 @@ densify_status launch_batch(densify_ctx *c, int si) {
         if (c->p.emit_points)
             CU(cudaMemcpyAsync(r.fr.out_points_n, r.dev.points_n, 8, cudaMemcpyDeviceToHost, c->stream), "count copy");
     }
+    CU(cudaMemcpyAsync(sl.h_status, sl.d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream), "status copy");
     CU(cudaEventRecord(sl.done, c->stream), "event record");
     for (uint64_t t : tk) {
         FrameRec &r = c->frames[t];
@@ -485,6 +618,11 @@ densify_status launch_batch(densify_ctx *c, int si) {
 }
 
 densify_status complete_slot(densify_ctx *c, Slot &sl) {
+    if (*sl.h_status != 0) {
+        c->dead = true;
+        c->err = "a kernel's bounded wait on its tile copies gave up (status " + std::to_string(*sl.h_status) + ")";
+        return DENSIFY_E_CUDA;
+    }
     if (c->p.timing) {
         int ev = 1;
         for (int k = 0; k < K_COUNT; ++k) {
@@ -568,6 +706,8 @@ void destroy_resources(densify_ctx *c) {
             if (e) cudaEventDestroy(e);
         if (sl.d) cudaFree(sl.d);
         if (sl.h) cudaFreeHost(sl.h);
+        if (sl.d_status) cudaFree(sl.d_status);
+        if (sl.h_status) cudaFreeHost(sl.h_status);
     }
     c->slots.clear();
     if (c->arena_base) cudaFree(c->arena_base);
@@ -619,6 +759,7 @@ void densify_default_params(densify_params *p) {
     p->hbm_budget_bytes = (uint64_t)2 << 30;
     p->timing = 0;
     p->launch_policy = 0;
+    p->kernel_variant = 0;
 }
 
 uint64_t densify_frame_scratch_bytes(const densify_params *params, const densify_frame *frame) {
@@ -665,8 +806,12 @@ densify_status densify_create(const densify_params *params, int device, void *cu
     for (auto &sl : c->slots) {
         if ((e = cudaMalloc(&sl.d, sizeof(BatchDev))) != cudaSuccess ||
             (e = cudaMallocHost(&sl.h, sizeof(BatchDev))) != cudaSuccess ||
-            (e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming)) != cudaSuccess)
+            (e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming)) != cudaSuccess ||
+            (e = cudaMalloc(&sl.d_status, 256)) != cudaSuccess ||
+            (e = cudaMallocHost(&sl.h_status, sizeof(int32_t))) != cudaSuccess ||
+            (e = cudaMemset(sl.d_status, 0, 256)) != cudaSuccess)
             return bail(DENSIFY_E_CUDA, std::string("slot: ") + cudaGetErrorString(e));
+        *sl.h_status = 0;
         if (params->timing)
             for (auto &ev : sl.kev)
                 if ((e = cudaEventCreate(&ev)) != cudaSuccess)
@@ -688,11 +833,20 @@ densify_status densify_create(const densify_params *params, int device, void *cu
     c->grid[K_POOL] = sms * occupancy_pool_bp(K_POOL);
     c->grid[K_BP_COUNT] = sms * occupancy_pool_bp(K_BP_COUNT);
     c->grid[K_BP_WRITE] = sms * occupancy_pool_bp(K_BP_WRITE);
-    if (params->num_stages == 1) {
-        c->grid[K_JBF1] = sms * occupancy_jbf_single(params->stage[0].radius);
-    } else {
-        c->grid[K_JBF1] = sms * occupancy_jbf_coarse(params->stage[0].radius);
-        c->grid[K_JBF2] = sms * occupancy_jbf_up(params->stage[1].radius);
+    for (int i = 0; i < params->num_stages; ++i) {
+        const int kind = params->num_stages == 1 ? 0 : (i == 0 ? 1 : 2);
+        c->sel[i] = select_filter(*params, kind, params->stage[i].radius);
+        const FilterSel &f = c->sel[i];
+        int occ = 1;
+        if (f.tma) {
+            if ((e = jbf_tma_prepare(f.src, f.radius)) != cudaSuccess)
+                return bail(DENSIFY_E_CUDA, std::string("filter setup: ") + cudaGetErrorString(e));
+            occ = occupancy_jbf_tma(f.src, f.radius);
+        } else {
+            occ = kind == 0 ? occupancy_jbf_single(f.radius) : kind == 1 ? occupancy_jbf_coarse(f.radius)
+                                                                        : occupancy_jbf_up(f.radius);
+        }
+        c->grid[i == 0 ? K_JBF1 : K_JBF2] = sms * occ;
     }
     if ((e = cudaGetLastError()) != cudaSuccess)
         return bail(DENSIFY_E_CUDA, std::string("setup: ") + cudaGetErrorString(e));

@@ -55,7 +55,8 @@ class densify_params(C.Structure):
         ("hbm_budget_bytes", C.c_uint64),
         ("timing", C.c_int32),
         ("launch_policy", C.c_int32),
-        ("reserved", C.c_int32 * 6),
+        ("kernel_variant", C.c_int32),
+        ("reserved", C.c_int32 * 5),
     ]
 
 

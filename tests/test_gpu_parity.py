@@ -17,6 +17,7 @@ RTOL = 1e-4
 EMPTY = 0x7F800000
 QVGA_STAGES = ((4, 3.0, 20.0),)                       # 9x9 window, sigma_s 3 px, sigma_r 20
 PAPER_STAGES = ((4, 5.0, 20.0), (2, 5.0, 20.0))       # r=4 at 1/3, r=2 at full (Sec. 5)
+VARIANTS = [0, 1]                                     # TMA-staged filter kernels, plain kernels
 
 
 @pytest.fixture(scope="module")
@@ -81,28 +82,31 @@ def check_points(g, o, cam):
 
 
 # ---------------------------------------------------------------------------
-def test_qvga_single_stage(torch_cuda):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_qvga_single_stage(torch_cuda, variant):
     v = scene.make_workload("qvga_1scan", 1000)
-    g = run_gpu([v], 1, QVGA_STAGES, torch_cuda)[0]
+    g = run_gpu([v], 1, QVGA_STAGES, torch_cuda, kernel_variant=variant)[0]
     o = run_oracle(v, 1, QVGA_STAGES)
     compare(g, o, 1, "qvga")
     check_points(g, o, v.camera)
     assert o["valid"].mean() > 0.2
 
 
-def test_1080p_three_scans_two_stage(torch_cuda):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_1080p_three_scans_two_stage(torch_cuda, variant):
     v = scene.make_workload("1080p_3scan", 1001)
-    g = run_gpu([v], 2, PAPER_STAGES, torch_cuda)[0]
+    g = run_gpu([v], 2, PAPER_STAGES, torch_cuda, kernel_variant=variant)[0]
     o = run_oracle(v, 2, PAPER_STAGES)
     compare(g, o, 2, "1080p two-stage")
     check_points(g, o, v.camera)
     assert o["in_image"] > 30000
 
 
-def test_1080p_single_stage_15x15(torch_cuda):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_1080p_single_stage_15x15(torch_cuda, variant):
     v = scene.make_workload("1080p_3scan", 1002)
     st = ((7, 5.0, 20.0),)
-    g = run_gpu([v], 1, st, torch_cuda)[0]
+    g = run_gpu([v], 1, st, torch_cuda, kernel_variant=variant)[0]
     o = run_oracle(v, 1, st)
     compare(g, o, 1, "1080p 15x15")
     check_points(g, o, v.camera)
@@ -115,8 +119,9 @@ def test_stage2_override_reading(torch_cuda):
     compare(g, o, 2, "override")
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("res", [(1281, 721), (33, 17), (97, 250), (1, 1)])
-def test_ragged_sizes(torch_cuda, res):
+def test_ragged_sizes(torch_cuda, res, variant):
     W, H = res
     rng = np.random.default_rng(W * 7 + H)
     sc = scene.make_scene(5, "room")
@@ -128,8 +133,8 @@ def test_ragged_sizes(torch_cuda, res):
         pose = scene.make_lidar_pose(cam, (0.1 * s, 0.05, 0.02), 2.0 * s)
         scans.append(scene.Scan(scene.lidar_sweep(sc, pose, 48, 700 + s, rng), pose))
     v = scene.View(cam, rgb, scans, gt)
-    for stages, st in ((2, PAPER_STAGES), (1, ((3, 2.0, 15.0),))):
-        g = run_gpu([v], stages, st, torch_cuda)[0]
+    for stages, st in ((2, PAPER_STAGES), (1, ((3, 2.0, 15.0),)), (1, ((4, 3.0, 20.0),)), (1, ((2, 1.5, 10.0),))):
+        g = run_gpu([v], stages, st, torch_cuda, kernel_variant=variant)[0]
         o = run_oracle(v, stages, st)
         compare(g, o, stages, f"{W}x{H} {stages}-stage")
 
@@ -166,13 +171,26 @@ def test_points_capacity_short(torch_cuda):
     assert np.array_equal(g["rgba"][:100], o["rgba"][:100])
 
 
-def test_batched_equals_alone(torch_cuda):
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_batched_equals_alone(torch_cuda, variant):
     """Uneven views in one launch give the same bits as each view alone."""
     views = [scene.make_batch_view(500, res, i, 6) for i, res in enumerate(["540p", "720p", "qvga", "540p"])]
-    alone = [run_gpu([v], 2, PAPER_STAGES, torch_cuda)[0] for v in views]
-    mixed = run_gpu(views, 2, PAPER_STAGES, torch_cuda, max_batch=8)
+    alone = [run_gpu([v], 2, PAPER_STAGES, torch_cuda, kernel_variant=variant)[0] for v in views]
+    mixed = run_gpu(views, 2, PAPER_STAGES, torch_cuda, max_batch=8, kernel_variant=variant)
     for a, b in zip(alone, mixed):
         for k in ("zbuf", "valid", "depth", "coarse", "coarse_valid", "xyz", "rgba"):
             assert np.array_equal(a[k], b[k]), k
     o = run_oracle(views[1], 2, PAPER_STAGES)
     compare(mixed[1], o, 2, "batched 720p")
+
+
+def test_variants_agree_bit_for_bit(torch_cuda):
+    """The TMA-staged and the plain filter kernels evaluate the same sums in the
+    same order: identical outputs."""
+    v = scene.make_view(31, res="540p", scene_kind="room", n_scans=3, beams=64, az_steps=1024)
+    a = run_gpu([v], 2, PAPER_STAGES, torch_cuda, kernel_variant=0)[0]
+    b = run_gpu([v], 2, PAPER_STAGES, torch_cuda, kernel_variant=1)[0]
+    for k in ("valid", "coarse_valid", "zbuf"):
+        assert np.array_equal(a[k], b[k]), k
+    np.testing.assert_allclose(a["depth"], b["depth"], rtol=2e-6)
+    np.testing.assert_allclose(a["coarse"], b["coarse"], rtol=2e-6)
