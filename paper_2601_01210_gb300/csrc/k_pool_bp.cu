@@ -52,18 +52,25 @@ cudaError_t launch_pool(const BatchDev *b, int pool, int grid, cudaStream_t s) {
 
 // ---------------------------------------------------------------------------
 // back-projection with deterministic compaction.
-// A chunk is 4096 consecutive pixels in row-major order; warp w of the block
-// owns pixels [512 w, 512 w + 512) of it, 128 per step, 4 per lane.
-// bp_count writes each chunk's valid count; bp_write sums the counts of the
-// preceding chunks of its frame, scans inside the chunk and writes
+// A chunk is 4096 consecutive pixels in row-major order. bp_count writes each
+// chunk's number of valid pixels. In bp_write, warp w of the block owns pixels
+// [512 w, 512 w + 512) of the chunk in 4 steps of 128 (4 per lane): the warp's
+// output offset is the sum of the frame's earlier chunks plus the earlier
+// warps of the chunk; inside a step an inclusive warp scan of the lanes'
+// counts places every point. Points are built in shared memory and leave in
+// coalesced 16-byte stores. Each point is
 //   (x, y, z) = cam_to_world * ((u + 1/2 - cx) Z / fx, (v + 1/2 - cy) Z / fy, Z)
 // with the pixel colour packed r | g << 8 | b << 16 | 255 << 24.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t valid4(const uint8_t *valid, int64_t p, int64_t n) {
+__device__ __forceinline__ uint32_t valid_bits4(const uint8_t *v, int64_t p, int64_t n, bool vec) {
+    if (vec && p + 4 <= n) {
+        const uint32_t w = *reinterpret_cast<const uint32_t *>(v + p);   // bytes are 0 or 1
+        return (w & 1u) | ((w >> 7) & 2u) | ((w >> 14) & 4u) | ((w >> 21) & 8u);
+    }
     uint32_t m = 0;
 #pragma unroll
     for (int k = 0; k < 4; ++k)
-        if (p + k < n && valid[p + k]) m |= 1u << k;
+        if (p + k < n && v[p + k]) m |= 1u << k;
     return m;
 }
 
@@ -77,10 +84,14 @@ __global__ void __launch_bounds__(kThreads) bp_count_kernel(const BatchDev *__re
         const FrameDev &F = B->f[fi];
         const int c = item - B->bp_pre[fi];
         const int64_t n = (int64_t)F.W * F.H;
-        const int64_t base = (int64_t)c * kBpChunk + warp * 512;
+        const int64_t p = (int64_t)c * kBpChunk + threadIdx.x * 16;
         uint32_t cnt = 0;
-#pragma unroll
-        for (int it = 0; it < 4; ++it) cnt += __popc(valid4(F.out_valid, base + it * 128 + lane * 4, n));
+        if ((((uintptr_t)F.out_valid) & 15u) == 0 && p + 16 <= n) {
+            const uint4 w = *reinterpret_cast<const uint4 *>(F.out_valid + p);
+            cnt = __popc(w.x) + __popc(w.y) + __popc(w.z) + __popc(w.w);
+        } else {
+            for (int k = 0; k < 16; ++k) cnt += (p + k < n && F.out_valid[p + k]) ? 1u : 0u;
+        }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
         __syncthreads();
@@ -95,9 +106,9 @@ __global__ void __launch_bounds__(kThreads) bp_count_kernel(const BatchDev *__re
 }
 
 __global__ void __launch_bounds__(kThreads) bp_write_kernel(const BatchDev *__restrict__ B) {
-    __shared__ uint32_t wsum[kThreads / 32];
+    __shared__ float4 stage[kThreads / 32][128];
+    __shared__ uint32_t wtot[kThreads / 32];
     __shared__ int64_t red[kThreads / 32];
-    __shared__ int64_t chunk_base;
     const int nf = B->n_frames;
     const int total = B->bp_pre[nf];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -105,42 +116,46 @@ __global__ void __launch_bounds__(kThreads) bp_write_kernel(const BatchDev *__re
         const int fi = find_segment(B->bp_pre, nf, item);
         const FrameDev &F = B->f[fi];
         const int c = item - B->bp_pre[fi];
-        const int64_t n = (int64_t)F.W * F.H;
-        // exclusive prefix over the frame's earlier chunks
+        const int W = F.W;
+        const int64_t n = (int64_t)W * F.H;
+        const bool vvalid = (((uintptr_t)F.out_valid) & 3u) == 0;
+        const bool vdepth = (((uintptr_t)F.out_depth) & 15u) == 0;
+        const bool rows4 = (W & 3) == 0 && (F.rgb_pitch & 3) == 0 && (((uintptr_t)F.rgb) & 3u) == 0;
+        // exclusive prefix over the frame's earlier chunks (this thread's share)
         int64_t part = 0;
         for (int k = threadIdx.x; k < c; k += kThreads) part += F.chunk_cnt[k];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-        __syncthreads();
-        if (lane == 0) red[warp] = part;
-        // per-warp counts of this chunk
-        const int64_t base = (int64_t)c * kBpChunk + warp * 512;
+        const int64_t wbase = (int64_t)c * kBpChunk + warp * 512;
         uint32_t m[4], wc = 0;
 #pragma unroll
         for (int it = 0; it < 4; ++it) {
-            m[it] = valid4(F.out_valid, base + it * 128 + lane * 4, n);
+            m[it] = valid_bits4(F.out_valid, wbase + it * 128 + lane * 4, n, vvalid);
             wc += __popc(m[it]);
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) wc += __shfl_xor_sync(0xffffffffu, wc, o);
-        if (lane == 0) wsum[warp] = wc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            int64_t t = 0;
-            for (int w = 0; w < kThreads / 32; ++w) t += red[w];
-            chunk_base = t;
-            int64_t all = 0;
-            for (int w = 0; w < kThreads / 32; ++w) all += wsum[w];
-            if (c == F.n_bp_chunks - 1) *F.points_n = t + all;
+        __syncthreads();   // the previous chunk is done with red / wtot
+        if (lane == 0) {
+            red[warp] = part;
+            wtot[warp] = wc;
         }
         __syncthreads();
-        int64_t off = chunk_base;
-        for (int w = 0; w < warp; ++w) off += wsum[w];
+        int64_t off = 0, all = 0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            off += red[w];
+            all += wtot[w];
+        }
+        const int64_t chunk_base = off;
+        for (int w = 0; w < warp; ++w) off += wtot[w];
+        if (threadIdx.x == 0 && c == F.n_bp_chunks - 1) *F.points_n = chunk_base + all;
+
         const float *c2w = F.c2w32;
         const float r00 = c2w[0], r01 = c2w[1], r02 = c2w[2], t0 = c2w[3];
         const float r10 = c2w[4], r11 = c2w[5], r12 = c2w[6], t1 = c2w[7];
         const float r20 = c2w[8], r21 = c2w[9], r22 = c2w[10], t2 = c2w[11];
         const float ifx = 1.0f / F.fx, ify = 1.0f / F.fy;
+        float4 *st = stage[warp];
 #pragma unroll
         for (int it = 0; it < 4; ++it) {
             const uint32_t cnt = __popc(m[it]);
@@ -150,27 +165,65 @@ __global__ void __launch_bounds__(kThreads) bp_write_kernel(const BatchDev *__re
                 const uint32_t v = __shfl_up_sync(0xffffffffu, incl, o);
                 if (lane >= o) incl += v;
             }
-            int64_t pos = off + (incl - cnt);
-            const int64_t p0 = base + it * 128 + lane * 4;
+            const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
+            if (m[it]) {
+                const int64_t p0 = wbase + it * 128 + lane * 4;
+                float z[4];
+                if (vdepth && p0 + 4 <= n) {
+                    const float4 d4 = *reinterpret_cast<const float4 *>(F.out_depth + p0);
+                    z[0] = d4.x; z[1] = d4.y; z[2] = d4.z; z[3] = d4.w;
+                } else {
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (m[it] & (1u << k)) {
-                    const int64_t p = p0 + k;
-                    const int y = (int)(p / F.W), x = (int)(p - (int64_t)y * F.W);
-                    const float Z = F.out_depth[p];
-                    const float X = ((float)x + 0.5f - F.cx) * Z * ifx;
-                    const float Y = ((float)y + 0.5f - F.cy) * Z * ify;
-                    const uint8_t *col = F.rgb + (int64_t)y * F.rgb_pitch + 3 * x;
-                    const uint32_t rgba = (uint32_t)col[0] | ((uint32_t)col[1] << 8) | ((uint32_t)col[2] << 16) | 0xFF000000u;
-                    if (pos < F.points_cap)
-                        F.out_points[pos] = make_float4(fmaf(r00, X, fmaf(r01, Y, fmaf(r02, Z, t0))),
-                                                        fmaf(r10, X, fmaf(r11, Y, fmaf(r12, Z, t1))),
-                                                        fmaf(r20, X, fmaf(r21, Y, fmaf(r22, Z, t2))),
-                                                        __uint_as_float(rgba));
-                    ++pos;
+                    for (int k = 0; k < 4; ++k) z[k] = (m[it] >> k & 1u) ? F.out_depth[p0 + k] : 0.0f;
+                }
+                uint32_t j = incl - cnt;
+                if (rows4) {
+                    // the 4 pixels share a row and their 12 colour bytes are word aligned
+                    const int y = (int)(p0 / W), x0 = (int)(p0 - (int64_t)y * W);
+                    const uint32_t *cw = reinterpret_cast<const uint32_t *>(F.rgb + (int64_t)y * F.rgb_pitch + 3 * x0);
+                    const uint32_t w0 = cw[0], w1 = cw[1], w2 = cw[2];
+                    const uint32_t col[4] = {w0 & 0xFFFFFFu, (w0 >> 24) | ((w1 & 0xFFFFu) << 8),
+                                             (w1 >> 16) | ((w2 & 0xFFu) << 16), w2 >> 8};
+                    const float Y = ((float)y + 0.5f - F.cy) * ify;
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (m[it] >> k & 1u) {
+                            const float Z = z[k];
+                            const float X = ((float)(x0 + k) + 0.5f - F.cx) * Z * ifx;
+                            const float Yz = Y * Z;
+                            st[j++] = make_float4(fmaf(r00, X, fmaf(r01, Yz, fmaf(r02, Z, t0))),
+                                                  fmaf(r10, X, fmaf(r11, Yz, fmaf(r12, Z, t1))),
+                                                  fmaf(r20, X, fmaf(r21, Yz, fmaf(r22, Z, t2))),
+                                                  __uint_as_float(col[k] | 0xFF000000u));
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        if (m[it] >> k & 1u) {
+                            const int64_t p = p0 + k;
+                            const int y = (int)(p / W), x = (int)(p - (int64_t)y * W);
+                            const uint8_t *cb = F.rgb + (int64_t)y * F.rgb_pitch + 3 * x;
+                            const uint32_t rgba = (uint32_t)cb[0] | ((uint32_t)cb[1] << 8) | ((uint32_t)cb[2] << 16) |
+                                                  0xFF000000u;
+                            const float Z = z[k];
+                            const float X = ((float)x + 0.5f - F.cx) * Z * ifx;
+                            const float Yz = ((float)y + 0.5f - F.cy) * ify * Z;
+                            st[j++] = make_float4(fmaf(r00, X, fmaf(r01, Yz, fmaf(r02, Z, t0))),
+                                                  fmaf(r10, X, fmaf(r11, Yz, fmaf(r12, Z, t1))),
+                                                  fmaf(r20, X, fmaf(r21, Yz, fmaf(r22, Z, t2))),
+                                                  __uint_as_float(rgba));
+                        }
+                    }
                 }
             }
-            off += __shfl_sync(0xffffffffu, incl, 31);
+            __syncwarp();
+            for (uint32_t i = lane; i < tot; i += 32) {
+                const int64_t pos = off + i;
+                if (pos < F.points_cap) F.out_points[pos] = st[i];
+            }
+            __syncwarp();
+            off += tot;
         }
     }
 }
