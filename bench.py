@@ -54,6 +54,9 @@ def parse():
     ap.add_argument("--no-clocks", action="store_true", help="skip the clock-sampling window (profiling runs)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-frames", type=int, default=4, help="frames in the oracle's timed sample")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="duration of the paper-rate serving run (16 viewpoints x 30 fps)")
     return ap.parse_args()
 
 
@@ -68,16 +71,78 @@ def _gen(args):
     return v
 
 
-def make_views(n, seed0):
+def _gen_mixed(args):
+    import scene
+    seed, res, idx, n = args
+    return scene.make_batch_view(seed, res, idx, n)
+
+
+def make_mixed_views(n, seed0):
+    """Serving viewpoints: mixed 1080p / 720p / 540p, 1-3 sweeps of 64-128 x 512-2048."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    res = ["1080p", "720p", "540p"]
+    jobs = [(seed0, res[i % 3], i, n) for i in range(n)]
+    with cf.ProcessPoolExecutor(max(1, min(n, (os.cpu_count() or 2) - 1, 12)),
+                                mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_gen_mixed, jobs))
+
+
+def serve_measure(views, dev, stream, seconds, precision):
+    """Frames/s and p50/p99 latency of the serving loop: single-frame launches
+    against continuous batching, at the paper's load (16 viewpoints x 30 fps,
+    Poisson-jittered) and at a saturating load."""
+    from paper_2601_01210_gb300 import Densifier
+    from paper_2601_01210_gb300.frames import FrameBuffers
+    from paper_2601_01210_gb300.serve import ServeLoop, poisson_arrivals
+    ring = [[FrameBuffers(v.camera, v.rgb, [(s.xyz, s.lidar_to_world) for s in v.scans], device=dev)
+             for _ in range(3)] for v in views]
+    frames = [[b.frame for b in r] for r in ring]
+    modes = {
+        "single_frame_fp32": dict(max_batch=1, batches_in_flight=1, precision=0),
+        "batched": dict(max_batch=16, batches_in_flight=2, precision=precision),
+    }
+    loads = {"paper_rate_30fps": (30.0, seconds), "saturating_1000fps": (1000.0, 2.0)}
+    out = {}
+    for mname, extra in modes.items():
+        params = dict(num_stages=2, stages=STAGES, max_inflight=32, launch_policy=0,
+                      hbm_budget_bytes=4 << 30, **extra)
+        with Densifier(params, device=dev.index, stream=stream.cuda_stream) as d:
+            # warm-up (graph capture, first-touch)
+            ServeLoop(d, frames).run(poisson_arrivals(len(views), 200.0, 0.1, seed=9), 0.1)
+            for lname, (fps, dur) in loads.items():
+                arr = poisson_arrivals(len(views), fps, dur, seed=11)
+                st = ServeLoop(d, frames).run(arr, dur, drain_s=10.0)
+                out[f"{mname}/{lname}"] = st.summary()
+    return out
+
+
+def make_views(n, seed0, rank=0):
     """Distinct 1080p three-scan viewpoints, generated in a spawn pool."""
     import concurrent.futures as cf
     import multiprocessing as mp
-    jobs = [(seed0 + i, i % 7, 7) for i in range(n)]
+    jobs = [(s, i % 7, 7) for i, s in enumerate(rank_seeds(rank, n, seed0))]
     workers = max(1, min(n, (os.cpu_count() or 2) - 1, 12))
     if workers == 1:
         return [_gen(j) for j in jobs]
     with cf.ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
         return list(ex.map(_gen, jobs))
+
+
+# ---------------------------------------------------------------------------
+# replicas: viewpoints are independent, each rank densifies its own views
+# ---------------------------------------------------------------------------
+def rank_seeds(rank, n_views, base=1001):
+    """Seeds of the distinct views rank ``rank`` generates (disjoint across ranks)."""
+    return [base + 1000 * rank + i for i in range(n_views)]
+
+
+def job_throughput(step_ms_local, frames_per_step, world, reduce_max):
+    """Whole-job frames/s: all ranks' frames over the slowest rank's summed step time.
+    ``reduce_max`` maps a local float to the max over ranks (identity at N=1)."""
+    total_ms = reduce_max(float(sum(step_ms_local)))
+    steps = len(step_ms_local)
+    return world * frames_per_step * steps / (total_ms / 1000.0), total_ms
 
 
 # ---------------------------------------------------------------------------
@@ -159,7 +224,7 @@ def cpu_oracle_rate(views, frames):
 def reference_arm(a, rank, world):
     if rank != 0:
         return
-    views = make_views(max(1, min(a.views, a.cpu_frames)), 1001)
+    views = make_views(max(1, min(a.views, a.cpu_frames)), 1001, 0)
     import oracle
     oracle.build()
     for _ in range(min(a.warmup, 1)):
@@ -209,7 +274,8 @@ def ours_arm(a, rank, world, local_rank):
     from paper_2601_01210_gb300.densify import DENSIFY_MEM_HOST
     from paper_2601_01210_gb300.frames import FrameBuffers
 
-    views = make_views(a.views, 1001 + 1000 * rank)   # before any CUDA call (spawn pool)
+    views = make_views(a.views, 1001, rank)   # before any CUDA call (spawn pool)
+    mixed_views = make_mixed_views(16, 4004) if (not a.no_serve and rank == 0) else None
     build.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -282,14 +348,17 @@ def ours_arm(a, rank, world, local_rank):
         torch.cuda.synchronize()
         ck = clocks.stop() if not a.no_clocks else {"skipped": "--no-clocks"}
         step_ms = [s.elapsed_time(e) for s, e in ev]
-        total_ms = sum(step_ms)
         n_launch = sum(n for _, n in times.values())
         gpu_launches = n_launch
-        total_t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        if world > 1:
-            torch.distributed.all_reduce(total_t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(total_t.item())
-        value = world * B * a.steps / (total_ms / 1000.0)
+
+        def reduce_max(x):
+            if world == 1:
+                return x
+            t = torch.tensor([x], dtype=torch.float64, device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            return float(t.item())
+
+        value, total_ms = job_throughput(step_ms, B, world, reduce_max)
 
         # e2e: host buffers through the C ABI
         e2e = None
@@ -309,6 +378,9 @@ def ours_arm(a, rank, world, local_rank):
             d2h = sum(b.W * b.H * 5 + 8 + b.n_points() * 16 for b in hb)
             e2e = {"value": B * a.steps / dt * world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                    "d2h_bytes_per_step": int(d2h)}
+        serving = None
+        if not a.no_serve and rank == 0:
+            serving = serve_measure(mixed_views, dev, stream, a.serve_seconds, 0)
     if rank != 0:
         return
     peaks = {}
@@ -352,6 +424,9 @@ def ours_arm(a, rank, world, local_rank):
         "gpu_launches": gpu_launches,
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "serving": serving and {"viewpoints": "16 (1080p/720p/540p mixed, 1-3 sweeps each)",
+                                "note": "frames/s and latency from submit-arrival to completion seen by the loop",
+                                **serving},
     }
     print(json.dumps(out), flush=True)
 
