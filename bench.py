@@ -253,6 +253,24 @@ def reference_arm(a, rank, world):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
+def profiled_traffic(kernel):
+    """DRAM bytes per launch recorded in profiles/traffic.json for ``kernel``,
+    or None if the kernel's sources changed since that capture."""
+    import hashlib
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+    except Exception:
+        return None
+    for path, digest in rec["sources"].items():
+        try:
+            h = hashlib.sha256(open(os.path.join(ROOT, path), "rb").read()).hexdigest()[:16]
+        except OSError:
+            return None
+        if h != digest:
+            return None
+    return rec["dram_bytes_per_launch"]
+
+
 def valid_taps_stage2(coarse_valid, W, H, pool=3, r=2):
     """(output pixel, observed tap) pairs of the full-resolution filter."""
     import numpy as np
@@ -416,7 +434,8 @@ def ours_arm(a, rank, world, local_rank):
         "latency_ms_per_step": {"p50": sorted_ms[len(sorted_ms) // 2],
                                 "p99": sorted_ms[min(len(sorted_ms) - 1, int(0.99 * len(sorted_ms)))]},
         "roofline": {"kernel": "jbf_stage2", "bound": "alu", "achieved": achieved, "peak": peak_gtap,
-                     "unit": "Gtap/s", "frac": achieved / peak_gtap if peak_gtap else None, "traffic": None,
+                     "unit": "Gtap/s", "frac": achieved / peak_gtap if peak_gtap else None,
+                     "traffic": profiled_traffic("jbf_stage2"), "traffic_unit": "bytes per launch (ncu capture)",
                      "peak_basis": f"{sms} SMs x 128 lanes / 10 instructions per tap x {sm_max:.0f} MHz",
                      "taps_per_launch": taps2, "avg_launch_us": avg_us},
         "kernels": ktable,
