@@ -256,6 +256,35 @@ DENSIFY_API int32_t densify_kernel_times(densify_ctx *ctx, const char **names, d
 /* Zero the accumulated kernel times. */
 DENSIFY_API void densify_reset_kernel_times(densify_ctx *ctx);
 
+/* Densify one frame without allocating any device memory. (The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc, for example a
+ * real-time loop whose device-memory footprint is frozen after start-up, or a
+ * plug-in hosted by an application whose allocator owns the GPU's memory.)
+ *
+ * Runs the same steps as a context (calibration, projection, the filter stages
+ * of *params, back-projection) on `cuda_stream` (a cudaStream_t, NULL: the
+ * default stream) and returns once the work is enqueued; the results are in
+ * the frame's output buffers when the stream reaches that point. Every frame
+ * pointer must be a device pointer (memory = DENSIFY_MEM_DEVICE); out_depth
+ * and out_valid are required; out_points / out_points_n as for a context when
+ * params->emit_points is set; out_zbuf, out_coarse, out_coarse_valid optional.
+ * The filter runs in the plain shared-memory kernels (no TMA staging).
+ *
+ * Scratch (descriptor, z-buffer, pooled maps, first-stage result, compaction
+ * counts) is one fixed 16 MiB array in device memory that every GPU loading
+ * the library holds until the process exits: one 1920x1080 two-stage frame
+ * fits; a frame needing more returns DENSIFY_E_INVALID with the byte count.
+ * Every call reuses the same array and leaves its contents behind: all of it
+ * is rewritten or cleared before it is read, but calls whose work overlaps on
+ * the GPU (two streams, or two host threads) race on it; serialise them.
+ * The first call on a device looks up the array's device address and the SM
+ * count (once per device, with that device current); make that first call
+ * before any stream capture. No cudaMalloc, cudaFree or other allocating call
+ * is made. Errors: E_INVALID (bad argument or too large), E_CUDA (a launch
+ * failed); the message is in densify_last_error(NULL). */
+DENSIFY_API densify_status densify_frame_noalloc(const densify_params *params, const densify_frame *frame,
+                                                 void *cuda_stream);
+
 /* ABI version of the loaded library (DENSIFY_ABI_VERSION). */
 DENSIFY_API int32_t densify_abi_version(void);
 

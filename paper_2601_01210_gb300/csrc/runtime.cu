@@ -31,6 +31,7 @@
 
 #include "../../include/densify.h"
 #include "desc.cuh"
+#include "runtime_internal.h"
 #include "tma_info.h"
 
 using namespace dz;
@@ -972,3 +973,15 @@ void densify_reset_kernel_times(densify_ctx *c) {
 }
 
 }  // extern "C"
+
+namespace dz {
+
+void fill_stage_args(StageArgs &a, const densify_stage &st, int pool, int override_sparse) {
+    fill_stage(a, st, pool, override_sparse);
+}
+
+std::string check_params(const densify_params &p) { return validate_params(p); }
+
+void set_thread_error(const std::string &m) { g_create_error = m; }
+
+}  // namespace dz

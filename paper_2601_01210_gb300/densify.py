@@ -107,6 +107,7 @@ _SIGS = {
     "densify_kernel_times": ([C.c_void_p, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.POINTER(C.c_int64),
                               C.c_int32], C.c_int32),
     "densify_reset_kernel_times": ([C.c_void_p], None),
+    "densify_frame_noalloc": ([C.POINTER(densify_params), C.POINTER(densify_frame), C.c_void_p], C.c_int),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -196,6 +197,12 @@ def densify_kernel_times(ctx, cap: int = 16):
 
 def densify_reset_kernel_times(ctx) -> None:
     lib().densify_reset_kernel_times(ctx)
+
+
+def densify_frame_noalloc(params: densify_params, frame: densify_frame, stream: int | None = None) -> int:
+    """Enqueue one frame on ``stream`` using the library's fixed device scratch
+    (no allocation); returns the status."""
+    return lib().densify_frame_noalloc(C.byref(params), C.byref(frame), C.c_void_p(stream or 0))
 
 
 # ---------------------------------------------------------------------------
