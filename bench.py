@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-frames", type=int, default=4, help="frames in the oracle's timed sample")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
+    ap.add_argument("--no-fp16", action="store_true", help="skip the FP16-form measurement")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="duration of the paper-rate serving run (16 viewpoints x 30 fps)")
     return ap.parse_args()
@@ -100,7 +101,8 @@ def serve_measure(views, dev, stream, seconds, precision):
     frames = [[b.frame for b in r] for r in ring]
     modes = {
         "single_frame_fp32": dict(max_batch=1, batches_in_flight=1, precision=0),
-        "batched": dict(max_batch=16, batches_in_flight=2, precision=precision),
+        "batched_fp16" if precision else "batched_fp32": dict(max_batch=16, batches_in_flight=2,
+                                                              precision=precision),
     }
     loads = {"paper_rate_30fps": (30.0, seconds), "saturating_1000fps": (1000.0, 2.0)}
     out = {}
@@ -115,6 +117,42 @@ def serve_measure(views, dev, stream, seconds, precision):
                 st = ServeLoop(d, frames).run(arr, dur, drain_s=10.0)
                 out[f"{mname}/{lname}"] = st.summary()
     return out
+
+
+def fp16_measure(a, bufs, params, dev, stream, flush_buf, taps2):
+    """The same batches in the FP16 form (FP16 guide and weights in the
+    full-resolution stage, FP32 sums): device frames/s and the stage-2 kernel."""
+    import torch
+    from paper_2601_01210_gb300 import Densifier
+    p = dict(params, precision=1)
+    B = len(bufs)
+    with Densifier(p, device=dev.index, stream=stream.cuda_stream) as d:
+        def step(k, ev):
+            ts = [d.submit(b.frame) for b in bufs]
+            flush_buf.fill_(k)
+            if ev:
+                ev[0].record(stream)
+            d.flush(-1)
+            if ev:
+                ev[1].record(stream)
+            for t in ts:
+                d.poll(t, -1)
+
+        for k in range(max(3, a.warmup)):
+            step(k, None)
+        torch.cuda.synchronize()
+        d.reset_kernel_times()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+        for k in range(a.steps):
+            step(k, evs[k])
+        torch.cuda.synchronize()
+        ms = sum(s.elapsed_time(e) for s, e in evs)
+        kt = d.kernel_times()
+    s2 = kt.get("jbf_stage2", (0.0, 1))
+    avg = s2[0] / max(1, s2[1])
+    return {"value": B * a.steps / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms / a.steps,
+            "jbf_stage2_avg_us": avg, "jbf_stage2_gtap_s": taps2 / (avg * 1e-6) / 1e9 if avg > 0 else None,
+            "kernels": {k: round(v[0] / max(1, v[1]), 3) for k, v in kt.items()}}
 
 
 def make_views(n, seed0, rank=0):
@@ -398,7 +436,10 @@ def ours_arm(a, rank, world, local_rank):
                    "d2h_bytes_per_step": int(d2h)}
         serving = None
         if not a.no_serve and rank == 0:
-            serving = serve_measure(mixed_views, dev, stream, a.serve_seconds, 0)
+            serving = serve_measure(mixed_views, dev, stream, a.serve_seconds, 1)
+    fp16 = None
+    if not a.no_fp16:
+        fp16 = fp16_measure(a, bufs, params, dev, stream, flush_buf, taps2)
     if rank != 0:
         return
     peaks = {}
@@ -443,6 +484,7 @@ def ours_arm(a, rank, world, local_rank):
         "gpu_launches": gpu_launches,
         "e2e": e2e,
         "cpu_baseline": cpu,
+        "fp16": fp16 and {"precision": "full-resolution stage: FP16 guide and weights, FP32 sums", **fp16},
         "serving": serving and {"viewpoints": "16 (1080p/720p/540p mixed, 1-3 sweeps each)",
                                 "note": "frames/s and latency from submit-arrival to completion seen by the loop",
                                 **serving},

@@ -72,7 +72,8 @@ typedef enum densify_status {
 
 typedef enum densify_precision {
     DENSIFY_FP32 = 0,         /* FP32 guide, weights and accumulation */
-    DENSIFY_FP16 = 1          /* FP16 guide and weights, FP32 accumulation */
+    DENSIFY_FP16 = 1          /* full-resolution filter stage: FP16 guide and weights, FP32
+                                 numerator and weight sum (the pooled first stage stays FP32) */
 } densify_precision;
 
 typedef enum densify_memory {
@@ -125,6 +126,11 @@ typedef struct densify_stage {
  *                 single stage), the plain shared-memory kernels elsewhere.
  *                 1: the plain kernels everywhere (same results, for
  *                 comparison).
+ *   autotune      1: on the first batch, time every kernel that can run each
+ *                 filter stage (TMA-staged at each instantiated tile height,
+ *                 and the plain kernel) on that batch and keep the fastest for
+ *                 the context's lifetime; with DENSIFY_TUNE_CACHE=<file> in the
+ *                 environment, choices are stored there and reused.
  */
 typedef struct densify_params {
     int32_t num_stages;
@@ -141,7 +147,8 @@ typedef struct densify_params {
     int32_t timing;
     int32_t launch_policy;
     int32_t kernel_variant;
-    int32_t reserved[5];
+    int32_t autotune;
+    int32_t reserved[4];
 } densify_params;
 
 /* Pinhole intrinsics of the camera (Sec. 2: calibrated in advance). */
@@ -255,6 +262,12 @@ DENSIFY_API int32_t densify_kernel_times(densify_ctx *ctx, const char **names, d
 
 /* Zero the accumulated kernel times. */
 DENSIFY_API void densify_reset_kernel_times(densify_ctx *ctx);
+
+/* JSON text describing the filter kernels the context runs: per filter stage the
+ * chosen kernel (TMA-staged or plain, rows per thread, tile, grid) and, after
+ * autotuning, every candidate's measured time. Writes at most cap bytes
+ * (NUL-terminated); returns the length of the full text. */
+DENSIFY_API int32_t densify_describe(densify_ctx *ctx, char *buf, int32_t cap);
 
 /* Densify one frame without allocating any device memory. (The paper has no
  * counterpart: this serves callers that cannot call cudaMalloc, for example a

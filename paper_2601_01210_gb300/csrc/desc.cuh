@@ -92,6 +92,11 @@ struct StageArgs {
     int32_t pool;            // restore factor of the second stage
     int32_t override_sparse; // second stage: LiDAR depths replace the restored value
     float sp[(2 * kMaxR + 1) * (2 * kMaxR + 1)];   // -(dx^2 + dy^2) kp, row-major over (dy, dx)
+    // FP16 form (pairs of vertically adjacent output pixels, see jbf_tma.cuh):
+    uint32_t kc2;            // half2 bits of (-kc, -kc)
+    // half2 bits of (sp[d][dx], sp[d-1][dx]) for d = 0 .. 2R+1, row-major over (d, dx);
+    // a term outside 0..2R is -inf (its weight is 0)
+    uint32_t sp2[(2 * kMaxR + 2) * (2 * kMaxR + 1)];
 };
 
 // Largest i with pre[i] <= item (pre is non-decreasing, pre[0] = 0).

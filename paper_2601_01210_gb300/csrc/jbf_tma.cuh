@@ -24,7 +24,22 @@
 // (about 2 s); the CTA then sets bit 0 of the batch status word, waits (again
 // bounded) for its own copies in flight and leaves. The host reports the
 // status as a CUDA error of the batch.
+//
+// FP16 form (HALF = true; second stage and single stage): the staged neighbour
+// keeps its colour as three half2 (r, r), (g, g), (b, b) and its depth as
+// float. Each thread pairs output rows (2j, 2j+1) of its column: one staged
+// neighbour at row iy is tap (iy - 2j, dx) of the first pixel and tap
+// (iy - 2j - 1, dx) of the second, so colour difference, squared distance,
+// exponent and ex2 run once in half2 for both; the spatial term of a half whose
+// row offset falls outside the window is -inf (weight exactly 0). The weights
+// are widened to FP32 and the numerator and weight sum accumulate in FP32.
+// Unobserved neighbours carry the half colour 65504: the squared difference
+// overflows to +inf and the weight is exactly 0. Pixels whose weight sum is
+// below 2^-6 (dominant weight in the half subnormal range) are recomputed in
+// FP32 with shifted exponents.
 #pragma once
+
+#include <cuda_fp16.h>
 
 #include "jbf_core.cuh"
 
@@ -165,15 +180,67 @@ __device__ __noinline__ float jbf_tma_shifted(const float4 *q4, const float *cs,
     return nn / dd;
 }
 
-template <int SRC, int R, int KP>
+// FP16 staged record -> FP32 colour and depth (sentinel colour: unobserved).
+__device__ __forceinline__ bool half_record(const uint4 &q, float &r, float &g, float &b, float &d) {
+    r = __low2float(*reinterpret_cast<const __half2 *>(&q.x));
+    g = __low2float(*reinterpret_cast<const __half2 *>(&q.y));
+    b = __low2float(*reinterpret_cast<const __half2 *>(&q.z));
+    d = __uint_as_float(q.w);
+    return r < 65000.0f;
+}
+
+// FP32 shifted recomputation of one pixel of the FP16 form.
+template <int R, int SW>
+__device__ __noinline__ float jbf_tma_shifted_h(const uint4 *q4, int row0, int col0, float cr, float cg, float cb,
+                                                float kc, float kp) {
+    constexpr int T = 2 * R + 1;
+    float amax = -__int_as_float(0x7F800000);
+    for (int dy = 0; dy < T; ++dy)
+        for (int dx = 0; dx < T; ++dx) {
+            float r, g, b, d;
+            if (half_record(q4[(row0 + dy) * SW + col0 + dx], r, g, b, d)) {
+                const float dr = r - cr, dg = g - cg, db = b - cb;
+                const float n2 = fmaf(dr, dr, fmaf(dg, dg, db * db));
+                const float s2 = (float)((dx - R) * (dx - R) + (dy - R) * (dy - R));
+                amax = fmaxf(amax, fmaf(n2, -kc, -s2 * kp));
+            }
+        }
+    float nn = 0.0f, dd = 0.0f;
+    for (int dy = 0; dy < T; ++dy)
+        for (int dx = 0; dx < T; ++dx) {
+            float r, g, b, d;
+            if (half_record(q4[(row0 + dy) * SW + col0 + dx], r, g, b, d)) {
+                const float dr = r - cr, dg = g - cg, db = b - cb;
+                const float n2 = fmaf(dr, dr, fmaf(dg, dg, db * db));
+                const float s2 = (float)((dx - R) * (dx - R) + (dy - R) * (dy - R));
+                const float w = ex2_approx(fmaf(n2, -kc, -s2 * kp) - amax);
+                nn = fmaf(w, d, nn);
+                dd += w;
+            }
+        }
+    return nn / dd;
+}
+
+__device__ __forceinline__ __half2 h2bits(uint32_t u) { return *reinterpret_cast<const __half2 *>(&u); }
+__device__ __forceinline__ uint32_t h2u(__half2 h) { return *reinterpret_cast<const uint32_t *>(&h); }
+
+__device__ __forceinline__ __half2 h2exp2_approx(__half2 x) {
+    uint32_t y;
+    asm("ex2.approx.f16x2 %0, %1;" : "=r"(y) : "r"(h2u(x)));
+    return h2bits(y);
+}
+
+template <int SRC, int R, int KP, bool HALF = false>
 __global__ void __launch_bounds__(256, 2) jbf_tma_kernel(const BatchDev *__restrict__ B, const StageArgs a) {
     using G = TmaGeom<SRC, R, KP>;
     constexpr int TW = G::TW, TH = G::TH, SW = G::SW, SH = G::SH, T = 2 * R + 1;
+    static_assert(!HALF || (SRC != SRC_COARSE && KP % 2 == 0), "FP16 form: full-resolution stages, row pairs");
     extern __shared__ __align__(128) uint8_t smem[];
     // raw buffer b: A part at smem + b * (RAW_A + RAW_B), B part right after it
     auto rawA = [&](int b) { return smem + G::OFF_RAW + b * (G::RAW_A + G::RAW_B); };
     auto rawB = [&](int b) { return smem + G::OFF_RAW + b * (G::RAW_A + G::RAW_B) + G::RAW_A; };
     float4 *staged = reinterpret_cast<float4 *>(smem + G::OFF_STAGED);
+    uint4 *staged_h = reinterpret_cast<uint4 *>(smem + G::OFF_STAGED);   // FP16 records, same 16 bytes
     uint8_t *obs = smem + G::OFF_OBS;
     uint8_t *hor = smem + G::OFF_HOR;
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + G::OFF_BAR);
@@ -281,7 +348,13 @@ __global__ void __launch_bounds__(256, 2) jbf_tma_kernel(const BatchDev *__restr
                     }
                     if (o) v = make_float4((float)p[0], (float)p[1], (float)p[2], d);
                 }
-                staged[i] = v;
+                if (HALF) {
+                    const float rr = o ? v.x : 65504.0f;
+                    staged_h[i] = make_uint4(h2u(__float2half2_rn(rr)), h2u(__float2half2_rn(v.y)),
+                                             h2u(__float2half2_rn(v.z)), __float_as_uint(v.w));
+                } else {
+                    staged[i] = v;
+                }
                 obs[i] = o;
             }
             __syncthreads();
@@ -313,7 +386,7 @@ __global__ void __launch_bounds__(256, 2) jbf_tma_kernel(const BatchDev *__restr
             if (SRC == SRC_COARSE) {
                 const float4 c = cg[(rbase + k + R) * SW + lane + R];
                 cr[k] = c.x; cgr[k] = c.y; cb[k] = c.z;
-            } else {
+            } else if (!HALF) {
                 const uint8_t *p = rgbraw + (rbase + k + R) * G::RGB_BX + 3 * lane + G::RGB_LEAD;
                 cr[k] = (float)p[0]; cgr[k] = (float)p[1]; cb[k] = (float)p[2];
             }
@@ -325,7 +398,42 @@ __global__ void __launch_bounds__(256, 2) jbf_tma_kernel(const BatchDev *__restr
             val[k] = v;
             any_val |= v;
         }
-        if (__any_sync(0xffffffffu, any_val)) {
+        if (HALF && __any_sync(0xffffffffu, any_val)) {
+            // centre colours of row pairs (2j, 2j+1) as half2
+            __half2 cr2[KP / 2], cg2[KP / 2], cb2[KP / 2];
+#pragma unroll
+            for (int j = 0; j < KP / 2; ++j) {
+                const uint8_t *p0 = rgbraw + (rbase + 2 * j + R) * G::RGB_BX + 3 * lane + G::RGB_LEAD;
+                const uint8_t *p1 = p0 + G::RGB_BX;
+                cr2[j] = __floats2half2_rn((float)p0[0], (float)p1[0]);
+                cg2[j] = __floats2half2_rn((float)p0[1], (float)p1[1]);
+                cb2[j] = __floats2half2_rn((float)p0[2], (float)p1[2]);
+            }
+            const __half2 kc2 = h2bits(a.kc2);
+#pragma unroll
+            for (int iy = 0; iy < KP + 2 * R; ++iy) {
+#pragma unroll
+                for (int dx = 0; dx < T; ++dx) {
+                    const uint4 q = staged_h[(rbase + iy) * SW + lane + dx];
+                    const __half2 qr = h2bits(q.x), qg = h2bits(q.y), qb = h2bits(q.z);
+                    const float qd = __uint_as_float(q.w);
+#pragma unroll
+                    for (int j = 0; j < KP / 2; ++j) {
+                        const int d = iy - 2 * j;   // row offset of the pair's first pixel
+                        if (d >= 0 && d <= T) {
+                            const __half2 dr = __hsub2(qr, cr2[j]), dg = __hsub2(qg, cg2[j]), db = __hsub2(qb, cb2[j]);
+                            const __half2 n2 = __hfma2(dr, dr, __hfma2(dg, dg, __hmul2(db, db)));
+                            const __half2 w2 = h2exp2_approx(__hfma2(n2, kc2, h2bits(a.sp2[d * (2 * kMaxR + 1) + dx])));
+                            const float2 w = __half22float2(w2);
+                            num[2 * j] = fmaf(w.x, qd, num[2 * j]);
+                            den[2 * j] += w.x;
+                            num[2 * j + 1] = fmaf(w.y, qd, num[2 * j + 1]);
+                            den[2 * j + 1] += w.y;
+                        }
+                    }
+                }
+            }
+        } else if (!HALF && __any_sync(0xffffffffu, any_val)) {
             const float kc = a.kc;
 #pragma unroll
             for (int iy = 0; iy < KP + 2 * R; ++iy) {
@@ -364,8 +472,12 @@ __global__ void __launch_bounds__(256, 2) jbf_tma_kernel(const BatchDev *__restr
             const int y = y0 + rbase + k;
             float out = 0.0f;
             if (val[k]) {
-                if (den[k] >= 0x1p-60f) {
+                if (den[k] >= (HALF ? 0x1p-6f : 0x1p-60f)) {
                     out = num[k] / den[k];
+                } else if (HALF) {
+                    const uint8_t *p = rgbraw + (rbase + k + R) * G::RGB_BX + 3 * lane + G::RGB_LEAD;
+                    out = jbf_tma_shifted_h<R, SW>(staged_h, rbase + k, lane, (float)p[0], (float)p[1], (float)p[2],
+                                                   a.kc, a.kp);
                 } else {
                     out = jbf_tma_shifted<SRC, R, SW, G::S_BX, G::S_LEAD>(
                         SRC == SRC_COARSE ? cg : staged, cs, rbase + k, lane, cr[k], cgr[k], cb[k], a.kc, a.kp);

@@ -22,74 +22,86 @@ void fill_info(TmaKernelInfo *o) {
     o->cssum_box[0] = G::S_BX; o->cssum_box[1] = G::S_BY;
 }
 
-template <int SRC, int R, int KP>
+template <int SRC, int R, int KP, bool H>
 cudaError_t prep() {
-    return cudaFuncSetAttribute(jbf_tma_kernel<SRC, R, KP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    return cudaFuncSetAttribute(jbf_tma_kernel<SRC, R, KP, H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 TmaGeom<SRC, R, KP>::SMEM);
 }
 
-template <int SRC, int R, int KP>
+template <int SRC, int R, int KP, bool H>
 cudaError_t go(const BatchDev *b, const StageArgs &a, int grid, cudaStream_t s) {
-    jbf_tma_kernel<SRC, R, KP><<<grid, 256, TmaGeom<SRC, R, KP>::SMEM, s>>>(b, a);
+    jbf_tma_kernel<SRC, R, KP, H><<<grid, 256, TmaGeom<SRC, R, KP>::SMEM, s>>>(b, a);
     return cudaGetLastError();
 }
 
-template <int SRC, int R, int KP>
+template <int SRC, int R, int KP, bool H>
 int occ() {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, jbf_tma_kernel<SRC, R, KP>, 256, TmaGeom<SRC, R, KP>::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, jbf_tma_kernel<SRC, R, KP, H>, 256, TmaGeom<SRC, R, KP>::SMEM);
     return n > 0 ? n : 1;
 }
 
-// (source, radius) -> rows per thread; 0: no TMA variant
-constexpr int kp_of(int src, int r) {
-    return src == SRC_UP ? (r == 1 || r == 2 ? 8 : r == 3 ? 4 : 0)
-         : src == SRC_COARSE ? (r == 2 || r == 4 ? 4 : 0)
-         : src == SRC_ZBUF ? (r == 2 || r == 4 ? 8 : r == 7 ? 4 : 0)
-         : 0;
-}
-
+// (source, radius, rows per thread, FP16 form)
 #define DZ_TMA_CASES(X)           \
-    X(SRC_UP, 1, 8)               \
-    X(SRC_UP, 2, 8)               \
-    X(SRC_UP, 3, 4)               \
-    X(SRC_COARSE, 2, 4)           \
-    X(SRC_COARSE, 4, 4)           \
-    X(SRC_ZBUF, 2, 8)             \
-    X(SRC_ZBUF, 4, 8)             \
-    X(SRC_ZBUF, 7, 4)
+    X(SRC_UP, 1, 8, false)        \
+    X(SRC_UP, 2, 8, false)        \
+    X(SRC_UP, 2, 4, false)        \
+    X(SRC_UP, 3, 4, false)        \
+    X(SRC_COARSE, 2, 4, false)    \
+    X(SRC_COARSE, 4, 4, false)    \
+    X(SRC_COARSE, 4, 2, false)    \
+    X(SRC_ZBUF, 2, 8, false)      \
+    X(SRC_ZBUF, 4, 8, false)      \
+    X(SRC_ZBUF, 4, 4, false)      \
+    X(SRC_ZBUF, 7, 4, false)      \
+    X(SRC_UP, 1, 8, true)         \
+    X(SRC_UP, 2, 8, true)         \
+    X(SRC_UP, 2, 4, true)         \
+    X(SRC_UP, 3, 4, true)         \
+    X(SRC_ZBUF, 2, 8, true)       \
+    X(SRC_ZBUF, 4, 8, true)       \
+    X(SRC_ZBUF, 4, 4, true)       \
+    X(SRC_ZBUF, 7, 4, true)
 
 }  // namespace
 
-bool jbf_tma_info(int src, int r, TmaKernelInfo *out) {
+int jbf_tma_variants(int src, int r, bool half, int *kps, int cap) {
+    int n = 0;
+#define X(S, RR, K, H) if (src == S && r == RR && half == H && n < cap) kps[n++] = K;
+    DZ_TMA_CASES(X)
+#undef X
+    return n;
+}
+
+bool jbf_tma_info(int src, int r, int kp, bool half, TmaKernelInfo *out) {
     *out = TmaKernelInfo{};
-#define X(S, RR, K) if (src == S && r == RR) { fill_info<S, RR, K>(out); return true; }
+#define X(S, RR, K, H) if (src == S && r == RR && kp == K && half == H) { fill_info<S, RR, K>(out); return true; }
     DZ_TMA_CASES(X)
 #undef X
     return false;
 }
 
-cudaError_t jbf_tma_prepare(int src, int r) {
-#define X(S, RR, K) if (src == S && r == RR) return prep<S, RR, K>();
+cudaError_t jbf_tma_prepare(int src, int r, int kp, bool half) {
+#define X(S, RR, K, H) if (src == S && r == RR && kp == K && half == H) return prep<S, RR, K, H>();
     DZ_TMA_CASES(X)
 #undef X
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_jbf_tma(int src, int r, const BatchDev *b, const StageArgs &a, int grid, cudaStream_t s) {
-#define X(S, RR, K) if (src == S && r == RR) return go<S, RR, K>(b, a, grid, s);
+cudaError_t launch_jbf_tma(int src, int r, int kp, bool half, const BatchDev *b, const StageArgs &a, int grid,
+                           cudaStream_t s) {
+#define X(S, RR, K, H) if (src == S && r == RR && kp == K && half == H) return go<S, RR, K, H>(b, a, grid, s);
     DZ_TMA_CASES(X)
 #undef X
     return cudaErrorInvalidValue;
 }
 
-int occupancy_jbf_tma(int src, int r) {
-#define X(S, RR, K) if (src == S && r == RR) return occ<S, RR, K>();
+int occupancy_jbf_tma(int src, int r, int kp, bool half) {
+#define X(S, RR, K, H) if (src == S && r == RR && kp == K && half == H) return occ<S, RR, K, H>();
     DZ_TMA_CASES(X)
 #undef X
     return 1;
 }
 
-static_assert(kp_of(SRC_UP, 2) == 8, "paper second stage has a TMA variant");
 
 }  // namespace dz

@@ -27,6 +27,7 @@
 #include <thread>
 #include <vector>
 
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 #include "../../include/densify.h"
@@ -129,9 +130,13 @@ struct FilterSel {
     int kind = 0;        // 0 single, 1 coarse, 2 restored full resolution
     int radius = 0;
     bool tma = false;
+    bool half = false;   // FP16 form
     int src = 0;         // TMA source kind
+    int kp = 0;          // output rows per thread (tile height / 8)
     int tile_h = 0;
+    int occ = 1;         // resident CTAs per SM
     TmaKernelInfo info{};
+    float tuned_us = -1.0f;   // measured by the autotuner (-1: not tuned)
 };
 
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -185,6 +190,9 @@ struct densify_ctx {
     int admitted = 0;
     int grid[K_COUNT] = {};
     FilterSel sel[2];                    // first (or only) and second filter
+    std::vector<FilterSel> cands[2];     // kernels able to run each filter stage
+    int sms = 0;
+    bool tuned = true;                   // false until the autotuner ran (params.autotune)
     std::string err;
     bool dead = false;
     double t_us[K_COUNT] = {};
@@ -231,21 +239,40 @@ bool stage_supported(int kind, int r) {
     return r <= kMaxR;
 }
 
-FilterSel select_filter(const densify_params &p, int kind, int r) {
-    FilterSel s;
-    s.kind = kind;
-    s.radius = r;
+// Kernels that can run one filter stage: the TMA-staged kernel at each
+// instantiated tile height (rows per thread), then the plain kernel. The first
+// entry is the default; the autotuner times them all on the first batch.
+std::vector<FilterSel> filter_candidates(const densify_params &p, int kind, int r) {
+    std::vector<FilterSel> out;
     const int src = kind == 0 ? TMA_SRC_ZBUF : kind == 1 ? TMA_SRC_COARSE : TMA_SRC_UP;
     const bool allowed = p.kernel_variant == 0 && (kind != 2 || (p.pool == 3 && p.stage2_input == 0));
-    if (allowed && jbf_tma_info(src, r, &s.info)) {
-        s.tma = true;
-        s.src = src;
-        s.tile_h = s.info.tile_h;
-    } else {
-        const int kp = kind == 0 ? kp_jbf_single(r) : kind == 1 ? kp_jbf_coarse(r) : kp_jbf_up(r);
-        s.tile_h = 8 * kp;
+    // FP16: the full-resolution stage (the pooled first stage stays FP32)
+    const bool half = p.precision == DENSIFY_FP16 && kind != 1;
+    if (allowed) {
+        int kps[8];
+        const int n = jbf_tma_variants(src, r, half, kps, 8);
+        for (int i = 0; i < n; ++i) {
+            FilterSel s;
+            s.kind = kind;
+            s.radius = r;
+            s.tma = true;
+            s.half = half;
+            s.src = src;
+            s.kp = kps[i];
+            jbf_tma_info(src, r, kps[i], half, &s.info);
+            s.tile_h = s.info.tile_h;
+            out.push_back(s);
+        }
     }
-    return s;
+    if (!half) {
+        FilterSel s;
+        s.kind = kind;
+        s.radius = r;
+        s.kp = kind == 0 ? kp_jbf_single(r) : kind == 1 ? kp_jbf_coarse(r) : kp_jbf_up(r);
+        s.tile_h = 8 * s.kp;
+        out.push_back(s);
+    }
+    return out;
 }
 
 void fill_stage(StageArgs &a, const densify_stage &st, int pool, int override_sparse) {
@@ -260,6 +287,22 @@ void fill_stage(StageArgs &a, const densify_stage &st, int pool, int override_sp
             const double d2 = (double)((dx - R) * (dx - R) + (dy - R) * (dy - R));
             a.sp[dy * (2 * kMaxR + 1) + dx] = (float)(-d2 * log2e / (2.0 * (double)st.sigma_p * (double)st.sigma_p));
         }
+    // FP16 form: (-kc, -kc) and per row offset d of a pixel pair (sp[d][dx], sp[d-1][dx]), -inf outside 0..2R
+    auto h2 = [](float lo, float hi) {
+        const __half2 v = __floats2half2_rn(lo, hi);
+        uint32_t u;
+        std::memcpy(&u, &v, 4);
+        return u;
+    };
+    const float ninf = -INFINITY;
+    a.kc2 = h2(-a.kc, -a.kc);
+    const int T = 2 * R + 1;
+    for (int d = 0; d < 2 * kMaxR + 2; ++d)
+        for (int dx = 0; dx < 2 * kMaxR + 1; ++dx) {
+            const float first = (d < T && dx < T) ? a.sp[d * (2 * kMaxR + 1) + dx] : ninf;
+            const float second = (d >= 1 && d - 1 < T && dx < T) ? a.sp[(d - 1) * (2 * kMaxR + 1) + dx] : ninf;
+            a.sp2[d * (2 * kMaxR + 1) + dx] = h2(first, second);
+        }
 }
 
 std::string validate_params(const densify_params &p) {
@@ -272,13 +315,24 @@ std::string validate_params(const densify_params &p) {
             return "sigmas must be positive and finite";
     }
     if (p.num_stages == 2 && (p.pool < 1 || p.pool > 8)) return "pool must be in 1..8";
-    if (p.precision != DENSIFY_FP32) return "only DENSIFY_FP32 is built in this library";
+    if (p.precision != DENSIFY_FP32 && p.precision != DENSIFY_FP16) return "precision must be FP32 or FP16";
+    if (p.precision == DENSIFY_FP16) {
+        if (p.kernel_variant != 0) return "the FP16 form runs in the TMA kernels (kernel_variant 0)";
+        const int full = p.num_stages == 2 ? 1 : 0;   // the full-resolution stage
+        const int kind = p.num_stages == 2 ? 2 : 0;
+        int kps[8];
+        if (jbf_tma_variants(kind == 2 ? TMA_SRC_UP : TMA_SRC_ZBUF, p.stage[full].radius, true, kps, 8) == 0 ||
+            (kind == 2 && (p.pool != 3 || p.stage2_input != 0)))
+            return "FP16 form available for the full-resolution stage with radius 1-3 (pool 3, stage2_input 0) "
+                   "after a first stage, or radius 2, 4, 7 as the only stage";
+    }
     if (p.max_inflight < 1) return "max_inflight must be >= 1";
     if (p.max_batch < 1 || p.max_batch > kMaxBatch) return "max_batch must be in 1..64";
     if (p.batches_in_flight < 1 || p.batches_in_flight > 8) return "batches_in_flight must be in 1..8";
     if (p.hbm_budget_bytes < (1u << 20)) return "hbm_budget_bytes must be >= 1 MiB";
     if (p.launch_policy != 0 && p.launch_policy != 1) return "launch_policy must be 0 or 1";
     if (p.kernel_variant != 0 && p.kernel_variant != 1) return "kernel_variant must be 0 or 1";
+    if (p.autotune != 0 && p.autotune != 1) return "autotune must be 0 or 1";
     return "";
 }
 
@@ -435,10 +489,129 @@ void fill_batch(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &tk) {
     }
 }
 
+void set_filter(densify_ctx *c, int i, const FilterSel &f) {
+    c->sel[i] = f;
+    c->grid[i == 0 ? K_JBF1 : K_JBF2] = c->sms * f.occ;
+}
+
+cudaError_t launch_filter(densify_ctx *c, int i, const BatchDev *b, cudaStream_t s);
+void fill_batch(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &tk);
+std::string encode_maps(densify_ctx *c, FrameDev &d);
+
+// Autotuner: on the context's first batch, time every candidate kernel of each
+// filter stage (3 launches after one warm-up, CUDA events) on that batch's real
+// inputs and keep the fastest; stage 2 is tuned after stage 1's choice is made.
+// Choices are remembered per (stage kind, radius, precision, batch pixel class)
+// in the file named by DENSIFY_TUNE_CACHE, when set, and reused from it.
+std::string tune_key(const densify_ctx *c, int i, int64_t px) {
+    int cls = 0;
+    while ((int64_t(1) << (cls + 1)) <= px) ++cls;
+    const FilterSel &f = c->cands[i][0];
+    return "kind=" + std::to_string(f.kind) + ",r=" + std::to_string(f.radius) + ",half=" + std::to_string(f.half) +
+           ",px=2^" + std::to_string(cls);
+}
+
+bool cache_lookup(const std::string &key, std::string *val) {
+    const char *path = std::getenv("DENSIFY_TUNE_CACHE");
+    if (!path) return false;
+    FILE *fp = std::fopen(path, "r");
+    if (!fp) return false;
+    char line[512];
+    bool found = false;
+    while (std::fgets(line, sizeof line, fp)) {
+        std::string l(line);
+        while (!l.empty() && (l.back() == '\n' || l.back() == '\r')) l.pop_back();
+        const size_t sp = l.find(' ');
+        if (sp != std::string::npos && l.substr(0, sp) == key) {
+            *val = l.substr(sp + 1);
+            found = true;
+        }
+    }
+    std::fclose(fp);
+    return found;
+}
+
+void cache_store(const std::string &key, const std::string &val) {
+    const char *path = std::getenv("DENSIFY_TUNE_CACHE");
+    if (!path) return;
+    if (FILE *fp = std::fopen(path, "a")) {
+        std::fprintf(fp, "%s %s\n", key.c_str(), val.c_str());
+        std::fclose(fp);
+    }
+}
+
+std::string cand_name(const FilterSel &f) { return std::string(f.tma ? "tma" : "plain") + ":kp" + std::to_string(f.kp); }
+
+densify_status autotune(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &tk) {
+    int64_t px = 0;
+    for (uint64_t t : tk) px += (int64_t)c->frames[t].dev.W * c->frames[t].dev.H;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CU(cudaEventCreate(&e0), "tuner event");
+    CU(cudaEventCreate(&e1), "tuner event");
+    densify_status st = DENSIFY_OK;
+    for (int i = 0; i < c->p.num_stages && st == DENSIFY_OK; ++i) {
+        const std::string key = tune_key(c, i, px);
+        std::string cached;
+        int best = 0;
+        float best_us = -1.0f;
+        bool from_cache = false;
+        if (cache_lookup(key, &cached)) {
+            for (size_t j = 0; j < c->cands[i].size(); ++j)
+                if (cand_name(c->cands[i][j]) == cached) { best = (int)j; from_cache = true; }
+        }
+        if (!from_cache && c->cands[i].size() > 1) {
+            for (size_t j = 0; j < c->cands[i].size() && st == DENSIFY_OK; ++j) {
+                set_filter(c, i, c->cands[i][j]);
+                for (uint64_t t : tk) {   // tensor-map boxes follow the candidate's tile
+                    build_frame_dev(c, c->frames[t]);
+                    const std::string me = encode_maps(c, c->frames[t].dev);
+                    if (!me.empty()) {
+                        c->dead = true;
+                        c->err = me;
+                        st = DENSIFY_E_CUDA;
+                    }
+                }
+                if (st != DENSIFY_OK) break;
+                fill_batch(c, sl, tk);
+                const size_t bytes = offsetof(BatchDev, f) + sizeof(FrameDev) * tk.size();
+                cudaError_t e = cudaMemcpyAsync(sl.d, sl.h, bytes, cudaMemcpyHostToDevice, c->stream);
+                // inputs of this stage
+                if (e == cudaSuccess) e = launch_prep(sl.d, c->grid[K_PREP], c->stream);
+                if (e == cudaSuccess) e = launch_project(sl.d, c->grid[K_PROJECT], c->stream);
+                if (e == cudaSuccess && c->p.num_stages == 2) e = launch_pool(sl.d, c->p.pool, c->grid[K_POOL], c->stream);
+                if (e == cudaSuccess && i == 1) e = launch_filter(c, 0, sl.d, c->stream);
+                if (e == cudaSuccess) e = launch_filter(c, i, sl.d, c->stream);   // warm-up
+                if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
+                for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) e = launch_filter(c, i, sl.d, c->stream);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.0f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) {
+                    st = cuda_fail(c, e, "autotune");
+                    break;
+                }
+                const float us = 1000.0f * ms / 3.0f;
+                c->cands[i][j].tuned_us = us;
+                if (best_us < 0.0f || us < best_us) {
+                    best_us = us;
+                    best = (int)j;
+                }
+            }
+            if (st == DENSIFY_OK) cache_store(key, cand_name(c->cands[i][best]));
+        }
+        set_filter(c, i, c->cands[i][best]);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->tuned = true;
+    return st;
+}
+
 cudaError_t launch_filter(densify_ctx *c, int i, const BatchDev *b, cudaStream_t s) {
     const FilterSel &f = c->sel[i];
     const int k = i == 0 ? K_JBF1 : K_JBF2;
-    if (f.tma) return launch_jbf_tma(f.src, f.radius, b, c->sa[i], c->grid[k], s);
+    if (f.tma) return launch_jbf_tma(f.src, f.radius, f.kp, f.half, b, c->sa[i], c->grid[k], s);
     if (f.kind == 0) return launch_jbf_single(f.radius, b, c->sa[i], c->grid[k], s);
     if (f.kind == 1) return launch_jbf_coarse(f.radius, b, c->sa[i], c->grid[k], s);
     return launch_jbf_up(f.radius, b, c->sa[i], c->grid[k], s);
@@ -521,6 +694,10 @@ densify_status launch_batch(densify_ctx *c, int si) {
         c->queue.pop_front();
     }
     if (tk.empty()) return DENSIFY_OK;
+    if (!c->tuned) {   // first batch: pick the filter kernels
+        densify_status st = autotune(c, sl, tk);
+        if (st != DENSIFY_OK) return st;
+    }
     for (uint64_t t : tk) {
         build_frame_dev(c, c->frames[t]);
         const std::string e = encode_maps(c, c->frames[t].dev);
@@ -761,6 +938,7 @@ void densify_default_params(densify_params *p) {
     p->timing = 0;
     p->launch_policy = 0;
     p->kernel_variant = 0;
+    p->autotune = 0;
 }
 
 uint64_t densify_frame_scratch_bytes(const densify_params *params, const densify_frame *frame) {
@@ -834,21 +1012,24 @@ densify_status densify_create(const densify_params *params, int device, void *cu
     c->grid[K_POOL] = sms * occupancy_pool_bp(K_POOL);
     c->grid[K_BP_COUNT] = sms * occupancy_pool_bp(K_BP_COUNT);
     c->grid[K_BP_WRITE] = sms * occupancy_pool_bp(K_BP_WRITE);
+    c->sms = sms;
     for (int i = 0; i < params->num_stages; ++i) {
         const int kind = params->num_stages == 1 ? 0 : (i == 0 ? 1 : 2);
-        c->sel[i] = select_filter(*params, kind, params->stage[i].radius);
-        const FilterSel &f = c->sel[i];
-        int occ = 1;
-        if (f.tma) {
-            if ((e = jbf_tma_prepare(f.src, f.radius)) != cudaSuccess)
-                return bail(DENSIFY_E_CUDA, std::string("filter setup: ") + cudaGetErrorString(e));
-            occ = occupancy_jbf_tma(f.src, f.radius);
-        } else {
-            occ = kind == 0 ? occupancy_jbf_single(f.radius) : kind == 1 ? occupancy_jbf_coarse(f.radius)
-                                                                        : occupancy_jbf_up(f.radius);
+        c->cands[i] = filter_candidates(*params, kind, params->stage[i].radius);
+        if (c->cands[i].empty()) return bail(DENSIFY_E_INVALID, "no kernel for filter stage " + std::to_string(i));
+        for (FilterSel &f : c->cands[i]) {
+            if (f.tma) {
+                if ((e = jbf_tma_prepare(f.src, f.radius, f.kp, f.half)) != cudaSuccess)
+                    return bail(DENSIFY_E_CUDA, std::string("filter setup: ") + cudaGetErrorString(e));
+                f.occ = occupancy_jbf_tma(f.src, f.radius, f.kp, f.half);
+            } else {
+                f.occ = kind == 0 ? occupancy_jbf_single(f.radius) : kind == 1 ? occupancy_jbf_coarse(f.radius)
+                                                                              : occupancy_jbf_up(f.radius);
+            }
         }
-        c->grid[i == 0 ? K_JBF1 : K_JBF2] = sms * occ;
+        set_filter(c, i, c->cands[i][0]);
     }
+    c->tuned = !params->autotune;
     if ((e = cudaGetLastError()) != cudaSuccess)
         return bail(DENSIFY_E_CUDA, std::string("setup: ") + cudaGetErrorString(e));
     *out = c;
@@ -962,6 +1143,40 @@ int32_t densify_kernel_times(densify_ctx *c, const char **names, double *total_u
         ++n;
     }
     return n;
+}
+
+int32_t densify_describe(densify_ctx *c, char *buf, int32_t cap) {
+    if (!c) return 0;
+    auto one = [&](const FilterSel &f) {
+        char tmp[256];
+        std::snprintf(tmp, sizeof tmp,
+                      "{\"kernel\": \"%s\", \"kp\": %d, \"tile\": [32, %d], \"fp16\": %s, \"ctas_per_sm\": %d%s",
+                      f.tma ? "tma" : "plain", f.kp, f.tile_h, f.half ? "true" : "false", f.occ,
+                      f.tuned_us >= 0.0f ? "" : "}");
+        std::string s(tmp);
+        if (f.tuned_us >= 0.0f) {
+            std::snprintf(tmp, sizeof tmp, ", \"tuned_us\": %.3f}", f.tuned_us);
+            s += tmp;
+        }
+        return s;
+    };
+    std::string out = "{\"tuned\": " + std::string(c->tuned && c->p.autotune ? "true" : "false") + ", \"stages\": [";
+    for (int i = 0; i < c->p.num_stages; ++i) {
+        if (i) out += ", ";
+        out += "{\"chosen\": " + one(c->sel[i]) + ", \"candidates\": [";
+        for (size_t j = 0; j < c->cands[i].size(); ++j) {
+            if (j) out += ", ";
+            out += one(c->cands[i][j]);
+        }
+        out += "]}";
+    }
+    out += "]}";
+    if (buf && cap > 0) {
+        const size_t n = std::min<size_t>(out.size(), (size_t)cap - 1);
+        std::memcpy(buf, out.data(), n);
+        buf[n] = 0;
+    }
+    return (int32_t)out.size();
 }
 
 void densify_reset_kernel_times(densify_ctx *c) {

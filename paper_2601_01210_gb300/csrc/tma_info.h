@@ -21,9 +21,13 @@ struct TmaKernelInfo {
     int cssum_box[2];
 };
 
-bool jbf_tma_info(int src, int r, TmaKernelInfo *out);
-cudaError_t jbf_tma_prepare(int src, int r);
-cudaError_t launch_jbf_tma(int src, int r, const BatchDev *b, const StageArgs &a, int grid, cudaStream_t s);
-int occupancy_jbf_tma(int src, int r);
+// Instantiated variants: (source, radius, rows per thread kp, FP16 form). half: guide and
+// weights in FP16 with FP32 sums (full-resolution stages only).
+int jbf_tma_variants(int src, int r, bool half, int *kps, int cap);   // available kp values
+bool jbf_tma_info(int src, int r, int kp, bool half, TmaKernelInfo *out);
+cudaError_t jbf_tma_prepare(int src, int r, int kp, bool half);
+cudaError_t launch_jbf_tma(int src, int r, int kp, bool half, const BatchDev *b, const StageArgs &a, int grid,
+                           cudaStream_t s);
+int occupancy_jbf_tma(int src, int r, int kp, bool half);
 
 }  // namespace dz

@@ -56,7 +56,8 @@ class densify_params(C.Structure):
         ("timing", C.c_int32),
         ("launch_policy", C.c_int32),
         ("kernel_variant", C.c_int32),
-        ("reserved", C.c_int32 * 5),
+        ("autotune", C.c_int32),
+        ("reserved", C.c_int32 * 4),
     ]
 
 
@@ -107,6 +108,7 @@ _SIGS = {
     "densify_kernel_times": ([C.c_void_p, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.POINTER(C.c_int64),
                               C.c_int32], C.c_int32),
     "densify_reset_kernel_times": ([C.c_void_p], None),
+    "densify_describe": ([C.c_void_p, C.c_char_p, C.c_int32], C.c_int32),
     "densify_frame_noalloc": ([C.POINTER(densify_params), C.POINTER(densify_frame), C.c_void_p], C.c_int),
 }
 EXPORTED = tuple(_SIGS)
@@ -197,6 +199,14 @@ def densify_kernel_times(ctx, cap: int = 16):
 
 def densify_reset_kernel_times(ctx) -> None:
     lib().densify_reset_kernel_times(ctx)
+
+
+def densify_describe(ctx) -> str:
+    """The context's filter-kernel choices (JSON text)."""
+    n = lib().densify_describe(ctx, None, 0)
+    buf = C.create_string_buffer(n + 1)
+    lib().densify_describe(ctx, buf, n + 1)
+    return buf.value.decode()
 
 
 def densify_frame_noalloc(params: densify_params, frame: densify_frame, stream: int | None = None) -> int:
@@ -296,6 +306,10 @@ class Densifier:
 
     def kernel_times(self):
         return densify_kernel_times(self.ctx)
+
+    def describe(self):
+        import json
+        return json.loads(densify_describe(self.ctx))
 
     def reset_kernel_times(self):
         densify_reset_kernel_times(self.ctx)

@@ -1,0 +1,76 @@
+"""FP16 form against the FP64 oracle.
+
+The full-resolution filter stage keeps its RGB guide and weights in FP16 and
+accumulates the numerator and weight sum in FP32; projection, pooling and the
+first stage are FP32 as in the FP32 form. Bar: z-buffer and every validity
+mask bit-exact (integer decisions); depth within 1 mm absolute or 1e-3
+relative of the oracle at every valid pixel. The error statistics (max abs,
+p99 abs, max rel) are printed for the record.
+"""
+import numpy as np
+import pytest
+
+import scene
+
+pytestmark = pytest.mark.gpu
+
+PAPER_STAGES = ((4, 5.0, 20.0), (2, 5.0, 20.0))
+
+
+def _run(v, stages, precision, torch):
+    from paper_2601_01210_gb300 import Densifier, build
+    from paper_2601_01210_gb300.frames import FrameBuffers
+    build.build()
+    with Densifier(dict(num_stages=len(stages), stages=stages, precision=precision, launch_policy=1)) as d:
+        b = FrameBuffers(v.camera, v.rgb, [(s.xyz, s.lidar_to_world) for s in v.scans], debug=True,
+                         num_stages=len(stages))
+        assert d.poll(d.submit(b.frame), -1) == 0
+        torch.cuda.synchronize()
+        return b.results()
+
+
+def _check(g, o, label):
+    assert np.array_equal(g["zbuf"].reshape(-1), o["zbuf"].reshape(-1)), label
+    if "v1" in o:
+        assert np.array_equal(g["coarse_valid"], o["v1"]), label
+    assert np.array_equal(g["valid"], o["valid"]), label
+    m = o["valid"].astype(bool)
+    err = np.abs(g["depth"][m].astype(np.float64) - o["depth"][m])
+    rel = err / o["depth"][m]
+    bound = np.maximum(1e-3, 1e-3 * o["depth"][m])
+    stats = dict(max_abs_m=float(err.max()), p99_abs_m=float(np.percentile(err, 99)), max_rel=float(rel.max()),
+                 over_bound=int((err > bound).sum()), pixels=int(m.sum()))
+    print(f"\n{label} FP16 depth error vs FP64 oracle: {stats}")
+    assert stats["over_bound"] == 0, stats
+    assert g["n"] == int(m.sum())
+    assert np.array_equal(g["rgba"], o["rgba"])
+    return stats
+
+
+def test_fp16_1080p_two_stage():
+    import torch
+    import oracle
+    v = scene.make_workload("1080p_3scan", 1001)
+    g = _run(v, PAPER_STAGES, 1, torch)
+    o = oracle.densify_view(v, num_stages=2, stages=PAPER_STAGES)
+    _check(g, o, "1080p two-stage")
+
+
+def test_fp16_qvga_single_stage():
+    import torch
+    import oracle
+    v = scene.make_workload("qvga_1scan", 1000)
+    st = ((4, 3.0, 20.0),)
+    g = _run(v, st, 1, torch)
+    o = oracle.densify_view(v, num_stages=1, stages=st)
+    _check(g, o, "qvga 9x9")
+
+
+def test_fp16_rejected_where_unavailable():
+    from paper_2601_01210_gb300 import densify as D
+    p = D.densify_default_params()
+    p.precision = D.DENSIFY_FP16
+    p.kernel_variant = 1
+    with pytest.raises(D.DensifyError) as e:
+        D.densify_create(p)
+    assert e.value.status == D.DENSIFY_E_INVALID
