@@ -107,7 +107,7 @@ def serve_measure(views, dev, stream, seconds, precision):
     loads = {"paper_rate_30fps": (30.0, seconds), "saturating_1000fps": (1000.0, 2.0)}
     out = {}
     for mname, extra in modes.items():
-        params = dict(num_stages=2, stages=STAGES, max_inflight=32, launch_policy=0,
+        params = dict(num_stages=2, stages=STAGES, max_inflight=32, launch_policy=0, autotune=1,
                       hbm_budget_bytes=4 << 30, **extra)
         with Densifier(params, device=dev.index, stream=stream.cuda_stream) as d:
             # warm-up (graph capture, first-touch)
@@ -148,11 +148,12 @@ def fp16_measure(a, bufs, params, dev, stream, flush_buf, taps2):
         torch.cuda.synchronize()
         ms = sum(s.elapsed_time(e) for s, e in evs)
         kt = d.kernel_times()
+        choice = d.describe()
     s2 = kt.get("jbf_stage2", (0.0, 1))
     avg = s2[0] / max(1, s2[1])
     return {"value": B * a.steps / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms / a.steps,
             "jbf_stage2_avg_us": avg, "jbf_stage2_gtap_s": taps2 / (avg * 1e-6) / 1e9 if avg > 0 else None,
-            "kernels": {k: round(v[0] / max(1, v[1]), 3) for k, v in kt.items()}}
+            "kernels": {k: round(v[0] / max(1, v[1]), 3) for k, v in kt.items()}, "filter_kernels": choice}
 
 
 def make_views(n, seed0, rank=0):
@@ -344,7 +345,7 @@ def ours_arm(a, rank, world, local_rank):
 
     bufs = [fb(i) for i in range(B)]
     params = dict(num_stages=2, stages=STAGES, max_batch=min(64, 2 * B), max_inflight=max(B, 16), launch_policy=1,
-                  timing=1,
+                  timing=1, autotune=1,
                   batches_in_flight=1, hbm_budget_bytes=max(2 << 30, B * 48 << 20))
     flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     with Densifier(params, device=local_rank, stream=stream.cuda_stream) as d:
@@ -415,6 +416,7 @@ def ours_arm(a, rank, world, local_rank):
             return float(t.item())
 
         value, total_ms = job_throughput(step_ms, B, world, reduce_max)
+        kernel_choice = d.describe()
 
         # e2e: host buffers through the C ABI
         e2e = None
@@ -480,6 +482,7 @@ def ours_arm(a, rank, world, local_rank):
                      "peak_basis": f"{sms} SMs x 128 lanes / 10 instructions per tap x {sm_max:.0f} MHz",
                      "taps_per_launch": taps2, "avg_launch_us": avg_us},
         "kernels": ktable,
+        "filter_kernels": kernel_choice,
         "clocks": ck,
         "gpu_launches": gpu_launches,
         "e2e": e2e,

@@ -189,7 +189,7 @@ __global__ void __launch_bounds__(256) jbf_kernel(const BatchDev *__restrict__ B
             const int y = y0 + rbase + k;
             float out = 0.0f;
             if (val[k]) {
-                if (den[k] >= 0x1p-60f) out = num[k] / den[k];
+                if (den[k] >= 0x1p-60f) out = __fdividef(num[k], den[k]);
                 else out = jbf_shifted<R, SW>(sG, sD, rbase + k, lane, cr[k], cg[k], cb[k], a.kc, a.kp);
             }
             if (x < gw && y < gh) {

@@ -130,7 +130,7 @@ struct TmaGeom {
                                                       : RGB_BX * RGB_BY + Z_BX * Z_BY * 4;
     static constexpr int STAGED = SRC == SRC_COARSE ? 0 : SH * SW * 16;
     static constexpr int OBS = SRC == SRC_COARSE ? 0 : ceil_to(SH * SW, 16);
-    static constexpr int HOR = ceil_to(SH * TW, 16);
+    static constexpr int HOR = ceil_to(SH * 4, 16);
     static constexpr int OFF_RAW = 0;
     static constexpr int OFF_STAGED = OFF_RAW + 2 * (RAW_A + RAW_B);
     static constexpr int OFF_OBS = OFF_STAGED + STAGED;
@@ -139,47 +139,6 @@ struct TmaGeom {
     static constexpr int SMEM = OFF_BAR + 16;
 };
 
-// Shifted recomputation of one output pixel (rare: every observed neighbour
-// far in colour, so the plain weight sum fell below 2^-60). The exponents are
-// shifted by their maximum over the window; the quotient is unchanged.
-template <int SRC, int R, int SW, int S_BX, int S_LEAD>
-__device__ __noinline__ float jbf_tma_shifted(const float4 *q4, const float *cs, int row0, int col0, float cr, float cg,
-                                              float cb, float kc, float kp) {
-    constexpr int T = 2 * R + 1;
-    float amax = -__int_as_float(0x7F800000);
-    for (int dy = 0; dy < T; ++dy)
-        for (int dx = 0; dx < T; ++dx) {
-            const float4 q = q4[(row0 + dy) * SW + col0 + dx];
-            const bool seen = SRC == SRC_COARSE ? q.w > 0.0f : q.x < 1.0e17f;
-            if (seen) {
-                const float dr = q.x - cr, dg = q.y - cg, db = q.z - cb;
-                const float n2 = fmaf(dr, dr, fmaf(dg, dg, db * db));
-                const float s2 = (float)((dx - R) * (dx - R) + (dy - R) * (dy - R));
-                amax = fmaxf(amax, fmaf(n2, -kc, -s2 * kp));
-            }
-        }
-    float nn = 0.0f, dd = 0.0f;
-    for (int dy = 0; dy < T; ++dy)
-        for (int dx = 0; dx < T; ++dx) {
-            const float4 q = q4[(row0 + dy) * SW + col0 + dx];
-            const bool seen = SRC == SRC_COARSE ? q.w > 0.0f : q.x < 1.0e17f;
-            if (seen) {
-                const float dr = q.x - cr, dg = q.y - cg, db = q.z - cb;
-                const float n2 = fmaf(dr, dr, fmaf(dg, dg, db * db));
-                const float s2 = (float)((dx - R) * (dx - R) + (dy - R) * (dy - R));
-                const float w = ex2_approx(fmaf(n2, -kc, -s2 * kp) - amax);
-                if (SRC == SRC_COARSE) {
-                    nn = fmaf(w, cs[(row0 + dy) * S_BX + col0 + dx - R + S_LEAD], nn);
-                    dd = fmaf(w, q.w, dd);
-                } else {
-                    nn = fmaf(w, q.w, nn);
-                    dd += w;
-                }
-            }
-        }
-    return nn / dd;
-}
-
 // FP16 staged record -> FP32 colour and depth (sentinel colour: unobserved).
 __device__ __forceinline__ bool half_record(const uint4 &q, float &r, float &g, float &b, float &d) {
     r = __low2float(*reinterpret_cast<const __half2 *>(&q.x));
@@ -187,38 +146,6 @@ __device__ __forceinline__ bool half_record(const uint4 &q, float &r, float &g, 
     b = __low2float(*reinterpret_cast<const __half2 *>(&q.z));
     d = __uint_as_float(q.w);
     return r < 65000.0f;
-}
-
-// FP32 shifted recomputation of one pixel of the FP16 form.
-template <int R, int SW>
-__device__ __noinline__ float jbf_tma_shifted_h(const uint4 *q4, int row0, int col0, float cr, float cg, float cb,
-                                                float kc, float kp) {
-    constexpr int T = 2 * R + 1;
-    float amax = -__int_as_float(0x7F800000);
-    for (int dy = 0; dy < T; ++dy)
-        for (int dx = 0; dx < T; ++dx) {
-            float r, g, b, d;
-            if (half_record(q4[(row0 + dy) * SW + col0 + dx], r, g, b, d)) {
-                const float dr = r - cr, dg = g - cg, db = b - cb;
-                const float n2 = fmaf(dr, dr, fmaf(dg, dg, db * db));
-                const float s2 = (float)((dx - R) * (dx - R) + (dy - R) * (dy - R));
-                amax = fmaxf(amax, fmaf(n2, -kc, -s2 * kp));
-            }
-        }
-    float nn = 0.0f, dd = 0.0f;
-    for (int dy = 0; dy < T; ++dy)
-        for (int dx = 0; dx < T; ++dx) {
-            float r, g, b, d;
-            if (half_record(q4[(row0 + dy) * SW + col0 + dx], r, g, b, d)) {
-                const float dr = r - cr, dg = g - cg, db = b - cb;
-                const float n2 = fmaf(dr, dr, fmaf(dg, dg, db * db));
-                const float s2 = (float)((dx - R) * (dx - R) + (dy - R) * (dy - R));
-                const float w = ex2_approx(fmaf(n2, -kc, -s2 * kp) - amax);
-                nn = fmaf(w, d, nn);
-                dd += w;
-            }
-        }
-    return nn / dd;
 }
 
 __device__ __forceinline__ __half2 h2bits(uint32_t u) { return *reinterpret_cast<const __half2 *>(&u); }
@@ -242,7 +169,7 @@ __global__ void __launch_bounds__(256, 2) jbf_tma_kernel(const BatchDev *__restr
     float4 *staged = reinterpret_cast<float4 *>(smem + G::OFF_STAGED);
     uint4 *staged_h = reinterpret_cast<uint4 *>(smem + G::OFF_STAGED);   // FP16 records, same 16 bytes
     uint8_t *obs = smem + G::OFF_OBS;
-    uint8_t *hor = smem + G::OFF_HOR;
+    uint32_t *horw = reinterpret_cast<uint32_t *>(smem + G::OFF_HOR);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + G::OFF_BAR);
 
     const int32_t *pre = SRC == SRC_UP ? B->t2_pre : B->t1_pre;
@@ -329,50 +256,77 @@ __global__ void __launch_bounds__(256, 2) jbf_tma_kernel(const BatchDev *__restr
             const int cx0 = floor_div3(x0 - R) & ~1, cy0 = floor_div3(y0 - R);
             const float2 *craw = reinterpret_cast<const float2 *>(rawB(buf));
             const uint32_t *zraw = reinterpret_cast<const uint32_t *>(rawB(buf));
-            for (int i = threadIdx.x; i < SH * SW; i += 256) {
-                const int sy = i / SW, sx = i - sy * SW;
-                const int gx = x0 - R + sx, gy = y0 - R + sy;
-                float4 v = make_float4(kSentinel, 0.0f, 0.0f, 0.0f);
-                uint8_t o = 0;
-                if (gx >= 0 && gx < gw && gy >= 0 && gy < gh) {
-                    const uint8_t *p = rgbraw + sy * G::RGB_BX + 3 * sx - 3 * R + G::RGB_LEAD;
-                    float d = 0.0f;
-                    if (SRC == SRC_UP) {
-                        const float2 c = craw[(gy / 3 - cy0) * G::C_BX + (gx / 3 - cx0)];
-                        o = c.y > 0.0f;
-                        d = c.x;
-                    } else {
-                        const uint32_t z = zraw[sy * G::Z_BX + sx - R + G::Z_LEAD];
-                        o = z != kEmpty;
-                        d = __uint_as_float(z);
-                    }
-                    if (o) v = make_float4((float)p[0], (float)p[1], (float)p[2], d);
-                }
+            // one staged neighbour: colour (sentinel if unobserved), depth, observation byte
+            auto put = [&](int i, float r, float g, float b, float d, bool o) {
                 if (HALF) {
-                    const float rr = o ? v.x : 65504.0f;
-                    staged_h[i] = make_uint4(h2u(__float2half2_rn(rr)), h2u(__float2half2_rn(v.y)),
-                                             h2u(__float2half2_rn(v.z)), __float_as_uint(v.w));
+                    staged_h[i] = o ? make_uint4(h2u(__float2half2_rn(r)), h2u(__float2half2_rn(g)),
+                                                 h2u(__float2half2_rn(b)), __float_as_uint(d))
+                                    : make_uint4(h2u(__float2half2_rn(65504.0f)), 0u, 0u, 0u);
                 } else {
-                    staged[i] = v;
+                    staged[i] = o ? make_float4(r, g, b, d) : make_float4(kSentinel, 0.0f, 0.0f, 0.0f);
                 }
                 obs[i] = o;
+            };
+            auto depth_of = [&](int sy, int sx, int gx, int gy, float &d) -> bool {
+                if (SRC == SRC_UP) {
+                    const float2 c = craw[(gy / 3 - cy0) * G::C_BX + (gx / 3 - cx0)];
+                    d = c.x;
+                    return c.y > 0.0f;
+                }
+                const uint32_t z = zraw[sy * G::Z_BX + sx - R + G::Z_LEAD];
+                d = __uint_as_float(z);
+                return z != kEmpty;
+            };
+            // interior columns sx = R .. R+31 in groups of 4: their 12 colour bytes start on a
+            // word boundary (byte offset 12 g + RGB_LEAD)
+            for (int q = threadIdx.x; q < SH * 8; q += 256) {
+                const int sy = q >> 3, g4 = q & 7;
+                const int sx0 = R + 4 * g4, gx0 = x0 + 4 * g4, gy = y0 - R + sy;
+                const int i0 = sy * SW + sx0;
+                if (gy < 0 || gy >= gh || gx0 >= gw) {
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) put(i0 + k, 0.0f, 0.0f, 0.0f, 0.0f, false);
+                    continue;
+                }
+                const uint32_t *wp = reinterpret_cast<const uint32_t *>(rgbraw + sy * G::RGB_BX + 12 * g4 + G::RGB_LEAD);
+                const uint32_t w0 = wp[0], w1 = wp[1], w2 = wp[2];
+                const uint32_t col[4] = {w0, (w0 >> 24) | (w1 << 8), (w1 >> 16) | (w2 << 16), w2 >> 8};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    float d = 0.0f;
+                    const bool in = gx0 + k < gw;
+                    const bool o = in && depth_of(sy, sx0 + k, gx0 + k, gy, d);
+                    put(i0 + k, (float)(col[k] & 0xFFu), (float)((col[k] >> 8) & 0xFFu), (float)((col[k] >> 16) & 0xFFu),
+                        d, o);
+                }
+            }
+            // halo columns sx < R and sx >= R + 32, one pixel each
+            for (int q = threadIdx.x; q < SH * 2 * R; q += 256) {
+                const int sy = q / (2 * R), h = q - sy * 2 * R;
+                const int sx = h < R ? h : 32 + h;
+                const int gx = x0 - R + sx, gy = y0 - R + sy;
+                float d = 0.0f;
+                const bool in = gx >= 0 && gx < gw && gy >= 0 && gy < gh;
+                const bool o = in && depth_of(sy, sx, gx, gy, d);
+                const uint8_t *p = rgbraw + sy * G::RGB_BX + 3 * sx - 3 * R + G::RGB_LEAD;
+                put(sy * SW + sx, o ? (float)p[0] : 0.0f, o ? (float)p[1] : 0.0f, o ? (float)p[2] : 0.0f, d, o);
             }
             __syncthreads();
-            for (int i = threadIdx.x; i < SH * TW; i += 256) {
-                const int sy = i / TW, sx = i - sy * TW;
-                uint32_t any = 0;
-#pragma unroll
-                for (int dx = 0; dx < T; ++dx) any |= obs[sy * SW + sx + dx];
-                hor[i] = any != 0;
+        }
+        // ---- validity rows: bit x of horw[sy] = some observation at staged row sy, columns x .. x + 2R
+        for (int sy = warp; sy < SH; sy += 8) {
+            bool o0, o1;
+            if (SRC == SRC_COARSE) {
+                o0 = cg[sy * SW + lane].w > 0.0f;
+                o1 = lane + 32 < SW && cg[sy * SW + lane + 32].w > 0.0f;
+            } else {
+                o0 = obs[sy * SW + lane] != 0;
+                o1 = lane + 32 < SW && obs[sy * SW + lane + 32] != 0;
             }
-        } else {
-            for (int i = threadIdx.x; i < SH * TW; i += 256) {
-                const int sy = i / TW, sx = i - sy * TW;
-                bool any = false;
-#pragma unroll
-                for (int dx = 0; dx < T; ++dx) any |= cg[sy * SW + sx + dx].w > 0.0f;
-                hor[i] = any;
-            }
+            const uint64_t m = ((uint64_t)__ballot_sync(0xffffffffu, o1) << 32) | __ballot_sync(0xffffffffu, o0);
+            const bool any = ((m >> lane) & ((1ull << T) - 1ull)) != 0;
+            const uint32_t hb = __ballot_sync(0xffffffffu, any);
+            if (lane == 0) horw[sy] = hb;
         }
         __syncthreads();
 
@@ -392,11 +346,16 @@ __global__ void __launch_bounds__(256, 2) jbf_tma_kernel(const BatchDev *__restr
             }
             num[k] = 0.0f;
             den[k] = 0.0f;
-            bool v = false;
+        }
+        {
+            uint32_t rows = 0;   // bit iy: this column has an observation in staged row rbase + iy's window
 #pragma unroll
-            for (int dy = 0; dy < T; ++dy) v |= hor[(rbase + k + dy) * TW + lane] != 0;
-            val[k] = v;
-            any_val |= v;
+            for (int iy = 0; iy < KP + 2 * R; ++iy) rows |= ((horw[rbase + iy] >> lane) & 1u) << iy;
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+                val[k] = ((rows >> k) & ((1u << T) - 1u)) != 0;
+                any_val |= val[k];
+            }
         }
         if (HALF && __any_sync(0xffffffffu, any_val)) {
             // centre colours of row pairs (2j, 2j+1) as half2
@@ -467,33 +426,88 @@ __global__ void __launch_bounds__(256, 2) jbf_tma_kernel(const BatchDev *__restr
             }
         }
         const int x = x0 + lane;
-#pragma unroll
-        for (int k = 0; k < KP; ++k) {
+        auto store = [&](int k, float out, bool v) {
             const int y = y0 + rbase + k;
-            float out = 0.0f;
-            if (val[k]) {
-                if (den[k] >= (HALF ? 0x1p-6f : 0x1p-60f)) {
-                    out = num[k] / den[k];
-                } else if (HALF) {
-                    const uint8_t *p = rgbraw + (rbase + k + R) * G::RGB_BX + 3 * lane + G::RGB_LEAD;
-                    out = jbf_tma_shifted_h<R, SW>(staged_h, rbase + k, lane, (float)p[0], (float)p[1], (float)p[2],
-                                                   a.kc, a.kp);
-                } else {
-                    out = jbf_tma_shifted<SRC, R, SW, G::S_BX, G::S_LEAD>(
-                        SRC == SRC_COARSE ? cg : staged, cs, rbase + k, lane, cr[k], cgr[k], cb[k], a.kc, a.kp);
-                }
-            }
             if (x < gw && y < gh) {
                 const int64_t o = (int64_t)y * gw + x;
                 if (SRC == SRC_COARSE) {
-                    F.s1[(int64_t)y * F.cpitch + x] = make_float2(out, val[k] ? 1.0f : 0.0f);
+                    F.s1[(int64_t)y * F.cpitch + x] = make_float2(out, v ? 1.0f : 0.0f);
                     if (F.out_coarse) F.out_coarse[o] = out;
-                    if (F.out_coarse_valid) F.out_coarse_valid[o] = val[k];
+                    if (F.out_coarse_valid) F.out_coarse_valid[o] = v;
                 } else {
                     F.out_depth[o] = out;
-                    F.out_valid[o] = val[k];
+                    F.out_valid[o] = v;
                 }
             }
+        };
+        uint32_t slow = 0u;   // bit k: valid pixel whose weight sum is too small for the plain form
+#pragma unroll
+        for (int k = 0; k < KP; ++k) {
+            if (val[k] && !(den[k] >= (HALF ? 0x1p-6f : 0x1p-60f))) {
+                slow |= 1u << k;
+                continue;
+            }
+            store(k, val[k] ? __fdividef(num[k], den[k]) : 0.0f, val[k]);
+        }
+        // shifted recomputation in FP32 (rare): largest exponent of the window first
+        while (slow) {
+            const int k = __ffs(slow) - 1;
+            slow &= slow - 1u;
+            float cr0, cg0, cb0;
+            if (SRC == SRC_COARSE) {
+                const float4 c = cg[(rbase + k + R) * SW + lane + R];
+                cr0 = c.x; cg0 = c.y; cb0 = c.z;
+            } else {
+                const uint8_t *p = rgbraw + (rbase + k + R) * G::RGB_BX + 3 * lane + G::RGB_LEAD;
+                cr0 = (float)p[0]; cg0 = (float)p[1]; cb0 = (float)p[2];
+            }
+            auto tap = [&](int dy, int dx, float &arg, float &wd, float &wb) -> bool {
+                const int o = (rbase + k + dy) * SW + lane + dx;
+                float r, g, b;
+                bool seen;
+                if (SRC == SRC_COARSE) {
+                    const float4 q = cg[o];
+                    r = q.x; g = q.y; b = q.z;
+                    seen = q.w > 0.0f;
+                    wd = cs[(rbase + k + dy) * G::S_BX + lane + dx - R + G::S_LEAD];
+                    wb = q.w;
+                } else if (HALF) {
+                    seen = half_record(staged_h[o], r, g, b, wd);
+                    wb = 1.0f;
+                } else {
+                    const float4 q = staged[o];
+                    r = q.x; g = q.y; b = q.z;
+                    seen = q.x < 1.0e17f;
+                    wd = q.w;
+                    wb = 1.0f;
+                }
+                const float dr = r - cr0, dg = g - cg0, db = b - cb0;
+                const float n2 = fmaf(dr, dr, fmaf(dg, dg, db * db));
+                const float s2 = (float)((dx - R) * (dx - R) + (dy - R) * (dy - R));
+                arg = fmaf(n2, -a.kc, -s2 * a.kp);
+                return seen;
+            };
+            float amax = -__int_as_float(0x7F800000);
+#pragma unroll 1
+            for (int dy = 0; dy < T; ++dy)
+#pragma unroll 1
+                for (int dx = 0; dx < T; ++dx) {
+                    float arg, wd, wb;
+                    if (tap(dy, dx, arg, wd, wb)) amax = fmaxf(amax, arg);
+                }
+            float nn = 0.0f, dd = 0.0f;
+#pragma unroll 1
+            for (int dy = 0; dy < T; ++dy)
+#pragma unroll 1
+                for (int dx = 0; dx < T; ++dx) {
+                    float arg, wd, wb;
+                    if (tap(dy, dx, arg, wd, wb)) {
+                        const float w = ex2_approx(arg - amax);
+                        nn = fmaf(w, wd, nn);
+                        dd = fmaf(w, wb, dd);
+                    }
+                }
+            store(k, nn / dd, true);
         }
         __syncthreads();   // staged / raw[buf] / hor are reused by the next tile
     }

@@ -1,0 +1,57 @@
+"""Autotuner: on the first batch every kernel able to run a filter stage is
+timed on that batch and the fastest kept. All candidates evaluate the same
+sums in the same order, so tuned and untuned contexts give the same bits."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import scene
+
+pytestmark = pytest.mark.gpu
+
+STAGES = ((4, 5.0, 20.0), (2, 5.0, 20.0))
+
+
+def _run(views, torch, **params):
+    from paper_2601_01210_gb300 import Densifier, build
+    from paper_2601_01210_gb300.frames import FrameBuffers
+    build.build()
+    with Densifier(dict(num_stages=2, stages=STAGES, launch_policy=1, max_batch=8, **params)) as d:
+        bufs = [FrameBuffers(v.camera, v.rgb, [(s.xyz, s.lidar_to_world) for s in v.scans]) for v in views]
+        ts = [d.submit(b.frame) for b in bufs]
+        d.flush()
+        for t in ts:
+            assert d.poll(t, -1) == 0
+        torch.cuda.synchronize()
+        return [b.results() for b in bufs], d.describe()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_tuned_equals_untuned_and_cache_is_reused(tmp_path, monkeypatch, precision):
+    import torch
+    views = [scene.make_batch_view(77, r, i, 3) for i, r in enumerate(["1080p", "720p", "540p"])]
+    base, desc0 = _run(views, torch, precision=precision)
+    assert desc0["tuned"] is False
+    cache = tmp_path / "tune.txt"
+    monkeypatch.setenv("DENSIFY_TUNE_CACHE", str(cache))
+    tuned, desc = _run(views, torch, precision=precision, autotune=1)
+    assert desc["tuned"] is True
+    for st in desc["stages"]:
+        timed = [c for c in st["candidates"] if "tuned_us" in c]
+        if len(st["candidates"]) > 1:
+            assert len(timed) == len(st["candidates"])
+            best = min(timed, key=lambda c: c["tuned_us"])
+            assert (best["kernel"], best["kp"]) == (st["chosen"]["kernel"], st["chosen"]["kp"])
+    for a, b in zip(base, tuned):
+        for k in ("valid", "rgba"):
+            assert np.array_equal(a[k], b[k]), k
+        np.testing.assert_allclose(a["depth"], b["depth"], rtol=2e-6)
+    lines = cache.read_text().splitlines()
+    assert lines and all(" " in l for l in lines)
+    # a second context with the same workload takes the choices from the cache without timing
+    again, desc2 = _run(views, torch, precision=precision, autotune=1)
+    assert cache.read_text().splitlines() == lines
+    for s1, s2 in zip(desc["stages"], desc2["stages"]):
+        assert (s1["chosen"]["kernel"], s1["chosen"]["kp"]) == (s2["chosen"]["kernel"], s2["chosen"]["kp"])
