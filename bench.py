@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--cpu-frames", type=int, default=4, help="frames in the oracle's timed sample")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-fp16", action="store_true", help="skip the FP16-form measurement")
+    ap.add_argument("--autotune", type=int, default=1, help="1: pick filter kernels on the first batch")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="duration of the paper-rate serving run (16 viewpoints x 30 fps)")
     return ap.parse_args()
@@ -89,7 +90,7 @@ def make_mixed_views(n, seed0):
         return list(ex.map(_gen_mixed, jobs))
 
 
-def serve_measure(views, dev, stream, seconds, precision):
+def serve_measure(views, dev, stream, seconds, precision, autotune=1):
     """Frames/s and p50/p99 latency of the serving loop: single-frame launches
     against continuous batching, at the paper's load (16 viewpoints x 30 fps,
     Poisson-jittered) and at a saturating load."""
@@ -107,7 +108,7 @@ def serve_measure(views, dev, stream, seconds, precision):
     loads = {"paper_rate_30fps": (30.0, seconds), "saturating_1000fps": (1000.0, 2.0)}
     out = {}
     for mname, extra in modes.items():
-        params = dict(num_stages=2, stages=STAGES, max_inflight=32, launch_policy=0, autotune=1,
+        params = dict(num_stages=2, stages=STAGES, max_inflight=32, launch_policy=0, autotune=autotune,
                       hbm_budget_bytes=4 << 30, **extra)
         with Densifier(params, device=dev.index, stream=stream.cuda_stream) as d:
             # warm-up (graph capture, first-touch)
@@ -345,7 +346,7 @@ def ours_arm(a, rank, world, local_rank):
 
     bufs = [fb(i) for i in range(B)]
     params = dict(num_stages=2, stages=STAGES, max_batch=min(64, 2 * B), max_inflight=max(B, 16), launch_policy=1,
-                  timing=1, autotune=1,
+                  timing=1, autotune=a.autotune,
                   batches_in_flight=1, hbm_budget_bytes=max(2 << 30, B * 48 << 20))
     flush_buf = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device=dev)
     with Densifier(params, device=local_rank, stream=stream.cuda_stream) as d:
@@ -418,27 +419,40 @@ def ours_arm(a, rank, world, local_rank):
         value, total_ms = job_throughput(step_ms, B, world, reduce_max)
         kernel_choice = d.describe()
 
-        # e2e: host buffers through the C ABI
-        e2e = None
-        if not a.no_e2e:
-            hb = [fb(i, memory=DENSIFY_MEM_HOST) for i in range(B)]
-            for _ in range(2):
-                for t in [d.submit(b.frame) for b in hb]:
-                    d.poll(t, -1)
-            torch.cuda.synchronize()
-            h2d = sum(sum(x.numel() * 4 for x, _ in b.scans) + b.rgb.numel() for b in hb)
+    # e2e: pinned host buffers through the C ABI (points and RGB in, coloured points out), two batch
+    # slots on the context's own streams so that one batch's copies overlap the next batch's kernels
+    e2e = None
+    if not a.no_e2e:
+        hb = [[fb(i, memory=DENSIFY_MEM_HOST, depth_out=False) for i in range(B)] for _ in range(2)]
+        pe = dict(params, timing=0, batches_in_flight=2, max_batch=B, max_inflight=4 * B,
+                  hbm_budget_bytes=max(2 << 30, 2 * B * 64 << 20))
+        with Densifier(pe, device=local_rank) as d2:
+            def e2e_steps(n):
+                prev = None
+                for k in range(n):
+                    ts = [d2.submit(b.frame) for b in hb[k % 2]]   # the B-th submit launches the batch
+                    if prev:
+                        for t in prev:
+                            d2.poll(t, -1)
+                    prev = ts
+                for t in prev or []:
+                    d2.poll(t, -1)
+
+            e2e_steps(3)
+            if world > 1:
+                torch.distributed.barrier()
             t0 = time.perf_counter()
-            for _ in range(a.steps):
-                for t in [d.submit(b.frame) for b in hb]:
-                    d.poll(t, -1)
-            torch.cuda.synchronize()
+            e2e_steps(a.steps)
             dt = time.perf_counter() - t0
-            d2h = sum(b.W * b.H * 5 + 8 + b.n_points() * 16 for b in hb)
-            e2e = {"value": B * a.steps / dt * world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-                   "d2h_bytes_per_step": int(d2h)}
-        serving = None
-        if not a.no_serve and rank == 0:
-            serving = serve_measure(mixed_views, dev, stream, a.serve_seconds, 1)
+            dt = reduce_max(dt) if world > 1 else dt
+        h2d = sum(sum(x.numel() * 4 for x, _ in b.scans) + b.rgb.numel() for b in hb[0])
+        d2h = sum(8 + b.n_points() * 16 for b in hb[0])
+        e2e = {"value": B * a.steps / dt * world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h),
+               "what": "pinned host points + RGB in, coloured points out (written by the GPU into pinned memory)"}
+    serving = None
+    if not a.no_serve and rank == 0:
+        serving = serve_measure(mixed_views, dev, stream, a.serve_seconds, 1, a.autotune)
     fp16 = None
     if not a.no_fp16:
         fp16 = fp16_measure(a, bufs, params, dev, stream, flush_buf, taps2)

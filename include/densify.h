@@ -31,7 +31,9 @@
  *   - Unless a function says otherwise, pointers inside densify_frame are
  *     DEVICE pointers (memory = DENSIFY_MEM_DEVICE) owned by the caller; with
  *     memory = DENSIFY_MEM_HOST they are host pointers (page-locked for
- *     asynchronous copies) and the library copies inputs in and results out.
+ *     asynchronous copies) and the library copies inputs in and results out;
+ *     page-locked point and count buffers are written by the GPU directly,
+ *     at exact size, with no copy.
  *   - Every call returns a status; nothing throws across the ABI. Invalid
  *     point values (NaN, z <= 0 in the camera, outside the image) are not
  *     errors: such points are skipped.

@@ -156,6 +156,28 @@ __global__ void __launch_bounds__(kThreads) bp_write_kernel(const BatchDev *__re
         const float r20 = c2w[8], r21 = c2w[9], r22 = c2w[10], t2 = c2w[11];
         const float ifx = 1.0f / F.fx, ify = 1.0f / F.fy;
         float4 *st = stage[warp];
+        // issue the loads of all four steps before using any of them (memory-level parallelism)
+        float4 zq[4];
+        uint32_t cw[4][3];
+        int yq[4], xq[4];
+#pragma unroll
+        for (int it = 0; it < 4; ++it) {
+            const int64_t p0 = wbase + it * 128 + lane * 4;
+            zq[it] = make_float4(0.f, 0.f, 0.f, 0.f);
+            cw[it][0] = cw[it][1] = cw[it][2] = 0u;
+            yq[it] = 0;
+            xq[it] = 0;
+            if (m[it] && vdepth && rows4 && p0 + 4 <= n) {
+                zq[it] = *reinterpret_cast<const float4 *>(F.out_depth + p0);
+                yq[it] = (int)(p0 / W);
+                xq[it] = (int)(p0 - (int64_t)yq[it] * W);
+                const uint32_t *cp =
+                    reinterpret_cast<const uint32_t *>(F.rgb + (int64_t)yq[it] * F.rgb_pitch + 3 * xq[it]);
+                cw[it][0] = cp[0];
+                cw[it][1] = cp[1];
+                cw[it][2] = cp[2];
+            }
+        }
 #pragma unroll
         for (int it = 0; it < 4; ++it) {
             const uint32_t cnt = __popc(m[it]);
@@ -168,22 +190,14 @@ __global__ void __launch_bounds__(kThreads) bp_write_kernel(const BatchDev *__re
             const uint32_t tot = __shfl_sync(0xffffffffu, incl, 31);
             if (m[it]) {
                 const int64_t p0 = wbase + it * 128 + lane * 4;
-                float z[4];
-                if (vdepth && p0 + 4 <= n) {
-                    const float4 d4 = *reinterpret_cast<const float4 *>(F.out_depth + p0);
-                    z[0] = d4.x; z[1] = d4.y; z[2] = d4.z; z[3] = d4.w;
-                } else {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) z[k] = (m[it] >> k & 1u) ? F.out_depth[p0 + k] : 0.0f;
-                }
                 uint32_t j = incl - cnt;
-                if (rows4) {
-                    // the 4 pixels share a row and their 12 colour bytes are word aligned
-                    const int y = (int)(p0 / W), x0 = (int)(p0 - (int64_t)y * W);
-                    const uint32_t *cw = reinterpret_cast<const uint32_t *>(F.rgb + (int64_t)y * F.rgb_pitch + 3 * x0);
-                    const uint32_t w0 = cw[0], w1 = cw[1], w2 = cw[2];
+                if (vdepth && rows4 && p0 + 4 <= n) {
+                    // the 4 pixels share a row; colour bytes were loaded as 3 words
+                    const float z[4] = {zq[it].x, zq[it].y, zq[it].z, zq[it].w};
+                    const uint32_t w0 = cw[it][0], w1 = cw[it][1], w2 = cw[it][2];
                     const uint32_t col[4] = {w0 & 0xFFFFFFu, (w0 >> 24) | ((w1 & 0xFFFFu) << 8),
                                              (w1 >> 16) | ((w2 & 0xFFu) << 16), w2 >> 8};
+                    const int y = yq[it], x0 = xq[it];
                     const float Y = ((float)y + 0.5f - F.cy) * ify;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
@@ -206,7 +220,7 @@ __global__ void __launch_bounds__(kThreads) bp_write_kernel(const BatchDev *__re
                             const uint8_t *cb = F.rgb + (int64_t)y * F.rgb_pitch + 3 * x;
                             const uint32_t rgba = (uint32_t)cb[0] | ((uint32_t)cb[1] << 8) | ((uint32_t)cb[2] << 16) |
                                                   0xFF000000u;
-                            const float Z = z[k];
+                            const float Z = F.out_depth[p];
                             const float X = ((float)x + 0.5f - F.cx) * Z * ifx;
                             const float Yz = ((float)y + 0.5f - F.cy) * ify * Z;
                             st[j++] = make_float4(fmaf(r00, X, fmaf(r01, Yz, fmaf(r02, Z, t0))),

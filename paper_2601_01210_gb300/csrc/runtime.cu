@@ -98,6 +98,8 @@ struct Layout {
     uint64_t zbuf = 0, cguide = 0, cssum = 0, s1 = 0, chunk = 0, depth = 0, valid = 0;
     uint64_t pts[kMaxScans] = {0, 0, 0}, rgb = 0, points = 0, npts = 0, coarse = 0, coarse_valid = 0;
     int64_t rgb_pitch = 0;   // pitch of the staged RGB copy (0: the caller's frame is used in place)
+    float4 *points_direct = nullptr;    // device view of a page-locked host point buffer
+    int64_t *count_direct = nullptr;    // device view of a page-locked host count
     uint64_t total = 0;
     bool own_depth = false, own_valid = false;
 };
@@ -113,6 +115,8 @@ struct FrameRec {
 };
 
 struct Slot {
+    cudaStream_t stream = nullptr;   // the context stream, or the slot's own when the context owns its streams
+    bool own_stream = false;
     BatchDev *d = nullptr;       // device table
     BatchDev *h = nullptr;       // pinned host mirror
     int32_t *d_status = nullptr; // device status word (bounded waits that gave up)
@@ -364,6 +368,18 @@ std::string validate_frame(const densify_ctx *c, const densify_frame *f) {
     return "";
 }
 
+// Device address of page-locked host memory (unified addressing), or NULL.
+template <typename T>
+T *mapped_host(void *p) {
+    if (!p) return nullptr;
+    cudaPointerAttributes at{};
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost && at.devicePointer ? static_cast<T *>(at.devicePointer) : nullptr;
+}
+
 Layout layout_of(const densify_params &p, const densify_frame *f) {
     Layout L;
     const int64_t W = f->K.width, H = f->K.height, npx = W * H;
@@ -393,8 +409,11 @@ Layout layout_of(const densify_params &p, const densify_frame *f) {
     if (host) {
         for (int s = 0; s < f->num_scans; ++s) L.pts[s] = take((uint64_t)f->scans[s].count * f->scans[s].stride_bytes);
         if (p.emit_points) {
-            L.points = take((uint64_t)f->out_points_cap * 16);
-            L.npts = take(8);
+            // points go straight from the compaction kernel into page-locked host memory, at exact size
+            L.points_direct = mapped_host<float4>(f->out_points);
+            L.count_direct = mapped_host<int64_t>(f->out_points_n);
+            if (!L.points_direct) L.points = take((uint64_t)f->out_points_cap * 16);
+            if (!L.count_direct) L.npts = take(8);
         }
     } else if (p.emit_points) {
         L.npts = 0;
@@ -454,9 +473,9 @@ void build_frame_dev(densify_ctx *c, FrameRec &r) {
     d.out_depth = L.own_depth ? (float *)(base + L.depth) : f->out_depth;
     d.out_valid = L.own_valid ? (uint8_t *)(base + L.valid) : f->out_valid;
     if (c->p.emit_points) {
-        d.out_points = host ? (float4 *)(base + L.points) : (float4 *)f->out_points;
+        d.out_points = host ? (L.points_direct ? L.points_direct : (float4 *)(base + L.points)) : (float4 *)f->out_points;
         d.points_cap = f->out_points_cap;
-        d.points_n = host ? (int64_t *)(base + L.npts) : f->out_points_n;
+        d.points_n = host ? (L.count_direct ? L.count_direct : (int64_t *)(base + L.npts)) : f->out_points_n;
     }
 }
 
@@ -574,16 +593,16 @@ densify_status autotune(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &t
                 if (st != DENSIFY_OK) break;
                 fill_batch(c, sl, tk);
                 const size_t bytes = offsetof(BatchDev, f) + sizeof(FrameDev) * tk.size();
-                cudaError_t e = cudaMemcpyAsync(sl.d, sl.h, bytes, cudaMemcpyHostToDevice, c->stream);
+                cudaError_t e = cudaMemcpyAsync(sl.d, sl.h, bytes, cudaMemcpyHostToDevice, sl.stream);
                 // inputs of this stage
-                if (e == cudaSuccess) e = launch_prep(sl.d, c->grid[K_PREP], c->stream);
-                if (e == cudaSuccess) e = launch_project(sl.d, c->grid[K_PROJECT], c->stream);
-                if (e == cudaSuccess && c->p.num_stages == 2) e = launch_pool(sl.d, c->p.pool, c->grid[K_POOL], c->stream);
-                if (e == cudaSuccess && i == 1) e = launch_filter(c, 0, sl.d, c->stream);
-                if (e == cudaSuccess) e = launch_filter(c, i, sl.d, c->stream);   // warm-up
-                if (e == cudaSuccess) e = cudaEventRecord(e0, c->stream);
-                for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) e = launch_filter(c, i, sl.d, c->stream);
-                if (e == cudaSuccess) e = cudaEventRecord(e1, c->stream);
+                if (e == cudaSuccess) e = launch_prep(sl.d, c->grid[K_PREP], sl.stream);
+                if (e == cudaSuccess) e = launch_project(sl.d, c->grid[K_PROJECT], sl.stream);
+                if (e == cudaSuccess && c->p.num_stages == 2) e = launch_pool(sl.d, c->p.pool, c->grid[K_POOL], sl.stream);
+                if (e == cudaSuccess && i == 1) e = launch_filter(c, 0, sl.d, sl.stream);
+                if (e == cudaSuccess) e = launch_filter(c, i, sl.d, sl.stream);   // warm-up
+                if (e == cudaSuccess) e = cudaEventRecord(e0, sl.stream);
+                for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) e = launch_filter(c, i, sl.d, sl.stream);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, sl.stream);
                 if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                 float ms = 0.0f;
                 if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
@@ -709,7 +728,7 @@ densify_status launch_batch(densify_ctx *c, int si) {
     }
     fill_batch(c, sl, tk);
     const size_t bytes = offsetof(BatchDev, f) + sizeof(FrameDev) * tk.size();
-    CU(cudaMemcpyAsync(sl.d, sl.h, bytes, cudaMemcpyHostToDevice, c->stream), "descriptor upload");
+    CU(cudaMemcpyAsync(sl.d, sl.h, bytes, cudaMemcpyHostToDevice, sl.stream), "descriptor upload");
     // host frames: inputs in
     for (uint64_t t : tk) {
         FrameRec &r = c->frames[t];
@@ -718,7 +737,7 @@ densify_status launch_batch(densify_ctx *c, int si) {
             if (r.fr.scans[s].count > 0)
                 CU(cudaMemcpyAsync((void *)r.dev.scans[s].xyz, r.fr.scans[s].xyz,
                                    (size_t)r.fr.scans[s].count * r.fr.scans[s].stride_bytes, cudaMemcpyHostToDevice,
-                                   c->stream),
+                                   sl.stream),
                    "points upload");
     }
     // RGB staging (host frames, and device frames whose base or pitch is not 16-byte aligned)
@@ -728,7 +747,7 @@ densify_status launch_batch(densify_ctx *c, int si) {
         CU(cudaMemcpy2DAsync((void *)r.dev.rgb, (size_t)r.dev.rgb_pitch, r.fr.rgb, (size_t)r.fr.rgb_pitch,
                              (size_t)r.fr.K.width * 3, (size_t)r.fr.K.height,
                              r.fr.memory == DENSIFY_MEM_HOST ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice,
-                             c->stream),
+                             sl.stream),
            "rgb staging");
     }
     if (c->p.use_graphs) {
@@ -746,9 +765,9 @@ densify_status launch_batch(densify_ctx *c, int si) {
             cudaGraphDestroy(g);
             if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
         }
-        CU(cudaGraphLaunch(sl.exec, c->stream), "graph launch");
+        CU(cudaGraphLaunch(sl.exec, sl.stream), "graph launch");
     } else {
-        densify_status st = issue_kernels(c, sl, c->stream, c->p.timing != 0);
+        densify_status st = issue_kernels(c, sl, sl.stream, c->p.timing != 0);
         if (st != DENSIFY_OK) return st;
     }
     // debug z-buffer out (row pitch W), both memory kinds
@@ -758,7 +777,7 @@ densify_status launch_batch(densify_ctx *c, int si) {
         CU(cudaMemcpy2DAsync(r.fr.out_zbuf, (size_t)r.fr.K.width * 4, r.dev.zbuf, (size_t)r.dev.zpitch * 4,
                              (size_t)r.fr.K.width * 4, (size_t)r.fr.K.height,
                              r.fr.memory == DENSIFY_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
-                             c->stream),
+                             sl.stream),
            "zbuf copy");
     }
     // host frames: results out (points are copied at poll time, exactly n of them)
@@ -767,24 +786,24 @@ densify_status launch_batch(densify_ctx *c, int si) {
         if (r.fr.memory != DENSIFY_MEM_HOST) continue;
         const size_t npx = (size_t)r.fr.K.width * r.fr.K.height;
         if (r.fr.out_depth)
-            CU(cudaMemcpyAsync(r.fr.out_depth, r.dev.out_depth, npx * 4, cudaMemcpyDeviceToHost, c->stream), "depth copy");
+            CU(cudaMemcpyAsync(r.fr.out_depth, r.dev.out_depth, npx * 4, cudaMemcpyDeviceToHost, sl.stream), "depth copy");
         if (r.fr.out_valid)
-            CU(cudaMemcpyAsync(r.fr.out_valid, r.dev.out_valid, npx, cudaMemcpyDeviceToHost, c->stream), "valid copy");
+            CU(cudaMemcpyAsync(r.fr.out_valid, r.dev.out_valid, npx, cudaMemcpyDeviceToHost, sl.stream), "valid copy");
         if (c->p.num_stages == 2) {
             const size_t nc = (size_t)r.dev.Wc * r.dev.Hc;
             if (r.fr.out_coarse)
-                CU(cudaMemcpyAsync(r.fr.out_coarse, r.dev.out_coarse, nc * 4, cudaMemcpyDeviceToHost, c->stream),
+                CU(cudaMemcpyAsync(r.fr.out_coarse, r.dev.out_coarse, nc * 4, cudaMemcpyDeviceToHost, sl.stream),
                    "coarse copy");
             if (r.fr.out_coarse_valid)
                 CU(cudaMemcpyAsync(r.fr.out_coarse_valid, r.dev.out_coarse_valid, nc, cudaMemcpyDeviceToHost,
-                                   c->stream),
+                                   sl.stream),
                    "coarse valid copy");
         }
-        if (c->p.emit_points)
-            CU(cudaMemcpyAsync(r.fr.out_points_n, r.dev.points_n, 8, cudaMemcpyDeviceToHost, c->stream), "count copy");
+        if (c->p.emit_points && !r.L.count_direct)
+            CU(cudaMemcpyAsync(r.fr.out_points_n, r.dev.points_n, 8, cudaMemcpyDeviceToHost, sl.stream), "count copy");
     }
-    CU(cudaMemcpyAsync(sl.h_status, sl.d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, c->stream), "status copy");
-    CU(cudaEventRecord(sl.done, c->stream), "event record");
+    CU(cudaMemcpyAsync(sl.h_status, sl.d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, sl.stream), "status copy");
+    CU(cudaEventRecord(sl.done, sl.stream), "event record");
     for (uint64_t t : tk) {
         FrameRec &r = c->frames[t];
         r.state = 1;
@@ -864,7 +883,8 @@ densify_status wait_some(densify_ctx *c, int64_t deadline_ns) {
 }
 
 densify_status finalize(densify_ctx *c, FrameRec &r) {
-    if (r.fr.memory == DENSIFY_MEM_HOST && c->p.emit_points && r.fr.out_points && r.fr.out_points_cap > 0) {
+    if (r.fr.memory == DENSIFY_MEM_HOST && c->p.emit_points && r.fr.out_points && r.fr.out_points_cap > 0 &&
+        !r.L.points_direct) {
         const int64_t n = std::min<int64_t>(*r.fr.out_points_n, r.fr.out_points_cap);
         if (n > 0) {
             CU(cudaMemcpyAsync(r.fr.out_points, r.dev.out_points, (size_t)n * 16, cudaMemcpyDeviceToHost,
@@ -882,6 +902,7 @@ void destroy_resources(densify_ctx *c) {
         if (sl.done) cudaEventDestroy(sl.done);
         for (auto &e : sl.kev)
             if (e) cudaEventDestroy(e);
+        if (sl.own_stream && sl.stream) cudaStreamDestroy(sl.stream);
         if (sl.d) cudaFree(sl.d);
         if (sl.h) cudaFreeHost(sl.h);
         if (sl.d_status) cudaFree(sl.d_status);
@@ -983,6 +1004,15 @@ densify_status densify_create(const densify_params *params, int device, void *cu
     c->arena.init(params->hbm_budget_bytes);
     c->slots.resize(params->batches_in_flight);
     for (auto &sl : c->slots) {
+        // a context that owns its streams gives every slot its own, so that one batch's host copies
+        // overlap another batch's kernels; with a caller stream every batch is ordered on it
+        if (c->own_stream && c->slots.size() > 1) {
+            if ((e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking)) != cudaSuccess)
+                return bail(DENSIFY_E_CUDA, std::string("slot stream: ") + cudaGetErrorString(e));
+            sl.own_stream = true;
+        } else {
+            sl.stream = c->stream;
+        }
         if ((e = cudaMalloc(&sl.d, sizeof(BatchDev))) != cudaSuccess ||
             (e = cudaMallocHost(&sl.h, sizeof(BatchDev))) != cudaSuccess ||
             (e = cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming)) != cudaSuccess ||

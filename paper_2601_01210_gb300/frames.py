@@ -14,17 +14,20 @@ from .densify import DENSIFY_MEM_DEVICE, DENSIFY_MEM_HOST, make_frame
 
 class FrameBuffers:
     def __init__(self, camera, rgb, scans, *, device="cuda", num_stages=2, pool=3, emit_points=True,
-                 debug=False, memory=DENSIFY_MEM_DEVICE, points_cap=None, xyzw=False):
+                 debug=False, memory=DENSIFY_MEM_DEVICE, points_cap=None, xyzw=False, depth_out=True,
+                 pinned=True):
         self.camera = camera
         W, H = camera.width, camera.height
         self.W, self.H = W, H
         host = memory == DENSIFY_MEM_HOST
         dev = torch.device("cpu") if host else torch.device(device)
-        pin = dict(pin_memory=True) if host else {}
+        pin = dict(pin_memory=True) if host and pinned else {}
 
         def put(a):
             t = torch.from_numpy(np.ascontiguousarray(a))
-            return t.pin_memory() if host else t.to(dev)
+            if host:
+                return t.pin_memory() if pinned else t.clone()
+            return t.to(dev)
 
         self.rgb = put(rgb)
         self.scans = []
@@ -33,8 +36,9 @@ class FrameBuffers:
             if xyzw:
                 x = np.concatenate([x, np.zeros((x.shape[0], 1), np.float32)], 1)
             self.scans.append((put(x), np.asarray(l2w, np.float64)))
-        self.depth = torch.zeros((H, W), dtype=torch.float32, device=dev, **pin)
-        self.valid = torch.zeros((H, W), dtype=torch.uint8, device=dev, **pin)
+        # depth_out=False: only points come back (the library keeps depth and mask in its scratch)
+        self.depth = torch.zeros((H, W), dtype=torch.float32, device=dev, **pin) if depth_out else None
+        self.valid = torch.zeros((H, W), dtype=torch.uint8, device=dev, **pin) if depth_out else None
         cap = W * H if points_cap is None else points_cap
         self.points = torch.zeros((cap, 4), dtype=torch.float32, device=dev, **pin) if emit_points else None
         self.npoints = torch.zeros(1, dtype=torch.int64, device=dev, **pin) if emit_points else None
@@ -55,7 +59,9 @@ class FrameBuffers:
 
     def results(self):
         """Host copies of the outputs (numpy)."""
-        out = dict(depth=self.depth.cpu().numpy(), valid=self.valid.cpu().numpy())
+        out = {}
+        if self.depth is not None:
+            out.update(depth=self.depth.cpu().numpy(), valid=self.valid.cpu().numpy())
         if self.points is not None:
             n = min(self.n_points(), self.points.shape[0])
             pts = self.points[:n].cpu().numpy()
