@@ -80,6 +80,15 @@ def lib():
             L.oracle_backproject.argtypes = [_f64p, _u8p, _u8p, _i64, _int, _int, _dbl, _dbl, _dbl, _dbl,
                                              _f64p, _f64p, _u32p]
             L.oracle_backproject.restype = _i64
+            L.oracle_occlusion.argtypes = [_u32p, _int, _int, _int, _flt, _u32p]
+            L.oracle_occlusion.restype = _i64
+            L.oracle_motion_mask.argtypes = [_u8p, _i64, _u8p, _i64, _int, _int, _flt, _int, _u8p, _u8p]
+            L.oracle_motion_mask.restype = None
+            L.oracle_project_masked.argtypes = [_f32p, _f32p, _i64, _i64, _int, _int, _flt, _flt, _flt, _flt,
+                                                C.c_void_p, _int, _u32p]
+            L.oracle_project_masked.restype = _i64
+            L.oracle_contour.argtypes = [_f32p, _u8p, _int, _int, _flt, _f32p, _u8p]
+            L.oracle_contour.restype = _i64
             _lib = L
     return _lib
 
@@ -191,6 +200,47 @@ def backproject(depth, valid, rgb, fx, fy, cx, cy, cam_to_world):
     return xyz[: 3 * n].reshape(n, 3), rgba[:n]
 
 
+def occlusion(zbuf, W, H, rho, margin):
+    """Occluded-point removal on a merged z-buffer; returns (cleaned, removed)."""
+    zin = np.ascontiguousarray(zbuf, np.uint32).ravel()
+    zout = np.empty_like(zin)
+    n = lib().oracle_occlusion(zin, W, H, int(rho), float(margin), zout)
+    return zout, n
+
+
+def motion_mask(rgb, prev_rgb, tau, close_radius):
+    """Motion mask of consecutive frames after the closing; (H, W) uint8."""
+    H, W = rgb.shape[:2]
+    tmp = np.zeros(H * W, np.uint8)
+    mask = np.zeros(H * W, np.uint8)
+    lib().oracle_motion_mask(np.ascontiguousarray(rgb, np.uint8).reshape(-1), W * 3,
+                             np.ascontiguousarray(prev_rgb, np.uint8).reshape(-1), W * 3, W, H, float(tau),
+                             int(close_radius), tmp, mask)
+    return mask.reshape(H, W)
+
+
+def project_masked(M32, xyz, W, H, fx, fy, cx, cy, mask, newest, zbuf):
+    xyz = np.ascontiguousarray(xyz, np.float32)
+    n = xyz.shape[0]
+    m = np.ascontiguousarray(mask, np.uint8).ravel() if mask is not None else None
+    kept = lib().oracle_project_masked(np.ascontiguousarray(M32, np.float32).ravel(),
+                                       xyz.reshape(-1) if n else np.zeros(4, np.float32), n,
+                                       xyz.shape[1] if n else 3, W, H, fx, fy, cx, cy,
+                                       m.ctypes.data if m is not None else None, int(bool(newest)), zbuf)
+    return zbuf, kept
+
+
+def contour(depth32, valid, t):
+    """Contour removal on an FP32 depth map; returns (depth, valid, dropped)."""
+    H, W = valid.shape
+    d = np.ascontiguousarray(depth32, np.float32).ravel()
+    v = np.ascontiguousarray(valid, np.uint8).ravel()
+    do = np.empty_like(d)
+    vo = np.empty_like(v)
+    n = lib().oracle_contour(d, v, W, H, float(t), do, vo)
+    return do.reshape(H, W), vo.reshape(H, W), n
+
+
 # ----------------------------------------------------------------------------
 # whole path
 # ----------------------------------------------------------------------------
@@ -198,7 +248,8 @@ PAPER_TWO_STAGE = dict(num_stages=2, stages=((4, 5.0, 20.0), (2, 5.0, 20.0)), po
 
 
 def densify(cam, rgb, scans, num_stages=2, stages=((4, 5.0, 20.0), (2, 5.0, 20.0)), pool_factor=3,
-            stage2_input=0, emit_points=True, shifted=False):
+            stage2_input=0, emit_points=True, shifted=False, occlusion_radius=0, occlusion_margin=0.0,
+            prev_rgb=None, motion_threshold=0.0, motion_close_radius=0, newest_scan=None, contour_threshold=0.0):
     """Run the whole path on one view.
 
     cam: object with width, height, fx, fy, cx, cy, cam_to_world (4x4);
@@ -213,14 +264,25 @@ def densify(cam, rgb, scans, num_stages=2, stages=((4, 5.0, 20.0), (2, 5.0, 20.0
     zbuf = np.full(H * W, ZBUF_EMPTY, np.uint32)
     kept = 0
     mats = []
-    for xyz, l2w in scans:
+    mask = None
+    if prev_rgb is not None and motion_threshold > 0:        # afterimage removal (Sec. 4.1)
+        mask = motion_mask(rgb, prev_rgb, motion_threshold, motion_close_radius)
+        res["motion"] = mask
+    newest = len(scans) - 1 if newest_scan is None else newest_scan
+    for s, (xyz, l2w) in enumerate(scans):
         M64, M32 = compose(cam.cam_to_world, l2w)
         mats.append((M64, M32))
-        _, k = project(M32, xyz, W, H, cam.fx, cam.fy, cam.cx, cam.cy, zbuf)
+        if mask is not None:
+            _, k = project_masked(M32, xyz, W, H, cam.fx, cam.fy, cam.cx, cam.cy, mask, s == newest, zbuf)
+        else:
+            _, k = project(M32, xyz, W, H, cam.fx, cam.fy, cam.cx, cam.cy, zbuf)
         kept += k
     res["M"] = mats
-    res["zbuf"] = zbuf.reshape(H, W)
     res["in_image"] = kept
+    if occlusion_radius > 0:                                  # occluded-point removal (Sec. 4.1)
+        res["zbuf_merged"] = zbuf.reshape(H, W).copy()
+        zbuf, res["occluded"] = occlusion(zbuf, W, H, occlusion_radius, occlusion_margin)
+    res["zbuf"] = zbuf.reshape(H, W)
     if num_stages == 1:
         r, sp, sc = stages[0]
         D, B = zbuf_to_depth(zbuf)
@@ -237,6 +299,10 @@ def densify(cam, rgb, scans, num_stages=2, stages=((4, 5.0, 20.0), (2, 5.0, 20.0
         out, valid = jbf_gather(rgb.astype(np.float64), beta2, betad2, r2, sp2, sc2, shifted)
     else:
         raise ValueError("num_stages must be 1 or 2")
+    if contour_threshold > 0:                                 # contour removal (Sec. 5), on the FP32 map
+        res["depth_filtered"], res["valid_filtered"] = out, valid
+        d32, valid, res["contour_dropped"] = contour(out.astype(np.float32), valid, contour_threshold)
+        out = np.where(valid.astype(bool), out, 0.0)
     res["depth"] = out
     res["valid"] = valid
     if emit_points:

@@ -354,3 +354,158 @@ int64_t oracle_backproject(const double *depth, const uint8_t *valid, const uint
     }
     return n;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Occluded-point removal (Sec. 4.1: an averaging filter on the merged depth
+ * map; points significantly behind the average are removed). Reading: for an
+ * observed pixel p, the window average is the mean of the observed depths in
+ * the (2 rho + 1)^2 square around p (p included), summed in FP32 as row sums
+ * (dx ascending) added up over rows (dy ascending), divided by their count in
+ * FP32; p is removed iff D(p) > average + margin (FP32). The sums are
+ * evaluated in FP64 and rounded to FP32 after every operation, which is the
+ * FP32 result exactly. zin and zout are H x W bit patterns (empty 0x7F800000);
+ * returns the number of removed points. */
+int64_t oracle_occlusion(const uint32_t *zin, int W, int H, int rho, float margin, uint32_t *zout)
+{
+    int64_t removed = 0;
+    for (int y = 0; y < H; ++y) {
+        for (int x = 0; x < W; ++x) {
+            const int64_t o = (int64_t)y * W + x;
+            zout[o] = zin[o];
+            if (zin[o] == ZBUF_EMPTY) continue;
+            float sum = 0.0f;
+            int cnt = 0;
+            for (int dy = -rho; dy <= rho; ++dy) {
+                float row = 0.0f;
+                for (int dx = -rho; dx <= rho; ++dx) {
+                    const int qx = x + dx, qy = y + dy;
+                    if (qx < 0 || qx >= W || qy < 0 || qy >= H) continue;
+                    const uint32_t z = zin[(int64_t)qy * W + qx];
+                    if (z == ZBUF_EMPTY) continue;
+                    row = add32(row, bits_f32(z));
+                    ++cnt;
+                }
+                sum = add32(sum, row);
+            }
+            const float avg = div32(sum, (float)cnt);
+            if (bits_f32(zin[o]) > add32(avg, margin)) {
+                zout[o] = ZBUF_EMPTY;
+                ++removed;
+            }
+        }
+    }
+    return removed;
+}
+
+/* Afterimage removal, motion mask (Sec. 4.1: Euclidean RGB distance between
+ * consecutive frames above tau_m marks motion; a morphological closing fills
+ * the mask). Motion at p iff (dr^2 + dg^2 + db^2) > tau^2 (integers against
+ * the FP32 square of tau). Closing = dilation then erosion with the square
+ * (2c + 1)^2 structuring element; outside the image counts as no motion for
+ * the dilation and as motion for the erosion (so the closing never shrinks
+ * the mask at the border). mask is H x W (1 = motion). */
+void oracle_motion_mask(const uint8_t *rgb, int64_t pitch, const uint8_t *prev, int64_t prev_pitch, int W, int H,
+                        float tau, int c, uint8_t *tmp, uint8_t *mask)
+{
+    const float t2 = mul32(tau, tau);
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            int d2 = 0;
+            for (int ch = 0; ch < 3; ++ch) {
+                const int d = (int)rgb[(int64_t)y * pitch + 3 * x + ch] - (int)prev[(int64_t)y * prev_pitch + 3 * x + ch];
+                d2 += d * d;
+            }
+            mask[(int64_t)y * W + x] = (float)d2 > t2;
+        }
+    /* dilation */
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            uint8_t m = 0;
+            for (int dy = -c; dy <= c; ++dy)
+                for (int dx = -c; dx <= c; ++dx) {
+                    const int qx = x + dx, qy = y + dy;
+                    if (qx >= 0 && qx < W && qy >= 0 && qy < H && mask[(int64_t)qy * W + qx]) m = 1;
+                }
+            tmp[(int64_t)y * W + x] = m;
+        }
+    /* erosion */
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            uint8_t m = 1;
+            for (int dy = -c; dy <= c; ++dy)
+                for (int dx = -c; dx <= c; ++dx) {
+                    const int qx = x + dx, qy = y + dy;
+                    if (qx >= 0 && qx < W && qy >= 0 && qy < H && !tmp[(int64_t)qy * W + qx]) m = 0;
+                }
+            mask[(int64_t)y * W + x] = m;
+        }
+}
+
+/* Projection with afterimage removal: as oracle_project, but a point of a scan
+ * that is not the most recent one is dropped where the motion mask is set.
+ * newest = 1 marks the most recent scan. */
+int64_t oracle_project_masked(const float M[12], const float *xyz, int64_t n, int64_t stride_floats, int W, int H,
+                              float fx, float fy, float cx, float cy, const uint8_t *mask, int newest, uint32_t *zbuf)
+{
+    int64_t kept = 0;
+    for (int64_t k = 0; k < n; ++k) {
+        const float x = xyz[k * stride_floats + 0];
+        const float y = xyz[k * stride_floats + 1];
+        const float z = xyz[k * stride_floats + 2];
+        float c[3];
+        for (int i = 0; i < 3; ++i) {
+            float s = mul32(M[i * 4 + 0], x);
+            s = add32(s, mul32(M[i * 4 + 1], y));
+            s = add32(s, mul32(M[i * 4 + 2], z));
+            s = add32(s, M[i * 4 + 3]);
+            c[i] = s;
+        }
+        if (!(c[2] > 0.0f) || !(c[2] < INFINITY)) continue;
+        const float u = add32(mul32(fx, div32(c[0], c[2])), cx);
+        const float v = add32(mul32(fy, div32(c[1], c[2])), cy);
+        if (!(u >= 0.0f && u < (float)W && v >= 0.0f && v < (float)H)) continue;
+        const int i = (int)floor((double)u);
+        const int j = (int)floor((double)v);
+        if (!newest && mask && mask[(int64_t)j * W + i]) continue;
+        const uint32_t b = f32_bits(c[2]);
+        uint32_t *cell = &zbuf[(int64_t)j * W + i];
+        if (b < *cell) *cell = b;
+        ++kept;
+    }
+    return kept;
+}
+
+/* Contour removal (Sec. 5: unreliable depths near contours are removed by a
+ * threshold on the gradient of the depth map). Reading: a valid pixel p is
+ * dropped iff some valid 4-neighbour q has |D(q) - D(p)| > t * D(p) (FP32, the
+ * step relative to the pixel's depth). depth is FP32 here: the decision is
+ * taken on the map the filter produced, in its precision. Outputs: valid_out
+ * and depth_out (0 where dropped). */
+int64_t oracle_contour(const float *depth, const uint8_t *valid, int W, int H, float t, float *depth_out,
+                       uint8_t *valid_out)
+{
+    int64_t dropped = 0;
+    for (int y = 0; y < H; ++y)
+        for (int x = 0; x < W; ++x) {
+            const int64_t o = (int64_t)y * W + x;
+            depth_out[o] = depth[o];
+            valid_out[o] = valid[o];
+            if (!valid[o]) continue;
+            const float d = depth[o];
+            const float lim = mul32(t, d);
+            const int qx[4] = {x - 1, x + 1, x, x}, qy[4] = {y, y, y - 1, y + 1};
+            int drop = 0;
+            for (int k = 0; k < 4; ++k) {
+                if (qx[k] < 0 || qx[k] >= W || qy[k] < 0 || qy[k] >= H) continue;
+                const int64_t q = (int64_t)qy[k] * W + qx[k];
+                if (!valid[q]) continue;
+                if (fabsf(add32(depth[q], -d)) > lim) drop = 1;
+            }
+            if (drop) {
+                valid_out[o] = 0;
+                depth_out[o] = 0.0f;
+                ++dropped;
+            }
+        }
+    return dropped;
+}
