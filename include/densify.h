@@ -133,6 +133,20 @@ typedef struct densify_stage {
  *                 and the plain kernel) on that batch and keep the fastest for
  *                 the context's lifetime; with DENSIFY_TUNE_CACHE=<file> in the
  *                 environment, choices are stored there and reused.
+ * Preprocessing of the merged scans (Sec. 4.1) and post-filtering (Sec. 5);
+ * each is off at 0 (the paper gives no values):
+ *   occlusion_radius, occlusion_margin   occluded points: an observed pixel
+ *                 deeper than the mean observed depth of its (2 r + 1)^2
+ *                 window by more than the margin is removed before filtering
+ *                 (radius 1-16).
+ *   motion_threshold, motion_close_radius   afterimages: pixels whose RGB
+ *                 distance to the previous frame (frame.prev_rgb) exceeds the
+ *                 threshold, closed with a square element of this radius,
+ *                 keep only the points of the most recent scan
+ *                 (frame.newest_scan).
+ *   contour_threshold   contours: a dense pixel with a 4-neighbour whose depth
+ *                 differs by more than this fraction of its own depth is
+ *                 dropped before back-projection.
  */
 typedef struct densify_params {
     int32_t num_stages;
@@ -150,7 +164,12 @@ typedef struct densify_params {
     int32_t launch_policy;
     int32_t kernel_variant;
     int32_t autotune;
-    int32_t reserved[4];
+    int32_t occlusion_radius;
+    float occlusion_margin;
+    float motion_threshold;
+    int32_t motion_close_radius;
+    float contour_threshold;
+    int32_t reserved[3];
 } densify_params;
 
 /* Pinhole intrinsics of the camera (Sec. 2: calibrated in advance). */
@@ -186,6 +205,11 @@ typedef struct densify_scan {
  *                FP32 depths, 0x7F800000 where empty)
  *   out_coarse   ceil(H/pool) x ceil(W/pool) float: first-stage depth
  *   out_coarse_valid  same size, uint8: first-stage validity
+ * Afterimage removal (params.motion_threshold > 0):
+ *   prev_rgb     the viewpoint's previous RGB frame (same size; NULL: skip)
+ *   newest_scan  index of the most recent scan; the others lose their points
+ *                inside the motion mask
+ *   out_motion   optional H x W uint8 copy of the closed motion mask
  * memory says whether every pointer above is a device or a host pointer. */
 typedef struct densify_frame {
     densify_intrinsics K;
@@ -203,6 +227,11 @@ typedef struct densify_frame {
     uint32_t *out_zbuf;
     float *out_coarse;
     uint8_t *out_coarse_valid;
+    const uint8_t *prev_rgb;
+    int64_t prev_rgb_pitch;
+    int32_t newest_scan;
+    int32_t reserved_f;
+    uint8_t *out_motion;
 } densify_frame;
 
 /* Fill *p with the paper's two-stage configuration (Sec. 5: pool 3, radius 4

@@ -26,6 +26,7 @@ constexpr int kPtsPerChunk = kThreads * kPtsPerThread;        // 1024 points
 constexpr int kZbWordsPerChunk = 8192;                        // z-buffer clear
 constexpr int kPoolPerChunk = kThreads;                       // coarse pixels
 constexpr int kBpChunk = 4096;                                // compaction: 8 warps x 512 px
+constexpr int kPxChunk = 1024;                                // per-pixel kernels: 256 threads x 4 px
 
 struct ScanDev {
     const float *xyz;
@@ -60,6 +61,17 @@ struct alignas(64) FrameDev {
     float *cssum;            // Hc x cpitch: pooled depth sum
     float2 *s1;              // Hc x cpitch: first-stage depth and validity (0/1)
     uint32_t *chunk_cnt;     // n_bp_chunks valid-pixel counts
+    // preprocessing (Sec. 4.1) and post-filtering (Sec. 5); NULL / 0 when off
+    const uint8_t *prev_rgb;     // previous RGB frame (afterimage removal)
+    int64_t prev_pitch;
+    uint8_t *motion;             // H x W motion mask after the closing
+    uint8_t *motion_tmp;         // H x W raw mask, then the dilation
+    uint32_t *zbuf_raw;          // projection target when occluded points are removed into zbuf
+    int32_t newest_scan;         // scan kept inside the motion mask
+    int32_t n_px_chunks;         // ceil(W H / kPxChunk)
+    // filter outputs (== out_* unless contour removal rewrites them)
+    float *flt_depth;
+    uint8_t *flt_valid;
     // outputs (caller memory, or arena staging for host frames)
     float *out_depth;
     uint8_t *out_valid;
@@ -80,6 +92,8 @@ struct BatchDev {
     int32_t t1_pre[kMaxBatch + 1];                 // tiles of the first (or only) filter
     int32_t t2_pre[kMaxBatch + 1];                 // tiles of the full-resolution second filter
     int32_t bp_pre[kMaxBatch + 1];                 // compaction chunks
+    int32_t px_pre[kMaxBatch + 1];                 // pixel chunks of the motion / contour kernels
+    int32_t oc_pre[kMaxBatch + 1];                 // tiles of the occlusion kernel
     FrameDev f[kMaxBatch];
 };
 
@@ -111,8 +125,24 @@ __device__ __forceinline__ int find_segment(const int32_t *pre, int n, int item)
 
 // Kernel launchers. Grids are persistent: a multiple of the SM count.
 enum KernelId {
-    K_PREP = 0, K_PROJECT, K_POOL, K_JBF1, K_JBF2, K_BP_COUNT, K_BP_WRITE, K_COUNT
+    K_PREP = 0, K_MOTION, K_DILATE, K_ERODE, K_PROJECT, K_OCCLUSION, K_POOL, K_JBF1, K_JBF2, K_CONTOUR,
+    K_BP_COUNT, K_BP_WRITE, K_COUNT
 };
+
+// Preprocessing / post-filtering (k_prepost.cu).
+struct PrepostArgs {
+    float motion_t2;      // squared RGB distance threshold (FP32)
+    int32_t close_radius; // closing structuring element radius
+    int32_t occ_radius;   // averaging window radius
+    float occ_margin;     // depth margin behind the window average
+    float contour_t;      // relative depth step threshold
+};
+cudaError_t launch_motion(const BatchDev *b, const PrepostArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_morph(const BatchDev *b, const PrepostArgs &a, bool dilate, int grid, cudaStream_t s);
+cudaError_t launch_occlusion(const BatchDev *b, const PrepostArgs &a, int grid, cudaStream_t s);
+cudaError_t launch_contour(const BatchDev *b, const PrepostArgs &a, int grid, cudaStream_t s);
+int occupancy_prepost(KernelId k);
+constexpr int kOccTile = 32;   // occlusion kernel output tile (32 x 32)
 
 cudaError_t launch_prep(const BatchDev *b, int grid, cudaStream_t s);
 cudaError_t launch_project(const BatchDev *b, int grid, cudaStream_t s);

@@ -199,8 +199,8 @@ __global__ void __launch_bounds__(256) jbf_kernel(const BatchDev *__restrict__ B
                     if (F.out_coarse) F.out_coarse[o] = out;
                     if (F.out_coarse_valid) F.out_coarse_valid[o] = val[k];
                 } else {
-                    F.out_depth[o] = out;
-                    F.out_valid[o] = val[k];
+                    F.flt_depth[o] = out;
+                    F.flt_valid[o] = val[k];
                 }
             }
         }

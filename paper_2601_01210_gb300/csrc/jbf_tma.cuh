@@ -277,39 +277,26 @@ __global__ void __launch_bounds__(256, 2) jbf_tma_kernel(const BatchDev *__restr
                 d = __uint_as_float(z);
                 return z != kEmpty;
             };
-            // interior columns sx = R .. R+31 in groups of 4: their 12 colour bytes start on a
-            // word boundary (byte offset 12 g + RGB_LEAD)
-            for (int q = threadIdx.x; q < SH * 8; q += 256) {
-                const int sy = q >> 3, g4 = q & 7;
-                const int sx0 = R + 4 * g4, gx0 = x0 + 4 * g4, gy = y0 - R + sy;
-                const int i0 = sy * SW + sx0;
-                if (gy < 0 || gy >= gh || gx0 >= gw) {
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) put(i0 + k, 0.0f, 0.0f, 0.0f, 0.0f, false);
-                    continue;
-                }
-                const uint32_t *wp = reinterpret_cast<const uint32_t *>(rgbraw + sy * G::RGB_BX + 12 * g4 + G::RGB_LEAD);
-                const uint32_t w0 = wp[0], w1 = wp[1], w2 = wp[2];
-                const uint32_t col[4] = {w0, (w0 >> 24) | (w1 << 8), (w1 >> 16) | (w2 << 16), w2 >> 8};
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
+            // warp per staged row, lane per column: consecutive lanes write consecutive records
+            for (int sy = warp; sy < SH; sy += 8) {
+                const int gy = y0 - R + sy;
+                const bool row_in = gy >= 0 && gy < gh;
+                const uint8_t *rowp = rgbraw + sy * G::RGB_BX;
+                for (int sx = lane; sx < SW; sx += 32) {
+                    const int gx = x0 - R + sx;
                     float d = 0.0f;
-                    const bool in = gx0 + k < gw;
-                    const bool o = in && depth_of(sy, sx0 + k, gx0 + k, gy, d);
-                    put(i0 + k, (float)(col[k] & 0xFFu), (float)((col[k] >> 8) & 0xFFu), (float)((col[k] >> 16) & 0xFFu),
+                    bool o = false;
+                    uint32_t col = 0;
+                    if (row_in && gx >= 0 && gx < gw) {
+                        // the pixel's 3 bytes from two aligned words (bytes past the row are never used)
+                        const int off = 3 * sx - 3 * R + G::RGB_LEAD;
+                        const uint32_t *wp = reinterpret_cast<const uint32_t *>(rowp + (off & ~3));
+                        col = __funnelshift_r(wp[0], wp[1], (off & 3) * 8);
+                        o = depth_of(sy, sx, gx, gy, d);
+                    }
+                    put(sy * SW + sx, (float)(col & 0xFFu), (float)((col >> 8) & 0xFFu), (float)((col >> 16) & 0xFFu),
                         d, o);
                 }
-            }
-            // halo columns sx < R and sx >= R + 32, one pixel each
-            for (int q = threadIdx.x; q < SH * 2 * R; q += 256) {
-                const int sy = q / (2 * R), h = q - sy * 2 * R;
-                const int sx = h < R ? h : 32 + h;
-                const int gx = x0 - R + sx, gy = y0 - R + sy;
-                float d = 0.0f;
-                const bool in = gx >= 0 && gx < gw && gy >= 0 && gy < gh;
-                const bool o = in && depth_of(sy, sx, gx, gy, d);
-                const uint8_t *p = rgbraw + sy * G::RGB_BX + 3 * sx - 3 * R + G::RGB_LEAD;
-                put(sy * SW + sx, o ? (float)p[0] : 0.0f, o ? (float)p[1] : 0.0f, o ? (float)p[2] : 0.0f, d, o);
             }
             __syncthreads();
         }
@@ -435,8 +422,8 @@ __global__ void __launch_bounds__(256, 2) jbf_tma_kernel(const BatchDev *__restr
                     if (F.out_coarse) F.out_coarse[o] = out;
                     if (F.out_coarse_valid) F.out_coarse_valid[o] = v;
                 } else {
-                    F.out_depth[o] = out;
-                    F.out_valid[o] = v;
+                    F.flt_depth[o] = out;
+                    F.flt_valid[o] = v;
                 }
             }
         };

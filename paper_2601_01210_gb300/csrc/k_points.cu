@@ -55,7 +55,7 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(BatchDev *__restrict__ B
         const int64_t n = (int64_t)F.zpitch * F.H;
         const int64_t w0 = (int64_t)c * kZbWordsPerChunk;
         const int64_t w1 = min(n, w0 + kZbWordsPerChunk);
-        uint32_t *z = F.zbuf;
+        uint32_t *z = F.zbuf_raw;
         // arena buffers are 256-byte aligned and w0 is a multiple of 4
         const int64_t v1 = w0 + ((w1 - w0) & ~int64_t(3));
         const uint4 e4 = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
@@ -70,7 +70,7 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(BatchDev *__restrict__ B
 // each thread takes 4 points with 16-byte vector loads.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void project_one(const float (&M)[12], float x, float y, float z, const FrameDev &F,
-                                            uint32_t *zbuf) {
+                                            uint32_t *zbuf, bool old_scan) {
     const float xc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[0], x), __fmul_rn(M[1], y)), __fmul_rn(M[2], z)), M[3]);
     const float yc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[4], x), __fmul_rn(M[5], y)), __fmul_rn(M[6], z)), M[7]);
     const float zc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[8], x), __fmul_rn(M[9], y)), __fmul_rn(M[10], z)), M[11]);
@@ -80,6 +80,8 @@ __device__ __forceinline__ void project_one(const float (&M)[12], float x, float
     if (!(u >= 0.0f && u < (float)F.W && v >= 0.0f && v < (float)F.H)) return;
     const int i = __float2int_rz(u);   // u >= 0: truncation is floor
     const int j = __float2int_rz(v);
+    // afterimage removal: points of older scans are dropped where the scene moved
+    if (old_scan && F.motion && F.motion[(int64_t)j * F.W + i]) return;
     atomicMin(zbuf + (int64_t)j * F.zpitch + i, __float_as_uint(zc));
 }
 
@@ -95,19 +97,20 @@ __global__ void __launch_bounds__(kThreads) project_kernel(const BatchDev *__res
         for (int e = 0; e < 12; ++e) M[e] = S.M[e];
         const int64_t p0 = (int64_t)(item - B->pt_pre[seg]) * kPtsPerChunk + (int64_t)threadIdx.x * kPtsPerThread;
         if (p0 >= S.count) continue;
-        uint32_t *zbuf = F.zbuf;
+        uint32_t *zbuf = F.zbuf_raw;
+        const bool old_scan = (seg % kMaxScans) != F.newest_scan;
         if (S.stride_floats == 3) {
             if (p0 + 4 <= S.count) {
                 // 4 packed points = 48 bytes = 3 aligned float4 (base 16-byte aligned, p0 % 4 == 0)
                 const float4 *q = reinterpret_cast<const float4 *>(S.xyz + p0 * 3);
                 const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
-                project_one(M, a.x, a.y, a.z, F, zbuf);
-                project_one(M, a.w, b.x, b.y, F, zbuf);
-                project_one(M, b.z, b.w, c.x, F, zbuf);
-                project_one(M, c.y, c.z, c.w, F, zbuf);
+                project_one(M, a.x, a.y, a.z, F, zbuf, old_scan);
+                project_one(M, a.w, b.x, b.y, F, zbuf, old_scan);
+                project_one(M, b.z, b.w, c.x, F, zbuf, old_scan);
+                project_one(M, c.y, c.z, c.w, F, zbuf, old_scan);
             } else {
                 for (int64_t p = p0; p < S.count; ++p)
-                    project_one(M, __ldg(S.xyz + 3 * p), __ldg(S.xyz + 3 * p + 1), __ldg(S.xyz + 3 * p + 2), F, zbuf);
+                    project_one(M, __ldg(S.xyz + 3 * p), __ldg(S.xyz + 3 * p + 1), __ldg(S.xyz + 3 * p + 2), F, zbuf, old_scan);
             }
         } else {
             const float4 *q = reinterpret_cast<const float4 *>(S.xyz) + p0;
@@ -116,7 +119,7 @@ __global__ void __launch_bounds__(kThreads) project_kernel(const BatchDev *__res
             for (int k = 0; k < 4; ++k) {
                 if (k < n) {
                     const float4 a = __ldg(q + k);
-                    project_one(M, a.x, a.y, a.z, F, zbuf);
+                    project_one(M, a.x, a.y, a.z, F, zbuf, old_scan);
                 }
             }
         }

@@ -94,6 +94,8 @@ extern "C" DENSIFY_API densify_status densify_frame_noalloc(const densify_params
     const std::string perr = check_params(*params);
     if (!perr.empty()) return fail(DENSIFY_E_INVALID, perr);
     if (f->memory != DENSIFY_MEM_DEVICE) return fail(DENSIFY_E_INVALID, "the no-allocation entry takes device frames");
+    if (params->occlusion_radius > 0 || params->motion_threshold > 0.0f || params->contour_threshold > 0.0f)
+        return fail(DENSIFY_E_INVALID, "the no-allocation entry runs without occlusion, afterimage or contour removal");
     const int W = f->K.width, H = f->K.height;
     if (W < 1 || H < 1 || W > 16384 || H > 16384) return fail(DENSIFY_E_INVALID, "image size must be in 1..16384");
     if (f->num_scans < 0 || f->num_scans > kMaxScans) return fail(DENSIFY_E_INVALID, "num_scans must be in 0..3");
@@ -183,6 +185,8 @@ extern "C" DENSIFY_API densify_status densify_frame_noalloc(const densify_params
     d.rgb = f->rgb;
     d.rgb_pitch = f->rgb_pitch;
     d.zbuf = reinterpret_cast<uint32_t *>(base + off_zbuf);
+    d.zbuf_raw = d.zbuf;
+    d.newest_scan = -1;
     if (params->num_stages == 2) {
         d.cguide = reinterpret_cast<float4 *>(base + off_cg);
         d.cssum = reinterpret_cast<float *>(base + off_cs);
@@ -193,6 +197,8 @@ extern "C" DENSIFY_API densify_status densify_frame_noalloc(const densify_params
     d.chunk_cnt = reinterpret_cast<uint32_t *>(base + off_cnt);
     d.out_depth = f->out_depth;
     d.out_valid = f->out_valid;
+    d.flt_depth = f->out_depth;
+    d.flt_valid = f->out_valid;
     if (params->emit_points) {
         d.out_points = reinterpret_cast<float4 *>(f->out_points);
         d.points_cap = f->out_points_cap;

@@ -39,8 +39,9 @@ using namespace dz;
 
 namespace {
 
-const char *const kKernelNames[K_COUNT] = {"prep_compose_clear", "project_zbuf", "pool3", "jbf_stage1",
-                                           "jbf_stage2",          "bp_count",     "bp_write"};
+const char *const kKernelNames[K_COUNT] = {"prep_compose_clear", "motion_mask", "motion_dilate", "motion_erode",
+                                           "project_zbuf",       "occlusion",   "pool3",         "jbf_stage1",
+                                           "jbf_stage2",         "contour",     "bp_count",      "bp_write"};
 
 constexpr uint64_t kAlign = 256;
 uint64_t align_up(uint64_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
@@ -96,6 +97,8 @@ private:
 // Scratch layout of one frame inside its arena block.
 struct Layout {
     uint64_t zbuf = 0, cguide = 0, cssum = 0, s1 = 0, chunk = 0, depth = 0, valid = 0;
+    uint64_t zbuf_raw = 0, motion = 0, motion_tmp = 0, prev = 0, depth_f = 0, valid_f = 0;
+    bool has_motion = false;
     uint64_t pts[kMaxScans] = {0, 0, 0}, rgb = 0, points = 0, npts = 0, coarse = 0, coarse_valid = 0;
     int64_t rgb_pitch = 0;   // pitch of the staged RGB copy (0: the caller's frame is used in place)
     float4 *points_direct = nullptr;    // device view of a page-locked host point buffer
@@ -185,6 +188,7 @@ struct densify_ctx {
     cudaStream_t d2h_stream = nullptr;   // exact-size point copies of host frames
     densify_params p{};
     StageArgs sa[2]{};
+    PrepostArgs pp{};
     void *arena_base = nullptr;
     Arena arena;
     std::vector<Slot> slots;
@@ -337,6 +341,11 @@ std::string validate_params(const densify_params &p) {
     if (p.launch_policy != 0 && p.launch_policy != 1) return "launch_policy must be 0 or 1";
     if (p.kernel_variant != 0 && p.kernel_variant != 1) return "kernel_variant must be 0 or 1";
     if (p.autotune != 0 && p.autotune != 1) return "autotune must be 0 or 1";
+    if (p.occlusion_radius < 0 || p.occlusion_radius > 16) return "occlusion_radius must be in 0..16";
+    if (!std::isfinite(p.occlusion_margin) || p.occlusion_margin < 0.0f) return "occlusion_margin must be >= 0";
+    if (!std::isfinite(p.motion_threshold) || p.motion_threshold < 0.0f) return "motion_threshold must be >= 0";
+    if (p.motion_close_radius < 0 || p.motion_close_radius > 16) return "motion_close_radius must be in 0..16";
+    if (!std::isfinite(p.contour_threshold) || p.contour_threshold < 0.0f) return "contour_threshold must be >= 0";
     return "";
 }
 
@@ -358,6 +367,10 @@ std::string validate_frame(const densify_ctx *c, const densify_frame *f) {
             return "scan xyz must be 16-byte aligned";
     }
     if (!f->rgb) return "rgb is NULL";
+    if (f->prev_rgb && f->prev_rgb_pitch < 3 * (int64_t)W) return "prev_rgb_pitch must be >= 3 * width";
+    if (c->p.motion_threshold > 0.0f && f->prev_rgb && f->num_scans > 0 &&
+        (f->newest_scan < 0 || f->newest_scan >= f->num_scans))
+        return "newest_scan must index one of the scans";
     if (f->rgb_pitch < 3 * (int64_t)W) return "rgb_pitch must be >= 3 * width";
     if (c->p.emit_points) {
         if (!f->out_points_n) return "out_points_n is NULL while points are on";
@@ -392,6 +405,17 @@ Layout layout_of(const densify_params &p, const densify_frame *f) {
     };
     const int64_t zp = (W + 3) & ~int64_t(3);
     L.zbuf = take(zp * H * 4);
+    if (p.occlusion_radius > 0) L.zbuf_raw = take(zp * H * 4);
+    L.has_motion = p.motion_threshold > 0.0f && f->prev_rgb;
+    if (L.has_motion) {
+        L.motion = take(npx);
+        L.motion_tmp = take(npx);
+        if (host) L.prev = take((uint64_t)npx * 3);
+    }
+    if (p.contour_threshold > 0.0f) {
+        L.depth_f = take(npx * 4);
+        L.valid_f = take(npx);
+    }
     if (p.num_stages == 2) {
         const int64_t Wc = (W + p.pool - 1) / p.pool, Hc = (H + p.pool - 1) / p.pool;
         const int64_t cp = (Wc + 3) & ~int64_t(3);
@@ -461,6 +485,15 @@ void build_frame_dev(densify_ctx *c, FrameRec &r) {
     d.rgb_pitch = L.rgb_pitch ? L.rgb_pitch : f->rgb_pitch;
     d.zpitch = (d.W + 3) & ~3;
     d.zbuf = (uint32_t *)(base + L.zbuf);
+    d.zbuf_raw = c->p.occlusion_radius > 0 ? (uint32_t *)(base + L.zbuf_raw) : d.zbuf;
+    d.newest_scan = f->newest_scan;
+    d.n_px_chunks = ceil_div((int64_t)d.W * d.H, kPxChunk);
+    if (L.has_motion) {
+        d.motion = (uint8_t *)(base + L.motion);
+        d.motion_tmp = (uint8_t *)(base + L.motion_tmp);
+        d.prev_rgb = host ? (const uint8_t *)(base + L.prev) : f->prev_rgb;
+        d.prev_pitch = host ? (int64_t)d.W * 3 : f->prev_rgb_pitch;
+    }
     if (c->p.num_stages == 2) {
         d.cguide = (float4 *)(base + L.cguide);
         d.cssum = (float *)(base + L.cssum);
@@ -472,6 +505,9 @@ void build_frame_dev(densify_ctx *c, FrameRec &r) {
     d.chunk_cnt = (uint32_t *)(base + L.chunk);
     d.out_depth = L.own_depth ? (float *)(base + L.depth) : f->out_depth;
     d.out_valid = L.own_valid ? (uint8_t *)(base + L.valid) : f->out_valid;
+    const bool contour = c->p.contour_threshold > 0.0f;
+    d.flt_depth = contour ? (float *)(base + L.depth_f) : d.out_depth;
+    d.flt_valid = contour ? (uint8_t *)(base + L.valid_f) : d.out_valid;
     if (c->p.emit_points) {
         d.out_points = host ? (L.points_direct ? L.points_direct : (float4 *)(base + L.points)) : (float4 *)f->out_points;
         d.points_cap = f->out_points_cap;
@@ -485,6 +521,7 @@ void fill_batch(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &tk) {
     b.n_frames = n;
     b.status = sl.d_status;
     b.zb_pre[0] = b.pt_pre[0] = b.pool_pre[0] = b.t1_pre[0] = b.t2_pre[0] = b.bp_pre[0] = 0;
+    b.px_pre[0] = b.oc_pre[0] = 0;
     const int nst = c->p.num_stages;
     const int r1 = c->p.stage[0].radius, r2 = nst == 2 ? c->p.stage[1].radius : 0;
     (void)r1;
@@ -505,6 +542,8 @@ void fill_batch(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &tk) {
         b.t1_pre[i + 1] = b.t1_pre[i] + ceil_div(g1w, 32) * ceil_div(g1h, th1);
         b.t2_pre[i + 1] = b.t2_pre[i] + (nst == 2 ? ceil_div(d.W, 32) * ceil_div(d.H, th2) : 0);
         b.bp_pre[i + 1] = b.bp_pre[i] + (c->p.emit_points ? d.n_bp_chunks : 0);
+        b.px_pre[i + 1] = b.px_pre[i] + d.n_px_chunks;
+        b.oc_pre[i + 1] = b.oc_pre[i] + ceil_div(d.W, kOccTile) * ceil_div(d.H, kOccTile);
     }
 }
 
@@ -596,7 +635,14 @@ densify_status autotune(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &t
                 cudaError_t e = cudaMemcpyAsync(sl.d, sl.h, bytes, cudaMemcpyHostToDevice, sl.stream);
                 // inputs of this stage
                 if (e == cudaSuccess) e = launch_prep(sl.d, c->grid[K_PREP], sl.stream);
+                if (e == cudaSuccess && c->p.motion_threshold > 0.0f) {
+                    e = launch_motion(sl.d, c->pp, c->grid[K_MOTION], sl.stream);
+                    if (e == cudaSuccess) e = launch_morph(sl.d, c->pp, true, c->grid[K_DILATE], sl.stream);
+                    if (e == cudaSuccess) e = launch_morph(sl.d, c->pp, false, c->grid[K_ERODE], sl.stream);
+                }
                 if (e == cudaSuccess) e = launch_project(sl.d, c->grid[K_PROJECT], sl.stream);
+                if (e == cudaSuccess && c->p.occlusion_radius > 0)
+                    e = launch_occlusion(sl.d, c->pp, c->grid[K_OCCLUSION], sl.stream);
                 if (e == cudaSuccess && c->p.num_stages == 2) e = launch_pool(sl.d, c->p.pool, c->grid[K_POOL], sl.stream);
                 if (e == cudaSuccess && i == 1) e = launch_filter(c, 0, sl.d, sl.stream);
                 if (e == cudaSuccess) e = launch_filter(c, i, sl.d, sl.stream);   // warm-up
@@ -683,8 +729,20 @@ densify_status issue_kernels(densify_ctx *c, Slot &sl, cudaStream_t s, bool reco
     CU(mark(-1), "event");
     CU(launch_prep(b, c->grid[K_PREP], s), "prep launch");
     CU(mark(K_PREP), "event");
+    if (c->p.motion_threshold > 0.0f) {
+        CU(launch_motion(b, c->pp, c->grid[K_MOTION], s), "motion launch");
+        CU(mark(K_MOTION), "event");
+        CU(launch_morph(b, c->pp, true, c->grid[K_DILATE], s), "dilate launch");
+        CU(mark(K_DILATE), "event");
+        CU(launch_morph(b, c->pp, false, c->grid[K_ERODE], s), "erode launch");
+        CU(mark(K_ERODE), "event");
+    }
     CU(launch_project(b, c->grid[K_PROJECT], s), "project launch");
     CU(mark(K_PROJECT), "event");
+    if (c->p.occlusion_radius > 0) {
+        CU(launch_occlusion(b, c->pp, c->grid[K_OCCLUSION], s), "occlusion launch");
+        CU(mark(K_OCCLUSION), "event");
+    }
     if (nst == 2) {
         CU(launch_pool(b, c->p.pool, c->grid[K_POOL], s), "pool launch");
         CU(mark(K_POOL), "event");
@@ -695,6 +753,10 @@ densify_status issue_kernels(densify_ctx *c, Slot &sl, cudaStream_t s, bool reco
     } else {
         CU(launch_filter(c, 0, b, s), "filter launch");
         CU(mark(K_JBF1), "event");
+    }
+    if (c->p.contour_threshold > 0.0f) {
+        CU(launch_contour(b, c->pp, c->grid[K_CONTOUR], s), "contour launch");
+        CU(mark(K_CONTOUR), "event");
     }
     if (c->p.emit_points) {
         CU(launch_bp_count(b, c->grid[K_BP_COUNT], s), "compaction count launch");
@@ -740,6 +802,14 @@ densify_status launch_batch(densify_ctx *c, int si) {
                                    sl.stream),
                    "points upload");
     }
+    // previous frame of host frames (afterimage removal)
+    for (uint64_t t : tk) {
+        FrameRec &r = c->frames[t];
+        if (!r.L.has_motion || r.fr.memory != DENSIFY_MEM_HOST) continue;
+        CU(cudaMemcpy2DAsync((void *)r.dev.prev_rgb, (size_t)r.dev.prev_pitch, r.fr.prev_rgb, (size_t)r.fr.prev_rgb_pitch,
+                             (size_t)r.fr.K.width * 3, (size_t)r.fr.K.height, cudaMemcpyHostToDevice, sl.stream),
+           "previous frame upload");
+    }
     // RGB staging (host frames, and device frames whose base or pitch is not 16-byte aligned)
     for (uint64_t t : tk) {
         FrameRec &r = c->frames[t];
@@ -769,6 +839,15 @@ densify_status launch_batch(densify_ctx *c, int si) {
     } else {
         densify_status st = issue_kernels(c, sl, sl.stream, c->p.timing != 0);
         if (st != DENSIFY_OK) return st;
+    }
+    // debug motion mask out, both memory kinds
+    for (uint64_t t : tk) {
+        FrameRec &r = c->frames[t];
+        if (!r.fr.out_motion || !r.L.has_motion) continue;
+        CU(cudaMemcpyAsync(r.fr.out_motion, r.dev.motion, (size_t)r.fr.K.width * r.fr.K.height,
+                           r.fr.memory == DENSIFY_MEM_HOST ? cudaMemcpyDeviceToHost : cudaMemcpyDeviceToDevice,
+                           sl.stream),
+           "motion copy");
     }
     // debug z-buffer out (row pitch W), both memory kinds
     for (uint64_t t : tk) {
@@ -1042,6 +1121,12 @@ densify_status densify_create(const densify_params *params, int device, void *cu
     c->grid[K_POOL] = sms * occupancy_pool_bp(K_POOL);
     c->grid[K_BP_COUNT] = sms * occupancy_pool_bp(K_BP_COUNT);
     c->grid[K_BP_WRITE] = sms * occupancy_pool_bp(K_BP_WRITE);
+    for (KernelId k : {K_MOTION, K_DILATE, K_ERODE, K_OCCLUSION, K_CONTOUR}) c->grid[k] = sms * occupancy_prepost(k);
+    c->pp.motion_t2 = params->motion_threshold * params->motion_threshold;
+    c->pp.close_radius = params->motion_close_radius;
+    c->pp.occ_radius = params->occlusion_radius;
+    c->pp.occ_margin = params->occlusion_margin;
+    c->pp.contour_t = params->contour_threshold;
     c->sms = sms;
     for (int i = 0; i < params->num_stages; ++i) {
         const int kind = params->num_stages == 1 ? 0 : (i == 0 ? 1 : 2);

@@ -57,7 +57,12 @@ class densify_params(C.Structure):
         ("launch_policy", C.c_int32),
         ("kernel_variant", C.c_int32),
         ("autotune", C.c_int32),
-        ("reserved", C.c_int32 * 4),
+        ("occlusion_radius", C.c_int32),
+        ("occlusion_margin", C.c_float),
+        ("motion_threshold", C.c_float),
+        ("motion_close_radius", C.c_int32),
+        ("contour_threshold", C.c_float),
+        ("reserved", C.c_int32 * 3),
     ]
 
 
@@ -88,6 +93,11 @@ class densify_frame(C.Structure):
         ("out_zbuf", C.c_void_p),
         ("out_coarse", C.c_void_p),
         ("out_coarse_valid", C.c_void_p),
+        ("prev_rgb", C.c_void_p),
+        ("prev_rgb_pitch", C.c_int64),
+        ("newest_scan", C.c_int32),
+        ("reserved_f", C.c_int32),
+        ("out_motion", C.c_void_p),
     ]
 
 
@@ -224,7 +234,8 @@ def _ptr(t):
 
 def make_frame(width, height, fx, fy, cx, cy, cam_to_world, rgb, scans, *, out_depth=None, out_valid=None,
                out_points=None, out_points_n=None, out_zbuf=None, out_coarse=None, out_coarse_valid=None,
-               memory=DENSIFY_MEM_DEVICE, rgb_pitch=None) -> densify_frame:
+               memory=DENSIFY_MEM_DEVICE, rgb_pitch=None, prev_rgb=None, newest_scan=None,
+               out_motion=None) -> densify_frame:
     """Pack a densify_frame. ``scans`` is a list of (xyz tensor (N, 3|4) float32,
     lidar_to_world 4x4 sequence). Tensors must stay alive until the ticket is
     collected; the struct holds raw pointers only."""
@@ -248,6 +259,10 @@ def make_frame(width, height, fx, fy, cx, cy, cam_to_world, rgb, scans, *, out_d
     f.out_zbuf = _ptr(out_zbuf)
     f.out_coarse = _ptr(out_coarse)
     f.out_coarse_valid = _ptr(out_coarse_valid)
+    f.prev_rgb = _ptr(prev_rgb)
+    f.prev_rgb_pitch = 3 * int(width) if prev_rgb is not None else 0
+    f.newest_scan = len(scans) - 1 if newest_scan is None else int(newest_scan)
+    f.out_motion = _ptr(out_motion)
     return f
 
 

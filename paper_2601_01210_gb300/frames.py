@@ -15,7 +15,7 @@ from .densify import DENSIFY_MEM_DEVICE, DENSIFY_MEM_HOST, make_frame
 class FrameBuffers:
     def __init__(self, camera, rgb, scans, *, device="cuda", num_stages=2, pool=3, emit_points=True,
                  debug=False, memory=DENSIFY_MEM_DEVICE, points_cap=None, xyzw=False, depth_out=True,
-                 pinned=True):
+                 pinned=True, prev_rgb=None):
         self.camera = camera
         W, H = camera.width, camera.height
         self.W, self.H = W, H
@@ -30,6 +30,8 @@ class FrameBuffers:
             return t.to(dev)
 
         self.rgb = put(rgb)
+        self.prev_rgb = put(prev_rgb) if prev_rgb is not None else None
+        self.motion = torch.zeros((H, W), dtype=torch.uint8, device=dev, **pin) if (debug and prev_rgb is not None) else None
         self.scans = []
         for xyz, l2w in scans:
             x = np.ascontiguousarray(xyz, np.float32)
@@ -52,7 +54,8 @@ class FrameBuffers:
         self.frame = make_frame(W, H, camera.fx, camera.fy, camera.cx, camera.cy, camera.cam_to_world, self.rgb,
                                 self.scans, out_depth=self.depth, out_valid=self.valid, out_points=self.points,
                                 out_points_n=self.npoints, out_zbuf=self.zbuf, out_coarse=self.coarse,
-                                out_coarse_valid=self.coarse_valid, memory=memory, rgb_pitch=3 * W)
+                                out_coarse_valid=self.coarse_valid, memory=memory, rgb_pitch=3 * W,
+                                prev_rgb=self.prev_rgb, out_motion=self.motion)
 
     def n_points(self) -> int:
         return int(self.npoints.item()) if self.npoints is not None else 0
@@ -70,6 +73,8 @@ class FrameBuffers:
             out["n"] = self.n_points()
         if self.zbuf is not None:
             out["zbuf"] = self.zbuf.cpu().numpy().view(np.uint32)
+        if self.motion is not None:
+            out["motion"] = self.motion.cpu().numpy()
         if self.coarse is not None:
             out["coarse"] = self.coarse.cpu().numpy()
             out["coarse_valid"] = self.coarse_valid.cpu().numpy()
