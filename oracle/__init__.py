@@ -89,6 +89,9 @@ def lib():
             L.oracle_project_masked.restype = _i64
             L.oracle_contour.argtypes = [_f32p, _u8p, _int, _int, _flt, _f32p, _u8p]
             L.oracle_contour.restype = _i64
+            L.oracle_jbf_grad.argtypes = [_f64p, _f64p, _f64p, C.c_void_p, _int, _int, _int, _dbl, _dbl,
+                                          _f64p, _u8p, _f64p]
+            L.oracle_jbf_grad.restype = None
             _lib = L
     return _lib
 
@@ -239,6 +242,56 @@ def contour(depth32, valid, t):
     vo = np.empty_like(v)
     n = lib().oracle_contour(d, v, W, H, float(t), do, vo)
     return do.reshape(H, W), vo.reshape(H, W), n
+
+
+def jbf_grad(guide, beta, beta_d, r, sigma_p, sigma_c, dbeta_d=None):
+    """Eq. (1)-(4) and its derivatives: (out, valid, dout[..., 4]) with dout =
+    d/dsigma_p, d/dsigma_c of this stage, then the derivatives carried in by
+    dbeta_d (shape (H, W, 2)) from an earlier stage."""
+    H, W = beta.shape
+    out = np.zeros(H * W)
+    valid = np.zeros(H * W, np.uint8)
+    dout = np.zeros(H * W * 4)
+    db = np.ascontiguousarray(dbeta_d, np.float64).ravel() if dbeta_d is not None else None
+    lib().oracle_jbf_grad(np.ascontiguousarray(guide, np.float64).ravel(),
+                          np.ascontiguousarray(beta, np.float64).ravel(),
+                          np.ascontiguousarray(beta_d, np.float64).ravel(),
+                          db.ctypes.data if db is not None else None, W, H, r, sigma_p, sigma_c, out, valid, dout)
+    return out.reshape(H, W), valid.reshape(H, W), dout.reshape(H, W, 4)
+
+
+def sigma_loss_grad(cam, rgb, scans, gt, num_stages=2, stages=((4, 5.0, 20.0), (2, 5.0, 20.0)), pool_factor=3):
+    """Mean squared depth error against ground truth (pixels with a filtered
+    depth and gt > 0) and its gradient with respect to (sigma_p, sigma_c) of
+    stage[0], then stage[1] (zeros for a single stage)."""
+    W, H = cam.width, cam.height
+    zbuf = np.full(H * W, ZBUF_EMPTY, np.uint32)
+    for xyz, l2w in scans:
+        _, M32 = compose(cam.cam_to_world, l2w)
+        project(M32, xyz, W, H, cam.fx, cam.fy, cam.cx, cam.cy, zbuf)
+    guide = rgb.astype(np.float64)
+    if num_stages == 1:
+        r, sp, sc = stages[0]
+        D, B = zbuf_to_depth(zbuf)
+        out, valid, dout = jbf_grad(guide, B.reshape(H, W), (D * B).reshape(H, W), r, sp, sc)
+        d4 = np.concatenate([dout[..., :2], np.zeros_like(dout[..., :2])], -1)
+    else:
+        f = pool_factor
+        ssum, cnt, guide_c = pool(zbuf, rgb, W, H, f)
+        (r1, sp1, sc1), (r2, sp2, sc2) = stages
+        d1, v1, dd1 = jbf_grad(guide_c, cnt, ssum, r1, sp1, sc1)
+        beta2, betad2 = upsample(d1, v1, f, W, H)
+        # restored derivative of the stage-2 input with respect to (sp1, sc1)
+        up = lambda a: np.kron(a, np.ones((f, f)))[:H, :W]
+        dbd = np.stack([beta2 * up(dd1[..., 0]), beta2 * up(dd1[..., 1])], -1)
+        out, valid, dout = jbf_grad(guide, beta2, betad2, r2, sp2, sc2, dbd)
+        d4 = np.stack([dout[..., 2], dout[..., 3], dout[..., 0], dout[..., 1]], -1)
+    m = valid.astype(bool) & (gt > 0)
+    n = int(m.sum())
+    err = out - gt
+    loss = float((err[m] ** 2).sum() / n)
+    grad = (2.0 * err[m, None] * d4[m]).sum(0) / n
+    return loss, grad, n
 
 
 # ----------------------------------------------------------------------------

@@ -509,3 +509,63 @@ int64_t oracle_contour(const float *depth, const uint8_t *valid, int W, int H, f
         }
     return dropped;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Gradient of the joint bilateral filter with respect to its sigmas (Sec. 4:
+ * the Gaussian variances can be optimised by backpropagation when dense
+ * ground truth exists). With e = ||dI||^2 / (2 sc^2) + ||dx||^2 / (2 sp^2) and
+ * w = exp(-e): dw/dsc = w ||dI||^2 / sc^3, dw/dsp = w ||dx||^2 / sp^3. For
+ * out = N / Wt (N = sum w beta_d, Wt = sum w beta):
+ *   d out / d theta = (sum dw/dtheta beta_d - out sum dw/dtheta beta) / Wt.
+ * dbeta_d (2 channels per pixel, or NULL) is the derivative of beta_d with
+ * respect to an earlier stage's (sp, sc); it passes through the weights:
+ *   d out / d theta_prev = sum w dbeta_d / Wt.
+ * dout receives 4 channels per pixel: d/dsp, d/dsc, d/dsp_prev, d/dsc_prev. */
+void oracle_jbf_grad(const double *guide, const double *beta, const double *beta_d, const double *dbeta_d,
+                     int W, int H, int r, double sp, double sc, double *out, uint8_t *valid, double *dout)
+{
+    for (int py = 0; py < H; ++py) {
+        for (int px = 0; px < W; ++px) {
+            const double *Ip = &guide[((int64_t)py * W + px) * 3];
+            double N = 0, Wt = 0, Np = 0, Wp = 0, Nc = 0, Wc = 0, Q0 = 0, Q1 = 0;
+            int any = 0;
+            for (int qy = py - r; qy <= py + r; ++qy) {
+                for (int qx = px - r; qx <= px + r; ++qx) {
+                    if (qx < 0 || qx >= W || qy < 0 || qy >= H) continue;
+                    const int64_t q = (int64_t)qy * W + qx;
+                    if (!(beta[q] > 0.0)) continue;
+                    const double *Iq = &guide[q * 3];
+                    const double dc = (Iq[0] - Ip[0]) * (Iq[0] - Ip[0]) + (Iq[1] - Ip[1]) * (Iq[1] - Ip[1]) +
+                                      (Iq[2] - Ip[2]) * (Iq[2] - Ip[2]);
+                    const double ds = (double)(qx - px) * (qx - px) + (double)(qy - py) * (qy - py);
+                    const double w = exp(-(dc / (2.0 * sc * sc) + ds / (2.0 * sp * sp)));
+                    const double wp = w * ds / (sp * sp * sp), wc = w * dc / (sc * sc * sc);
+                    N += w * beta_d[q];
+                    Wt += w * beta[q];
+                    Np += wp * beta_d[q];
+                    Wp += wp * beta[q];
+                    Nc += wc * beta_d[q];
+                    Wc += wc * beta[q];
+                    if (dbeta_d) {
+                        Q0 += w * dbeta_d[q * 2];
+                        Q1 += w * dbeta_d[q * 2 + 1];
+                    }
+                    any = 1;
+                }
+            }
+            const int64_t o = (int64_t)py * W + px;
+            valid[o] = (uint8_t)any;
+            if (!any) {
+                out[o] = 0.0;
+                dout[o * 4] = dout[o * 4 + 1] = dout[o * 4 + 2] = dout[o * 4 + 3] = 0.0;
+                continue;
+            }
+            const double D = N / Wt;
+            out[o] = D;
+            dout[o * 4 + 0] = (Np - D * Wp) / Wt;
+            dout[o * 4 + 1] = (Nc - D * Wc) / Wt;
+            dout[o * 4 + 2] = Q0 / Wt;
+            dout[o * 4 + 3] = Q1 / Wt;
+        }
+    }
+}
