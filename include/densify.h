@@ -329,6 +329,24 @@ DENSIFY_API int32_t densify_describe(densify_ctx *ctx, char *buf, int32_t cap);
 DENSIFY_API densify_status densify_frame_noalloc(const densify_params *params, const densify_frame *frame,
                                                  void *cuda_stream);
 
+/* Gradient of the depth error with respect to the filter's sigmas (Sec. 4:
+ * when dense ground truth exists, the Gaussian variances can be optimised by
+ * backpropagation). Runs the context's path on one device frame (calibration,
+ * projection, pooling, the filter stages with their sigma derivatives,
+ * chained through the restore of the two-stage form) and returns
+ *   *loss      mean over pixels with a filtered depth and gt_depth > 0 of
+ *              (depth - gt)^2,
+ *   grad[4]    d loss / d (stage[0].sigma_p, stage[0].sigma_c,
+ *              stage[1].sigma_p, stage[1].sigma_c) (the last two 0 for a
+ *              single stage),
+ *   *n_pixels  the number of pixels in the mean.
+ * gt_depth is a device H x W float map. Synchronous: waits for in-flight
+ * batches, uses arena scratch, returns when the numbers are on the host.
+ * Preprocessing and contour removal are not part of it. Errors: E_INVALID,
+ * E_AGAIN (scratch full), E_CUDA. */
+DENSIFY_API densify_status densify_sigma_grad(densify_ctx *ctx, const densify_frame *frame, const float *gt_depth,
+                                              double *loss, double *grad, int64_t *n_pixels);
+
 /* ABI version of the loaded library (DENSIFY_ABI_VERSION). */
 DENSIFY_API int32_t densify_abi_version(void);
 

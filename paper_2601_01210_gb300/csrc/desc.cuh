@@ -60,6 +60,7 @@ struct alignas(64) FrameDev {
     float4 *cguide;          // Hc x cpitch: pooled mean r, g, b and observation count
     float *cssum;            // Hc x cpitch: pooled depth sum
     float2 *s1;              // Hc x cpitch: first-stage depth and validity (0/1)
+    float2 *g1;              // Hc x cpitch: first-stage depth derivatives (sigma gradient only)
     uint32_t *chunk_cnt;     // n_bp_chunks valid-pixel counts
     // preprocessing (Sec. 4.1) and post-filtering (Sec. 5); NULL / 0 when off
     const uint8_t *prev_rgb;     // previous RGB frame (afterimage removal)

@@ -98,9 +98,9 @@ __device__ __forceinline__ int floor_div3(int a) { return a >= 0 ? a / 3 : -((2 
 constexpr int ceil_to(int x, int m) { return (x + m - 1) / m * m; }
 
 // Tile geometry shared by the kernel and the host (tensor-map boxes).
-template <int SRC, int R, int KP>
+template <int SRC, int R, int KP, int NW_ = 8>
 struct TmaGeom {
-    static constexpr int TW = 32, NW = 8, TH = NW * KP, SW = TW + 2 * R, SH = TH + 2 * R;
+    static constexpr int TW = 32, NW = NW_, TH = NW * KP, SW = TW + 2 * R, SH = TH + 2 * R;
     // RGB bytes: box starts at byte 3*x0 - RGB_LEAD (x0 is a multiple of 32, so 3*x0 of 16)
     static constexpr int RGB_LEAD = ceil_to(3 * R, 16);
     static constexpr int RGB_BX = ceil_to(3 * TW + 3 * R + RGB_LEAD, 16);
@@ -157,10 +157,12 @@ __device__ __forceinline__ __half2 h2exp2_approx(__half2 x) {
     return h2bits(y);
 }
 
-template <int SRC, int R, int KP, bool HALF = false>
-__global__ void __launch_bounds__(256, 2) jbf_tma_kernel(const BatchDev *__restrict__ B, const StageArgs a) {
-    using G = TmaGeom<SRC, R, KP>;
+template <int SRC, int R, int KP, bool HALF = false, int NW = 8>
+__global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 1) jbf_tma_kernel(const BatchDev *__restrict__ B,
+                                                                           const StageArgs a) {
+    using G = TmaGeom<SRC, R, KP, NW>;
     constexpr int TW = G::TW, TH = G::TH, SW = G::SW, SH = G::SH, T = 2 * R + 1;
+    constexpr int NT = NW * 32;   // threads
     static_assert(!HALF || (SRC != SRC_COARSE && KP % 2 == 0), "FP16 form: full-resolution stages, row pairs");
     extern __shared__ __align__(128) uint8_t smem[];
     // raw buffer b: A part at smem + b * (RAW_A + RAW_B), B part right after it
@@ -277,31 +279,18 @@ __global__ void __launch_bounds__(256, 2) jbf_tma_kernel(const BatchDev *__restr
                 d = __uint_as_float(z);
                 return z != kEmpty;
             };
-            // warp per staged row, lane per column: consecutive lanes write consecutive records
-            for (int sy = warp; sy < SH; sy += 8) {
-                const int gy = y0 - R + sy;
-                const bool row_in = gy >= 0 && gy < gh;
-                const uint8_t *rowp = rgbraw + sy * G::RGB_BX;
-                for (int sx = lane; sx < SW; sx += 32) {
-                    const int gx = x0 - R + sx;
-                    float d = 0.0f;
-                    bool o = false;
-                    uint32_t col = 0;
-                    if (row_in && gx >= 0 && gx < gw) {
-                        // the pixel's 3 bytes from two aligned words (bytes past the row are never used)
-                        const int off = 3 * sx - 3 * R + G::RGB_LEAD;
-                        const uint32_t *wp = reinterpret_cast<const uint32_t *>(rowp + (off & ~3));
-                        col = __funnelshift_r(wp[0], wp[1], (off & 3) * 8);
-                        o = depth_of(sy, sx, gx, gy, d);
-                    }
-                    put(sy * SW + sx, (float)(col & 0xFFu), (float)((col >> 8) & 0xFFu), (float)((col >> 16) & 0xFFu),
-                        d, o);
-                }
+            for (int i = threadIdx.x; i < SH * SW; i += NT) {
+                const int sy = i / SW, sx = i - sy * SW;
+                const int gx = x0 - R + sx, gy = y0 - R + sy;
+                float d = 0.0f;
+                const bool o = gx >= 0 && gx < gw && gy >= 0 && gy < gh && depth_of(sy, sx, gx, gy, d);
+                const uint8_t *p = rgbraw + sy * G::RGB_BX + 3 * sx - 3 * R + G::RGB_LEAD;
+                put(i, o ? (float)p[0] : 0.0f, o ? (float)p[1] : 0.0f, o ? (float)p[2] : 0.0f, d, o);
             }
             __syncthreads();
         }
         // ---- validity rows: bit x of horw[sy] = some observation at staged row sy, columns x .. x + 2R
-        for (int sy = warp; sy < SH; sy += 8) {
+        for (int sy = warp; sy < SH; sy += NW) {
             bool o0, o1;
             if (SRC == SRC_COARSE) {
                 o0 = cg[sy * SW + lane].w > 0.0f;

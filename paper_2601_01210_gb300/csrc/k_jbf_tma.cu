@@ -7,11 +7,12 @@ namespace dz {
 
 namespace {
 
-template <int SRC, int R, int KP>
+template <int SRC, int R, int KP, int NW>
 void fill_info(TmaKernelInfo *o) {
-    using G = TmaGeom<SRC, R, KP>;
+    using G = TmaGeom<SRC, R, KP, NW>;
     o->supported = 1;
     o->kp = KP;
+    o->threads = NW * 32;
     o->tile_w = G::TW;
     o->tile_h = G::TH;
     o->smem = G::SMEM;
@@ -22,82 +23,88 @@ void fill_info(TmaKernelInfo *o) {
     o->cssum_box[0] = G::S_BX; o->cssum_box[1] = G::S_BY;
 }
 
-template <int SRC, int R, int KP, bool H>
+template <int SRC, int R, int KP, bool H, int NW>
 cudaError_t prep() {
-    return cudaFuncSetAttribute(jbf_tma_kernel<SRC, R, KP, H>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                TmaGeom<SRC, R, KP>::SMEM);
+    return cudaFuncSetAttribute(jbf_tma_kernel<SRC, R, KP, H, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                TmaGeom<SRC, R, KP, NW>::SMEM);
 }
 
-template <int SRC, int R, int KP, bool H>
+template <int SRC, int R, int KP, bool H, int NW>
 cudaError_t go(const BatchDev *b, const StageArgs &a, int grid, cudaStream_t s) {
-    jbf_tma_kernel<SRC, R, KP, H><<<grid, 256, TmaGeom<SRC, R, KP>::SMEM, s>>>(b, a);
+    jbf_tma_kernel<SRC, R, KP, H, NW><<<grid, NW * 32, TmaGeom<SRC, R, KP, NW>::SMEM, s>>>(b, a);
     return cudaGetLastError();
 }
 
-template <int SRC, int R, int KP, bool H>
+template <int SRC, int R, int KP, bool H, int NW>
 int occ() {
     int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, jbf_tma_kernel<SRC, R, KP, H>, 256, TmaGeom<SRC, R, KP>::SMEM);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, jbf_tma_kernel<SRC, R, KP, H, NW>, NW * 32,
+                                                  TmaGeom<SRC, R, KP, NW>::SMEM);
     return n > 0 ? n : 1;
 }
 
-// (source, radius, rows per thread, FP16 form)
-#define DZ_TMA_CASES(X)           \
-    X(SRC_UP, 1, 8, false)        \
-    X(SRC_UP, 2, 8, false)        \
-    X(SRC_UP, 2, 4, false)        \
-    X(SRC_UP, 3, 4, false)        \
-    X(SRC_COARSE, 2, 4, false)    \
-    X(SRC_COARSE, 4, 4, false)    \
-    X(SRC_COARSE, 4, 2, false)    \
-    X(SRC_ZBUF, 2, 8, false)      \
-    X(SRC_ZBUF, 4, 8, false)      \
-    X(SRC_ZBUF, 4, 4, false)      \
-    X(SRC_ZBUF, 7, 4, false)      \
-    X(SRC_UP, 1, 8, true)         \
-    X(SRC_UP, 2, 8, true)         \
-    X(SRC_UP, 2, 4, true)         \
-    X(SRC_UP, 3, 4, true)         \
-    X(SRC_ZBUF, 2, 8, true)       \
-    X(SRC_ZBUF, 4, 8, true)       \
-    X(SRC_ZBUF, 4, 4, true)       \
-    X(SRC_ZBUF, 7, 4, true)
+// (source, radius, rows per thread, FP16 form, warps per CTA); the first listed
+// variant of a (source, radius, form) is the default before autotuning
+#define DZ_TMA_CASES(X)               \
+    X(SRC_UP, 1, 8, false, 8)         \
+    X(SRC_UP, 2, 8, false, 8)         \
+    X(SRC_UP, 2, 8, false, 16)        \
+    X(SRC_UP, 2, 4, false, 8)         \
+    X(SRC_UP, 3, 4, false, 8)         \
+    X(SRC_COARSE, 2, 4, false, 8)     \
+    X(SRC_COARSE, 4, 4, false, 8)     \
+    X(SRC_COARSE, 4, 2, false, 8)     \
+    X(SRC_ZBUF, 2, 8, false, 8)       \
+    X(SRC_ZBUF, 4, 8, false, 8)       \
+    X(SRC_ZBUF, 4, 4, false, 8)       \
+    X(SRC_ZBUF, 7, 4, false, 8)       \
+    X(SRC_UP, 1, 8, true, 8)          \
+    X(SRC_UP, 2, 8, true, 8)          \
+    X(SRC_UP, 2, 8, true, 16)         \
+    X(SRC_UP, 2, 4, true, 8)          \
+    X(SRC_UP, 3, 4, true, 8)          \
+    X(SRC_ZBUF, 2, 8, true, 8)        \
+    X(SRC_ZBUF, 4, 8, true, 8)        \
+    X(SRC_ZBUF, 4, 4, true, 8)        \
+    X(SRC_ZBUF, 7, 4, true, 8)
 
 }  // namespace
 
-int jbf_tma_variants(int src, int r, bool half, int *kps, int cap) {
+int jbf_tma_variants(int src, int r, bool half, TmaVariant *out, int cap) {
     int n = 0;
-#define X(S, RR, K, H) if (src == S && r == RR && half == H && n < cap) kps[n++] = K;
+#define X(S, RR, K, H, NW) if (src == S && r == RR && half == H && n < cap) out[n++] = TmaVariant{K, NW};
     DZ_TMA_CASES(X)
 #undef X
     return n;
 }
 
-bool jbf_tma_info(int src, int r, int kp, bool half, TmaKernelInfo *out) {
+bool jbf_tma_info(int src, int r, TmaVariant v, bool half, TmaKernelInfo *out) {
     *out = TmaKernelInfo{};
-#define X(S, RR, K, H) if (src == S && r == RR && kp == K && half == H) { fill_info<S, RR, K>(out); return true; }
+#define X(S, RR, K, H, NW) \
+    if (src == S && r == RR && v.kp == K && v.nw == NW && half == H) { fill_info<S, RR, K, NW>(out); return true; }
     DZ_TMA_CASES(X)
 #undef X
     return false;
 }
 
-cudaError_t jbf_tma_prepare(int src, int r, int kp, bool half) {
-#define X(S, RR, K, H) if (src == S && r == RR && kp == K && half == H) return prep<S, RR, K, H>();
+cudaError_t jbf_tma_prepare(int src, int r, TmaVariant v, bool half) {
+#define X(S, RR, K, H, NW) if (src == S && r == RR && v.kp == K && v.nw == NW && half == H) return prep<S, RR, K, H, NW>();
     DZ_TMA_CASES(X)
 #undef X
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_jbf_tma(int src, int r, int kp, bool half, const BatchDev *b, const StageArgs &a, int grid,
+cudaError_t launch_jbf_tma(int src, int r, TmaVariant v, bool half, const BatchDev *b, const StageArgs &a, int grid,
                            cudaStream_t s) {
-#define X(S, RR, K, H) if (src == S && r == RR && kp == K && half == H) return go<S, RR, K, H>(b, a, grid, s);
+#define X(S, RR, K, H, NW) \
+    if (src == S && r == RR && v.kp == K && v.nw == NW && half == H) return go<S, RR, K, H, NW>(b, a, grid, s);
     DZ_TMA_CASES(X)
 #undef X
     return cudaErrorInvalidValue;
 }
 
-int occupancy_jbf_tma(int src, int r, int kp, bool half) {
-#define X(S, RR, K, H) if (src == S && r == RR && kp == K && half == H) return occ<S, RR, K, H>();
+int occupancy_jbf_tma(int src, int r, TmaVariant v, bool half) {
+#define X(S, RR, K, H, NW) if (src == S && r == RR && v.kp == K && v.nw == NW && half == H) return occ<S, RR, K, H, NW>();
     DZ_TMA_CASES(X)
 #undef X
     return 1;

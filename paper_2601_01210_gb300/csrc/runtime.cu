@@ -32,6 +32,7 @@
 
 #include "../../include/densify.h"
 #include "desc.cuh"
+#include "grad.h"
 #include "runtime_internal.h"
 #include "tma_info.h"
 
@@ -139,7 +140,8 @@ struct FilterSel {
     bool tma = false;
     bool half = false;   // FP16 form
     int src = 0;         // TMA source kind
-    int kp = 0;          // output rows per thread (tile height / 8)
+    int kp = 0;          // output rows per thread
+    int nw = 8;          // warps per CTA (tile height = kp * nw)
     int tile_h = 0;
     int occ = 1;         // resident CTAs per SM
     TmaKernelInfo info{};
@@ -257,8 +259,8 @@ std::vector<FilterSel> filter_candidates(const densify_params &p, int kind, int 
     // FP16: the full-resolution stage (the pooled first stage stays FP32)
     const bool half = p.precision == DENSIFY_FP16 && kind != 1;
     if (allowed) {
-        int kps[8];
-        const int n = jbf_tma_variants(src, r, half, kps, 8);
+        TmaVariant vs[8];
+        const int n = jbf_tma_variants(src, r, half, vs, 8);
         for (int i = 0; i < n; ++i) {
             FilterSel s;
             s.kind = kind;
@@ -266,8 +268,9 @@ std::vector<FilterSel> filter_candidates(const densify_params &p, int kind, int 
             s.tma = true;
             s.half = half;
             s.src = src;
-            s.kp = kps[i];
-            jbf_tma_info(src, r, kps[i], half, &s.info);
+            s.kp = vs[i].kp;
+            s.nw = vs[i].nw;
+            jbf_tma_info(src, r, vs[i], half, &s.info);
             s.tile_h = s.info.tile_h;
             out.push_back(s);
         }
@@ -328,8 +331,8 @@ std::string validate_params(const densify_params &p) {
         if (p.kernel_variant != 0) return "the FP16 form runs in the TMA kernels (kernel_variant 0)";
         const int full = p.num_stages == 2 ? 1 : 0;   // the full-resolution stage
         const int kind = p.num_stages == 2 ? 2 : 0;
-        int kps[8];
-        if (jbf_tma_variants(kind == 2 ? TMA_SRC_UP : TMA_SRC_ZBUF, p.stage[full].radius, true, kps, 8) == 0 ||
+        TmaVariant vs[8];
+        if (jbf_tma_variants(kind == 2 ? TMA_SRC_UP : TMA_SRC_ZBUF, p.stage[full].radius, true, vs, 8) == 0 ||
             (kind == 2 && (p.pool != 3 || p.stage2_input != 0)))
             return "FP16 form available for the full-resolution stage with radius 1-3 (pool 3, stage2_input 0) "
                    "after a first stage, or radius 2, 4, 7 as the only stage";
@@ -598,7 +601,9 @@ void cache_store(const std::string &key, const std::string &val) {
     }
 }
 
-std::string cand_name(const FilterSel &f) { return std::string(f.tma ? "tma" : "plain") + ":kp" + std::to_string(f.kp); }
+std::string cand_name(const FilterSel &f) {
+    return std::string(f.tma ? "tma" : "plain") + ":kp" + std::to_string(f.kp) + ":nw" + std::to_string(f.nw);
+}
 
 densify_status autotune(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &tk) {
     int64_t px = 0;
@@ -676,7 +681,7 @@ densify_status autotune(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &t
 cudaError_t launch_filter(densify_ctx *c, int i, const BatchDev *b, cudaStream_t s) {
     const FilterSel &f = c->sel[i];
     const int k = i == 0 ? K_JBF1 : K_JBF2;
-    if (f.tma) return launch_jbf_tma(f.src, f.radius, f.kp, f.half, b, c->sa[i], c->grid[k], s);
+    if (f.tma) return launch_jbf_tma(f.src, f.radius, TmaVariant{f.kp, f.nw}, f.half, b, c->sa[i], c->grid[k], s);
     if (f.kind == 0) return launch_jbf_single(f.radius, b, c->sa[i], c->grid[k], s);
     if (f.kind == 1) return launch_jbf_coarse(f.radius, b, c->sa[i], c->grid[k], s);
     return launch_jbf_up(f.radius, b, c->sa[i], c->grid[k], s);
@@ -1134,9 +1139,9 @@ densify_status densify_create(const densify_params *params, int device, void *cu
         if (c->cands[i].empty()) return bail(DENSIFY_E_INVALID, "no kernel for filter stage " + std::to_string(i));
         for (FilterSel &f : c->cands[i]) {
             if (f.tma) {
-                if ((e = jbf_tma_prepare(f.src, f.radius, f.kp, f.half)) != cudaSuccess)
+                if ((e = jbf_tma_prepare(f.src, f.radius, TmaVariant{f.kp, f.nw}, f.half)) != cudaSuccess)
                     return bail(DENSIFY_E_CUDA, std::string("filter setup: ") + cudaGetErrorString(e));
-                f.occ = occupancy_jbf_tma(f.src, f.radius, f.kp, f.half);
+                f.occ = occupancy_jbf_tma(f.src, f.radius, TmaVariant{f.kp, f.nw}, f.half);
             } else {
                 f.occ = kind == 0 ? occupancy_jbf_single(f.radius) : kind == 1 ? occupancy_jbf_coarse(f.radius)
                                                                               : occupancy_jbf_up(f.radius);
@@ -1260,13 +1265,90 @@ int32_t densify_kernel_times(densify_ctx *c, const char **names, double *total_u
     return n;
 }
 
+densify_status densify_sigma_grad(densify_ctx *c, const densify_frame *frame, const float *gt, double *loss,
+                                  double *grad, int64_t *n_pixels) {
+    if (!c) return fail(nullptr, DENSIFY_E_INVALID, "ctx is NULL");
+    if (!gt || !loss || !grad) return fail(c, DENSIFY_E_INVALID, "gt_depth, loss and grad must not be NULL");
+    if (c->dead) return DENSIFY_E_CUDA;
+    const std::string ferr = validate_frame(c, frame);
+    if (!ferr.empty()) return fail(c, DENSIFY_E_INVALID, ferr);
+    if (frame->memory != DENSIFY_MEM_DEVICE) return fail(c, DENSIFY_E_INVALID, "the sigma gradient takes device frames");
+    DeviceGuard guard(c->device);
+    // in-flight batches first (bounded: 10 s each)
+    while (any_busy(c)) {
+        densify_status st = wait_some(c, now_ns() + 10ll * 1000 * 1000 * 1000);
+        if (st != DENSIFY_OK) return st == DENSIFY_E_TIMEOUT ? fail(c, st, "waiting for in-flight batches") : st;
+        if ((st = progress(c, false)) != DENSIFY_OK) return st;
+    }
+    densify_params p = c->p;
+    p.emit_points = 0;
+    FrameRec r;
+    r.fr = *frame;
+    r.fr.out_zbuf = nullptr;
+    r.L = layout_of(p, &r.fr);
+    const int grid = c->sms * 4;
+    const int pool = p.num_stages == 2 ? p.pool : 1;
+    const int64_t Wc = (frame->K.width + pool - 1) / pool, Hc = (frame->K.height + pool - 1) / pool;
+    const uint64_t off_g1 = r.L.total;
+    const uint64_t off_part = off_g1 + align_up((uint64_t)((Wc + 3) & ~3) * Hc * 8);
+    const uint64_t off_out = off_part + align_up((uint64_t)grid * 6 * 8);
+    const uint64_t hdr = offsetof(BatchDev, f) + sizeof(FrameDev);
+    const uint64_t off_batch = off_out + 256;
+    const uint64_t total = off_batch + align_up(hdr);
+    if (total > c->arena.size()) return fail(c, DENSIFY_E_NOMEM, "frame scratch exceeds hbm_budget_bytes");
+    if (!c->arena.alloc(total, &r.off)) return fail(c, DENSIFY_E_AGAIN, "scratch arena full");
+    char *base = (char *)c->arena_base + r.off;
+    build_frame_dev(c, r);
+    FrameDev &d = r.dev;
+    d.zbuf_raw = d.zbuf;       // no preprocessing in the gradient
+    d.motion = nullptr;
+    d.g1 = (float2 *)(base + off_g1);
+    std::vector<uint8_t> hbuf(hdr, 0);
+    BatchDev *hb = reinterpret_cast<BatchDev *>(hbuf.data());
+    hb->n_frames = 1;
+    hb->zb_pre[1] = ceil_div((int64_t)d.zpitch * d.H, kZbWordsPerChunk);
+    for (int s = 0; s < kMaxScans; ++s) hb->pt_pre[s + 1] = hb->pt_pre[s] + ceil_div(d.scans[s].count, kPtsPerChunk);
+    hb->pool_pre[1] = p.num_stages == 2 ? ceil_div((int64_t)d.Wc * d.Hc, kPoolPerChunk) : 0;
+    hb->px_pre[1] = d.n_px_chunks;
+    std::memcpy(&hb->f[0], &d, sizeof(FrameDev));
+    GradArgs ga{};
+    ga.two_stage = p.num_stages == 2;
+    ga.pool = pool;
+    for (int i = 0; i < p.num_stages; ++i) {
+        const double log2e = 1.4426950408889634, sp = p.stage[i].sigma_p, sc = p.stage[i].sigma_c;
+        ga.s[i].radius = p.stage[i].radius;
+        ga.s[i].kc = (float)(log2e / (2.0 * sc * sc));
+        ga.s[i].kp = (float)(log2e / (2.0 * sp * sp));
+        ga.s[i].inv_sc3 = (float)(1.0 / (sc * sc * sc));
+        ga.s[i].inv_sp3 = (float)(1.0 / (sp * sp * sp));
+    }
+    cudaStream_t s = c->slots[0].stream;
+    BatchDev *bd = (BatchDev *)(base + off_batch);
+    double host_out[6] = {0, 0, 0, 0, 0, 0};
+    cudaError_t e = cudaMemcpyAsync(bd, hb, hdr, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = launch_prep(bd, c->grid[K_PREP], s);
+    if (e == cudaSuccess) e = launch_project(bd, c->grid[K_PROJECT], s);
+    if (e == cudaSuccess && ga.two_stage) e = launch_pool(bd, pool, c->grid[K_POOL], s);
+    if (e == cudaSuccess) e = launch_grad(bd, ga, gt, (double *)(base + off_part), grid, (double *)(base + off_out), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, base + off_out, sizeof(host_out), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    c->arena.release(r.off, total);
+    if (e != cudaSuccess) return cuda_fail(c, e, "sigma gradient");
+    const double n = host_out[1];
+    *loss = n > 0 ? host_out[0] / n : 0.0;
+    for (int k = 0; k < 4; ++k) grad[k] = n > 0 ? host_out[2 + k] / n : 0.0;
+    if (n_pixels) *n_pixels = (int64_t)n;
+    return DENSIFY_OK;
+}
+
 int32_t densify_describe(densify_ctx *c, char *buf, int32_t cap) {
     if (!c) return 0;
     auto one = [&](const FilterSel &f) {
         char tmp[256];
         std::snprintf(tmp, sizeof tmp,
-                      "{\"kernel\": \"%s\", \"kp\": %d, \"tile\": [32, %d], \"fp16\": %s, \"ctas_per_sm\": %d%s",
-                      f.tma ? "tma" : "plain", f.kp, f.tile_h, f.half ? "true" : "false", f.occ,
+                      "{\"kernel\": \"%s\", \"kp\": %d, \"warps\": %d, \"tile\": [32, %d], \"fp16\": %s, "
+                      "\"ctas_per_sm\": %d%s",
+                      f.tma ? "tma" : "plain", f.kp, f.nw, f.tile_h, f.half ? "true" : "false", f.occ,
                       f.tuned_us >= 0.0f ? "" : "}");
         std::string s(tmp);
         if (f.tuned_us >= 0.0f) {

@@ -119,6 +119,8 @@ _SIGS = {
                               C.c_int32], C.c_int32),
     "densify_reset_kernel_times": ([C.c_void_p], None),
     "densify_describe": ([C.c_void_p, C.c_char_p, C.c_int32], C.c_int32),
+    "densify_sigma_grad": ([C.c_void_p, C.POINTER(densify_frame), C.c_void_p, C.POINTER(C.c_double),
+                            C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
     "densify_frame_noalloc": ([C.POINTER(densify_params), C.POINTER(densify_frame), C.c_void_p], C.c_int),
 }
 EXPORTED = tuple(_SIGS)
@@ -217,6 +219,16 @@ def densify_describe(ctx) -> str:
     buf = C.create_string_buffer(n + 1)
     lib().densify_describe(ctx, buf, n + 1)
     return buf.value.decode()
+
+
+def densify_sigma_grad(ctx, frame: densify_frame, gt_depth_ptr: int):
+    """(status, loss, grad[4], n_pixels) of the mean squared depth error against
+    the ground truth at ``gt_depth_ptr`` (device, H x W float)."""
+    loss = C.c_double(0.0)
+    grad = (C.c_double * 4)()
+    n = C.c_int64(0)
+    st = lib().densify_sigma_grad(ctx, C.byref(frame), C.c_void_p(gt_depth_ptr), C.byref(loss), grad, C.byref(n))
+    return st, loss.value, list(grad), n.value
 
 
 def densify_frame_noalloc(params: densify_params, frame: densify_frame, stream: int | None = None) -> int:
@@ -321,6 +333,13 @@ class Densifier:
 
     def kernel_times(self):
         return densify_kernel_times(self.ctx)
+
+    def sigma_grad(self, frame: densify_frame, gt_depth):
+        """(loss, grad[4], n) for a torch device tensor gt_depth (H, W)."""
+        st, loss, grad, n = densify_sigma_grad(self.ctx, frame, int(gt_depth.data_ptr()))
+        if st != DENSIFY_OK:
+            raise DensifyError(st, densify_last_error(self.ctx))
+        return loss, grad, n
 
     def describe(self):
         import json

@@ -43,7 +43,7 @@ def test_tuned_equals_untuned_and_cache_is_reused(tmp_path, monkeypatch, precisi
         if len(st["candidates"]) > 1:
             assert len(timed) == len(st["candidates"])
             best = min(timed, key=lambda c: c["tuned_us"])
-            assert (best["kernel"], best["kp"]) == (st["chosen"]["kernel"], st["chosen"]["kp"])
+            assert (best["kernel"], best["kp"], best["warps"]) == (st["chosen"]["kernel"], st["chosen"]["kp"], st["chosen"]["warps"])
     for a, b in zip(base, tuned):
         for k in ("valid", "rgba"):
             assert np.array_equal(a[k], b[k]), k
@@ -54,4 +54,4 @@ def test_tuned_equals_untuned_and_cache_is_reused(tmp_path, monkeypatch, precisi
     again, desc2 = _run(views, torch, precision=precision, autotune=1)
     assert cache.read_text().splitlines() == lines
     for s1, s2 in zip(desc["stages"], desc2["stages"]):
-        assert (s1["chosen"]["kernel"], s1["chosen"]["kp"]) == (s2["chosen"]["kernel"], s2["chosen"]["kp"])
+        assert (s1["chosen"]["kernel"], s1["chosen"]["kp"], s1["chosen"]["warps"]) == (s2["chosen"]["kernel"], s2["chosen"]["kp"], s2["chosen"]["warps"])
