@@ -22,6 +22,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <thread>
@@ -1303,8 +1304,8 @@ densify_status densify_sigma_grad(densify_ctx *c, const densify_frame *frame, co
     d.zbuf_raw = d.zbuf;       // no preprocessing in the gradient
     d.motion = nullptr;
     d.g1 = (float2 *)(base + off_g1);
-    std::vector<uint8_t> hbuf(hdr, 0);
-    BatchDev *hb = reinterpret_cast<BatchDev *>(hbuf.data());
+    std::unique_ptr<BatchDev> hbuf(new BatchDev());   // zeroed, correctly aligned
+    BatchDev *hb = hbuf.get();
     hb->n_frames = 1;
     hb->zb_pre[1] = ceil_div((int64_t)d.zpitch * d.H, kZbWordsPerChunk);
     for (int s = 0; s < kMaxScans; ++s) hb->pt_pre[s + 1] = hb->pt_pre[s] + ceil_div(d.scans[s].count, kPtsPerChunk);
