@@ -23,8 +23,8 @@ constexpr uint32_t kEmpty = 0x7F800000u;   // z-buffer cell with no depth (+inf)
 constexpr int kThreads = 256;
 constexpr int kPtsPerThread = 4;
 constexpr int kPtsPerChunk = kThreads * kPtsPerThread;        // 1024 points
-constexpr int kZbWordsPerChunk = 8192;                        // z-buffer clear
-constexpr int kPoolPerChunk = kThreads;                       // coarse pixels
+constexpr int kZbWordsPerChunk = 2048;                        // z-buffer clear
+constexpr int kPoolPerChunk = kThreads;                       // coarse pixels (one coarse row segment)
 constexpr int kBpChunk = 4096;                                // compaction: 8 warps x 512 px
 constexpr int kPxChunk = 1024;                                // per-pixel kernels: 256 threads x 4 px
 

@@ -12,36 +12,98 @@ namespace dz {
 // dropped because it cancels in the filter's ratio) and the mean RGB of the
 // block's in-image pixels as the coarse guide. Sums run in row-major order.
 // ---------------------------------------------------------------------------
+// Warp-cooperative form: one warp pools 32 consecutive coarse pixels of a
+// coarse row. The 3 full-resolution rows under them are read with coalesced
+// word loads into shared memory (z-buffer: 96 words a row; RGB: 288 bytes a
+// row when the row start is word aligned), then each lane sums its block.
+constexpr int kPoolWarps = kThreads / 32;
 __global__ void __launch_bounds__(kThreads) pool_kernel(const BatchDev *__restrict__ B, int f) {
+    __shared__ uint32_t sz[kPoolWarps][3][96];
+    __shared__ uint32_t sc[kPoolWarps][3][72];
     const int nf = B->n_frames;
     const int total = B->pool_pre[nf];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int fi = find_segment(B->pool_pre, nf, item);
         const FrameDev &F = B->f[fi];
-        const int idx = (item - B->pool_pre[fi]) * kPoolPerChunk + threadIdx.x;
-        if (idx >= F.Wc * F.Hc) continue;
-        const int I = idx % F.Wc, J = idx / F.Wc;
-        const int x0 = I * f, y0 = J * f;
-        const int x1 = min(x0 + f, F.W), y1 = min(y0 + f, F.H);
-        float s = 0.0f, cnt = 0.0f, r = 0.0f, g = 0.0f, b = 0.0f;
-        for (int y = y0; y < y1; ++y) {
-            const uint32_t *zr = F.zbuf + (int64_t)y * F.zpitch;
-            const uint8_t *cr = F.rgb + (int64_t)y * F.rgb_pitch;
-            for (int x = x0; x < x1; ++x) {
-                const uint32_t z = zr[x];
-                if (z != kEmpty) {
-                    s = __fadd_rn(s, __uint_as_float(z));
-                    cnt += 1.0f;
+        const int segs = (F.Wc + 255) / 256;                 // 256 coarse pixels per block item
+        const int t = item - B->pool_pre[fi];
+        const int J = t / segs;
+        const int I0 = (t - J * segs) * 256 + warp * 32;     // this warp's first coarse pixel
+        if (I0 >= F.Wc) continue;
+        const int I = I0 + lane;
+        const int y0 = J * f;
+        if (f == 3) {
+            const int x0 = 3 * I0;                            // first full-resolution column
+            const bool words = ((F.rgb_pitch & 3) == 0) && ((((uintptr_t)F.rgb) & 3u) == 0);
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const int y = y0 + r;
+                if (y >= F.H) break;
+                const uint32_t *zr = F.zbuf + (int64_t)y * F.zpitch;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const int x = x0 + lane + 32 * k;
+                    sz[warp][r][lane + 32 * k] = x < F.W ? zr[x] : kEmpty;
                 }
-                r += (float)cr[3 * x];
-                g += (float)cr[3 * x + 1];
-                b += (float)cr[3 * x + 2];
+                const uint8_t *cr = F.rgb + (int64_t)y * F.rgb_pitch + 3 * x0;
+                const int nbytes = 3 * min(96, F.W - x0);
+                if (words) {
+                    const uint32_t *cw = reinterpret_cast<const uint32_t *>(cr);
+                    for (int k = lane; k < 72; k += 32) sc[warp][r][k] = 4 * k < nbytes ? cw[k] : 0u;
+                } else {
+                    uint8_t *sb = reinterpret_cast<uint8_t *>(sc[warp][r]);
+                    for (int k = lane; k < 288; k += 32) sb[k] = k < nbytes ? cr[k] : 0;
+                }
             }
+            __syncwarp();
+            if (I < F.Wc) {
+                const int xa = 3 * I, xb = min(xa + 3, F.W), yb = min(y0 + 3, F.H);
+                float s = 0.0f, cnt = 0.0f, rr = 0.0f, gg = 0.0f, bb = 0.0f;
+                for (int y = y0; y < yb; ++y) {
+                    const int r = y - y0;
+                    const uint8_t *sb = reinterpret_cast<const uint8_t *>(sc[warp][r]);
+                    for (int x = xa; x < xb; ++x) {
+                        const uint32_t z = sz[warp][r][x - x0];
+                        if (z != kEmpty) {
+                            s = __fadd_rn(s, __uint_as_float(z));
+                            cnt += 1.0f;
+                        }
+                        const int o = 3 * (x - x0);
+                        rr += (float)sb[o];
+                        gg += (float)sb[o + 1];
+                        bb += (float)sb[o + 2];
+                    }
+                }
+                const float npx = (float)((xb - xa) * (yb - y0));
+                const int64_t o = (int64_t)J * F.cpitch + I;
+                F.cguide[o] = make_float4(__fdiv_rn(rr, npx), __fdiv_rn(gg, npx), __fdiv_rn(bb, npx), cnt);
+                F.cssum[o] = s;
+            }
+            __syncwarp();
+        } else if (I < F.Wc) {   // other pooling factors: direct loads
+            const int x0 = I * f;
+            const int x1 = min(x0 + f, F.W), y1 = min(y0 + f, F.H);
+            float s = 0.0f, cnt = 0.0f, r = 0.0f, g = 0.0f, b = 0.0f;
+            for (int y = y0; y < y1; ++y) {
+                const uint32_t *zr = F.zbuf + (int64_t)y * F.zpitch;
+                const uint8_t *cr = F.rgb + (int64_t)y * F.rgb_pitch;
+                for (int x = x0; x < x1; ++x) {
+                    const uint32_t z = zr[x];
+                    if (z != kEmpty) {
+                        s = __fadd_rn(s, __uint_as_float(z));
+                        cnt += 1.0f;
+                    }
+                    r += (float)cr[3 * x];
+                    g += (float)cr[3 * x + 1];
+                    b += (float)cr[3 * x + 2];
+                }
+            }
+            const float npx = (float)((x1 - x0) * (y1 - y0));
+            const int64_t o = (int64_t)J * F.cpitch + I;
+            F.cguide[o] = make_float4(__fdiv_rn(r, npx), __fdiv_rn(g, npx), __fdiv_rn(b, npx), cnt);
+            F.cssum[o] = s;
         }
-        const float npx = (float)((x1 - x0) * (y1 - y0));
-        const int64_t o = (int64_t)J * F.cpitch + I;
-        F.cguide[o] = make_float4(__fdiv_rn(r, npx), __fdiv_rn(g, npx), __fdiv_rn(b, npx), cnt);
-        F.cssum[o] = s;
     }
 }
 
@@ -105,10 +167,43 @@ __global__ void __launch_bounds__(kThreads) bp_count_kernel(const BatchDev *__re
     }
 }
 
+// Exclusive prefix of the chunk counts of every frame, in place, and the
+// frame's point count. One block per frame.
+__global__ void __launch_bounds__(kThreads) bp_scan_kernel(const BatchDev *__restrict__ B) {
+    __shared__ uint32_t wsum[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int fi = blockIdx.x; fi < B->n_frames; fi += gridDim.x) {
+        const FrameDev &F = B->f[fi];
+        if (F.n_bp_chunks == 0 || !F.points_n) continue;
+        uint32_t carry = 0;
+        for (int c0 = 0; c0 < F.n_bp_chunks; c0 += kThreads) {
+            const int c = c0 + threadIdx.x;
+            const uint32_t v = c < F.n_bp_chunks ? F.chunk_cnt[c] : 0u;
+            uint32_t incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            __syncthreads();
+            if (lane == 31) wsum[warp] = incl;
+            __syncthreads();
+            uint32_t before = carry, all = carry;
+            for (int w = 0; w < kThreads / 32; ++w) {
+                if (w < warp) before += wsum[w];
+                all += wsum[w];
+            }
+            if (c < F.n_bp_chunks) F.chunk_cnt[c] = before + incl - v;
+            carry = all;
+        }
+        if (threadIdx.x == 0) *F.points_n = (int64_t)carry;
+        __syncthreads();
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) bp_write_kernel(const BatchDev *__restrict__ B) {
     __shared__ float4 stage[kThreads / 32][128];
     __shared__ uint32_t wtot[kThreads / 32];
-    __shared__ int64_t red[kThreads / 32];
     const int nf = B->n_frames;
     const int total = B->bp_pre[nf];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -121,11 +216,6 @@ __global__ void __launch_bounds__(kThreads) bp_write_kernel(const BatchDev *__re
         const bool vvalid = (((uintptr_t)F.out_valid) & 3u) == 0;
         const bool vdepth = (((uintptr_t)F.out_depth) & 15u) == 0;
         const bool rows4 = (W & 3) == 0 && (F.rgb_pitch & 3) == 0 && (((uintptr_t)F.rgb) & 3u) == 0;
-        // exclusive prefix over the frame's earlier chunks (this thread's share)
-        int64_t part = 0;
-        for (int k = threadIdx.x; k < c; k += kThreads) part += F.chunk_cnt[k];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
         const int64_t wbase = (int64_t)c * kBpChunk + warp * 512;
         uint32_t m[4], wc = 0;
 #pragma unroll
@@ -135,20 +225,11 @@ __global__ void __launch_bounds__(kThreads) bp_write_kernel(const BatchDev *__re
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) wc += __shfl_xor_sync(0xffffffffu, wc, o);
-        __syncthreads();   // the previous chunk is done with red / wtot
-        if (lane == 0) {
-            red[warp] = part;
-            wtot[warp] = wc;
-        }
+        __syncthreads();   // the previous chunk is done with wtot
+        if (lane == 0) wtot[warp] = wc;
         __syncthreads();
-        int64_t off = 0, all = 0;
-        for (int w = 0; w < kThreads / 32; ++w) {
-            off += red[w];
-            all += wtot[w];
-        }
-        const int64_t chunk_base = off;
+        int64_t off = F.chunk_cnt[c];   // exclusive prefix of the chunk counts (bp_scan_kernel)
         for (int w = 0; w < warp; ++w) off += wtot[w];
-        if (threadIdx.x == 0 && c == F.n_bp_chunks - 1) *F.points_n = chunk_base + all;
 
         const float *c2w = F.c2w32;
         const float r00 = c2w[0], r01 = c2w[1], r02 = c2w[2], t0 = c2w[3];
@@ -244,6 +325,9 @@ __global__ void __launch_bounds__(kThreads) bp_write_kernel(const BatchDev *__re
 
 cudaError_t launch_bp_count(const BatchDev *b, int grid, cudaStream_t s) {
     bp_count_kernel<<<grid, kThreads, 0, s>>>(b);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    bp_scan_kernel<<<kMaxBatch, kThreads, 0, s>>>(b);
     return cudaGetLastError();
 }
 

@@ -211,7 +211,7 @@ extern "C" DENSIFY_API densify_status densify_frame_noalloc(const densify_params
     for (int k = 0; k < kMaxScans; ++k) pre.pt[k] = cdiv(d.scans[k].count, kPtsPerChunk);
     const int r1 = params->stage[0].radius, r2 = params->num_stages == 2 ? params->stage[1].radius : 0;
     if (params->num_stages == 2) {
-        pre.pool = cdiv((int64_t)Wc * Hc, kPoolPerChunk);
+        pre.pool = cdiv(Wc, kPoolPerChunk) * Hc;
         pre.t1 = cdiv(Wc, 32) * cdiv(Hc, 8 * kp_jbf_coarse(r1));
         pre.t2 = cdiv(W, 32) * cdiv(H, 8 * kp_jbf_up(r2));
     } else {

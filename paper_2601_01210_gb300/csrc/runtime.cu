@@ -541,7 +541,7 @@ void fill_batch(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &tk) {
             const int k = i * kMaxScans + s;
             b.pt_pre[k + 1] = b.pt_pre[k] + ceil_div(d.scans[s].count, kPtsPerChunk);
         }
-        b.pool_pre[i + 1] = b.pool_pre[i] + (nst == 2 ? ceil_div((int64_t)d.Wc * d.Hc, kPoolPerChunk) : 0);
+        b.pool_pre[i + 1] = b.pool_pre[i] + (nst == 2 ? ceil_div(d.Wc, kPoolPerChunk) * d.Hc : 0);
         const int g1w = nst == 2 ? d.Wc : d.W, g1h = nst == 2 ? d.Hc : d.H;
         b.t1_pre[i + 1] = b.t1_pre[i] + ceil_div(g1w, 32) * ceil_div(g1h, th1);
         b.t2_pre[i + 1] = b.t2_pre[i] + (nst == 2 ? ceil_div(d.W, 32) * ceil_div(d.H, th2) : 0);
@@ -1309,7 +1309,7 @@ densify_status densify_sigma_grad(densify_ctx *c, const densify_frame *frame, co
     hb->n_frames = 1;
     hb->zb_pre[1] = ceil_div((int64_t)d.zpitch * d.H, kZbWordsPerChunk);
     for (int s = 0; s < kMaxScans; ++s) hb->pt_pre[s + 1] = hb->pt_pre[s] + ceil_div(d.scans[s].count, kPtsPerChunk);
-    hb->pool_pre[1] = p.num_stages == 2 ? ceil_div((int64_t)d.Wc * d.Hc, kPoolPerChunk) : 0;
+    hb->pool_pre[1] = p.num_stages == 2 ? ceil_div(d.Wc, kPoolPerChunk) * d.Hc : 0;
     hb->px_pre[1] = d.n_px_chunks;
     std::memcpy(&hb->f[0], &d, sizeof(FrameDev));
     GradArgs ga{};
