@@ -38,6 +38,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "1080p dense-depth frames/s (3 merged LiDAR scans, two-stage JBF r=4@1/3 + r=2, coloured points)"
 UNIT = "frames/s"
+TAP_INSTR = 6          # issue slots of the minimal filter tap (see the roofline note below)
 STAGES = ((4, 5.0, 20.0), (2, 5.0, 20.0))
 L2_FLUSH_BYTES = 256 << 20
 
@@ -400,14 +401,13 @@ def ours_arm(a, rank, world, local_rank):
         if world > 1:
             torch.distributed.barrier()
         times = d.kernel_times()
+        gpu_launches = d.kernel_launches()   # CUDA kernels of the timed steps
         t_end = time.perf_counter() + (0.0 if a.no_clocks else 0.5)
         while time.perf_counter() < t_end:
             step(0, False)
         torch.cuda.synchronize()
         ck = clocks.stop() if not a.no_clocks else {"skipped": "--no-clocks"}
         step_ms = [s.elapsed_time(e) for s, e in ev]
-        n_launch = sum(n for _, n in times.values())
-        gpu_launches = n_launch
 
         def reduce_max(x):
             if world == 1:
@@ -464,10 +464,11 @@ def ours_arm(a, rank, world, local_rank):
     except Exception:
         pass
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    # ALU peak of the filter: 152 SMs x 4 SMSPs x 32 lanes issue one instruction per clock; a tap needs
-    # 10 (3 sub, 3 mul/fma for the colour distance, 1 fma for the exponent, 1 ex2, 2 fma accumulate).
+    # ALU peak of the filter: 152 SMs x 4 SMSPs x 32 lanes issue one instruction per clock; a tap needs at
+    # least 6 (with the squared colour distance expanded, 3 fma give the exponent, 1 ex2, 2 fma accumulate);
+    # the ex2 unit (32 lanes per SM) and the FP32 pipe (128 lanes, 5 fma a tap) bound it less tightly.
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_gtap = sms * 128 / 10.0 * sm_max * 1e6 / 1e9
+    peak_gtap = sms * 128 / TAP_INSTR * sm_max * 1e6 / 1e9
     s2 = times.get("jbf_stage2", (0.0, 1))
     avg_us = s2[0] / max(1, s2[1])
     achieved = taps2 / (avg_us * 1e-6) / 1e9 if avg_us > 0 else 0.0
@@ -493,7 +494,7 @@ def ours_arm(a, rank, world, local_rank):
         "roofline": {"kernel": "jbf_stage2", "bound": "alu", "achieved": achieved, "peak": peak_gtap,
                      "unit": "Gtap/s", "frac": achieved / peak_gtap if peak_gtap else None,
                      "traffic": profiled_traffic("jbf_stage2"), "traffic_unit": "bytes per launch (ncu capture)",
-                     "peak_basis": f"{sms} SMs x 128 lanes / 10 instructions per tap x {sm_max:.0f} MHz",
+                     "peak_basis": f"{sms} SMs x 128 lanes / {TAP_INSTR} instructions per tap x {sm_max:.0f} MHz",
                      "taps_per_launch": taps2, "avg_launch_us": avg_us},
         "kernels": ktable,
         "filter_kernels": kernel_choice,

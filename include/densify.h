@@ -126,8 +126,14 @@ typedef struct densify_stage {
  *                 stage has one (radius 1-3 second stage with pool 3 and
  *                 stage2_input 0; radius 2 or 4 first stage; radius 2, 4 or 7
  *                 single stage), the plain shared-memory kernels elsewhere.
- *                 1: the plain kernels everywhere (same results, for
- *                 comparison).
+ *                 In FP32 the TMA kernels take the expanded form (squared
+ *                 colour distance as |c_p|^2 - 2 c_p.c_q + |c_q|^2 with colours
+ *                 centred at 128; same sums, different rounding, within the
+ *                 FP32 tolerance) where log2(e) / (2 sigma_c^2) * 3 * 128^2 +
+ *                 log2(e) / (2 sigma_p^2) * 2 r^2 <= 100, else the difference
+ *                 form. 1: the plain kernels everywhere (difference form,
+ *                 for comparison). 2: the TMA kernels in the difference form
+ *                 only (the same bits as 1).
  *   autotune      1: on the first batch, time every kernel that can run each
  *                 filter stage (TMA-staged at each instantiated tile height,
  *                 and the plain kernel) on that batch and keep the fastest for
@@ -291,8 +297,14 @@ DENSIFY_API uint64_t densify_frame_scratch_bytes(const densify_params *params, c
 DENSIFY_API int32_t densify_kernel_times(densify_ctx *ctx, const char **names, double *total_us,
                              int64_t *launches, int32_t cap);
 
-/* Zero the accumulated kernel times. */
+/* Zero the accumulated kernel times and the kernel launch count. */
 DENSIFY_API void densify_reset_kernel_times(densify_ctx *ctx);
+
+/* Number of CUDA kernels launched by the context's completed batches since
+ * creation or the last densify_reset_kernel_times (a replayed graph counts each
+ * of its kernels; the autotuner's trial launches are not counted). With
+ * timing = 1 or 0 alike. */
+DENSIFY_API int64_t densify_kernel_launches(densify_ctx *ctx);
 
 /* JSON text describing the filter kernels the context runs: per filter stage the
  * chosen kernel (TMA-staged or plain, rows per thread, tile, grid) and, after

@@ -26,6 +26,8 @@ constexpr int kPtsPerChunk = kThreads * kPtsPerThread;        // 1024 points
 constexpr int kZbWordsPerChunk = 2048;                        // z-buffer clear
 constexpr int kPoolPerChunk = kThreads;                       // coarse pixels (one coarse row segment)
 constexpr int kBpChunk = 4096;                                // compaction: 8 warps x 512 px
+constexpr int kBpWarps = kThreads / 32;                       // parts of a chunk, one per warp
+constexpr int kBpPart = kBpChunk / kBpWarps;                  // 512 pixels
 constexpr int kPxChunk = 1024;                                // per-pixel kernels: 256 threads x 4 px
 
 struct ScanDev {
@@ -61,7 +63,7 @@ struct alignas(64) FrameDev {
     float *cssum;            // Hc x cpitch: pooled depth sum
     float2 *s1;              // Hc x cpitch: first-stage depth and validity (0/1)
     float2 *g1;              // Hc x cpitch: first-stage depth derivatives (sigma gradient only)
-    uint32_t *chunk_cnt;     // n_bp_chunks valid-pixel counts
+    uint32_t *chunk_cnt;     // n_bp_chunks * kBpWarps valid-pixel counts of 512-pixel parts
     // preprocessing (Sec. 4.1) and post-filtering (Sec. 5); NULL / 0 when off
     const uint8_t *prev_rgb;     // previous RGB frame (afterimage removal)
     int64_t prev_pitch;
@@ -95,6 +97,11 @@ struct BatchDev {
     int32_t bp_pre[kMaxBatch + 1];                 // compaction chunks
     int32_t px_pre[kMaxBatch + 1];                 // pixel chunks of the motion / contour kernels
     int32_t oc_pre[kMaxBatch + 1];                 // tiles of the occlusion kernel
+    // TMA filters (index 0: first or only filter, 1: second): tiles that some observation
+    // reaches, found by tile_scan_kernel, as frame << 24 | tile; the count is zeroed on the
+    // stream before every scan
+    int32_t tl_count[2];
+    int32_t *tl_list[2];
     FrameDev f[kMaxBatch];
 };
 
@@ -112,6 +119,11 @@ struct StageArgs {
     // half2 bits of (sp[d][dx], sp[d-1][dx]) for d = 0 .. 2R+1, row-major over (d, dx);
     // a term outside 0..2R is -inf (its weight is 0)
     uint32_t sp2[(2 * kMaxR + 2) * (2 * kMaxR + 1)];
+    // Expanded FP32 form (see jbf_tma.cuh): the spatial weight of offset
+    // (dx - R, dy - R) split into a column factor ex_sx[dx] = 2^(-(dx-R)^2 kp)
+    // and a row exponent ex_sy[dy] = -(dy-R)^2 kp (0 beyond 2R)
+    float ex_sx[2 * kMaxR + 1];
+    float ex_sy[2 * kMaxR + 1];
 };
 
 // Largest i with pre[i] <= item (pre is non-decreasing, pre[0] = 0).

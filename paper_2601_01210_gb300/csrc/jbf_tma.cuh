@@ -98,7 +98,7 @@ __device__ __forceinline__ int floor_div3(int a) { return a >= 0 ? a / 3 : -((2 
 constexpr int ceil_to(int x, int m) { return (x + m - 1) / m * m; }
 
 // Tile geometry shared by the kernel and the host (tensor-map boxes).
-template <int SRC, int R, int KP, int NW_ = 8>
+template <int SRC, int R, int KP, int NW_ = 8, bool EXP = false>
 struct TmaGeom {
     static constexpr int TW = 32, NW = NW_, TH = NW * KP, SW = TW + 2 * R, SH = TH + 2 * R;
     // RGB bytes: box starts at byte 3*x0 - RGB_LEAD (x0 is a multiple of 32, so 3*x0 of 16)
@@ -128,12 +128,14 @@ struct TmaGeom {
     static constexpr int TX_BYTES = SRC == SRC_COARSE ? G_BX * G_BY * 4 + S_BX * S_BY * 4
                                     : SRC == SRC_UP   ? RGB_BX * RGB_BY + C_BX * C_BY * 8
                                                       : RGB_BX * RGB_BY + Z_BX * Z_BY * 4;
-    static constexpr int STAGED = SRC == SRC_COARSE ? 0 : SH * SW * 16;
+    static constexpr int STAGED = SRC == SRC_COARSE && !EXP ? 0 : SH * SW * 16;
+    static constexpr int STAGED_G = EXP ? ceil_to(SH * SW * 4, 16) : 0;   // expanded form: F_q times depth
     static constexpr int OBS = SRC == SRC_COARSE ? 0 : ceil_to(SH * SW, 16);
     static constexpr int HOR = ceil_to(SH * 4, 16);
     static constexpr int OFF_RAW = 0;
     static constexpr int OFF_STAGED = OFF_RAW + 2 * (RAW_A + RAW_B);
-    static constexpr int OFF_OBS = OFF_STAGED + STAGED;
+    static constexpr int OFF_G = OFF_STAGED + STAGED;
+    static constexpr int OFF_OBS = OFF_G + STAGED_G;
     static constexpr int OFF_HOR = OFF_OBS + OBS;
     static constexpr int OFF_BAR = ceil_to(OFF_HOR + HOR, 16);
     static constexpr int SMEM = OFF_BAR + 16;
@@ -157,10 +159,13 @@ __device__ __forceinline__ __half2 h2exp2_approx(__half2 x) {
     return h2bits(y);
 }
 
-template <int SRC, int R, int KP, bool HALF = false, int NW = 8>
-__global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 1) jbf_tma_kernel(const BatchDev *__restrict__ B,
+enum { FORM_FP32 = 0, FORM_FP16 = 1, FORM_EXP = 2 };
+
+template <int SRC, int R, int KP, int FORM = FORM_FP32, int NW = 8>
+__global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDev *__restrict__ B,
                                                                            const StageArgs a) {
-    using G = TmaGeom<SRC, R, KP, NW>;
+    constexpr bool HALF = FORM == FORM_FP16, EXP = FORM == FORM_EXP;
+    using G = TmaGeom<SRC, R, KP, NW, EXP>;
     constexpr int TW = G::TW, TH = G::TH, SW = G::SW, SH = G::SH, T = 2 * R + 1;
     constexpr int NT = NW * 32;   // threads
     static_assert(!HALF || (SRC != SRC_COARSE && KP % 2 == 0), "FP16 form: full-resolution stages, row pairs");
@@ -170,22 +175,25 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 1) jbf_tma_kernel(const
     auto rawB = [&](int b) { return smem + G::OFF_RAW + b * (G::RAW_A + G::RAW_B) + G::RAW_A; };
     float4 *staged = reinterpret_cast<float4 *>(smem + G::OFF_STAGED);
     uint4 *staged_h = reinterpret_cast<uint4 *>(smem + G::OFF_STAGED);   // FP16 records, same 16 bytes
+    float *staged_g = reinterpret_cast<float *>(smem + G::OFF_G);         // expanded form: F_q times depth
     uint8_t *obs = smem + G::OFF_OBS;
     uint32_t *horw = reinterpret_cast<uint32_t *>(smem + G::OFF_HOR);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + G::OFF_BAR);
 
-    const int32_t *pre = SRC == SRC_UP ? B->t2_pre : B->t1_pre;
-    const int nf = B->n_frames;
-    const int total = pre[nf];
+    // the tiles that some observation reaches (tile_scan_kernel wrote the list and zero-filled the rest)
+    const int stage = SRC == SRC_UP ? 1 : 0;
+    const int total = B->tl_count[stage];
+    const int32_t *list = B->tl_list[stage];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    // tile -> (frame, x0, y0)
+    // list entry -> (frame, x0, y0)
     auto locate = [&](int item, int &fi, int &x0, int &y0) {
-        fi = find_segment(pre, nf, item);
+        const int e = list[item];
+        fi = e >> 24;
         const FrameDev &F = B->f[fi];
         const int gw = SRC == SRC_COARSE ? F.Wc : F.W;
         const int tiles_x = (gw + TW - 1) / TW;
-        const int t = item - pre[fi];
+        const int t = e & 0xFFFFFF;
         x0 = (t % tiles_x) * TW;
         y0 = (t / tiles_x) * TH;
     };
@@ -253,39 +261,58 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 1) jbf_tma_kernel(const
         const float4 *cg = reinterpret_cast<const float4 *>(rawA(buf));
         const float *cs = reinterpret_cast<const float *>(rawB(buf));
 
-        // ---- conversion (SRC_UP / SRC_ZBUF) and observation map
+        // ---- conversion and observation map
+        // staged position (sy, sx): colour bytes in the raw RGB box, depth and observation
+        // from the raw first-stage box (SRC_UP) or z-buffer box (SRC_ZBUF)
+        const int cx0 = floor_div3(x0 - R) & ~1, cy0 = floor_div3(y0 - R);
+        const float2 *craw = reinterpret_cast<const float2 *>(rawB(buf));
+        const uint32_t *zraw = reinterpret_cast<const uint32_t *>(rawB(buf));
+        auto rgb_at = [&](int sy, int sx) { return rgbraw + sy * G::RGB_BX + 3 * sx - 3 * R + G::RGB_LEAD; };
+        auto depth_of = [&](int sy, int sx, float &d) -> bool {
+            const int gx = x0 - R + sx, gy = y0 - R + sy;
+            if (gx < 0 || gx >= gw || gy < 0 || gy >= gh) return false;
+            if (SRC == SRC_UP) {
+                const float2 c = craw[(gy / 3 - cy0) * G::C_BX + (gx / 3 - cx0)];
+                d = c.x;
+                return c.y > 0.0f;
+            }
+            const uint32_t z = zraw[sy * G::Z_BX + sx - R + G::Z_LEAD];
+            d = __uint_as_float(z);
+            return z != kEmpty;
+        };
         if (SRC != SRC_COARSE) {
-            const int cx0 = floor_div3(x0 - R) & ~1, cy0 = floor_div3(y0 - R);
-            const float2 *craw = reinterpret_cast<const float2 *>(rawB(buf));
-            const uint32_t *zraw = reinterpret_cast<const uint32_t *>(rawB(buf));
-            // one staged neighbour: colour (sentinel if unobserved), depth, observation byte
-            auto put = [&](int i, float r, float g, float b, float d, bool o) {
+            for (int i = threadIdx.x; i < SH * SW; i += NT) {
+                const int sy = i / SW, sx = i - sy * SW;
+                float d = 0.0f;
+                const bool o = depth_of(sy, sx, d);
+                const uint8_t *p = rgb_at(sy, sx);
+                const float r = o ? (float)p[0] : 0.0f, g = o ? (float)p[1] : 0.0f, b = o ? (float)p[2] : 0.0f;
                 if (HALF) {
                     staged_h[i] = o ? make_uint4(h2u(__float2half2_rn(r)), h2u(__float2half2_rn(g)),
                                                  h2u(__float2half2_rn(b)), __float_as_uint(d))
                                     : make_uint4(h2u(__float2half2_rn(65504.0f)), 0u, 0u, 0u);
+                } else if (EXP) {
+                    // centred colour (exact), F_q = 2^(-kc |c'_q|^2); unobserved: F_q = 0
+                    const float rr = r - 128.0f, gg = g - 128.0f, bb = b - 128.0f;
+                    const float f = o ? ex2_approx(-a.kc * fmaf(rr, rr, fmaf(gg, gg, bb * bb))) : 0.0f;
+                    staged[i] = o ? make_float4(rr, gg, bb, f) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                    staged_g[i] = o ? f * d : 0.0f;   // an empty z-buffer cell holds +inf
                 } else {
                     staged[i] = o ? make_float4(r, g, b, d) : make_float4(kSentinel, 0.0f, 0.0f, 0.0f);
                 }
                 obs[i] = o;
-            };
-            auto depth_of = [&](int sy, int sx, int gx, int gy, float &d) -> bool {
-                if (SRC == SRC_UP) {
-                    const float2 c = craw[(gy / 3 - cy0) * G::C_BX + (gx / 3 - cx0)];
-                    d = c.x;
-                    return c.y > 0.0f;
-                }
-                const uint32_t z = zraw[sy * G::Z_BX + sx - R + G::Z_LEAD];
-                d = __uint_as_float(z);
-                return z != kEmpty;
-            };
+            }
+            __syncthreads();
+        } else if (EXP) {
+            // pooled guide: F_q times the count and times the depth sum (count 0: weight 0)
             for (int i = threadIdx.x; i < SH * SW; i += NT) {
                 const int sy = i / SW, sx = i - sy * SW;
-                const int gx = x0 - R + sx, gy = y0 - R + sy;
-                float d = 0.0f;
-                const bool o = gx >= 0 && gx < gw && gy >= 0 && gy < gh && depth_of(sy, sx, gx, gy, d);
-                const uint8_t *p = rgbraw + sy * G::RGB_BX + 3 * sx - 3 * R + G::RGB_LEAD;
-                put(i, o ? (float)p[0] : 0.0f, o ? (float)p[1] : 0.0f, o ? (float)p[2] : 0.0f, d, o);
+                const float4 q = cg[i];
+                const float sum = cs[sy * G::S_BX + sx - R + G::S_LEAD];
+                const float rr = q.x - 128.0f, gg = q.y - 128.0f, bb = q.z - 128.0f;
+                const float f = ex2_approx(-a.kc * fmaf(rr, rr, fmaf(gg, gg, bb * bb)));
+                staged[i] = make_float4(rr, gg, bb, f * q.w);
+                staged_g[i] = f * sum;
             }
             __syncthreads();
         }
@@ -368,7 +395,43 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 1) jbf_tma_kernel(const
                     }
                 }
             }
-        } else if (!HALF && __any_sync(0xffffffffu, any_val)) {
+        } else if (EXP && __any_sync(0xffffffffu, any_val)) {
+            // exponent 2 kc c'_p . c'_q - kc |c'_p|^2 + ex_sy[dy]; weight times F_q ex_sx[dx]
+            const float kc = a.kc, kc2 = 2.0f * a.kc;
+            float ar[KP], ag[KP], ab[KP], cp[KP];
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+                const float rr = cr[k] - 128.0f, gg = cgr[k] - 128.0f, bb = cb[k] - 128.0f;
+                ar[k] = kc2 * rr;
+                ag[k] = kc2 * gg;
+                ab[k] = kc2 * bb;
+                cp[k] = -kc * fmaf(rr, rr, fmaf(gg, gg, bb * bb));
+            }
+#pragma unroll
+            for (int iy = 0; iy < KP + 2 * R; ++iy) {
+                float dd[KP];
+#pragma unroll
+                for (int k = 0; k < KP; ++k) {
+                    const int dy = iy - k;
+                    dd[k] = (dy >= 0 && dy < T) ? cp[k] + a.ex_sy[dy] : 0.0f;
+                }
+#pragma unroll
+                for (int dx = 0; dx < T; ++dx) {
+                    const int o = (rbase + iy) * SW + lane + dx;
+                    const float4 q = staged[o];
+                    const float fx = q.w * a.ex_sx[dx], gx = staged_g[o] * a.ex_sx[dx];
+#pragma unroll
+                    for (int k = 0; k < KP; ++k) {
+                        const int dy = iy - k;
+                        if (dy >= 0 && dy < T) {
+                            const float w = ex2_approx(fmaf(ar[k], q.x, fmaf(ag[k], q.y, fmaf(ab[k], q.z, dd[k]))));
+                            num[k] = fmaf(w, gx, num[k]);
+                            den[k] = fmaf(w, fx, den[k]);
+                        }
+                    }
+                }
+            }
+        } else if (!HALF && !EXP && __any_sync(0xffffffffu, any_val)) {
             const float kc = a.kc;
 #pragma unroll
             for (int iy = 0; iy < KP + 2 * R; ++iy) {
@@ -450,6 +513,13 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 1) jbf_tma_kernel(const
                 } else if (HALF) {
                     seen = half_record(staged_h[o], r, g, b, wd);
                     wb = 1.0f;
+                } else if (EXP) {   // from the raw boxes
+                    const int sy = rbase + k + dy, sx = lane + dx;
+                    const uint8_t *p = rgb_at(sy, sx);
+                    r = (float)p[0]; g = (float)p[1]; b = (float)p[2];
+                    wd = 0.0f;
+                    seen = obs[o] != 0 && depth_of(sy, sx, wd);
+                    wb = 1.0f;
                 } else {
                     const float4 q = staged[o];
                     r = q.x; g = q.y; b = q.z;
@@ -486,6 +556,67 @@ __global__ void __launch_bounds__(NW * 32, NW == 8 ? 2 : 1) jbf_tma_kernel(const
             store(k, nn / dd, true);
         }
         __syncthreads();   // staged / raw[buf] / hor are reused by the next tile
+    }
+}
+
+// Tile scan for the TMA filters: one block per tile of the stage's grid (tiles
+// of 32 x th, row-major per frame, as the stage's prefix array counts them);
+// the block's threads test the footprint (the tile grown by the radius, clipped
+// to the grid) with all their loads in flight at once. A tile whose footprint
+// holds no observation has only invalid outputs: the block writes them (depth
+// 0, invalid) and the tile is not listed. Every other tile is appended to the
+// stage's list (order immaterial: each tile is written by one CTA only).
+constexpr int kScanThreads = 256;
+template <int SRC>
+__global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(BatchDev *__restrict__ B, int stage, int th, int r) {
+    const int32_t *pre = stage ? B->t2_pre : B->t1_pre;
+    const int nf = B->n_frames;
+    const int total = pre[nf];
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int fi = find_segment(pre, nf, item);
+        const FrameDev &F = B->f[fi];
+        const int gw = SRC == SRC_COARSE ? F.Wc : F.W;
+        const int gh = SRC == SRC_COARSE ? F.Hc : F.H;
+        const int tiles_x = (gw + 31) / 32;
+        const int t = item - pre[fi];
+        const int x0 = (t % tiles_x) * 32, y0 = (t / tiles_x) * th;
+        int qx0 = max(0, x0 - r), qx1 = min(gw - 1, x0 + 31 + r);
+        int qy0 = max(0, y0 - r), qy1 = min(gh - 1, y0 + th - 1 + r);
+        if (SRC == SRC_UP) {   // observations of the restored first stage: its valid pooled pixels
+            qx0 /= 3; qx1 /= 3; qy0 /= 3; qy1 /= 3;
+        }
+        const int ncx = qx1 - qx0 + 1, n = ncx * (qy1 - qy0 + 1);
+        bool any = false;
+        for (int i0 = 0; i0 < n; i0 += 8 * kScanThreads) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) {
+                const int i = i0 + k * kScanThreads + threadIdx.x;
+                if (i < n) {
+                    const int qy = qy0 + i / ncx, qx = qx0 + i % ncx;
+                    any |= SRC == SRC_UP       ? F.s1[(int64_t)qy * F.cpitch + qx].y > 0.0f
+                           : SRC == SRC_COARSE ? F.cguide[(int64_t)qy * F.cpitch + qx].w > 0.0f
+                                               : F.zbuf[(int64_t)qy * F.zpitch + qx] != kEmpty;
+                }
+            }
+        }
+        if (__syncthreads_or(any)) {
+            if (threadIdx.x == 0) B->tl_list[stage][atomicAdd(&B->tl_count[stage], 1)] = (fi << 24) | t;
+            continue;
+        }
+        const int rows = min(th, gh - y0), w = min(32, gw - x0);
+        for (int i = threadIdx.x; i < rows * 32; i += kScanThreads) {
+            const int y = y0 + i / 32, x = x0 + i % 32;
+            if (i % 32 >= w) continue;
+            const int64_t o = (int64_t)y * gw + x;
+            if (SRC == SRC_COARSE) {
+                F.s1[(int64_t)y * F.cpitch + x] = make_float2(0.0f, 0.0f);
+                if (F.out_coarse) F.out_coarse[o] = 0.0f;
+                if (F.out_coarse_valid) F.out_coarse_valid[o] = 0;
+            } else {
+                F.flt_depth[o] = 0.0f;
+                F.flt_valid[o] = 0;
+            }
+        }
     }
 }
 

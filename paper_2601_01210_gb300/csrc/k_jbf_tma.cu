@@ -1,114 +1,74 @@
-// Instantiations of the TMA-staged joint bilateral filter and the host-side
-// description of their tiles (tensor-map boxes, shared memory, rows per tile).
-#include "jbf_tma.cuh"
-#include "tma_info.h"
+// Instantiations of the TMA-staged joint bilateral filter in the FP32
+// difference form and the FP16 form, and the public lookups over all forms
+// (the expanded FP32 form is instantiated in k_jbf_tma_exp.cu).
+#include "jbf_tma_dispatch.cuh"
 
 namespace dz {
 
 namespace {
 
-template <int SRC, int R, int KP, int NW>
-void fill_info(TmaKernelInfo *o) {
-    using G = TmaGeom<SRC, R, KP, NW>;
-    o->supported = 1;
-    o->kp = KP;
-    o->threads = NW * 32;
-    o->tile_w = G::TW;
-    o->tile_h = G::TH;
-    o->smem = G::SMEM;
-    o->rgb_box[0] = G::RGB_BX; o->rgb_box[1] = G::RGB_BY;
-    o->s1_box[0] = G::C_BX;    o->s1_box[1] = G::C_BY;
-    o->zbuf_box[0] = G::Z_BX;  o->zbuf_box[1] = G::Z_BY;
-    o->cguide_box[0] = G::G_BX; o->cguide_box[1] = G::G_BY;
-    o->cssum_box[0] = G::S_BX; o->cssum_box[1] = G::S_BY;
-}
-
-template <int SRC, int R, int KP, bool H, int NW>
-cudaError_t prep() {
-    return cudaFuncSetAttribute(jbf_tma_kernel<SRC, R, KP, H, NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                TmaGeom<SRC, R, KP, NW>::SMEM);
-}
-
-template <int SRC, int R, int KP, bool H, int NW>
-cudaError_t go(const BatchDev *b, const StageArgs &a, int grid, cudaStream_t s) {
-    jbf_tma_kernel<SRC, R, KP, H, NW><<<grid, NW * 32, TmaGeom<SRC, R, KP, NW>::SMEM, s>>>(b, a);
-    return cudaGetLastError();
-}
-
-template <int SRC, int R, int KP, bool H, int NW>
-int occ() {
-    int n = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, jbf_tma_kernel<SRC, R, KP, H, NW>, NW * 32,
-                                                  TmaGeom<SRC, R, KP, NW>::SMEM);
-    return n > 0 ? n : 1;
-}
-
-// (source, radius, rows per thread, FP16 form, warps per CTA); the first listed
+// (source, radius, rows per thread, form, warps per CTA); the first listed
 // variant of a (source, radius, form) is the default before autotuning
-#define DZ_TMA_CASES(X)               \
-    X(SRC_UP, 1, 8, false, 8)         \
-    X(SRC_UP, 2, 8, false, 8)         \
-    X(SRC_UP, 2, 8, false, 16)        \
-    X(SRC_UP, 2, 4, false, 8)         \
-    X(SRC_UP, 3, 4, false, 8)         \
-    X(SRC_COARSE, 2, 4, false, 8)     \
-    X(SRC_COARSE, 4, 4, false, 8)     \
-    X(SRC_COARSE, 4, 2, false, 8)     \
-    X(SRC_ZBUF, 2, 8, false, 8)       \
-    X(SRC_ZBUF, 4, 8, false, 8)       \
-    X(SRC_ZBUF, 4, 4, false, 8)       \
-    X(SRC_ZBUF, 7, 4, false, 8)       \
-    X(SRC_UP, 1, 8, true, 8)          \
-    X(SRC_UP, 2, 8, true, 8)          \
-    X(SRC_UP, 2, 8, true, 16)         \
-    X(SRC_UP, 2, 4, true, 8)          \
-    X(SRC_UP, 3, 4, true, 8)          \
-    X(SRC_ZBUF, 2, 8, true, 8)        \
-    X(SRC_ZBUF, 4, 8, true, 8)        \
-    X(SRC_ZBUF, 4, 4, true, 8)        \
-    X(SRC_ZBUF, 7, 4, true, 8)
+#define DZ_TMA_CASES(X)                   \
+    X(SRC_UP, 1, 8, FORM_FP32, 8)         \
+    X(SRC_UP, 2, 8, FORM_FP32, 8)         \
+    X(SRC_UP, 2, 8, FORM_FP32, 16)        \
+    X(SRC_UP, 2, 4, FORM_FP32, 8)         \
+    X(SRC_UP, 3, 4, FORM_FP32, 8)         \
+    X(SRC_COARSE, 2, 4, FORM_FP32, 8)     \
+    X(SRC_COARSE, 4, 4, FORM_FP32, 8)     \
+    X(SRC_COARSE, 4, 2, FORM_FP32, 8)     \
+    X(SRC_ZBUF, 2, 8, FORM_FP32, 8)       \
+    X(SRC_ZBUF, 4, 8, FORM_FP32, 8)       \
+    X(SRC_ZBUF, 4, 4, FORM_FP32, 8)       \
+    X(SRC_ZBUF, 7, 4, FORM_FP32, 8)       \
+    X(SRC_UP, 1, 8, FORM_FP16, 8)         \
+    X(SRC_UP, 2, 8, FORM_FP16, 8)         \
+    X(SRC_UP, 2, 8, FORM_FP16, 16)        \
+    X(SRC_UP, 2, 4, FORM_FP16, 8)         \
+    X(SRC_UP, 3, 4, FORM_FP16, 8)         \
+    X(SRC_ZBUF, 2, 8, FORM_FP16, 8)       \
+    X(SRC_ZBUF, 4, 8, FORM_FP16, 8)       \
+    X(SRC_ZBUF, 4, 4, FORM_FP16, 8)       \
+    X(SRC_ZBUF, 7, 4, FORM_FP16, 8)
+
+DZ_TMA_LOOKUPS(DZ_TMA_CASES, base)
 
 }  // namespace
 
-int jbf_tma_variants(int src, int r, bool half, TmaVariant *out, int cap) {
-    int n = 0;
-#define X(S, RR, K, H, NW) if (src == S && r == RR && half == H && n < cap) out[n++] = TmaVariant{K, NW};
-    DZ_TMA_CASES(X)
-#undef X
-    return n;
+int jbf_tma_variants(int src, int r, int form, TmaVariant *out, int cap) {
+    const int n = base_variants(src, r, form, out, cap);
+    return n + jbf_tma_exp_variants(src, r, form, out + n, cap - n);
 }
 
-bool jbf_tma_info(int src, int r, TmaVariant v, bool half, TmaKernelInfo *out) {
+bool jbf_tma_info(int src, int r, TmaVariant v, int form, TmaKernelInfo *out) {
     *out = TmaKernelInfo{};
-#define X(S, RR, K, H, NW) \
-    if (src == S && r == RR && v.kp == K && v.nw == NW && half == H) { fill_info<S, RR, K, NW>(out); return true; }
-    DZ_TMA_CASES(X)
-#undef X
-    return false;
+    return base_info(src, r, v, form, out) || jbf_tma_exp_info(src, r, v, form, out);
 }
 
-cudaError_t jbf_tma_prepare(int src, int r, TmaVariant v, bool half) {
-#define X(S, RR, K, H, NW) if (src == S && r == RR && v.kp == K && v.nw == NW && half == H) return prep<S, RR, K, H, NW>();
-    DZ_TMA_CASES(X)
-#undef X
-    return cudaErrorInvalidValue;
+cudaError_t jbf_tma_prepare(int src, int r, TmaVariant v, int form) {
+    return form == TMA_FORM_EXP ? jbf_tma_exp_prepare(src, r, v, form) : base_prepare(src, r, v, form);
 }
 
-cudaError_t launch_jbf_tma(int src, int r, TmaVariant v, bool half, const BatchDev *b, const StageArgs &a, int grid,
+cudaError_t launch_jbf_tma(int src, int r, TmaVariant v, int form, const BatchDev *b, const StageArgs &a, int grid,
                            cudaStream_t s) {
-#define X(S, RR, K, H, NW) \
-    if (src == S && r == RR && v.kp == K && v.nw == NW && half == H) return go<S, RR, K, H, NW>(b, a, grid, s);
-    DZ_TMA_CASES(X)
-#undef X
-    return cudaErrorInvalidValue;
+    return form == TMA_FORM_EXP ? jbf_tma_exp_launch(src, r, v, form, b, a, grid, s)
+                                : base_launch(src, r, v, form, b, a, grid, s);
 }
 
-int occupancy_jbf_tma(int src, int r, TmaVariant v, bool half) {
-#define X(S, RR, K, H, NW) if (src == S && r == RR && v.kp == K && v.nw == NW && half == H) return occ<S, RR, K, H, NW>();
-    DZ_TMA_CASES(X)
-#undef X
-    return 1;
+cudaError_t launch_tile_scan(int src, const BatchDev *b, int stage, int th, int r, int grid, cudaStream_t s) {
+    BatchDev *bb = const_cast<BatchDev *>(b);
+    cudaError_t e = cudaMemsetAsync(&bb->tl_count[stage], 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return e;
+    if (src == TMA_SRC_UP) tile_scan_kernel<SRC_UP><<<grid, kScanThreads, 0, s>>>(bb, stage, th, r);
+    else if (src == TMA_SRC_COARSE) tile_scan_kernel<SRC_COARSE><<<grid, kScanThreads, 0, s>>>(bb, stage, th, r);
+    else tile_scan_kernel<SRC_ZBUF><<<grid, kScanThreads, 0, s>>>(bb, stage, th, r);
+    return cudaGetLastError();
 }
 
+int occupancy_jbf_tma(int src, int r, TmaVariant v, int form) {
+    const int n = form == TMA_FORM_EXP ? jbf_tma_exp_occupancy(src, r, v, form) : base_occupancy(src, r, v, form);
+    return n > 0 ? n : 1;
+}
 
 }  // namespace dz

@@ -12,86 +12,81 @@ namespace dz {
 // dropped because it cancels in the filter's ratio) and the mean RGB of the
 // block's in-image pixels as the coarse guide. Sums run in row-major order.
 // ---------------------------------------------------------------------------
-// Warp-cooperative form: one warp pools 32 consecutive coarse pixels of a
-// coarse row. The 3 full-resolution rows under them are read with coalesced
-// word loads into shared memory (z-buffer: 96 words a row; RGB: 288 bytes a
-// row when the row start is word aligned), then each lane sums its block.
-constexpr int kPoolWarps = kThreads / 32;
+// A work item is one coarse row J and a segment of 256 coarse pixels; one
+// thread per coarse pixel. For f = 3, a block inside the image and
+// word-aligned rows, the thread issues all 18 word loads of its block first:
+// per row the 3 z-buffer words and the 3 aligned RGB words covering the row's
+// 9 colour bytes (byte offset 9I, rounded down to a word). The colour bytes are
+// shifted into place, each channel's 3 bytes gathered by a byte permute and
+// summed by dp4a: integer sums, exactly the FP32 sums of the bytes. Blocks at
+// the image border, other factors and layouts use plain loads.
+__device__ __forceinline__ bool pool_words_ok(const FrameDev &F) {
+    return ((((uintptr_t)F.zbuf) | ((uintptr_t)F.rgb)) & 3u) == 0 && (F.rgb_pitch & 3) == 0;
+}
+
+__device__ __forceinline__ void pool_store(const FrameDev &F, int I, int J, float rr, float gg, float bb, float cnt,
+                                           float s, float npx) {
+    const int64_t o = (int64_t)J * F.cpitch + I;
+    F.cguide[o] = make_float4(__fdiv_rn(rr, npx), __fdiv_rn(gg, npx), __fdiv_rn(bb, npx), cnt);
+    F.cssum[o] = s;
+}
+
 __global__ void __launch_bounds__(kThreads) pool_kernel(const BatchDev *__restrict__ B, int f) {
-    __shared__ uint32_t sz[kPoolWarps][3][96];
-    __shared__ uint32_t sc[kPoolWarps][3][72];
     const int nf = B->n_frames;
     const int total = B->pool_pre[nf];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int fi = find_segment(B->pool_pre, nf, item);
         const FrameDev &F = B->f[fi];
-        const int segs = (F.Wc + 255) / 256;                 // 256 coarse pixels per block item
+        const int segs = (F.Wc + kPoolPerChunk - 1) / kPoolPerChunk;
         const int t = item - B->pool_pre[fi];
         const int J = t / segs;
-        const int I0 = (t - J * segs) * 256 + warp * 32;     // this warp's first coarse pixel
-        if (I0 >= F.Wc) continue;
-        const int I = I0 + lane;
-        const int y0 = J * f;
-        if (f == 3) {
-            const int x0 = 3 * I0;                            // first full-resolution column
-            const bool words = ((F.rgb_pitch & 3) == 0) && ((((uintptr_t)F.rgb) & 3u) == 0);
+        const int I = (t - J * segs) * kPoolPerChunk + threadIdx.x;
+        if (I >= F.Wc) continue;
+        const int x0 = I * f, y0 = J * f;
+        const int o = (9 * I) & 3;                            // first colour byte inside its word
+        const int64_t wb = 9 * (int64_t)I - o;                // byte offset of the first covering word
+        if (f == 3 && x0 + 3 <= F.W && y0 + 3 <= F.H && wb + 12 <= 3 * (int64_t)F.W && pool_words_ok(F)) {
+            uint32_t z[3][3], c[3][3];
 #pragma unroll
             for (int r = 0; r < 3; ++r) {
-                const int y = y0 + r;
-                if (y >= F.H) break;
-                const uint32_t *zr = F.zbuf + (int64_t)y * F.zpitch;
+                const uint32_t *zr = F.zbuf + (int64_t)(y0 + r) * F.zpitch + x0;
+                const uint32_t *cw = reinterpret_cast<const uint32_t *>(F.rgb + (int64_t)(y0 + r) * F.rgb_pitch + wb);
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    const int x = x0 + lane + 32 * k;
-                    sz[warp][r][lane + 32 * k] = x < F.W ? zr[x] : kEmpty;
-                }
-                const uint8_t *cr = F.rgb + (int64_t)y * F.rgb_pitch + 3 * x0;
-                const int nbytes = 3 * min(96, F.W - x0);
-                if (words) {
-                    const uint32_t *cw = reinterpret_cast<const uint32_t *>(cr);
-                    for (int k = lane; k < 72; k += 32) sc[warp][r][k] = 4 * k < nbytes ? cw[k] : 0u;
-                } else {
-                    uint8_t *sb = reinterpret_cast<uint8_t *>(sc[warp][r]);
-                    for (int k = lane; k < 288; k += 32) sb[k] = k < nbytes ? cr[k] : 0;
+                for (int j = 0; j < 3; ++j) {
+                    z[r][j] = zr[j];
+                    c[r][j] = cw[j];
                 }
             }
-            __syncwarp();
-            if (I < F.Wc) {
-                const int xa = 3 * I, xb = min(xa + 3, F.W), yb = min(y0 + 3, F.H);
-                float s = 0.0f, cnt = 0.0f, rr = 0.0f, gg = 0.0f, bb = 0.0f;
-                for (int y = y0; y < yb; ++y) {
-                    const int r = y - y0;
-                    const uint8_t *sb = reinterpret_cast<const uint8_t *>(sc[warp][r]);
-                    for (int x = xa; x < xb; ++x) {
-                        const uint32_t z = sz[warp][r][x - x0];
-                        if (z != kEmpty) {
-                            s = __fadd_rn(s, __uint_as_float(z));
-                            cnt += 1.0f;
-                        }
-                        const int o = 3 * (x - x0);
-                        rr += (float)sb[o];
-                        gg += (float)sb[o + 1];
-                        bb += (float)sb[o + 2];
+            float s = 0.0f, cnt = 0.0f;
+            uint32_t rs = 0u, gs = 0u, bs = 0u;
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+#pragma unroll
+                for (int j = 0; j < 3; ++j) {
+                    if (z[r][j] != kEmpty) {
+                        s = __fadd_rn(s, __uint_as_float(z[r][j]));
+                        cnt += 1.0f;
                     }
                 }
-                const float npx = (float)((xb - xa) * (yb - y0));
-                const int64_t o = (int64_t)J * F.cpitch + I;
-                F.cguide[o] = make_float4(__fdiv_rn(rr, npx), __fdiv_rn(gg, npx), __fdiv_rn(bb, npx), cnt);
-                F.cssum[o] = s;
+                // bytes c0 .. c8 of the row (r, g, b of 3 pixels) into a0 = c0..c3, a1 = c4..c7, a2 = c8..
+                const uint32_t a0 = __funnelshift_r(c[r][0], c[r][1], 8 * o);
+                const uint32_t a1 = __funnelshift_r(c[r][1], c[r][2], 8 * o);
+                const uint32_t a2 = c[r][2] >> (8 * o);
+                rs = __dp4a(__byte_perm(a0, a1, 0x0630), 0x00010101u, rs);   // c0 + c3 + c6
+                gs = __dp4a(__byte_perm(a0, a1, 0x0741), 0x00010101u, gs);   // c1 + c4 + c7
+                bs = __dp4a(__byte_perm(a0, a1, 0x0052), 0x00000101u, bs) + (a2 & 0xFFu);   // c2 + c5 + c8
             }
-            __syncwarp();
-        } else if (I < F.Wc) {   // other pooling factors: direct loads
-            const int x0 = I * f;
+            pool_store(F, I, J, (float)rs, (float)gs, (float)bs, cnt, s, 9.0f);
+        } else {
             const int x1 = min(x0 + f, F.W), y1 = min(y0 + f, F.H);
             float s = 0.0f, cnt = 0.0f, r = 0.0f, g = 0.0f, b = 0.0f;
             for (int y = y0; y < y1; ++y) {
                 const uint32_t *zr = F.zbuf + (int64_t)y * F.zpitch;
                 const uint8_t *cr = F.rgb + (int64_t)y * F.rgb_pitch;
                 for (int x = x0; x < x1; ++x) {
-                    const uint32_t z = zr[x];
-                    if (z != kEmpty) {
-                        s = __fadd_rn(s, __uint_as_float(z));
+                    const uint32_t zz = zr[x];
+                    if (zz != kEmpty) {
+                        s = __fadd_rn(s, __uint_as_float(zz));
                         cnt += 1.0f;
                     }
                     r += (float)cr[3 * x];
@@ -99,10 +94,7 @@ __global__ void __launch_bounds__(kThreads) pool_kernel(const BatchDev *__restri
                     b += (float)cr[3 * x + 2];
                 }
             }
-            const float npx = (float)((x1 - x0) * (y1 - y0));
-            const int64_t o = (int64_t)J * F.cpitch + I;
-            F.cguide[o] = make_float4(__fdiv_rn(r, npx), __fdiv_rn(g, npx), __fdiv_rn(b, npx), cnt);
-            F.cssum[o] = s;
+            pool_store(F, I, J, r, g, b, cnt, s, (float)((x1 - x0) * (y1 - y0)));
         }
     }
 }
@@ -114,12 +106,12 @@ cudaError_t launch_pool(const BatchDev *b, int pool, int grid, cudaStream_t s) {
 
 // ---------------------------------------------------------------------------
 // back-projection with deterministic compaction.
-// A chunk is 4096 consecutive pixels in row-major order. bp_count writes each
-// chunk's number of valid pixels. In bp_write, warp w of the block owns pixels
-// [512 w, 512 w + 512) of the chunk in 4 steps of 128 (4 per lane): the warp's
-// output offset is the sum of the frame's earlier chunks plus the earlier
-// warps of the chunk; inside a step an inclusive warp scan of the lanes'
-// counts places every point. Points are built in shared memory and leave in
+// A chunk is 4096 consecutive pixels in row-major order, a part its 512-pixel
+// eighth. bp_count writes each part's number of valid pixels and bp_scan turns
+// them into each frame's exclusive prefix. In bp_write, warp w of the block
+// owns part w of the chunk in 4 steps of 128 pixels (4 per lane): the warp's
+// output offset is its part's prefix, so warps never wait for one another;
+// inside a step an inclusive warp scan of the lanes' counts places every point. Points are built in shared memory and leave in
 // coalesced 16-byte stores. Each point is
 //   (x, y, z) = cam_to_world * ((u + 1/2 - cx) Z / fx, (v + 1/2 - cy) Z / fy, Z)
 // with the pixel colour packed r | g << 8 | b << 16 | 255 << 24.
@@ -136,74 +128,93 @@ __device__ __forceinline__ uint32_t valid_bits4(const uint8_t *v, int64_t p, int
     return m;
 }
 
+// One count per warp: valid pixels of its 512-pixel part of the chunk (16 per lane).
 __global__ void __launch_bounds__(kThreads) bp_count_kernel(const BatchDev *__restrict__ B) {
-    __shared__ uint32_t wsum[kThreads / 32];
     const int nf = B->n_frames;
-    const int total = B->bp_pre[nf];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int total = B->bp_pre[nf] * kBpWarps;
+    const int lane = threadIdx.x & 31;
+    for (int wi = blockIdx.x * kBpWarps + (threadIdx.x >> 5); wi < total; wi += gridDim.x * kBpWarps) {
+        const int item = wi / kBpWarps;
         const int fi = find_segment(B->bp_pre, nf, item);
         const FrameDev &F = B->f[fi];
-        const int c = item - B->bp_pre[fi];
+        const int sub = (item - B->bp_pre[fi]) * kBpWarps + wi % kBpWarps;   // the frame's part index
         const int64_t n = (int64_t)F.W * F.H;
-        const int64_t p = (int64_t)c * kBpChunk + threadIdx.x * 16;
+        const int64_t p = (int64_t)sub * kBpPart + lane * 16;
         uint32_t cnt = 0;
         if ((((uintptr_t)F.out_valid) & 15u) == 0 && p + 16 <= n) {
-            const uint4 w = *reinterpret_cast<const uint4 *>(F.out_valid + p);
+            const uint4 w = *reinterpret_cast<const uint4 *>(F.out_valid + p);   // bytes are 0 or 1
             cnt = __popc(w.x) + __popc(w.y) + __popc(w.z) + __popc(w.w);
         } else {
             for (int k = 0; k < 16; ++k) cnt += (p + k < n && F.out_valid[p + k]) ? 1u : 0u;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        __syncthreads();
-        if (lane == 0) wsum[warp] = cnt;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            uint32_t t = 0;
-            for (int w = 0; w < kThreads / 32; ++w) t += wsum[w];
-            F.chunk_cnt[c] = t;
-        }
+        if (lane == 0) F.chunk_cnt[sub] = cnt;
     }
 }
 
-// Exclusive prefix of the chunk counts of every frame, in place, and the
-// frame's point count. One block per frame.
-__global__ void __launch_bounds__(kThreads) bp_scan_kernel(const BatchDev *__restrict__ B) {
-    __shared__ uint32_t wsum[kThreads / 32];
+// Exclusive prefix of the part counts of every frame, in place, and the
+// frame's point count. One block of kScanBlock threads per frame: thread t
+// takes the contiguous run of E = ceil(parts / kScanBlock) counts starting at
+// t * E, sums it, the block scans the run sums (warp scans, then the warp
+// totals) and each thread writes its run's exclusive prefixes.
+constexpr int kScanBlock = 1024;
+__global__ void __launch_bounds__(kScanBlock) bp_scan_kernel(const BatchDev *__restrict__ B) {
+    __shared__ uint32_t wsum[kScanBlock / 32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int fi = blockIdx.x; fi < B->n_frames; fi += gridDim.x) {
         const FrameDev &F = B->f[fi];
-        if (F.n_bp_chunks == 0 || !F.points_n) continue;
-        uint32_t carry = 0;
-        for (int c0 = 0; c0 < F.n_bp_chunks; c0 += kThreads) {
-            const int c = c0 + threadIdx.x;
-            const uint32_t v = c < F.n_bp_chunks ? F.chunk_cnt[c] : 0u;
-            uint32_t incl = v;
+        const int nparts = F.n_bp_chunks * kBpWarps;
+        if (nparts == 0 || !F.points_n) continue;
+        const int E = (nparts + kScanBlock - 1) / kScanBlock;
+        const int c0 = threadIdx.x * E, c1 = min(nparts, c0 + E);
+        uint32_t run = 0;
+#pragma unroll 4
+        for (int c = c0; c < c1; ++c) run += F.chunk_cnt[c];
+        uint32_t incl = run;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += u;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            const uint32_t v = wsum[lane];
+            uint32_t w = v;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t u = __shfl_up_sync(0xffffffffu, incl, o);
-                if (lane >= o) incl += u;
+                const uint32_t u = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += u;
             }
-            __syncthreads();
-            if (lane == 31) wsum[warp] = incl;
-            __syncthreads();
-            uint32_t before = carry, all = carry;
-            for (int w = 0; w < kThreads / 32; ++w) {
-                if (w < warp) before += wsum[w];
-                all += wsum[w];
-            }
-            if (c < F.n_bp_chunks) F.chunk_cnt[c] = before + incl - v;
-            carry = all;
+            wsum[lane] = w - v;                                  // exclusive over warps
+            if (lane == 31 && threadIdx.x == 31) *F.points_n = (int64_t)w;   // the frame's total
         }
-        if (threadIdx.x == 0) *F.points_n = (int64_t)carry;
         __syncthreads();
+        uint32_t before = wsum[warp] + incl - run;
+        for (int c = c0; c < c1; ++c) {
+            const uint32_t v = F.chunk_cnt[c];
+            F.chunk_cnt[c] = before;
+            before += v;
+        }
+        __syncthreads();                                         // wsum is reused by the next frame
     }
 }
 
-__global__ void __launch_bounds__(kThreads) bp_write_kernel(const BatchDev *__restrict__ B) {
+// (row, column) of pixel p of a row-major image of width W: a float estimate of
+// p / W corrected by integer steps (exact for every p; one step at most while
+// p < 2^24)
+__device__ __forceinline__ void row_col(int64_t p, int W, float inv_w, int &y, int &x) {
+    int64_t q = (int64_t)((float)p * inv_w);
+    int64_t r = p - q * W;
+    while (r < 0) { --q; r += W; }
+    while (r >= W) { ++q; r -= W; }
+    y = (int)q;
+    x = (int)r;
+}
+
+__global__ void __launch_bounds__(kThreads, 4) bp_write_kernel(const BatchDev *__restrict__ B) {
     __shared__ float4 stage[kThreads / 32][128];
-    __shared__ uint32_t wtot[kThreads / 32];
     const int nf = B->n_frames;
     const int total = B->bp_pre[nf];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -217,48 +228,34 @@ __global__ void __launch_bounds__(kThreads) bp_write_kernel(const BatchDev *__re
         const bool vdepth = (((uintptr_t)F.out_depth) & 15u) == 0;
         const bool rows4 = (W & 3) == 0 && (F.rgb_pitch & 3) == 0 && (((uintptr_t)F.rgb) & 3u) == 0;
         const int64_t wbase = (int64_t)c * kBpChunk + warp * 512;
-        uint32_t m[4], wc = 0;
-#pragma unroll
-        for (int it = 0; it < 4; ++it) {
-            m[it] = valid_bits4(F.out_valid, wbase + it * 128 + lane * 4, n, vvalid);
-            wc += __popc(m[it]);
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) wc += __shfl_xor_sync(0xffffffffu, wc, o);
-        __syncthreads();   // the previous chunk is done with wtot
-        if (lane == 0) wtot[warp] = wc;
-        __syncthreads();
-        int64_t off = F.chunk_cnt[c];   // exclusive prefix of the chunk counts (bp_scan_kernel)
-        for (int w = 0; w < warp; ++w) off += wtot[w];
-
         const float *c2w = F.c2w32;
         const float r00 = c2w[0], r01 = c2w[1], r02 = c2w[2], t0 = c2w[3];
         const float r10 = c2w[4], r11 = c2w[5], r12 = c2w[6], t1 = c2w[7];
         const float r20 = c2w[8], r21 = c2w[9], r22 = c2w[10], t2 = c2w[11];
-        const float ifx = 1.0f / F.fx, ify = 1.0f / F.fy;
+        const float ifx = 1.0f / F.fx, ify = 1.0f / F.fy, iw = 1.0f / (float)W;
         float4 *st = stage[warp];
-        // issue the loads of all four steps before using any of them (memory-level parallelism)
+        // all loads of the four steps (validity, depth, colour) are issued before any is used:
+        // one memory round trip per chunk; depth and colour lines are mostly needed anyway
+        uint32_t m[4];
         float4 zq[4];
         uint32_t cw[4][3];
-        int yq[4], xq[4];
 #pragma unroll
         for (int it = 0; it < 4; ++it) {
             const int64_t p0 = wbase + it * 128 + lane * 4;
+            m[it] = valid_bits4(F.out_valid, p0, n, vvalid);
             zq[it] = make_float4(0.f, 0.f, 0.f, 0.f);
             cw[it][0] = cw[it][1] = cw[it][2] = 0u;
-            yq[it] = 0;
-            xq[it] = 0;
-            if (m[it] && vdepth && rows4 && p0 + 4 <= n) {
+            if (vdepth && rows4 && p0 + 4 <= n) {
                 zq[it] = *reinterpret_cast<const float4 *>(F.out_depth + p0);
-                yq[it] = (int)(p0 / W);
-                xq[it] = (int)(p0 - (int64_t)yq[it] * W);
-                const uint32_t *cp =
-                    reinterpret_cast<const uint32_t *>(F.rgb + (int64_t)yq[it] * F.rgb_pitch + 3 * xq[it]);
+                int y, x;
+                row_col(p0, W, iw, y, x);
+                const uint32_t *cp = reinterpret_cast<const uint32_t *>(F.rgb + (int64_t)y * F.rgb_pitch + 3 * x);
                 cw[it][0] = cp[0];
                 cw[it][1] = cp[1];
                 cw[it][2] = cp[2];
             }
         }
+        int64_t off = F.chunk_cnt[c * kBpWarps + warp];   // exclusive prefix of the part counts (bp_scan_kernel)
 #pragma unroll
         for (int it = 0; it < 4; ++it) {
             const uint32_t cnt = __popc(m[it]);
@@ -278,7 +275,8 @@ __global__ void __launch_bounds__(kThreads) bp_write_kernel(const BatchDev *__re
                     const uint32_t w0 = cw[it][0], w1 = cw[it][1], w2 = cw[it][2];
                     const uint32_t col[4] = {w0 & 0xFFFFFFu, (w0 >> 24) | ((w1 & 0xFFFFu) << 8),
                                              (w1 >> 16) | ((w2 & 0xFFu) << 16), w2 >> 8};
-                    const int y = yq[it], x0 = xq[it];
+                    int y, x0;
+                    row_col(p0, W, iw, y, x0);
                     const float Y = ((float)y + 0.5f - F.cy) * ify;
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
@@ -297,7 +295,8 @@ __global__ void __launch_bounds__(kThreads) bp_write_kernel(const BatchDev *__re
                     for (int k = 0; k < 4; ++k) {
                         if (m[it] >> k & 1u) {
                             const int64_t p = p0 + k;
-                            const int y = (int)(p / W), x = (int)(p - (int64_t)y * W);
+                            int y, x;
+                            row_col(p, W, iw, y, x);
                             const uint8_t *cb = F.rgb + (int64_t)y * F.rgb_pitch + 3 * x;
                             const uint32_t rgba = (uint32_t)cb[0] | ((uint32_t)cb[1] << 8) | ((uint32_t)cb[2] << 16) |
                                                   0xFF000000u;
@@ -327,7 +326,7 @@ cudaError_t launch_bp_count(const BatchDev *b, int grid, cudaStream_t s) {
     bp_count_kernel<<<grid, kThreads, 0, s>>>(b);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    bp_scan_kernel<<<kMaxBatch, kThreads, 0, s>>>(b);
+    bp_scan_kernel<<<kMaxBatch, kScanBlock, 0, s>>>(b);
     return cudaGetLastError();
 }
 

@@ -136,7 +136,7 @@ extern "C" DENSIFY_API densify_status densify_frame_noalloc(const densify_params
         o += up256((size_t)cpitch * Hc * 8);
     }
     const size_t off_cnt = o;
-    o += up256((size_t)n_bp * 4);
+    o += up256((size_t)n_bp * kBpWarps * 4);
     if (o > kNoallocScratchBytes)
         return fail(DENSIFY_E_INVALID, "frame needs " + std::to_string(o) + " bytes of scratch; the no-allocation "
                                        "entry holds " + std::to_string(kNoallocScratchBytes) +

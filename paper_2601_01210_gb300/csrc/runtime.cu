@@ -132,6 +132,9 @@ struct Slot {
     cudaGraphExec_t exec = nullptr;
     bool busy = false;
     std::vector<uint64_t> tickets;
+    int32_t *d_tiles = nullptr;  // tile lists of the TMA filters (both stages)
+    int64_t tiles_cap = 0;
+    int nkern = 0;               // CUDA kernels one batch of this slot launches
 };
 
 // One filter launch: which kernel runs it and its tile height.
@@ -140,6 +143,7 @@ struct FilterSel {
     int radius = 0;
     bool tma = false;
     bool half = false;   // FP16 form
+    int form = 0;        // arithmetic form of a TMA kernel (TMA_FORM_*)
     int src = 0;         // TMA source kind
     int kp = 0;          // output rows per thread
     int nw = 8;          // warps per CTA (tile height = kp * nw)
@@ -208,6 +212,7 @@ struct densify_ctx {
     bool dead = false;
     double t_us[K_COUNT] = {};
     int64_t t_n[K_COUNT] = {};
+    int64_t kernel_launches = 0;   // CUDA kernels of completed batches
 };
 
 namespace {
@@ -256,24 +261,39 @@ bool stage_supported(int kind, int r) {
 std::vector<FilterSel> filter_candidates(const densify_params &p, int kind, int r) {
     std::vector<FilterSel> out;
     const int src = kind == 0 ? TMA_SRC_ZBUF : kind == 1 ? TMA_SRC_COARSE : TMA_SRC_UP;
-    const bool allowed = p.kernel_variant == 0 && (kind != 2 || (p.pool == 3 && p.stage2_input == 0));
+    const bool allowed = p.kernel_variant != 1 && (kind != 2 || (p.pool == 3 && p.stage2_input == 0));
     // FP16: the full-resolution stage (the pooled first stage stays FP32)
     const bool half = p.precision == DENSIFY_FP16 && kind != 1;
-    if (allowed) {
-        TmaVariant vs[8];
-        const int n = jbf_tma_variants(src, r, half, vs, 8);
+    auto add_tma = [&](int form) {
+        TmaVariant vs[16];
+        const int n = jbf_tma_variants(src, r, form, vs, 16);
         for (int i = 0; i < n; ++i) {
             FilterSel s;
             s.kind = kind;
             s.radius = r;
             s.tma = true;
-            s.half = half;
+            s.half = form == TMA_FORM_FP16;
+            s.form = form;
             s.src = src;
             s.kp = vs[i].kp;
             s.nw = vs[i].nw;
-            jbf_tma_info(src, r, vs[i], half, &s.info);
+            jbf_tma_info(src, r, vs[i], form, &s.info);
             s.tile_h = s.info.tile_h;
             out.push_back(s);
+        }
+    };
+    if (allowed) {
+        if (half) {
+            add_tma(TMA_FORM_FP16);
+        } else {
+            // expanded FP32 form first where its weights stay in range (colours centred at 128)
+            const densify_stage &st = p.stage[kind == 2 ? 1 : 0];
+            const double log2e = 1.4426950408889634;
+            const double kc = log2e / (2.0 * (double)st.sigma_c * (double)st.sigma_c);
+            const double kp = log2e / (2.0 * (double)st.sigma_p * (double)st.sigma_p);
+            if (p.kernel_variant == 0 && kc * 3.0 * 128.0 * 128.0 + kp * 2.0 * r * r <= kExpRange)
+                add_tma(TMA_FORM_EXP);
+            add_tma(TMA_FORM_FP32);
         }
     }
     if (!half) {
@@ -315,6 +335,12 @@ void fill_stage(StageArgs &a, const densify_stage &st, int pool, int override_sp
             const float second = (d >= 1 && d - 1 < T && dx < T) ? a.sp[(d - 1) * (2 * kMaxR + 1) + dx] : ninf;
             a.sp2[d * (2 * kMaxR + 1) + dx] = h2(first, second);
         }
+    const double kp = log2e / (2.0 * (double)st.sigma_p * (double)st.sigma_p);
+    for (int i = 0; i < 2 * kMaxR + 1; ++i) {
+        const double o2 = (double)((i - R) * (i - R));
+        a.ex_sx[i] = i < T ? (float)std::exp2(-o2 * kp) : 0.0f;
+        a.ex_sy[i] = i < T ? (float)(-o2 * kp) : 0.0f;
+    }
 }
 
 std::string validate_params(const densify_params &p) {
@@ -333,7 +359,7 @@ std::string validate_params(const densify_params &p) {
         const int full = p.num_stages == 2 ? 1 : 0;   // the full-resolution stage
         const int kind = p.num_stages == 2 ? 2 : 0;
         TmaVariant vs[8];
-        if (jbf_tma_variants(kind == 2 ? TMA_SRC_UP : TMA_SRC_ZBUF, p.stage[full].radius, true, vs, 8) == 0 ||
+        if (jbf_tma_variants(kind == 2 ? TMA_SRC_UP : TMA_SRC_ZBUF, p.stage[full].radius, TMA_FORM_FP16, vs, 8) == 0 ||
             (kind == 2 && (p.pool != 3 || p.stage2_input != 0)))
             return "FP16 form available for the full-resolution stage with radius 1-3 (pool 3, stage2_input 0) "
                    "after a first stage, or radius 2, 4, 7 as the only stage";
@@ -343,7 +369,7 @@ std::string validate_params(const densify_params &p) {
     if (p.batches_in_flight < 1 || p.batches_in_flight > 8) return "batches_in_flight must be in 1..8";
     if (p.hbm_budget_bytes < (1u << 20)) return "hbm_budget_bytes must be >= 1 MiB";
     if (p.launch_policy != 0 && p.launch_policy != 1) return "launch_policy must be 0 or 1";
-    if (p.kernel_variant != 0 && p.kernel_variant != 1) return "kernel_variant must be 0 or 1";
+    if (p.kernel_variant < 0 || p.kernel_variant > 2) return "kernel_variant must be 0, 1 or 2";
     if (p.autotune != 0 && p.autotune != 1) return "autotune must be 0 or 1";
     if (p.occlusion_radius < 0 || p.occlusion_radius > 16) return "occlusion_radius must be in 0..16";
     if (!std::isfinite(p.occlusion_margin) || p.occlusion_margin < 0.0f) return "occlusion_margin must be >= 0";
@@ -429,7 +455,7 @@ Layout layout_of(const densify_params &p, const densify_frame *f) {
         if (host && f->out_coarse) L.coarse = take(Wc * Hc * 4);
         if (host && f->out_coarse_valid) L.coarse_valid = take(Wc * Hc);
     }
-    L.chunk = take(((npx + kBpChunk - 1) / kBpChunk) * 4);
+    L.chunk = take(((npx + kBpChunk - 1) / kBpChunk) * kBpWarps * 4);
     L.own_depth = host || !f->out_depth;
     L.own_valid = host || !f->out_valid;
     if (L.own_depth) L.depth = take(npx * 4);
@@ -558,6 +584,7 @@ void set_filter(densify_ctx *c, int i, const FilterSel &f) {
 
 cudaError_t launch_filter(densify_ctx *c, int i, const BatchDev *b, cudaStream_t s);
 void fill_batch(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &tk);
+densify_status prepare_tile_lists(densify_ctx *c, Slot &sl);
 std::string encode_maps(densify_ctx *c, FrameDev &d);
 
 // Autotuner: on the context's first batch, time every candidate kernel of each
@@ -603,7 +630,9 @@ void cache_store(const std::string &key, const std::string &val) {
 }
 
 std::string cand_name(const FilterSel &f) {
-    return std::string(f.tma ? "tma" : "plain") + ":kp" + std::to_string(f.kp) + ":nw" + std::to_string(f.nw);
+    static const char *forms[] = {"fp32", "fp16", "exp"};
+    return std::string(f.tma ? "tma" : "plain") + ":kp" + std::to_string(f.kp) + ":nw" + std::to_string(f.nw) +
+           (f.tma ? std::string(":") + forms[f.form] : std::string());
 }
 
 densify_status autotune(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &tk) {
@@ -637,6 +666,7 @@ densify_status autotune(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &t
                 }
                 if (st != DENSIFY_OK) break;
                 fill_batch(c, sl, tk);
+                if ((st = prepare_tile_lists(c, sl)) != DENSIFY_OK) break;
                 const size_t bytes = offsetof(BatchDev, f) + sizeof(FrameDev) * tk.size();
                 cudaError_t e = cudaMemcpyAsync(sl.d, sl.h, bytes, cudaMemcpyHostToDevice, sl.stream);
                 // inputs of this stage
@@ -679,10 +709,40 @@ densify_status autotune(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &t
     return st;
 }
 
+// Tile lists of the batch's TMA filters: room for every tile of both stages,
+// pointers and zero counts in the host descriptor (uploaded with it).
+densify_status prepare_tile_lists(densify_ctx *c, Slot &sl) {
+    BatchDev &b = *sl.h;
+    const int n = b.n_frames;
+    const int64_t need = (int64_t)b.t1_pre[n] + b.t2_pre[n];
+    if (need > sl.tiles_cap) {
+        if (sl.d_tiles) {
+            CU(cudaStreamSynchronize(sl.stream), "tile list");
+            cudaFree(sl.d_tiles);
+            sl.d_tiles = nullptr;
+            sl.tiles_cap = 0;
+        }
+        const int64_t cap = std::max<int64_t>(need + need / 2, 4096);
+        CU(cudaMalloc(&sl.d_tiles, (size_t)cap * sizeof(int32_t)), "tile list allocation");
+        sl.tiles_cap = cap;
+    }
+    b.tl_count[0] = b.tl_count[1] = 0;
+    b.tl_list[0] = sl.d_tiles;
+    b.tl_list[1] = sl.d_tiles + b.t1_pre[n];
+    return DENSIFY_OK;
+}
+
+// CUDA kernels of one filter launch (TMA: tile scan + filter).
+int filter_kernels(const densify_ctx *c, int i) { return c->sel[i].tma ? 2 : 1; }
+
 cudaError_t launch_filter(densify_ctx *c, int i, const BatchDev *b, cudaStream_t s) {
     const FilterSel &f = c->sel[i];
     const int k = i == 0 ? K_JBF1 : K_JBF2;
-    if (f.tma) return launch_jbf_tma(f.src, f.radius, TmaVariant{f.kp, f.nw}, f.half, b, c->sa[i], c->grid[k], s);
+    if (f.tma) {
+        cudaError_t e = launch_tile_scan(f.src, b, i, f.tile_h, f.radius, c->sms * 8, s);
+        if (e != cudaSuccess) return e;
+        return launch_jbf_tma(f.src, f.radius, TmaVariant{f.kp, f.nw}, f.form, b, c->sa[i], c->grid[k], s);
+    }
     if (f.kind == 0) return launch_jbf_single(f.radius, b, c->sa[i], c->grid[k], s);
     if (f.kind == 1) return launch_jbf_coarse(f.radius, b, c->sa[i], c->grid[k], s);
     return launch_jbf_up(f.radius, b, c->sa[i], c->grid[k], s);
@@ -732,6 +792,10 @@ densify_status issue_kernels(densify_ctx *c, Slot &sl, cudaStream_t s, bool reco
         return cudaEventRecordWithFlags(sl.kev[ev++], s, s == c->cap_stream ? cudaEventRecordExternal : 0);
     };
     for (int k = 0; k < K_COUNT; ++k) sl.ktimed[k] = false;
+    int nk = 1 + (c->p.motion_threshold > 0.0f ? 3 : 0) + 1 + (c->p.occlusion_radius > 0 ? 1 : 0) +
+             (nst == 2 ? 1 + filter_kernels(c, 0) + filter_kernels(c, 1) : filter_kernels(c, 0)) +
+             (c->p.contour_threshold > 0.0f ? 1 : 0) + (c->p.emit_points ? 3 : 0);
+    sl.nkern = nk;   // prep, motion (3), project, occlusion, pool, filters, contour, compaction (3)
     CU(mark(-1), "event");
     CU(launch_prep(b, c->grid[K_PREP], s), "prep launch");
     CU(mark(K_PREP), "event");
@@ -795,6 +859,10 @@ densify_status launch_batch(densify_ctx *c, int si) {
         }
     }
     fill_batch(c, sl, tk);
+    {
+        densify_status st = prepare_tile_lists(c, sl);
+        if (st != DENSIFY_OK) return st;
+    }
     const size_t bytes = offsetof(BatchDev, f) + sizeof(FrameDev) * tk.size();
     CU(cudaMemcpyAsync(sl.d, sl.h, bytes, cudaMemcpyHostToDevice, sl.stream), "descriptor upload");
     // host frames: inputs in
@@ -916,6 +984,7 @@ densify_status complete_slot(densify_ctx *c, Slot &sl) {
             ++ev;
         }
     }
+    c->kernel_launches += sl.nkern;
     for (uint64_t t : sl.tickets) {
         auto it = c->frames.find(t);
         if (it != c->frames.end()) it->second.state = 2;
@@ -991,6 +1060,7 @@ void destroy_resources(densify_ctx *c) {
         if (sl.d) cudaFree(sl.d);
         if (sl.h) cudaFreeHost(sl.h);
         if (sl.d_status) cudaFree(sl.d_status);
+        if (sl.d_tiles) cudaFree(sl.d_tiles);
         if (sl.h_status) cudaFreeHost(sl.h_status);
     }
     c->slots.clear();
@@ -1140,9 +1210,9 @@ densify_status densify_create(const densify_params *params, int device, void *cu
         if (c->cands[i].empty()) return bail(DENSIFY_E_INVALID, "no kernel for filter stage " + std::to_string(i));
         for (FilterSel &f : c->cands[i]) {
             if (f.tma) {
-                if ((e = jbf_tma_prepare(f.src, f.radius, TmaVariant{f.kp, f.nw}, f.half)) != cudaSuccess)
+                if ((e = jbf_tma_prepare(f.src, f.radius, TmaVariant{f.kp, f.nw}, f.form)) != cudaSuccess)
                     return bail(DENSIFY_E_CUDA, std::string("filter setup: ") + cudaGetErrorString(e));
-                f.occ = occupancy_jbf_tma(f.src, f.radius, TmaVariant{f.kp, f.nw}, f.half);
+                f.occ = occupancy_jbf_tma(f.src, f.radius, TmaVariant{f.kp, f.nw}, f.form);
             } else {
                 f.occ = kind == 0 ? occupancy_jbf_single(f.radius) : kind == 1 ? occupancy_jbf_coarse(f.radius)
                                                                               : occupancy_jbf_up(f.radius);
@@ -1348,8 +1418,10 @@ int32_t densify_describe(densify_ctx *c, char *buf, int32_t cap) {
         char tmp[256];
         std::snprintf(tmp, sizeof tmp,
                       "{\"kernel\": \"%s\", \"kp\": %d, \"warps\": %d, \"tile\": [32, %d], \"fp16\": %s, "
-                      "\"ctas_per_sm\": %d%s",
-                      f.tma ? "tma" : "plain", f.kp, f.nw, f.tile_h, f.half ? "true" : "false", f.occ,
+                      "\"form\": \"%s\", \"ctas_per_sm\": %d%s",
+                      f.tma ? "tma" : "plain", f.kp, f.nw, f.tile_h, f.half ? "true" : "false",
+                      f.half ? "fp16" : f.form == TMA_FORM_EXP ? "fp32_expanded" : "fp32",
+                      f.occ,
                       f.tuned_us >= 0.0f ? "" : "}");
         std::string s(tmp);
         if (f.tuned_us >= 0.0f) {
@@ -1383,6 +1455,14 @@ void densify_reset_kernel_times(densify_ctx *c) {
         c->t_us[k] = 0.0;
         c->t_n[k] = 0;
     }
+    c->kernel_launches = 0;
+}
+
+int64_t densify_kernel_launches(densify_ctx *c) {
+    if (!c) return 0;
+    DeviceGuard guard(c->device);
+    progress(c, false);
+    return c->kernel_launches;
 }
 
 }  // extern "C"

@@ -27,13 +27,30 @@ struct TmaKernelInfo {
     int cssum_box[2];
 };
 
-// Instantiated variants: (source, radius, rows per thread kp, FP16 form). half: guide and
-// weights in FP16 with FP32 sums (full-resolution stages only).
-int jbf_tma_variants(int src, int r, bool half, TmaVariant *out, int cap);   // instantiated variants
-bool jbf_tma_info(int src, int r, TmaVariant v, bool half, TmaKernelInfo *out);
-cudaError_t jbf_tma_prepare(int src, int r, TmaVariant v, bool half);
-cudaError_t launch_jbf_tma(int src, int r, TmaVariant v, bool half, const BatchDev *b, const StageArgs &a, int grid,
+// Arithmetic forms of the filter kernels: FP32 with colour differences, FP16
+// guide and weights with FP32 sums (full-resolution stages only), FP32 with the
+// squared colour distance expanded into a dot product (weights kept in range
+// only while kc * 3 * 128^2 + kp * 2 R^2 <= kExpRange, see jbf_tma.cuh).
+enum { TMA_FORM_FP32 = 0, TMA_FORM_FP16 = 1, TMA_FORM_EXP = 2 };
+constexpr double kExpRange = 100.0;
+
+// Instantiated variants of (source, radius, form).
+int jbf_tma_variants(int src, int r, int form, TmaVariant *out, int cap);
+bool jbf_tma_info(int src, int r, TmaVariant v, int form, TmaKernelInfo *out);
+cudaError_t jbf_tma_prepare(int src, int r, TmaVariant v, int form);
+cudaError_t launch_jbf_tma(int src, int r, TmaVariant v, int form, const BatchDev *b, const StageArgs &a, int grid,
                            cudaStream_t s);
-int occupancy_jbf_tma(int src, int r, TmaVariant v, bool half);
+int occupancy_jbf_tma(int src, int r, TmaVariant v, int form);
+// Zero the stage's tile count, then list the tiles of the stage's grid (32 x th) that
+// some observation within radius r reaches and zero-fill the outputs of the others.
+cudaError_t launch_tile_scan(int src, const BatchDev *b, int stage, int th, int r, int grid, cudaStream_t s);
+
+// the expanded form's instantiations (k_jbf_tma_exp.cu)
+int jbf_tma_exp_variants(int src, int r, int form, TmaVariant *out, int cap);
+bool jbf_tma_exp_info(int src, int r, TmaVariant v, int form, TmaKernelInfo *out);
+cudaError_t jbf_tma_exp_prepare(int src, int r, TmaVariant v, int form);
+cudaError_t jbf_tma_exp_launch(int src, int r, TmaVariant v, int form, const BatchDev *b, const StageArgs &a,
+                               int grid, cudaStream_t s);
+int jbf_tma_exp_occupancy(int src, int r, TmaVariant v, int form);
 
 }  // namespace dz

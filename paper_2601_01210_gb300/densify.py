@@ -118,6 +118,7 @@ _SIGS = {
     "densify_kernel_times": ([C.c_void_p, C.POINTER(C.c_char_p), C.POINTER(C.c_double), C.POINTER(C.c_int64),
                               C.c_int32], C.c_int32),
     "densify_reset_kernel_times": ([C.c_void_p], None),
+    "densify_kernel_launches": ([C.c_void_p], C.c_int64),
     "densify_describe": ([C.c_void_p, C.c_char_p, C.c_int32], C.c_int32),
     "densify_sigma_grad": ([C.c_void_p, C.POINTER(densify_frame), C.c_void_p, C.POINTER(C.c_double),
                             C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
@@ -211,6 +212,10 @@ def densify_kernel_times(ctx, cap: int = 16):
 
 def densify_reset_kernel_times(ctx) -> None:
     lib().densify_reset_kernel_times(ctx)
+
+
+def densify_kernel_launches(ctx) -> int:
+    return int(lib().densify_kernel_launches(ctx))
 
 
 def densify_describe(ctx) -> str:
@@ -347,6 +352,10 @@ class Densifier:
 
     def reset_kernel_times(self):
         densify_reset_kernel_times(self.ctx)
+
+    def kernel_launches(self):
+        """CUDA kernels launched by completed batches since the last reset."""
+        return densify_kernel_launches(self.ctx)
 
     def close(self):
         if self.ctx:

@@ -1,6 +1,8 @@
 """Autotuner: on the first batch every kernel able to run a filter stage is
-timed on that batch and the fastest kept. All candidates evaluate the same
-sums in the same order, so tuned and untuned contexts give the same bits."""
+timed on that batch and the fastest kept. Candidates of one arithmetic form
+evaluate the same sums in the same order; the expanded and the difference FP32
+forms round differently, so tuned and untuned contexts agree bit for bit on
+every integer decision and within FP32 rounding on depth."""
 import json
 import os
 
@@ -43,15 +45,16 @@ def test_tuned_equals_untuned_and_cache_is_reused(tmp_path, monkeypatch, precisi
         if len(st["candidates"]) > 1:
             assert len(timed) == len(st["candidates"])
             best = min(timed, key=lambda c: c["tuned_us"])
-            assert (best["kernel"], best["kp"], best["warps"]) == (st["chosen"]["kernel"], st["chosen"]["kp"], st["chosen"]["warps"])
+            key = ("kernel", "kp", "warps", "form")
+            assert tuple(best[k] for k in key) == tuple(st["chosen"][k] for k in key)
     for a, b in zip(base, tuned):
         for k in ("valid", "rgba"):
             assert np.array_equal(a[k], b[k]), k
-        np.testing.assert_allclose(a["depth"], b["depth"], rtol=2e-6)
+        np.testing.assert_allclose(a["depth"], b["depth"], rtol=3e-5)
     lines = cache.read_text().splitlines()
     assert lines and all(" " in l for l in lines)
     # a second context with the same workload takes the choices from the cache without timing
     again, desc2 = _run(views, torch, precision=precision, autotune=1)
     assert cache.read_text().splitlines() == lines
     for s1, s2 in zip(desc["stages"], desc2["stages"]):
-        assert (s1["chosen"]["kernel"], s1["chosen"]["kp"], s1["chosen"]["warps"]) == (s2["chosen"]["kernel"], s2["chosen"]["kp"], s2["chosen"]["warps"])
+        assert all(s1["chosen"][k] == s2["chosen"][k] for k in ("kernel", "kp", "warps", "form"))

@@ -17,7 +17,7 @@ RTOL = 1e-4
 EMPTY = 0x7F800000
 QVGA_STAGES = ((4, 3.0, 20.0),)                       # 9x9 window, sigma_s 3 px, sigma_r 20
 PAPER_STAGES = ((4, 5.0, 20.0), (2, 5.0, 20.0))       # r=4 at 1/3, r=2 at full (Sec. 5)
-VARIANTS = [0, 1]                                     # TMA-staged filter kernels, plain kernels
+VARIANTS = [0, 1, 2]   # TMA kernels (expanded FP32 form where in range), plain kernels, TMA difference form
 
 
 @pytest.fixture(scope="module")
@@ -185,12 +185,19 @@ def test_batched_equals_alone(torch_cuda, variant):
 
 
 def test_variants_agree_bit_for_bit(torch_cuda):
-    """The TMA-staged and the plain filter kernels evaluate the same sums in the
-    same order: identical outputs."""
+    """The TMA-staged and the plain filter kernels in the difference form
+    evaluate the same sums in the same order: identical outputs. The expanded
+    form evaluates the same weights with other roundings: identical integer
+    decisions, depths within FP32 rounding (the exponent's terms reach about
+    2 * 88.6 in log2 units, so a few units of 2^-17 per exponent)."""
     v = scene.make_view(31, res="540p", scene_kind="room", n_scans=3, beams=64, az_steps=1024)
-    a = run_gpu([v], 2, PAPER_STAGES, torch_cuda, kernel_variant=0)[0]
+    e = run_gpu([v], 2, PAPER_STAGES, torch_cuda, kernel_variant=0)[0]
     b = run_gpu([v], 2, PAPER_STAGES, torch_cuda, kernel_variant=1)[0]
+    a = run_gpu([v], 2, PAPER_STAGES, torch_cuda, kernel_variant=2)[0]
     for k in ("valid", "coarse_valid", "zbuf"):
         assert np.array_equal(a[k], b[k]), k
+        assert np.array_equal(e[k], b[k]), k
     np.testing.assert_allclose(a["depth"], b["depth"], rtol=2e-6)
     np.testing.assert_allclose(a["coarse"], b["coarse"], rtol=2e-6)
+    np.testing.assert_allclose(e["depth"], b["depth"], rtol=3e-5)
+    np.testing.assert_allclose(e["coarse"], b["coarse"], rtol=3e-5)
