@@ -116,7 +116,10 @@ typedef struct densify_stage {
  *                 admission fails with DENSIFY_E_AGAIN when it is full.
  *   use_graphs    1: replay each batch slot's launch sequence as a CUDA graph.
  *   timing        1: record CUDA events around every kernel of every batch and
- *                 accumulate per-kernel device time (densify_kernel_times).
+ *                 accumulate per-kernel device time (densify_kernel_times);
+ *                 each event is a node of the batch's graph and adds a small
+ *                 gap between kernels. 2: events around the full-resolution
+ *                 (last) filter kernel only. 0: none.
  *   launch_policy 0 (eager): a queued frame goes to the GPU as soon as a
  *                 launch slot is free; frames that arrive while every slot is
  *                 busy are launched together when one frees (continuous

@@ -130,8 +130,12 @@ struct TmaGeom {
                                                       : RGB_BX * RGB_BY + Z_BX * Z_BY * 4;
     static constexpr int STAGED = SRC == SRC_COARSE && !EXP ? 0 : SH * SW * 16;
     static constexpr int STAGED_G = EXP ? ceil_to(SH * SW * 4, 16) : 0;   // expanded form: F_q times depth
-    static constexpr int OBS = SRC == SRC_COARSE ? 0 : ceil_to(SH * SW, 16);
-    static constexpr int HOR = ceil_to(SH * 4, 16);
+    // observation bitmap: bit i = staged position i observed; one word per 32 positions for
+    // every position the conversion loop visits, plus a zero guard word
+    static constexpr int NT = NW * 32, NCONV = (SH * SW + NT - 1) / NT;
+    static constexpr int OBS_WORDS = NCONV * NT / 32 + 1;
+    static constexpr int OBS = ceil_to(OBS_WORDS * 4, 16);
+    static constexpr int HOR = 0;
     static constexpr int OFF_RAW = 0;
     static constexpr int OFF_STAGED = OFF_RAW + 2 * (RAW_A + RAW_B);
     static constexpr int OFF_G = OFF_STAGED + STAGED;
@@ -176,8 +180,7 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
     float4 *staged = reinterpret_cast<float4 *>(smem + G::OFF_STAGED);
     uint4 *staged_h = reinterpret_cast<uint4 *>(smem + G::OFF_STAGED);   // FP16 records, same 16 bytes
     float *staged_g = reinterpret_cast<float *>(smem + G::OFF_G);         // expanded form: F_q times depth
-    uint8_t *obs = smem + G::OFF_OBS;
-    uint32_t *horw = reinterpret_cast<uint32_t *>(smem + G::OFF_HOR);
+    uint32_t *obsw = reinterpret_cast<uint32_t *>(smem + G::OFF_OBS);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + G::OFF_BAR);
 
     // the tiles that some observation reaches (tile_scan_kernel wrote the list and zero-filled the rest)
@@ -186,9 +189,12 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
     const int32_t *list = B->tl_list[stage];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    // list entry -> (frame, x0, y0)
-    auto locate = [&](int item, int &fi, int &x0, int &y0) {
-        const int e = list[item];
+    // Thread 0 issues the copies of the CTA's next tile while the CTA works on the current one. It
+    // reads the tile list one entry ahead (pend), acquires each frame's tensor maps once, and leaves
+    // the tile's (frame, x0, y0) in s_tile[buffer] for the other threads, so the start of a tile
+    // waits on no global load.
+    __shared__ int s_tile[2][3];
+    auto locate = [&](int e, int &fi, int &x0, int &y0) {
         fi = e >> 24;
         const FrameDev &F = B->f[fi];
         const int gw = SRC == SRC_COARSE ? F.Wc : F.W;
@@ -197,24 +203,32 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
         x0 = (t % tiles_x) * TW;
         y0 = (t / tiles_x) * TH;
     };
-    auto issue = [&](int item, int buf) {
+    uint64_t acquired = 0u;   // thread 0: frames whose tensor maps were acquired
+    auto issue = [&](int e, int buf) {
         int fi, x0, y0;
-        locate(item, fi, x0, y0);
+        locate(e, fi, x0, y0);
+        s_tile[buf][0] = fi;
+        s_tile[buf][1] = x0;
+        s_tile[buf][2] = y0;
         const FrameDev &F = B->f[fi];
+        const bool acq = !((acquired >> fi) & 1u);
+        acquired |= 1ull << fi;
         mbar_expect_tx(&bar[buf], G::TX_BYTES);
         if (SRC == SRC_COARSE) {
-            tmap_acquire(&F.tm[TM_CGUIDE]);
-            tmap_acquire(&F.tm[TM_CSSUM]);
+            if (acq) {
+                tmap_acquire(&F.tm[TM_CGUIDE]);
+                tmap_acquire(&F.tm[TM_CSSUM]);
+            }
             tma_load_2d(rawA(buf), &F.tm[TM_CGUIDE], 4 * (x0 - R), y0 - R, &bar[buf]);
             tma_load_2d(rawB(buf), &F.tm[TM_CSSUM], x0 - G::S_LEAD, y0 - R, &bar[buf]);
         } else {
-            tmap_acquire(&F.tm[TM_RGB]);
+            if (acq) tmap_acquire(&F.tm[TM_RGB]);
             tma_load_2d(rawA(buf), &F.tm[TM_RGB], 3 * x0 - G::RGB_LEAD, y0 - R, &bar[buf]);
             if (SRC == SRC_UP) {
-                tmap_acquire(&F.tm[TM_S1]);
+                if (acq) tmap_acquire(&F.tm[TM_S1]);
                 tma_load_2d(rawB(buf), &F.tm[TM_S1], floor_div3(x0 - R) & ~1, floor_div3(y0 - R), &bar[buf]);
             } else {
-                tmap_acquire(&F.tm[TM_ZBUF]);
+                if (acq) tmap_acquire(&F.tm[TM_ZBUF]);
                 tma_load_2d(rawB(buf), &F.tm[TM_ZBUF], x0 - G::Z_LEAD, y0 - R, &bar[buf]);
             }
         }
@@ -224,21 +238,26 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         mbar_fence_init();
+        obsw[G::OBS_WORDS - 1] = 0u;   // guard word, never rewritten
     }
     __syncthreads();
     uint32_t inflight = 0u;   // bit b: thread 0 issued copies into buffer b not yet consumed
     uint32_t phase = 0u;      // bit b: parity of buffer b's barrier
+    int pend = 0;             // thread 0: list entry of the tile it issues next
     if (threadIdx.x == 0 && (int)blockIdx.x < total) {
-        issue(blockIdx.x, 0);
+        issue(list[blockIdx.x], 0);
         inflight |= 1u;
+        if ((int)(blockIdx.x + gridDim.x) < total) pend = list[blockIdx.x + gridDim.x];
     }
+    __syncthreads();          // s_tile[0]
     int it = 0;
     for (int item = blockIdx.x; item < total; item += gridDim.x, ++it) {
         const int buf = it & 1;
         const int next = item + gridDim.x;
         if (threadIdx.x == 0 && next < total) {   // the other buffer was released by the last barrier
-            issue(next, buf ^ 1);
+            issue(pend, buf ^ 1);
             inflight |= 1u << (buf ^ 1);
+            if (next + (int)gridDim.x < total) pend = list[next + gridDim.x];   // used one tile later
         }
         const bool ok = mbar_wait_bounded(&bar[buf], (phase >> buf) & 1u);
         if (__syncthreads_or(!ok)) {
@@ -252,8 +271,7 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
         phase ^= 1u << buf;
         inflight &= ~(1u << buf);
 
-        int fi, x0, y0;
-        locate(item, fi, x0, y0);
+        const int fi = s_tile[buf][0], x0 = s_tile[buf][1], y0 = s_tile[buf][2];
         const FrameDev &F = B->f[fi];
         const int gw = SRC == SRC_COARSE ? F.Wc : F.W;
         const int gh = SRC == SRC_COARSE ? F.Hc : F.H;
@@ -272,7 +290,7 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
             const int gx = x0 - R + sx, gy = y0 - R + sy;
             if (gx < 0 || gx >= gw || gy < 0 || gy >= gh) return false;
             if (SRC == SRC_UP) {
-                const float2 c = craw[(gy / 3 - cy0) * G::C_BX + (gx / 3 - cx0)];
+                const float2 c = craw[((int)((unsigned)gy / 3u) - cy0) * G::C_BX + ((int)((unsigned)gx / 3u) - cx0)];
                 d = c.x;
                 return c.y > 0.0f;
             }
@@ -280,56 +298,75 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
             d = __uint_as_float(z);
             return z != kEmpty;
         };
-        if (SRC != SRC_COARSE) {
-            for (int i = threadIdx.x; i < SH * SW; i += NT) {
+        // Every thread converts positions threadIdx.x + j * NT in two unrolled passes: first every
+        // load of its positions (raw boxes; shared-memory stores in between would keep the compiler
+        // from overlapping them), then the records; a warp's ballot gives one word of the
+        // observation bitmap.
+        uint32_t omask = 0u;                     // bit j: position j observed
+        float dq[G::NCONV];                      // depth (SRC_UP / SRC_ZBUF) or depth sum (SRC_COARSE)
+        uint32_t c0[G::NCONV], c1[G::NCONV], c2[G::NCONV];   // colour bytes, or guide bits (SRC_COARSE)
+        float cw[G::NCONV];                      // pooled count (SRC_COARSE)
+#pragma unroll
+        for (int j = 0; j < G::NCONV; ++j) {
+            const int i = threadIdx.x + j * NT;
+            dq[j] = 0.0f;
+            c0[j] = c1[j] = c2[j] = 0u;
+            cw[j] = 0.0f;
+            if (i < SH * SW) {
                 const int sy = i / SW, sx = i - sy * SW;
-                float d = 0.0f;
-                const bool o = depth_of(sy, sx, d);
-                const uint8_t *p = rgb_at(sy, sx);
-                const float r = o ? (float)p[0] : 0.0f, g = o ? (float)p[1] : 0.0f, b = o ? (float)p[2] : 0.0f;
-                if (HALF) {
-                    staged_h[i] = o ? make_uint4(h2u(__float2half2_rn(r)), h2u(__float2half2_rn(g)),
-                                                 h2u(__float2half2_rn(b)), __float_as_uint(d))
-                                    : make_uint4(h2u(__float2half2_rn(65504.0f)), 0u, 0u, 0u);
-                } else if (EXP) {
-                    // centred colour (exact), F_q = 2^(-kc |c'_q|^2); unobserved: F_q = 0
-                    const float rr = r - 128.0f, gg = g - 128.0f, bb = b - 128.0f;
-                    const float f = o ? ex2_approx(-a.kc * fmaf(rr, rr, fmaf(gg, gg, bb * bb))) : 0.0f;
-                    staged[i] = o ? make_float4(rr, gg, bb, f) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                    staged_g[i] = o ? f * d : 0.0f;   // an empty z-buffer cell holds +inf
+                if (SRC != SRC_COARSE) {
+                    float d = 0.0f;
+                    if (depth_of(sy, sx, d)) omask |= 1u << j;
+                    dq[j] = d;
+                    const uint8_t *p = rgb_at(sy, sx);
+                    c0[j] = p[0];
+                    c1[j] = p[1];
+                    c2[j] = p[2];
                 } else {
-                    staged[i] = o ? make_float4(r, g, b, d) : make_float4(kSentinel, 0.0f, 0.0f, 0.0f);
+                    const float4 q = cg[i];
+                    c0[j] = __float_as_uint(q.x);
+                    c1[j] = __float_as_uint(q.y);
+                    c2[j] = __float_as_uint(q.z);
+                    cw[j] = q.w;
+                    if (q.w > 0.0f) omask |= 1u << j;
+                    if (EXP) dq[j] = cs[sy * G::S_BX + sx - R + G::S_LEAD];
                 }
-                obs[i] = o;
             }
-            __syncthreads();
-        } else if (EXP) {
-            // pooled guide: F_q times the count and times the depth sum (count 0: weight 0)
-            for (int i = threadIdx.x; i < SH * SW; i += NT) {
-                const int sy = i / SW, sx = i - sy * SW;
-                const float4 q = cg[i];
-                const float sum = cs[sy * G::S_BX + sx - R + G::S_LEAD];
-                const float rr = q.x - 128.0f, gg = q.y - 128.0f, bb = q.z - 128.0f;
-                const float f = ex2_approx(-a.kc * fmaf(rr, rr, fmaf(gg, gg, bb * bb)));
-                staged[i] = make_float4(rr, gg, bb, f * q.w);
-                staged_g[i] = f * sum;
-            }
-            __syncthreads();
         }
-        // ---- validity rows: bit x of horw[sy] = some observation at staged row sy, columns x .. x + 2R
-        for (int sy = warp; sy < SH; sy += NW) {
-            bool o0, o1;
-            if (SRC == SRC_COARSE) {
-                o0 = cg[sy * SW + lane].w > 0.0f;
-                o1 = lane + 32 < SW && cg[sy * SW + lane + 32].w > 0.0f;
-            } else {
-                o0 = obs[sy * SW + lane] != 0;
-                o1 = lane + 32 < SW && obs[sy * SW + lane + 32] != 0;
+        // byte b as an exact float minus bias: 2^23 + b has b in its low mantissa bits
+        auto bytef = [](uint32_t b, float bias) { return __uint_as_float(0x4B000000u | b) - (8388608.0f + bias); };
+#pragma unroll
+        for (int j = 0; j < G::NCONV; ++j) {
+            const int i = threadIdx.x + j * NT;
+            const bool o = (omask >> j) & 1u;
+            if (i < SH * SW) {
+                if (SRC != SRC_COARSE) {
+                    const float d = dq[j];
+                    if (HALF) {
+                        staged_h[i] = o ? make_uint4(h2u(__float2half2_rn(bytef(c0[j], 0.0f))),
+                                                     h2u(__float2half2_rn(bytef(c1[j], 0.0f))),
+                                                     h2u(__float2half2_rn(bytef(c2[j], 0.0f))), __float_as_uint(d))
+                                        : make_uint4(h2u(__float2half2_rn(65504.0f)), 0u, 0u, 0u);
+                    } else if (EXP) {
+                        // centred colour (exact), F_q = 2^(-kc |c'_q|^2); unobserved: F_q = 0
+                        const float rr = bytef(c0[j], 128.0f), gg = bytef(c1[j], 128.0f), bb = bytef(c2[j], 128.0f);
+                        const float f = o ? ex2_approx(-a.kc * fmaf(rr, rr, fmaf(gg, gg, bb * bb))) : 0.0f;
+                        staged[i] = o ? make_float4(rr, gg, bb, f) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                        staged_g[i] = o ? f * d : 0.0f;   // an empty z-buffer cell holds +inf
+                    } else {
+                        staged[i] = o ? make_float4(bytef(c0[j], 0.0f), bytef(c1[j], 0.0f), bytef(c2[j], 0.0f), d)
+                                      : make_float4(kSentinel, 0.0f, 0.0f, 0.0f);
+                    }
+                } else if (EXP) {   // pooled guide: F_q times the count and times the depth sum (count 0: weight 0)
+                    const float rr = __uint_as_float(c0[j]) - 128.0f, gg = __uint_as_float(c1[j]) - 128.0f,
+                                bb = __uint_as_float(c2[j]) - 128.0f;
+                    const float f = ex2_approx(-a.kc * fmaf(rr, rr, fmaf(gg, gg, bb * bb)));
+                    staged[i] = make_float4(rr, gg, bb, f * cw[j]);
+                    staged_g[i] = f * dq[j];
+                }
             }
-            const uint64_t m = ((uint64_t)__ballot_sync(0xffffffffu, o1) << 32) | __ballot_sync(0xffffffffu, o0);
-            const bool any = ((m >> lane) & ((1ull << T) - 1ull)) != 0;
-            const uint32_t hb = __ballot_sync(0xffffffffu, any);
-            if (lane == 0) horw[sy] = hb;
+            const uint32_t bits = __ballot_sync(0xffffffffu, o);
+            if (lane == 0) obsw[(threadIdx.x + j * NT) >> 5] = bits;
         }
         __syncthreads();
 
@@ -351,9 +388,13 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
             den[k] = 0.0f;
         }
         {
-            uint32_t rows = 0;   // bit iy: this column has an observation in staged row rbase + iy's window
+            uint32_t rows = 0;   // bit iy: an observation in staged row rbase + iy, columns lane .. lane + 2R
 #pragma unroll
-            for (int iy = 0; iy < KP + 2 * R; ++iy) rows |= ((horw[rbase + iy] >> lane) & 1u) << iy;
+            for (int iy = 0; iy < KP + 2 * R; ++iy) {
+                const int bit = (rbase + iy) * SW + lane;   // the window never leaves its row
+                const uint32_t win = __funnelshift_r(obsw[bit >> 5], obsw[(bit >> 5) + 1], bit & 31);
+                rows |= ((win & ((1u << T) - 1u)) != 0 ? 1u : 0u) << iy;
+            }
 #pragma unroll
             for (int k = 0; k < KP; ++k) {
                 val[k] = ((rows >> k) & ((1u << T) - 1u)) != 0;
@@ -518,7 +559,7 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
                     const uint8_t *p = rgb_at(sy, sx);
                     r = (float)p[0]; g = (float)p[1]; b = (float)p[2];
                     wd = 0.0f;
-                    seen = obs[o] != 0 && depth_of(sy, sx, wd);
+                    seen = depth_of(sy, sx, wd);
                     wb = 1.0f;
                 } else {
                     const float4 q = staged[o];
@@ -559,20 +600,23 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
     }
 }
 
-// Tile scan for the TMA filters: one block per tile of the stage's grid (tiles
-// of 32 x th, row-major per frame, as the stage's prefix array counts them);
-// the block's threads test the footprint (the tile grown by the radius, clipped
-// to the grid) with all their loads in flight at once. A tile whose footprint
-// holds no observation has only invalid outputs: the block writes them (depth
-// 0, invalid) and the tile is not listed. Every other tile is appended to the
-// stage's list (order immaterial: each tile is written by one CTA only).
+// Tile scan for the TMA filters: one warp per tile of the stage's grid (tiles
+// of 32 x th, row-major per frame, as the stage's prefix array counts them).
+// The warp tests the tile's footprint (the tile grown by the radius, clipped
+// to the grid) for an observation, each lane keeping 8 loads of the footprint
+// in flight at a time. A tile whose footprint holds none has only invalid
+// outputs: the warp writes them (depth 0, invalid) and the tile is not listed.
+// Every other tile is appended to the stage's list (order immaterial: each
+// tile is written by one CTA only).
 constexpr int kScanThreads = 256;
 template <int SRC>
 __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(BatchDev *__restrict__ B, int stage, int th, int r) {
+    constexpr int kWarps = kScanThreads / 32, kBatch = 8;
     const int32_t *pre = stage ? B->t2_pre : B->t1_pre;
     const int nf = B->n_frames;
     const int total = pre[nf];
-    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+    const int lane = threadIdx.x & 31;
+    for (int item = blockIdx.x * kWarps + (threadIdx.x >> 5); item < total; item += gridDim.x * kWarps) {
         const int fi = find_segment(pre, nf, item);
         const FrameDev &F = B->f[fi];
         const int gw = SRC == SRC_COARSE ? F.Wc : F.W;
@@ -586,27 +630,35 @@ __global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(BatchDev *__res
             qx0 /= 3; qx1 /= 3; qy0 /= 3; qy1 /= 3;
         }
         const int ncx = qx1 - qx0 + 1, n = ncx * (qy1 - qy0 + 1);
+        // the 4-byte word holding each footprint cell's flag: s1 validity, pooled count, z-buffer cell
+        const uint32_t *flags = SRC == SRC_UP       ? reinterpret_cast<const uint32_t *>(F.s1) + 1
+                                : SRC == SRC_COARSE ? reinterpret_cast<const uint32_t *>(F.cguide) + 3
+                                                    : F.zbuf;
+        const int step = SRC == SRC_UP ? 2 : SRC == SRC_COARSE ? 4 : 1;   // words per cell
+        const int64_t pitch = SRC == SRC_ZBUF ? F.zpitch : F.cpitch;
         bool any = false;
-        for (int i0 = 0; i0 < n; i0 += 8 * kScanThreads) {
+        for (int i0 = 0; i0 < n && !__any_sync(0xffffffffu, any); i0 += 32 * kBatch) {
+            uint32_t w[kBatch];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) {
-                const int i = i0 + k * kScanThreads + threadIdx.x;
+            for (int k = 0; k < kBatch; ++k) {
+                const int i = i0 + k * 32 + lane;
+                w[k] = SRC == SRC_ZBUF ? kEmpty : 0u;
                 if (i < n) {
                     const int qy = qy0 + i / ncx, qx = qx0 + i % ncx;
-                    any |= SRC == SRC_UP       ? F.s1[(int64_t)qy * F.cpitch + qx].y > 0.0f
-                           : SRC == SRC_COARSE ? F.cguide[(int64_t)qy * F.cpitch + qx].w > 0.0f
-                                               : F.zbuf[(int64_t)qy * F.zpitch + qx] != kEmpty;
+                    w[k] = flags[((int64_t)qy * pitch + qx) * step];
                 }
             }
+#pragma unroll
+            for (int k = 0; k < kBatch; ++k)
+                any |= SRC == SRC_ZBUF ? w[k] != kEmpty : __uint_as_float(w[k]) > 0.0f;
         }
-        if (__syncthreads_or(any)) {
-            if (threadIdx.x == 0) B->tl_list[stage][atomicAdd(&B->tl_count[stage], 1)] = (fi << 24) | t;
+        if (__any_sync(0xffffffffu, any)) {
+            if (lane == 0) B->tl_list[stage][atomicAdd(&B->tl_count[stage], 1)] = (fi << 24) | t;
             continue;
         }
-        const int rows = min(th, gh - y0), w = min(32, gw - x0);
-        for (int i = threadIdx.x; i < rows * 32; i += kScanThreads) {
-            const int y = y0 + i / 32, x = x0 + i % 32;
-            if (i % 32 >= w) continue;
+        const int x = x0 + lane;
+        if (x >= gw) continue;
+        for (int y = y0; y < min(y0 + th, gh); ++y) {
             const int64_t o = (int64_t)y * gw + x;
             if (SRC == SRC_COARSE) {
                 F.s1[(int64_t)y * F.cpitch + x] = make_float2(0.0f, 0.0f);

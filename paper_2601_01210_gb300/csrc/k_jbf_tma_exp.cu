@@ -11,17 +11,12 @@ namespace dz {
 #define DZ_TMA_EXP_CASES(X)              \
     X(SRC_UP, 2, 8, FORM_EXP, 16)        \
     X(SRC_UP, 2, 8, FORM_EXP, 8)         \
-    X(SRC_UP, 2, 8, FORM_EXP, 4)         \
-    X(SRC_UP, 2, 8, FORM_EXP, 2)         \
-    X(SRC_UP, 2, 4, FORM_EXP, 4)         \
     X(SRC_UP, 2, 4, FORM_EXP, 8)         \
     X(SRC_UP, 1, 8, FORM_EXP, 8)         \
     X(SRC_UP, 3, 4, FORM_EXP, 8)         \
     X(SRC_COARSE, 4, 4, FORM_EXP, 8)     \
     X(SRC_COARSE, 4, 2, FORM_EXP, 8)     \
-    X(SRC_COARSE, 4, 4, FORM_EXP, 4)     \
     X(SRC_COARSE, 4, 2, FORM_EXP, 4)     \
-    X(SRC_COARSE, 4, 4, FORM_EXP, 2)     \
     X(SRC_COARSE, 2, 4, FORM_EXP, 8)     \
     X(SRC_ZBUF, 2, 8, FORM_EXP, 8)       \
     X(SRC_ZBUF, 4, 4, FORM_EXP, 8)       \

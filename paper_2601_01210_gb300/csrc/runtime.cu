@@ -43,7 +43,8 @@ namespace {
 
 const char *const kKernelNames[K_COUNT] = {"prep_compose_clear", "motion_mask", "motion_dilate", "motion_erode",
                                            "project_zbuf",       "occlusion",   "pool3",         "jbf_stage1",
-                                           "jbf_stage2",         "contour",     "bp_count",      "bp_write"};
+                                           "jbf_stage2",         "contour",     "bp_count",      "bp_write",
+                                           "tile_scan1",         "tile_scan2"};
 
 constexpr uint64_t kAlign = 256;
 uint64_t align_up(uint64_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
@@ -128,7 +129,8 @@ struct Slot {
     int32_t *h_status = nullptr; // pinned copy, written at the end of every batch
     cudaEvent_t done = nullptr;
     cudaEvent_t kev[K_COUNT + 1] = {};
-    bool ktimed[K_COUNT] = {};
+    int kord[K_COUNT] = {};      // timed steps in launch order: step j lies between kev[j] and kev[j + 1]
+    int ntimed = 0;
     cudaGraphExec_t exec = nullptr;
     bool busy = false;
     std::vector<uint64_t> tickets;
@@ -369,6 +371,7 @@ std::string validate_params(const densify_params &p) {
     if (p.batches_in_flight < 1 || p.batches_in_flight > 8) return "batches_in_flight must be in 1..8";
     if (p.hbm_budget_bytes < (1u << 20)) return "hbm_budget_bytes must be >= 1 MiB";
     if (p.launch_policy != 0 && p.launch_policy != 1) return "launch_policy must be 0 or 1";
+    if (p.timing < 0 || p.timing > 2) return "timing must be 0, 1 or 2";
     if (p.kernel_variant < 0 || p.kernel_variant > 2) return "kernel_variant must be 0, 1 or 2";
     if (p.autotune != 0 && p.autotune != 1) return "autotune must be 0 or 1";
     if (p.occlusion_radius < 0 || p.occlusion_radius > 16) return "occlusion_radius must be in 0..16";
@@ -735,17 +738,24 @@ densify_status prepare_tile_lists(densify_ctx *c, Slot &sl) {
 // CUDA kernels of one filter launch (TMA: tile scan + filter).
 int filter_kernels(const densify_ctx *c, int i) { return c->sel[i].tma ? 2 : 1; }
 
-cudaError_t launch_filter(densify_ctx *c, int i, const BatchDev *b, cudaStream_t s) {
+// The tile scan in front of a TMA filter (nothing for the plain kernels).
+cudaError_t launch_filter_scan(densify_ctx *c, int i, const BatchDev *b, cudaStream_t s) {
+    const FilterSel &f = c->sel[i];
+    return f.tma ? launch_tile_scan(f.src, b, i, f.tile_h, f.radius, c->sms * 8, s) : cudaSuccess;
+}
+
+cudaError_t launch_filter_kernel(densify_ctx *c, int i, const BatchDev *b, cudaStream_t s) {
     const FilterSel &f = c->sel[i];
     const int k = i == 0 ? K_JBF1 : K_JBF2;
-    if (f.tma) {
-        cudaError_t e = launch_tile_scan(f.src, b, i, f.tile_h, f.radius, c->sms * 8, s);
-        if (e != cudaSuccess) return e;
-        return launch_jbf_tma(f.src, f.radius, TmaVariant{f.kp, f.nw}, f.form, b, c->sa[i], c->grid[k], s);
-    }
+    if (f.tma) return launch_jbf_tma(f.src, f.radius, TmaVariant{f.kp, f.nw}, f.form, b, c->sa[i], c->grid[k], s);
     if (f.kind == 0) return launch_jbf_single(f.radius, b, c->sa[i], c->grid[k], s);
     if (f.kind == 1) return launch_jbf_coarse(f.radius, b, c->sa[i], c->grid[k], s);
     return launch_jbf_up(f.radius, b, c->sa[i], c->grid[k], s);
+}
+
+cudaError_t launch_filter(densify_ctx *c, int i, const BatchDev *b, cudaStream_t s) {
+    cudaError_t e = launch_filter_scan(c, i, b, s);
+    return e != cudaSuccess ? e : launch_filter_kernel(c, i, b, s);
 }
 
 // Tensor maps of one frame for the TMA filter kernels of the context.
@@ -786,17 +796,27 @@ densify_status issue_kernels(densify_ctx *c, Slot &sl, cudaStream_t s, bool reco
     const BatchDev *b = sl.d;
     const int nst = c->p.num_stages;
     int ev = 0;
-    auto mark = [&](int k) -> cudaError_t {
-        if (!record_events) return cudaSuccess;
-        if (k >= 0) sl.ktimed[k] = true;
+    // timing 1: an event after every kernel (and one in front); timing 2: events around the
+    // last filter kernel only (the full-resolution stage), which adds two graph nodes a batch
+    const int last = nst == 2 ? K_JBF2 : K_JBF1;
+    const bool all = c->p.timing == 1;
+    auto record = [&]() -> cudaError_t {
         return cudaEventRecordWithFlags(sl.kev[ev++], s, s == c->cap_stream ? cudaEventRecordExternal : 0);
     };
-    for (int k = 0; k < K_COUNT; ++k) sl.ktimed[k] = false;
+    auto mark = [&](int k) -> cudaError_t {
+        if (!record_events || (!all && k != last)) return cudaSuccess;
+        if (k >= 0) sl.kord[sl.ntimed++] = k;
+        return record();
+    };
+    auto start_last = [&]() -> cudaError_t {   // timing 2: the event in front of the last filter kernel
+        return record_events && !all ? record() : cudaSuccess;
+    };
+    sl.ntimed = 0;
     int nk = 1 + (c->p.motion_threshold > 0.0f ? 3 : 0) + 1 + (c->p.occlusion_radius > 0 ? 1 : 0) +
              (nst == 2 ? 1 + filter_kernels(c, 0) + filter_kernels(c, 1) : filter_kernels(c, 0)) +
              (c->p.contour_threshold > 0.0f ? 1 : 0) + (c->p.emit_points ? 3 : 0);
     sl.nkern = nk;   // prep, motion (3), project, occlusion, pool, filters, contour, compaction (3)
-    CU(mark(-1), "event");
+    if (all) CU(mark(-1), "event");
     CU(launch_prep(b, c->grid[K_PREP], s), "prep launch");
     CU(mark(K_PREP), "event");
     if (c->p.motion_threshold > 0.0f) {
@@ -816,12 +836,26 @@ densify_status issue_kernels(densify_ctx *c, Slot &sl, cudaStream_t s, bool reco
     if (nst == 2) {
         CU(launch_pool(b, c->p.pool, c->grid[K_POOL], s), "pool launch");
         CU(mark(K_POOL), "event");
-        CU(launch_filter(c, 0, b, s), "stage-1 filter launch");
+        if (c->sel[0].tma) {
+            CU(launch_filter_scan(c, 0, b, s), "stage-1 tile scan launch");
+            CU(mark(K_SCAN1), "event");
+        }
+        CU(launch_filter_kernel(c, 0, b, s), "stage-1 filter launch");
         CU(mark(K_JBF1), "event");
-        CU(launch_filter(c, 1, b, s), "stage-2 filter launch");
+        if (c->sel[1].tma) {
+            CU(launch_filter_scan(c, 1, b, s), "stage-2 tile scan launch");
+            CU(mark(K_SCAN2), "event");
+        }
+        CU(start_last(), "event");
+        CU(launch_filter_kernel(c, 1, b, s), "stage-2 filter launch");
         CU(mark(K_JBF2), "event");
     } else {
-        CU(launch_filter(c, 0, b, s), "filter launch");
+        if (c->sel[0].tma) {
+            CU(launch_filter_scan(c, 0, b, s), "tile scan launch");
+            CU(mark(K_SCAN1), "event");
+        }
+        CU(start_last(), "event");
+        CU(launch_filter_kernel(c, 0, b, s), "filter launch");
         CU(mark(K_JBF1), "event");
     }
     if (c->p.contour_threshold > 0.0f) {
@@ -974,14 +1008,12 @@ densify_status complete_slot(densify_ctx *c, Slot &sl) {
         return DENSIFY_E_CUDA;
     }
     if (c->p.timing) {
-        int ev = 1;
-        for (int k = 0; k < K_COUNT; ++k) {
-            if (!sl.ktimed[k]) continue;
+        for (int j = 0; j < sl.ntimed; ++j) {
+            const int k = sl.kord[j];
             float ms = 0.0f;
-            CU(cudaEventElapsedTime(&ms, sl.kev[ev - 1], sl.kev[ev]), "elapsed time");
+            CU(cudaEventElapsedTime(&ms, sl.kev[j], sl.kev[j + 1]), "elapsed time");
             c->t_us[k] += 1000.0 * ms;
             c->t_n[k] += 1;
-            ++ev;
         }
     }
     c->kernel_launches += sl.nkern;
