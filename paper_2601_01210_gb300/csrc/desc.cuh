@@ -29,6 +29,7 @@ constexpr int kBpChunk = 4096;                                // compaction: 8 w
 constexpr int kBpWarps = kThreads / 32;                       // parts of a chunk, one per warp
 constexpr int kBpPart = kBpChunk / kBpWarps;                  // 512 pixels
 constexpr int kPxChunk = 1024;                                // per-pixel kernels: 256 threads x 4 px
+constexpr int kMarkBand = 16;                                 // tile marks: rows of a warp's band
 
 struct ScanDev {
     const float *xyz;
@@ -97,11 +98,13 @@ struct BatchDev {
     int32_t bp_pre[kMaxBatch + 1];                 // compaction chunks
     int32_t px_pre[kMaxBatch + 1];                 // pixel chunks of the motion / contour kernels
     int32_t oc_pre[kMaxBatch + 1];                 // tiles of the occlusion kernel
-    // TMA filters (index 0: first or only filter, 1: second): tiles that some observation
-    // reaches, found by tile_scan_kernel, as frame << 24 | tile; the count is zeroed on the
-    // stream before every scan
-    int32_t tl_count[2];
-    int32_t *tl_list[2];
+    int32_t mk_pre[kMaxBatch + 1];                 // 32-pixel row segments of the observation grid
+    // TMA filters (index 0: first or only filter, 1: second): one flag per tile of the stage
+    // (in the order its prefix array counts them), nonzero when some observation reaches the
+    // tile; zeroed on the stream and set by tile_mark_kernel before every filter launch
+    int32_t *tl_flags[2];
+    int32_t tl_next[2];                            // the filter's tile counter (reset by the marks)
+    int32_t pad2[2];
     FrameDev f[kMaxBatch];
 };
 
@@ -139,7 +142,7 @@ __device__ __forceinline__ int find_segment(const int32_t *pre, int n, int item)
 // Kernel launchers. Grids are persistent: a multiple of the SM count.
 enum KernelId {
     K_PREP = 0, K_MOTION, K_DILATE, K_ERODE, K_PROJECT, K_OCCLUSION, K_POOL, K_JBF1, K_JBF2, K_CONTOUR,
-    K_BP_COUNT, K_BP_WRITE, K_SCAN1, K_SCAN2, K_COUNT
+    K_BP_COUNT, K_BP_WRITE, K_MARK1, K_MARK2, K_COUNT
 };
 
 // Preprocessing / post-filtering (k_prepost.cu).

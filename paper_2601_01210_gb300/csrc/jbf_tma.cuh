@@ -183,33 +183,42 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
     uint32_t *obsw = reinterpret_cast<uint32_t *>(smem + G::OFF_OBS);
     uint64_t *bar = reinterpret_cast<uint64_t *>(smem + G::OFF_BAR);
 
-    // the tiles that some observation reaches (tile_scan_kernel wrote the list and zero-filled the rest)
+    // every tile of the stage; tile_mark_kernel flagged those that some observation reaches
     const int stage = SRC == SRC_UP ? 1 : 0;
-    const int total = B->tl_count[stage];
-    const int32_t *list = B->tl_list[stage];
+    const int32_t *pre = stage ? B->t2_pre : B->t1_pre;
+    const int nf = B->n_frames;
+    const int total = pre[nf];
+    const int32_t *flags = B->tl_flags[stage];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
-    // Thread 0 issues the copies of the CTA's next tile while the CTA works on the current one. It
-    // reads the tile list one entry ahead (pend), acquires each frame's tensor maps once, and leaves
-    // the tile's (frame, x0, y0) in s_tile[buffer] for the other threads, so the start of a tile
-    // waits on no global load.
-    __shared__ int s_tile[2][3];
-    auto locate = [&](int e, int &fi, int &x0, int &y0) {
-        fi = e >> 24;
+    // Tiles are handed out dynamically: a CTA starts with tile blockIdx.x and takes every further
+    // tile from the stage's counter (gridDim.x + atomicAdd), so CTAs stay balanced however the
+    // tiles without observations are placed. Thread 0 issues the copies of the CTA's next tile
+    // while the CTA works on the current one: it takes the tile and reads its flag one tile ahead,
+    // acquires each frame's tensor maps once, and leaves the tile's (frame, x0, y0, copies issued,
+    // tile index or -1 when there is none) in s_tile[buffer] for the other threads, so the start of
+    // a tile waits on no global load. A tile no observation reaches gets no copies.
+    __shared__ int s_tile[2][5];
+    auto locate = [&](int item, int &fi, int &x0, int &y0) {
+        fi = find_segment(pre, nf, item);
         const FrameDev &F = B->f[fi];
         const int gw = SRC == SRC_COARSE ? F.Wc : F.W;
         const int tiles_x = (gw + TW - 1) / TW;
-        const int t = e & 0xFFFFFF;
+        const int t = item - pre[fi];
         x0 = (t % tiles_x) * TW;
         y0 = (t / tiles_x) * TH;
     };
     uint64_t acquired = 0u;   // thread 0: frames whose tensor maps were acquired
-    auto issue = [&](int e, int buf) {
+    auto issue = [&](int item, int flag, int buf) {
+        s_tile[buf][4] = item < total ? item : -1;
+        if (item >= total) return;
         int fi, x0, y0;
-        locate(e, fi, x0, y0);
+        locate(item, fi, x0, y0);
         s_tile[buf][0] = fi;
         s_tile[buf][1] = x0;
         s_tile[buf][2] = y0;
+        s_tile[buf][3] = flag != 0;
+        if (!flag) return;
         const FrameDev &F = B->f[fi];
         const bool acq = !((acquired >> fi) & 1u);
         acquired |= 1ull << fi;
@@ -243,38 +252,71 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
     __syncthreads();
     uint32_t inflight = 0u;   // bit b: thread 0 issued copies into buffer b not yet consumed
     uint32_t phase = 0u;      // bit b: parity of buffer b's barrier
-    int pend = 0;             // thread 0: list entry of the tile it issues next
-    if (threadIdx.x == 0 && (int)blockIdx.x < total) {
-        issue(list[blockIdx.x], 0);
-        inflight |= 1u;
-        if ((int)(blockIdx.x + gridDim.x) < total) pend = list[blockIdx.x + gridDim.x];
+    // thread 0 looks two tiles ahead: n1 (issued at the next iteration, its flag f1 already
+    // requested) and n2 (taken from the counter); every global result is used one tile after it
+    // was requested, so the issuing thread never waits on a load. The counter is only ever
+    // touched atomically (the descriptor's other fields are read-only here).
+    int n1 = 0, f1 = 0, n2 = 0;
+    auto take = [&]() { return (int)gridDim.x + atomicAdd(const_cast<int32_t *>(&B->tl_next[stage]), 1); };
+    if (threadIdx.x == 0) {
+        const int f0 = (int)blockIdx.x < total ? flags[blockIdx.x] : 0;
+        issue(blockIdx.x, f0, 0);
+        if (f0) inflight |= 1u;
+        if ((int)blockIdx.x < total) {
+            n1 = take();
+            f1 = n1 < total ? flags[n1] : 0;
+            n2 = take();
+        }
     }
     __syncthreads();          // s_tile[0]
-    int it = 0;
-    for (int item = blockIdx.x; item < total; item += gridDim.x, ++it) {
+    for (int it = 0;; ++it) {
         const int buf = it & 1;
-        const int next = item + gridDim.x;
-        if (threadIdx.x == 0 && next < total) {   // the other buffer was released by the last barrier
-            issue(pend, buf ^ 1);
-            inflight |= 1u << (buf ^ 1);
-            if (next + (int)gridDim.x < total) pend = list[next + gridDim.x];   // used one tile later
-        }
-        const bool ok = mbar_wait_bounded(&bar[buf], (phase >> buf) & 1u);
-        if (__syncthreads_or(!ok)) {
-            if (threadIdx.x == 0) {
-                atomicOr(B->status, 1);
-                for (int b = 0; b < 2; ++b)
-                    if ((inflight >> b) & 1u) mbar_wait_bounded(&bar[b], (phase >> b) & 1u);
+        if (s_tile[buf][4] < 0) break;   // the same for every thread of the CTA
+        if (threadIdx.x == 0) {   // the other buffer was released by the last barrier
+            issue(n1, f1, buf ^ 1);
+            if (n1 < total) {
+                if (f1) inflight |= 1u << (buf ^ 1);
+                n1 = n2;
+                f1 = n2 < total ? flags[n2] : 0;
+                n2 = take();
             }
-            return;
         }
-        phase ^= 1u << buf;
-        inflight &= ~(1u << buf);
+        const bool copied = s_tile[buf][3] != 0;   // the same for every thread of the CTA
+        if (copied) {
+            const bool ok = mbar_wait_bounded(&bar[buf], (phase >> buf) & 1u);
+            if (__syncthreads_or(!ok)) {
+                if (threadIdx.x == 0) {
+                    atomicOr(B->status, 1);
+                    for (int b = 0; b < 2; ++b)
+                        if ((inflight >> b) & 1u) mbar_wait_bounded(&bar[b], (phase >> b) & 1u);
+                }
+                return;
+            }
+            phase ^= 1u << buf;
+            inflight &= ~(1u << buf);
+        }
 
         const int fi = s_tile[buf][0], x0 = s_tile[buf][1], y0 = s_tile[buf][2];
         const FrameDev &F = B->f[fi];
         const int gw = SRC == SRC_COARSE ? F.Wc : F.W;
         const int gh = SRC == SRC_COARSE ? F.Hc : F.H;
+        if (!copied) {   // no observation reaches the tile: every output is (0, invalid)
+            for (int i = threadIdx.x; i < TW * TH; i += NT) {
+                const int x = x0 + i % TW, y = y0 + i / TW;
+                if (x >= gw || y >= gh) continue;
+                const int64_t o = (int64_t)y * gw + x;
+                if (SRC == SRC_COARSE) {
+                    F.s1[(int64_t)y * F.cpitch + x] = make_float2(0.0f, 0.0f);
+                    if (F.out_coarse) F.out_coarse[o] = 0.0f;
+                    if (F.out_coarse_valid) F.out_coarse_valid[o] = 0;
+                } else {
+                    F.flt_depth[o] = 0.0f;
+                    F.flt_valid[o] = 0;
+                }
+            }
+            __syncthreads();   // s_tile[buf] is rewritten for the tile after next
+            continue;
+        }
         const uint8_t *rgbraw = rawA(buf);
         const float4 *cg = reinterpret_cast<const float4 *>(rawA(buf));
         const float *cs = reinterpret_cast<const float *>(rawB(buf));
@@ -600,75 +642,62 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
     }
 }
 
-// Tile scan for the TMA filters: one warp per tile of the stage's grid (tiles
-// of 32 x th, row-major per frame, as the stage's prefix array counts them).
-// The warp tests the tile's footprint (the tile grown by the radius, clipped
-// to the grid) for an observation, each lane keeping 8 loads of the footprint
-// in flight at a time. A tile whose footprint holds none has only invalid
-// outputs: the warp writes them (depth 0, invalid) and the tile is not listed.
-// Every other tile is appended to the stage's list (order immaterial: each
-// tile is written by one CTA only).
-constexpr int kScanThreads = 256;
+// Tile marks for the TMA filters. One warp per band of 32 columns x kMarkRows
+// rows of the observation grid (the pooled grid for SRC_UP and SRC_COARSE, the
+// image for SRC_ZBUF); every lane reads its column's kMarkRows observation flags
+// (in flight together). The output pixels the band's observations reach (grown
+// by the radius; a pooled pixel covers a 3 x 3 block at full resolution for
+// SRC_UP) span a range of the stage's tiles (32 x th, row-major per frame), whose
+// flags the warp sets. The range spans the band's first to last observed column
+// and row, a superset: a flagged tile that no observation reaches is filtered to
+// all-invalid outputs, as it should be. The first block also resets the
+// filter's tile counter.
+constexpr int kMarkThreads = 256, kMarkRows = kMarkBand;
 template <int SRC>
-__global__ void __launch_bounds__(kScanThreads) tile_scan_kernel(BatchDev *__restrict__ B, int stage, int th, int r) {
-    constexpr int kWarps = kScanThreads / 32, kBatch = 8;
-    const int32_t *pre = stage ? B->t2_pre : B->t1_pre;
+__global__ void __launch_bounds__(kMarkThreads) tile_mark_kernel(BatchDev *__restrict__ B, int stage, int th, int r) {
+    constexpr int kWarps = kMarkThreads / 32;
+    if (blockIdx.x == 0 && threadIdx.x == 0) B->tl_next[stage] = 0;
+    const int32_t *tpre = stage ? B->t2_pre : B->t1_pre;
+    const int32_t *mpre = B->mk_pre;
     const int nf = B->n_frames;
-    const int total = pre[nf];
+    const int total = mpre[nf];
     const int lane = threadIdx.x & 31;
     for (int item = blockIdx.x * kWarps + (threadIdx.x >> 5); item < total; item += gridDim.x * kWarps) {
-        const int fi = find_segment(pre, nf, item);
+        const int fi = find_segment(mpre, nf, item);
         const FrameDev &F = B->f[fi];
-        const int gw = SRC == SRC_COARSE ? F.Wc : F.W;
-        const int gh = SRC == SRC_COARSE ? F.Hc : F.H;
+        const int ow = SRC == SRC_ZBUF ? F.W : F.Wc, oh = SRC == SRC_ZBUF ? F.H : F.Hc;
+        const int segs = (ow + 31) / 32;
+        const int t = item - mpre[fi];
+        const int band = t / segs, sx0 = (t - band * segs) * 32, ox = sx0 + lane, oy0 = band * kMarkRows;
+        uint32_t w[kMarkRows];
+#pragma unroll
+        for (int k = 0; k < kMarkRows; ++k) {
+            const int oy = oy0 + k;
+            w[k] = SRC == SRC_ZBUF ? kEmpty : 0u;
+            if (ox < ow && oy < oh) {
+                if (SRC == SRC_UP) w[k] = __float_as_uint(F.s1[(int64_t)oy * F.cpitch + ox].y);
+                else if (SRC == SRC_COARSE) w[k] = __float_as_uint(F.cguide[(int64_t)oy * F.cpitch + ox].w);
+                else w[k] = F.zbuf[(int64_t)oy * F.zpitch + ox];
+            }
+        }
+        uint32_t rows = 0u;   // bit k: this lane's column is observed in row oy0 + k
+#pragma unroll
+        for (int k = 0; k < kMarkRows; ++k)
+            if (SRC == SRC_ZBUF ? w[k] != kEmpty : __uint_as_float(w[k]) > 0.0f) rows |= 1u << k;
+        const uint32_t cols = __ballot_sync(0xffffffffu, rows != 0);
+        const uint32_t all = __reduce_or_sync(0xffffffffu, rows);
+        if (!cols) continue;
+        const int gw = SRC == SRC_COARSE ? F.Wc : F.W, gh = SRC == SRC_COARSE ? F.Hc : F.H;
+        const int ox0 = sx0 + __ffs(cols) - 1, ox1 = sx0 + 31 - __clz(cols);
+        const int oy1 = oy0 + 31 - __clz(all), oyf = oy0 + __ffs(all) - 1;
+        const int f = SRC == SRC_UP ? 3 : 1;   // output pixels per observation pixel and axis
+        const int xlo = max(0, f * ox0 - r), xhi = min(gw - 1, f * ox1 + f - 1 + r);
+        const int ylo = max(0, f * oyf - r), yhi = min(gh - 1, f * oy1 + f - 1 + r);
+        if (xlo > xhi || ylo > yhi) continue;
+        const int tx0 = xlo / 32, ntx = xhi / 32 - tx0 + 1, ty0 = ylo / th, n = ntx * (yhi / th - ty0 + 1);
         const int tiles_x = (gw + 31) / 32;
-        const int t = item - pre[fi];
-        const int x0 = (t % tiles_x) * 32, y0 = (t / tiles_x) * th;
-        int qx0 = max(0, x0 - r), qx1 = min(gw - 1, x0 + 31 + r);
-        int qy0 = max(0, y0 - r), qy1 = min(gh - 1, y0 + th - 1 + r);
-        if (SRC == SRC_UP) {   // observations of the restored first stage: its valid pooled pixels
-            qx0 /= 3; qx1 /= 3; qy0 /= 3; qy1 /= 3;
-        }
-        const int ncx = qx1 - qx0 + 1, n = ncx * (qy1 - qy0 + 1);
-        // the 4-byte word holding each footprint cell's flag: s1 validity, pooled count, z-buffer cell
-        const uint32_t *flags = SRC == SRC_UP       ? reinterpret_cast<const uint32_t *>(F.s1) + 1
-                                : SRC == SRC_COARSE ? reinterpret_cast<const uint32_t *>(F.cguide) + 3
-                                                    : F.zbuf;
-        const int step = SRC == SRC_UP ? 2 : SRC == SRC_COARSE ? 4 : 1;   // words per cell
-        const int64_t pitch = SRC == SRC_ZBUF ? F.zpitch : F.cpitch;
-        bool any = false;
-        for (int i0 = 0; i0 < n && !__any_sync(0xffffffffu, any); i0 += 32 * kBatch) {
-            uint32_t w[kBatch];
-#pragma unroll
-            for (int k = 0; k < kBatch; ++k) {
-                const int i = i0 + k * 32 + lane;
-                w[k] = SRC == SRC_ZBUF ? kEmpty : 0u;
-                if (i < n) {
-                    const int qy = qy0 + i / ncx, qx = qx0 + i % ncx;
-                    w[k] = flags[((int64_t)qy * pitch + qx) * step];
-                }
-            }
-#pragma unroll
-            for (int k = 0; k < kBatch; ++k)
-                any |= SRC == SRC_ZBUF ? w[k] != kEmpty : __uint_as_float(w[k]) > 0.0f;
-        }
-        if (__any_sync(0xffffffffu, any)) {
-            if (lane == 0) B->tl_list[stage][atomicAdd(&B->tl_count[stage], 1)] = (fi << 24) | t;
-            continue;
-        }
-        const int x = x0 + lane;
-        if (x >= gw) continue;
-        for (int y = y0; y < min(y0 + th, gh); ++y) {
-            const int64_t o = (int64_t)y * gw + x;
-            if (SRC == SRC_COARSE) {
-                F.s1[(int64_t)y * F.cpitch + x] = make_float2(0.0f, 0.0f);
-                if (F.out_coarse) F.out_coarse[o] = 0.0f;
-                if (F.out_coarse_valid) F.out_coarse_valid[o] = 0;
-            } else {
-                F.flt_depth[o] = 0.0f;
-                F.flt_valid[o] = 0;
-            }
-        }
+        int32_t *flags = B->tl_flags[stage] + tpre[fi];
+        for (int j = lane; j < n; j += 32) flags[(ty0 + j / ntx) * tiles_x + tx0 + j % ntx] = 1;
     }
 }
 

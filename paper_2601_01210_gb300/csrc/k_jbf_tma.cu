@@ -56,13 +56,11 @@ cudaError_t launch_jbf_tma(int src, int r, TmaVariant v, int form, const BatchDe
                                 : base_launch(src, r, v, form, b, a, grid, s);
 }
 
-cudaError_t launch_tile_scan(int src, const BatchDev *b, int stage, int th, int r, int grid, cudaStream_t s) {
+cudaError_t launch_tile_mark(int src, const BatchDev *b, int stage, int th, int r, int grid, cudaStream_t s) {
     BatchDev *bb = const_cast<BatchDev *>(b);
-    cudaError_t e = cudaMemsetAsync(&bb->tl_count[stage], 0, sizeof(int32_t), s);
-    if (e != cudaSuccess) return e;
-    if (src == TMA_SRC_UP) tile_scan_kernel<SRC_UP><<<grid, kScanThreads, 0, s>>>(bb, stage, th, r);
-    else if (src == TMA_SRC_COARSE) tile_scan_kernel<SRC_COARSE><<<grid, kScanThreads, 0, s>>>(bb, stage, th, r);
-    else tile_scan_kernel<SRC_ZBUF><<<grid, kScanThreads, 0, s>>>(bb, stage, th, r);
+    if (src == TMA_SRC_UP) tile_mark_kernel<SRC_UP><<<grid, kMarkThreads, 0, s>>>(bb, stage, th, r);
+    else if (src == TMA_SRC_COARSE) tile_mark_kernel<SRC_COARSE><<<grid, kMarkThreads, 0, s>>>(bb, stage, th, r);
+    else tile_mark_kernel<SRC_ZBUF><<<grid, kMarkThreads, 0, s>>>(bb, stage, th, r);
     return cudaGetLastError();
 }
 

@@ -71,6 +71,8 @@ __global__ void noalloc_init_kernel(BatchDev *b, FrameWords f, Prefix p, int32_t
         b->t2_pre[1] = p.t2;
         b->bp_pre[0] = 0;
         b->bp_pre[1] = p.bp;
+        b->mk_pre[0] = b->mk_pre[1] = 0;
+        b->tl_flags[0] = b->tl_flags[1] = nullptr;   // plain filter kernels only: no tile flags
     }
 }
 

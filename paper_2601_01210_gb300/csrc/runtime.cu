@@ -44,7 +44,7 @@ namespace {
 const char *const kKernelNames[K_COUNT] = {"prep_compose_clear", "motion_mask", "motion_dilate", "motion_erode",
                                            "project_zbuf",       "occlusion",   "pool3",         "jbf_stage1",
                                            "jbf_stage2",         "contour",     "bp_count",      "bp_write",
-                                           "tile_scan1",         "tile_scan2"};
+                                           "tile_mark1",         "tile_mark2"};
 
 constexpr uint64_t kAlign = 256;
 uint64_t align_up(uint64_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
@@ -554,7 +554,7 @@ void fill_batch(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &tk) {
     b.n_frames = n;
     b.status = sl.d_status;
     b.zb_pre[0] = b.pt_pre[0] = b.pool_pre[0] = b.t1_pre[0] = b.t2_pre[0] = b.bp_pre[0] = 0;
-    b.px_pre[0] = b.oc_pre[0] = 0;
+    b.px_pre[0] = b.oc_pre[0] = b.mk_pre[0] = 0;
     const int nst = c->p.num_stages;
     const int r1 = c->p.stage[0].radius, r2 = nst == 2 ? c->p.stage[1].radius : 0;
     (void)r1;
@@ -577,6 +577,8 @@ void fill_batch(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &tk) {
         b.bp_pre[i + 1] = b.bp_pre[i] + (c->p.emit_points ? d.n_bp_chunks : 0);
         b.px_pre[i + 1] = b.px_pre[i] + d.n_px_chunks;
         b.oc_pre[i + 1] = b.oc_pre[i] + ceil_div(d.W, kOccTile) * ceil_div(d.H, kOccTile);
+        b.mk_pre[i + 1] = b.mk_pre[i] + (nst == 2 ? ceil_div(d.Hc, kMarkBand) * ceil_div(d.Wc, 32)
+                                                  : ceil_div(d.H, kMarkBand) * ceil_div(d.W, 32));
     }
 }
 
@@ -712,8 +714,8 @@ densify_status autotune(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &t
     return st;
 }
 
-// Tile lists of the batch's TMA filters: room for every tile of both stages,
-// pointers and zero counts in the host descriptor (uploaded with it).
+// Tile flags of the batch's TMA filters: one word per tile of both stages
+// (contiguous, stage 1 first), pointers in the host descriptor (uploaded with it).
 densify_status prepare_tile_lists(densify_ctx *c, Slot &sl) {
     BatchDev &b = *sl.h;
     const int n = b.n_frames;
@@ -729,19 +731,18 @@ densify_status prepare_tile_lists(densify_ctx *c, Slot &sl) {
         CU(cudaMalloc(&sl.d_tiles, (size_t)cap * sizeof(int32_t)), "tile list allocation");
         sl.tiles_cap = cap;
     }
-    b.tl_count[0] = b.tl_count[1] = 0;
-    b.tl_list[0] = sl.d_tiles;
-    b.tl_list[1] = sl.d_tiles + b.t1_pre[n];
+    b.tl_flags[0] = sl.d_tiles;
+    b.tl_flags[1] = sl.d_tiles + b.t1_pre[n];
     return DENSIFY_OK;
 }
 
-// CUDA kernels of one filter launch (TMA: tile scan + filter).
+// CUDA kernels of one filter launch (TMA: tile marks + filter).
 int filter_kernels(const densify_ctx *c, int i) { return c->sel[i].tma ? 2 : 1; }
 
-// The tile scan in front of a TMA filter (nothing for the plain kernels).
+// The tile marks in front of a TMA filter (nothing for the plain kernels).
 cudaError_t launch_filter_scan(densify_ctx *c, int i, const BatchDev *b, cudaStream_t s) {
     const FilterSel &f = c->sel[i];
-    return f.tma ? launch_tile_scan(f.src, b, i, f.tile_h, f.radius, c->sms * 8, s) : cudaSuccess;
+    return f.tma ? launch_tile_mark(f.src, b, i, f.tile_h, f.radius, c->sms * 8, s) : cudaSuccess;
 }
 
 cudaError_t launch_filter_kernel(densify_ctx *c, int i, const BatchDev *b, cudaStream_t s) {
@@ -837,22 +838,22 @@ densify_status issue_kernels(densify_ctx *c, Slot &sl, cudaStream_t s, bool reco
         CU(launch_pool(b, c->p.pool, c->grid[K_POOL], s), "pool launch");
         CU(mark(K_POOL), "event");
         if (c->sel[0].tma) {
-            CU(launch_filter_scan(c, 0, b, s), "stage-1 tile scan launch");
-            CU(mark(K_SCAN1), "event");
+            CU(launch_filter_scan(c, 0, b, s), "stage-1 tile mark launch");
+            CU(mark(K_MARK1), "event");
         }
         CU(launch_filter_kernel(c, 0, b, s), "stage-1 filter launch");
         CU(mark(K_JBF1), "event");
         if (c->sel[1].tma) {
-            CU(launch_filter_scan(c, 1, b, s), "stage-2 tile scan launch");
-            CU(mark(K_SCAN2), "event");
+            CU(launch_filter_scan(c, 1, b, s), "stage-2 tile mark launch");
+            CU(mark(K_MARK2), "event");
         }
         CU(start_last(), "event");
         CU(launch_filter_kernel(c, 1, b, s), "stage-2 filter launch");
         CU(mark(K_JBF2), "event");
     } else {
         if (c->sel[0].tma) {
-            CU(launch_filter_scan(c, 0, b, s), "tile scan launch");
-            CU(mark(K_SCAN1), "event");
+            CU(launch_filter_scan(c, 0, b, s), "tile mark launch");
+            CU(mark(K_MARK1), "event");
         }
         CU(start_last(), "event");
         CU(launch_filter_kernel(c, 0, b, s), "filter launch");

@@ -41,9 +41,9 @@ cudaError_t jbf_tma_prepare(int src, int r, TmaVariant v, int form);
 cudaError_t launch_jbf_tma(int src, int r, TmaVariant v, int form, const BatchDev *b, const StageArgs &a, int grid,
                            cudaStream_t s);
 int occupancy_jbf_tma(int src, int r, TmaVariant v, int form);
-// Zero the stage's tile count, then list the tiles of the stage's grid (32 x th) that
-// some observation within radius r reaches and zero-fill the outputs of the others.
-cudaError_t launch_tile_scan(int src, const BatchDev *b, int stage, int th, int r, int grid, cudaStream_t s);
+// Flag the tiles of the stage's grid (32 x th) that some observation within radius r
+// reaches (the flags were zeroed by the batch's first kernel).
+cudaError_t launch_tile_mark(int src, const BatchDev *b, int stage, int th, int r, int grid, cudaStream_t s);
 
 // the expanded form's instantiations (k_jbf_tma_exp.cu)
 int jbf_tma_exp_variants(int src, int r, int form, TmaVariant *out, int cap);
