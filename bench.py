@@ -329,6 +329,26 @@ def valid_taps_stage1(cnt_pos, r=4):
     return int(correlate(cnt_pos.astype(np.float64), np.ones((2 * r + 1, 2 * r + 1)), mode="constant").sum())
 
 
+def host_link_gbps(dev, mb=256, reps=5):
+    """Pinned host <-> device copy rates (GB/s), CUDA events."""
+    import torch
+    h = torch.empty(mb << 20, dtype=torch.uint8, pin_memory=True)
+    d = torch.empty(mb << 20, dtype=torch.uint8, device=dev)
+    out = {}
+    for name, fn in (("h2d_GBps", lambda: d.copy_(h, non_blocking=True)),
+                     ("d2h_GBps", lambda: h.copy_(d, non_blocking=True))):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = round(reps * (mb << 20) / (e0.elapsed_time(e1) / 1e3) / 1e9, 1)
+    return out
+
+
 def ours_arm(a, rank, world, local_rank):
     import numpy as np
     import torch
@@ -470,9 +490,15 @@ def ours_arm(a, rank, world, local_rank):
             dt = reduce_max(dt) if world > 1 else dt
         h2d = sum(sum(x.numel() * 4 for x, _ in b.scans) + b.rgb.numel() for b in hb[0])
         d2h = sum(8 + b.n_points() * 16 for b in hb[0])
+        link = host_link_gbps(dev)
+        # the step's bytes cross the host link one direction at a time at the measured copy rates
+        bound = B / (h2d / (link["h2d_GBps"] * 1e9) + d2h / (link["d2h_GBps"] * 1e9)) * world
         e2e = {"value": B * a.steps / dt * world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h),
-               "what": "pinned host points + RGB in, coloured points out (written by the GPU into pinned memory)"}
+               "what": "pinned host points + RGB in, coloured points out (written by the GPU into pinned memory)",
+               "host_link": dict(link, bound_frames_per_s=round(bound, 1),
+                                 note="copy-engine rates, 256 MiB pinned <-> device; bound = bytes in / h2d rate + "
+                                      "bytes out / d2h rate per step")}
     serving = None
     if not a.no_serve and rank == 0:
         serving = serve_measure(mixed_views, dev, stream, a.serve_seconds, 1, a.autotune)

@@ -58,8 +58,12 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
 
 __device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
+// Relaxed: the issuing thread's earlier global stores need not be performed first (a release
+// arrive waits for them). Nothing is published through this arrive: tile coordinates reach the
+// CTA through a barrier, and copies into a buffer are issued only after the barrier that frees it.
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+    asm volatile("mbarrier.arrive.expect_tx.relaxed.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
 }
 
 __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
@@ -208,38 +212,26 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
         x0 = (t % tiles_x) * TW;
         y0 = (t / tiles_x) * TH;
     };
-    uint64_t acquired = 0u;   // thread 0: frames whose tensor maps were acquired
-    auto issue = [&](int item, int flag, int buf) {
+    // the tile's coordinates (fi, x0, y0) were located beforehand
+    auto issue = [&](int item, int flag, int fi, int x0, int y0, int buf) {
         s_tile[buf][4] = item < total ? item : -1;
         if (item >= total) return;
-        int fi, x0, y0;
-        locate(item, fi, x0, y0);
         s_tile[buf][0] = fi;
         s_tile[buf][1] = x0;
         s_tile[buf][2] = y0;
         s_tile[buf][3] = flag != 0;
         if (!flag) return;
         const FrameDev &F = B->f[fi];
-        const bool acq = !((acquired >> fi) & 1u);
-        acquired |= 1ull << fi;
         mbar_expect_tx(&bar[buf], G::TX_BYTES);
         if (SRC == SRC_COARSE) {
-            if (acq) {
-                tmap_acquire(&F.tm[TM_CGUIDE]);
-                tmap_acquire(&F.tm[TM_CSSUM]);
-            }
             tma_load_2d(rawA(buf), &F.tm[TM_CGUIDE], 4 * (x0 - R), y0 - R, &bar[buf]);
             tma_load_2d(rawB(buf), &F.tm[TM_CSSUM], x0 - G::S_LEAD, y0 - R, &bar[buf]);
         } else {
-            if (acq) tmap_acquire(&F.tm[TM_RGB]);
             tma_load_2d(rawA(buf), &F.tm[TM_RGB], 3 * x0 - G::RGB_LEAD, y0 - R, &bar[buf]);
-            if (SRC == SRC_UP) {
-                if (acq) tmap_acquire(&F.tm[TM_S1]);
+            if (SRC == SRC_UP)
                 tma_load_2d(rawB(buf), &F.tm[TM_S1], floor_div3(x0 - R) & ~1, floor_div3(y0 - R), &bar[buf]);
-            } else {
-                if (acq) tmap_acquire(&F.tm[TM_ZBUF]);
+            else
                 tma_load_2d(rawB(buf), &F.tm[TM_ZBUF], x0 - G::Z_LEAD, y0 - R, &bar[buf]);
-            }
         }
     };
 
@@ -248,24 +240,50 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
         mbar_init(&bar[1], 1);
         mbar_fence_init();
         obsw[G::OBS_WORDS - 1] = 0u;   // guard word, never rewritten
+        // the tensor maps of every frame of the batch, acquired once before thread 0 has any memory
+        // operation outstanding (a fence later in the loop would wait for its stores and atomics)
+        for (int f = 0; f < nf; ++f) {
+            const FrameDev &F = B->f[f];
+            if (SRC == SRC_COARSE) {
+                tmap_acquire(&F.tm[TM_CGUIDE]);
+                tmap_acquire(&F.tm[TM_CSSUM]);
+            } else {
+                tmap_acquire(&F.tm[TM_RGB]);
+                tmap_acquire(SRC == SRC_UP ? &F.tm[TM_S1] : &F.tm[TM_ZBUF]);
+            }
+        }
     }
     __syncthreads();
     uint32_t inflight = 0u;   // bit b: thread 0 issued copies into buffer b not yet consumed
     uint32_t phase = 0u;      // bit b: parity of buffer b's barrier
-    // thread 0 looks two tiles ahead: n1 (issued at the next iteration, its flag f1 already
-    // requested) and n2 (taken from the counter); every global result is used one tile after it
-    // was requested, so the issuing thread never waits on a load. The counter is only ever
-    // touched atomically (the descriptor's other fields are read-only here).
-    int n1 = 0, f1 = 0, n2 = 0;
-    auto take = [&]() { return (int)gridDim.x + atomicAdd(const_cast<int32_t *>(&B->tl_next[stage]), 1); };
+    // Thread 0 keeps the next tile n1 ready (its flag f1 requested and its coordinates located)
+    // and the counter's reply for the tile after it (n2raw) requested. At the top of a tile it
+    // only issues n1's copies; the queue advances after the conversion barrier, while the CTA
+    // filters, and every global result is used one tile after it was requested: the issuing
+    // thread never waits on a load or on the counter, which a whole grid of CTAs shares. The
+    // counter is only ever touched atomically (the descriptor's other fields are read-only here).
+    int n1 = total, f1 = 0, l1f = 0, l1x = 0, l1y = 0, n2raw = 0;
+    auto request = [&]() { return atomicAdd(const_cast<int32_t *>(&B->tl_next[stage]), 1); };
+    auto advance = [&]() {   // thread 0: n1 <- the counter's last reply; request the next one
+        n1 = (int)gridDim.x + n2raw;
+        if (n1 < total) {
+            f1 = flags[n1];
+            locate(n1, l1f, l1x, l1y);
+            n2raw = request();
+        }
+    };
     if (threadIdx.x == 0) {
-        const int f0 = (int)blockIdx.x < total ? flags[blockIdx.x] : 0;
-        issue(blockIdx.x, f0, 0);
-        if (f0) inflight |= 1u;
-        if ((int)blockIdx.x < total) {
-            n1 = take();
-            f1 = n1 < total ? flags[n1] : 0;
-            n2 = take();
+        const int t0 = blockIdx.x;
+        if (t0 < total) {
+            int fi, x0, y0;
+            locate(t0, fi, x0, y0);
+            const int f0 = flags[t0];
+            issue(t0, f0, fi, x0, y0, 0);
+            if (f0) inflight |= 1u;
+            n2raw = request();
+            advance();
+        } else {
+            s_tile[0][4] = -1;
         }
     }
     __syncthreads();          // s_tile[0]
@@ -273,13 +291,8 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
         const int buf = it & 1;
         if (s_tile[buf][4] < 0) break;   // the same for every thread of the CTA
         if (threadIdx.x == 0) {   // the other buffer was released by the last barrier
-            issue(n1, f1, buf ^ 1);
-            if (n1 < total) {
-                if (f1) inflight |= 1u << (buf ^ 1);
-                n1 = n2;
-                f1 = n2 < total ? flags[n2] : 0;
-                n2 = take();
-            }
+            issue(n1, f1, l1f, l1x, l1y, buf ^ 1);
+            if (n1 < total && f1) inflight |= 1u << (buf ^ 1);
         }
         const bool copied = s_tile[buf][3] != 0;   // the same for every thread of the CTA
         if (copied) {
@@ -301,6 +314,7 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
         const int gw = SRC == SRC_COARSE ? F.Wc : F.W;
         const int gh = SRC == SRC_COARSE ? F.Hc : F.H;
         if (!copied) {   // no observation reaches the tile: every output is (0, invalid)
+            if (threadIdx.x == 0 && n1 < total) advance();
             for (int i = threadIdx.x; i < TW * TH; i += NT) {
                 const int x = x0 + i % TW, y = y0 + i / TW;
                 if (x >= gw || y >= gh) continue;
@@ -411,6 +425,8 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
             if (lane == 0) obsw[(threadIdx.x + j * NT) >> 5] = bits;
         }
         __syncthreads();
+
+        if (threadIdx.x == 0 && n1 < total) advance();   // off the path of the CTA's barriers
 
         // ---- filter: thread owns column lane, rows rbase .. rbase + KP - 1 of the tile
         const int rbase = warp * KP;
