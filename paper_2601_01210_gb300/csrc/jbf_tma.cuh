@@ -270,6 +270,7 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
             f1 = flags[n1];
             locate(n1, l1f, l1x, l1y);
             n2raw = request();
+            asm volatile("" ::"r"(f1));   // wait for the flag here, in warp 0's filter phase, not at the next issue
         }
     };
     if (threadIdx.x == 0) {
