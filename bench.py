@@ -297,13 +297,15 @@ def reference_arm(a, rank, world):
 # ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
-def profiled_traffic(kernel):
-    """DRAM bytes per launch recorded in profiles/traffic.json for ``kernel``,
-    or None if the kernel's sources changed since that capture."""
+def profiled_traffic(kernel, chosen=None):
+    """DRAM bytes per launch recorded in profiles/traffic.json for ``kernel``, or None if
+    the kernel's sources changed since that capture or the run chose another variant."""
     import hashlib
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
     except Exception:
+        return None
+    if chosen is not None and any(chosen.get(k) != v for k, v in rec.get("variant", {}).items()):
         return None
     for path, digest in rec["sources"].items():
         try:
@@ -542,7 +544,8 @@ def ours_arm(a, rank, world, local_rank):
                                 "p99": sorted_ms[min(len(sorted_ms) - 1, int(0.99 * len(sorted_ms)))]},
         "roofline": {"kernel": "jbf_stage2", "bound": "alu", "achieved": achieved, "peak": peak_gtap,
                      "unit": "Gtap/s", "frac": achieved / peak_gtap if peak_gtap else None,
-                     "traffic": profiled_traffic("jbf_stage2"), "traffic_unit": "bytes per launch (ncu capture)",
+                     "traffic": profiled_traffic("jbf_stage2", kernel_choice["stages"][-1]["chosen"]),
+                     "traffic_unit": "bytes per launch (ncu capture of the same kernel variant)",
                      "peak_basis": f"{sms} SMs x 128 lanes / {TAP_INSTR} instructions per tap x {sm_max:.0f} MHz",
                      "taps_per_launch": taps2, "avg_launch_us": avg_us},
         "kernels": ktable,

@@ -579,6 +579,22 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
                 }
             }
         };
+        if (SRC == SRC_COARSE && B->tl_th[1] > 0) {   // flag the second-stage tiles the valid pixels reach
+            uint32_t cols = 0u;
+            int kf = KP, kl = -1;
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+                const uint32_t m = __ballot_sync(0xffffffffu, val[k] && x < gw && y0 + rbase + k < gh);
+                cols |= m;
+                if (m) {
+                    kf = min(kf, k);
+                    kl = k;
+                }
+            }
+            if (cols)
+                mark_reach(B->tl_flags[1] + B->t2_pre[fi], (F.W + 31) / 32, B->tl_th[1], B->tl_r[1], a.pool, F.W, F.H,
+                           x0 + __ffs(cols) - 1, x0 + 31 - __clz(cols), y0 + rbase + kf, y0 + rbase + kl, lane);
+        }
         uint32_t slow = 0u;   // bit k: valid pixel whose weight sum is too small for the plain form
 #pragma unroll
         for (int k = 0; k < KP; ++k) {

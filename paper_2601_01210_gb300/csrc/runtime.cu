@@ -733,16 +733,27 @@ densify_status prepare_tile_lists(densify_ctx *c, Slot &sl) {
     }
     b.tl_flags[0] = sl.d_tiles;
     b.tl_flags[1] = sl.d_tiles + b.t1_pre[n];
+    // tile geometry of the TMA stages: the second stage's tiles are flagged by the first
+    // filter's epilogue (two-stage path), the first (or only) stage's by the mark kernel
+    for (int i = 0; i < 2; ++i) {
+        const bool on = i < c->p.num_stages && c->sel[i].tma;
+        b.tl_th[i] = on ? c->sel[i].tile_h : 0;
+        b.tl_r[i] = on ? c->sel[i].radius : 0;
+    }
     return DENSIFY_OK;
 }
 
-// CUDA kernels of one filter launch (TMA: tile marks + filter).
-int filter_kernels(const densify_ctx *c, int i) { return c->sel[i].tma ? 2 : 1; }
+// CUDA kernels of one filter launch (a TMA first or only stage: tile marks + filter).
+int filter_kernels(const densify_ctx *c, int i) { return c->sel[i].tma && i == 0 ? 2 : 1; }
 
-// The tile marks in front of a TMA filter (nothing for the plain kernels).
+// In front of a TMA filter: the tile mark kernel, which also resets the tile counter (first or
+// only stage), or the counter reset alone (second stage, whose tiles the first filter flags).
+// Nothing for the plain kernels.
 cudaError_t launch_filter_scan(densify_ctx *c, int i, const BatchDev *b, cudaStream_t s) {
     const FilterSel &f = c->sel[i];
-    return f.tma ? launch_tile_mark(f.src, b, i, f.tile_h, f.radius, c->sms * 8, s) : cudaSuccess;
+    if (!f.tma) return cudaSuccess;
+    if (i == 1) return cudaMemsetAsync(const_cast<int32_t *>(&b->tl_next[i]), 0, sizeof(int32_t), s);
+    return launch_tile_mark(f.src, b, i, f.tile_h, f.radius, c->sms * 8, s);
 }
 
 cudaError_t launch_filter_kernel(densify_ctx *c, int i, const BatchDev *b, cudaStream_t s) {
@@ -843,10 +854,7 @@ densify_status issue_kernels(densify_ctx *c, Slot &sl, cudaStream_t s, bool reco
         }
         CU(launch_filter_kernel(c, 0, b, s), "stage-1 filter launch");
         CU(mark(K_JBF1), "event");
-        if (c->sel[1].tma) {
-            CU(launch_filter_scan(c, 1, b, s), "stage-2 tile mark launch");
-            CU(mark(K_MARK2), "event");
-        }
+        CU(launch_filter_scan(c, 1, b, s), "stage-2 tile counter reset");
         CU(start_last(), "event");
         CU(launch_filter_kernel(c, 1, b, s), "stage-2 filter launch");
         CU(mark(K_JBF2), "event");
