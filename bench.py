@@ -302,19 +302,21 @@ def profiled_traffic(kernel, chosen=None):
     the kernel's sources changed since that capture or the run chose another variant."""
     import hashlib
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+        recs = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
     except Exception:
         return None
-    if chosen is not None and any(chosen.get(k) != v for k, v in rec.get("variant", {}).items()):
-        return None
-    for path, digest in rec["sources"].items():
-        try:
-            h = hashlib.sha256(open(os.path.join(ROOT, path), "rb").read()).hexdigest()[:16]
-        except OSError:
-            return None
-        if h != digest:
-            return None
-    return rec["dram_bytes_per_launch"]
+    for rec in recs if isinstance(recs, list) else [recs]:
+        if chosen is not None and any(chosen.get(k) != v for k, v in rec.get("variant", {}).items()):
+            continue
+        ok = True
+        for path, digest in rec["sources"].items():
+            try:
+                ok &= hashlib.sha256(open(os.path.join(ROOT, path), "rb").read()).hexdigest()[:16] == digest
+            except OSError:
+                ok = False
+        if ok:
+            return rec["dram_bytes_per_launch"]
+    return None
 
 
 def valid_taps_stage2(coarse_valid, W, H, pool=3, r=2):

@@ -642,7 +642,7 @@ std::string cand_name(const FilterSel &f) {
 
 densify_status autotune(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &tk) {
     int64_t px = 0;
-    for (uint64_t t : tk) px += (int64_t)c->frames[t].dev.W * c->frames[t].dev.H;
+    for (uint64_t t : tk) px += (int64_t)c->frames[t].fr.K.width * c->frames[t].fr.K.height;   // the frames themselves (their descriptors are built later)
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CU(cudaEventCreate(&e0), "tuner event");
     CU(cudaEventCreate(&e1), "tuner event");

@@ -53,6 +53,9 @@ def test_tuned_equals_untuned_and_cache_is_reused(tmp_path, monkeypatch, precisi
         np.testing.assert_allclose(a["depth"], b["depth"], rtol=3e-5)
     lines = cache.read_text().splitlines()
     assert lines and all(" " in l for l in lines)
+    # the key's pixel class is the batch's pixel count: 1920x1080 + 1280x720 + 960x540 -> 2^21
+    px = sum(v.rgb.shape[0] * v.rgb.shape[1] for v in views)
+    assert all(l.split(" ")[0].endswith(f",px=2^{px.bit_length() - 1}") for l in lines), lines
     # a second context with the same workload takes the choices from the cache without timing
     again, desc2 = _run(views, torch, precision=precision, autotune=1)
     assert cache.read_text().splitlines() == lines
