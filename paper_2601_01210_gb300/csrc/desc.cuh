@@ -104,6 +104,7 @@ struct BatchDev {
     // tile; zeroed on the stream and set by tile_mark_kernel before every filter launch
     int32_t *tl_flags[2];
     int32_t tl_next[2];                            // the filter's tile counter (reset before each filter launch)
+    int32_t tl_tw[2];                              // tile width of a TMA filter stage (32 or 64)
     int32_t tl_th[2];                              // tile height of a TMA filter stage (0: no tile flags)
     int32_t tl_r[2];                               // its radius
     FrameDev f[kMaxBatch];
@@ -130,16 +131,17 @@ struct StageArgs {
     float ex_sy[2 * kMaxR + 1];
 };
 
-// Flag the filter tiles (32 x th output pixels, row-major per frame, tiles_x across) that an
-// observation range reaches: columns [ox0, ox1] and rows [oy0, oy1] of a grid f times coarser
-// than the gw x gh output grid, grown by the radius r. The lanes of one warp share the stores,
-// plain stores of the same value (no read first: the caller does not wait on a load).
-__device__ __forceinline__ void mark_reach(int32_t *flags, int tiles_x, int th, int r, int f, int gw, int gh,
-                                           int ox0, int ox1, int oy0, int oy1, int lane) {
+// Flag the filter tiles (tw x th output pixels, row-major per frame) that an observation range
+// reaches: columns [ox0, ox1] and rows [oy0, oy1] of a grid f times coarser than the gw x gh
+// output grid, grown by the radius r. The lanes of one warp share the stores, plain stores of
+// the same value (no read first: the caller does not wait on a load).
+__device__ __forceinline__ void mark_reach(int32_t *flags, int tw, int th, int r, int f, int gw, int gh, int ox0,
+                                           int ox1, int oy0, int oy1, int lane) {
     const int xlo = max(0, f * ox0 - r), xhi = min(gw - 1, f * ox1 + f - 1 + r);
     const int ylo = max(0, f * oy0 - r), yhi = min(gh - 1, f * oy1 + f - 1 + r);
     if (xlo > xhi || ylo > yhi) return;
-    const int tx0 = xlo / 32, ntx = xhi / 32 - tx0 + 1, ty0 = ylo / th, n = ntx * (yhi / th - ty0 + 1);
+    const int tiles_x = (gw + tw - 1) / tw;
+    const int tx0 = xlo / tw, ntx = xhi / tw - tx0 + 1, ty0 = ylo / th, n = ntx * (yhi / th - ty0 + 1);
     for (int j = lane; j < n; j += 32) {
         flags[(ty0 + j / ntx) * tiles_x + tx0 + j % ntx] = 1;
     }

@@ -37,117 +37,21 @@
 // overflows to +inf and the weight is exactly 0. Pixels whose weight sum is
 // below 2^-6 (dominant weight in the half subnormal range) are recomputed in
 // FP32 with shifted exponents.
+//
+// Expanded FP32 forms: FORM_EXP expands the squared colour distance into a dot
+// product (per-neighbour factors staged once, see the tap loop); FORM_EXP_PAIRS
+// runs the same arithmetic on 64-column tiles, two output columns per thread in
+// packed two-lane FP32 instructions (pair_tile, jbf_pair.cuh). The scheduling,
+// copies and waits below are shared by all forms.
 #pragma once
 
 #include <cuda_fp16.h>
 
 #include "jbf_core.cuh"
+#include "jbf_pair.cuh"
+#include "tma_common.cuh"
 
 namespace dz {
-
-constexpr long long kWaitCycles = 4000000000LL;
-constexpr float kSentinel = 1.0e18f;
-
-enum { SRC_UP = 0, SRC_ZBUF = 1, SRC_COARSE = 2 };
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-
-// Relaxed: the issuing thread's earlier global stores need not be performed first (a release
-// arrive waits for them). Nothing is published through this arrive: tile coordinates reach the
-// CTA through a barrier, and copies into a buffer are issued only after the barrier that frees it.
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.relaxed.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
-    const long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kWaitCycles) return false;
-    return true;
-}
-
-__device__ __forceinline__ void tmap_acquire(const CUtensorMap *m) {
-    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)m) : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *m, int x, int y, uint64_t *bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
-            "r"(smem_u32(dst)),
-        "l"((uint64_t)m), "r"(x), "r"(y), "r"(smem_u32(bar))
-        : "memory");
-}
-
-__device__ __forceinline__ int floor_div3(int a) { return a >= 0 ? a / 3 : -((2 - a) / 3); }
-
-constexpr int ceil_to(int x, int m) { return (x + m - 1) / m * m; }
-
-// Tile geometry shared by the kernel and the host (tensor-map boxes).
-template <int SRC, int R, int KP, int NW_ = 8, bool EXP = false>
-struct TmaGeom {
-    static constexpr int TW = 32, NW = NW_, TH = NW * KP, SW = TW + 2 * R, SH = TH + 2 * R;
-    // RGB bytes: box starts at byte 3*x0 - RGB_LEAD (x0 is a multiple of 32, so 3*x0 of 16)
-    static constexpr int RGB_LEAD = ceil_to(3 * R, 16);
-    static constexpr int RGB_BX = ceil_to(3 * TW + 3 * R + RGB_LEAD, 16);
-    static constexpr int RGB_BY = SH;
-    // first-stage result (float2) on the pooled grid, pool 3: rows floor((y0-R)/3) ..
-    // floor((y0+TH-1+R)/3); columns from floor((x0-R)/3) rounded down to even
-    static constexpr int C_BX = ceil_to(2 + (SW + 1) / 3, 2);
-    static constexpr int C_BY = 1 + (SH + 1) / 3;
-    // z-buffer (uint32): box starts at x0 - Z_LEAD
-    static constexpr int Z_LEAD = ceil_to(R, 4);
-    static constexpr int Z_BX = ceil_to(TW + R + Z_LEAD, 4);
-    static constexpr int Z_BY = SH;
-    // pooled guide (float4, as 4 floats per element) and pooled sums (float, starts at x0 - S_LEAD)
-    static constexpr int G_BX = 4 * SW;
-    static constexpr int G_BY = SH;
-    static constexpr int S_LEAD = ceil_to(R, 4);
-    static constexpr int S_BX = ceil_to(TW + R + S_LEAD, 4);
-    static constexpr int S_BY = SH;
-
-    // raw buffer bytes (each rounded to 128 for TMA destination alignment)
-    static constexpr int RAW_A = SRC == SRC_COARSE ? ceil_to(G_BX * G_BY * 4, 128) : ceil_to(RGB_BX * RGB_BY, 128);
-    static constexpr int RAW_B = SRC == SRC_UP     ? ceil_to(C_BX * C_BY * 8, 128)
-                                 : SRC == SRC_ZBUF ? ceil_to(Z_BX * Z_BY * 4, 128)
-                                                   : ceil_to(S_BX * S_BY * 4, 128);
-    static constexpr int TX_BYTES = SRC == SRC_COARSE ? G_BX * G_BY * 4 + S_BX * S_BY * 4
-                                    : SRC == SRC_UP   ? RGB_BX * RGB_BY + C_BX * C_BY * 8
-                                                      : RGB_BX * RGB_BY + Z_BX * Z_BY * 4;
-    static constexpr int STAGED = SRC == SRC_COARSE && !EXP ? 0 : SH * SW * 16;
-    static constexpr int STAGED_G = EXP ? ceil_to(SH * SW * 4, 16) : 0;   // expanded form: F_q times depth
-    // observation bitmap: bit i = staged position i observed; one word per 32 positions for
-    // every position the conversion loop visits, plus a zero guard word
-    static constexpr int NT = NW * 32, NCONV = (SH * SW + NT - 1) / NT;
-    static constexpr int OBS_WORDS = NCONV * NT / 32 + 1;
-    static constexpr int OBS = ceil_to(OBS_WORDS * 4, 16);
-    static constexpr int HOR = 0;
-    static constexpr int OFF_RAW = 0;
-    static constexpr int OFF_STAGED = OFF_RAW + 2 * (RAW_A + RAW_B);
-    static constexpr int OFF_G = OFF_STAGED + STAGED;
-    static constexpr int OFF_OBS = OFF_G + STAGED_G;
-    static constexpr int OFF_HOR = OFF_OBS + OBS;
-    static constexpr int OFF_BAR = ceil_to(OFF_HOR + HOR, 16);
-    static constexpr int SMEM = OFF_BAR + 16;
-};
 
 // FP16 staged record -> FP32 colour and depth (sentinel colour: unobserved).
 __device__ __forceinline__ bool half_record(const uint4 &q, float &r, float &g, float &b, float &d) {
@@ -167,13 +71,11 @@ __device__ __forceinline__ __half2 h2exp2_approx(__half2 x) {
     return h2bits(y);
 }
 
-enum { FORM_FP32 = 0, FORM_FP16 = 1, FORM_EXP = 2 };
-
 template <int SRC, int R, int KP, int FORM = FORM_FP32, int NW = 8>
 __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDev *__restrict__ B,
                                                                            const StageArgs a) {
     constexpr bool HALF = FORM == FORM_FP16, EXP = FORM == FORM_EXP;
-    using G = TmaGeom<SRC, R, KP, NW, EXP>;
+    using G = TmaGeom<SRC, R, KP, NW, FORM>;
     constexpr int TW = G::TW, TH = G::TH, SW = G::SW, SH = G::SH, T = 2 * R + 1;
     constexpr int NT = NW * 32;   // threads
     static_assert(!HALF || (SRC != SRC_COARSE && KP % 2 == 0), "FP16 form: full-resolution stages, row pairs");
@@ -239,7 +141,8 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
         mbar_fence_init();
-        obsw[G::OBS_WORDS - 1] = 0u;   // guard word, never rewritten
+        obsw[G::OBS_WORDS - 1] = 0u;   // guard words, never rewritten
+        if (G::PAIRS) obsw[G::OBS_ONE / 4 + G::OBS_WORDS - 1] = 0u;
         // the tensor maps of every frame of the batch, acquired once before thread 0 has any memory
         // operation outstanding (a fence later in the loop would wait for its stores and atomics)
         for (int f = 0; f < nf; ++f) {
@@ -330,6 +233,13 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
                 }
             }
             __syncthreads();   // s_tile[buf] is rewritten for the tile after next
+            continue;
+        }
+        if constexpr (G::PAIRS) {
+            pair_tile<SRC, R, KP, NW>(F, a, x0, y0, gw, gh, rawA(buf), rawB(buf), smem, [&]() {
+                if (threadIdx.x == 0 && n1 < total) advance();   // off the path of the CTA's barriers
+            });
+            __syncthreads();   // staged records / raw[buf] are reused by the next tile
             continue;
         }
         const uint8_t *rgbraw = rawA(buf);
@@ -592,7 +502,7 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
                 }
             }
             if (cols)
-                mark_reach(B->tl_flags[1] + B->t2_pre[fi], (F.W + 31) / 32, B->tl_th[1], B->tl_r[1], a.pool, F.W, F.H,
+                mark_reach(B->tl_flags[1] + B->t2_pre[fi], B->tl_tw[1], B->tl_th[1], B->tl_r[1], a.pool, F.W, F.H,
                            x0 + __ffs(cols) - 1, x0 + 31 - __clz(cols), y0 + rbase + kf, y0 + rbase + kl, lane);
         }
         uint32_t slow = 0u;   // bit k: valid pixel whose weight sum is too small for the plain form
@@ -680,7 +590,7 @@ __global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDe
 // image for SRC_ZBUF); every lane reads its column's kMarkRows observation flags
 // (in flight together). The output pixels the band's observations reach (grown
 // by the radius; a pooled pixel covers a 3 x 3 block at full resolution for
-// SRC_UP) span a range of the stage's tiles (32 x th, row-major per frame), whose
+// SRC_UP) span a range of the stage's tiles (tw x th, row-major per frame), whose
 // flags the warp sets. The range spans the band's first to last observed column
 // and row, a superset: a flagged tile that no observation reaches is filtered to
 // all-invalid outputs, as it should be. The first block also resets the
@@ -724,13 +634,7 @@ __global__ void __launch_bounds__(kMarkThreads) tile_mark_kernel(BatchDev *__res
         const int ox0 = sx0 + __ffs(cols) - 1, ox1 = sx0 + 31 - __clz(cols);
         const int oy1 = oy0 + 31 - __clz(all), oyf = oy0 + __ffs(all) - 1;
         const int f = SRC == SRC_UP ? 3 : 1;   // output pixels per observation pixel and axis
-        const int xlo = max(0, f * ox0 - r), xhi = min(gw - 1, f * ox1 + f - 1 + r);
-        const int ylo = max(0, f * oyf - r), yhi = min(gh - 1, f * oy1 + f - 1 + r);
-        if (xlo > xhi || ylo > yhi) continue;
-        const int tx0 = xlo / 32, ntx = xhi / 32 - tx0 + 1, ty0 = ylo / th, n = ntx * (yhi / th - ty0 + 1);
-        const int tiles_x = (gw + 31) / 32;
-        int32_t *flags = B->tl_flags[stage] + tpre[fi];
-        for (int j = lane; j < n; j += 32) flags[(ty0 + j / ntx) * tiles_x + tx0 + j % ntx] = 1;
+        mark_reach(B->tl_flags[stage] + tpre[fi], B->tl_tw[stage], th, r, f, gw, gh, ox0, ox1, oyf, oy1, lane);
     }
 }
 

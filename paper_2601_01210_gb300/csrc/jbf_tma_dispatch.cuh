@@ -10,7 +10,7 @@ namespace dz {
 namespace tma_detail {
 
 template <int SRC, int R, int KP, int FORM, int NW>
-using Geom = TmaGeom<SRC, R, KP, NW, FORM == FORM_EXP>;
+using Geom = TmaGeom<SRC, R, KP, NW, FORM>;
 
 template <int SRC, int R, int KP, int FORM, int NW>
 void fill_info(TmaKernelInfo *o) {

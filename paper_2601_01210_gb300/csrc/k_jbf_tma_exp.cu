@@ -1,7 +1,7 @@
 // Instantiations of the TMA-staged joint bilateral filter in the expanded
-// FP32 form (squared colour distance expanded into a dot product; see
-// jbf_tma.cuh), in a translation unit of their own so that the library's
-// sources compile in parallel.
+// FP32 forms (squared colour distance expanded into a dot product; scalar, see
+// jbf_tma.cuh, and on column pairs, see jbf_pair.cuh), in a translation unit of
+// their own so that the library's sources compile in parallel.
 #include "jbf_tma_dispatch.cuh"
 
 namespace dz {
@@ -9,6 +9,9 @@ namespace dz {
 // (source, radius, rows per thread, form, warps per CTA); the first listed
 // variant of a (source, radius) is the default before autotuning
 #define DZ_TMA_EXP_CASES(X)              \
+    X(SRC_UP, 2, 4, FORM_EXP_PAIRS, 8)   \
+    X(SRC_UP, 2, 2, FORM_EXP_PAIRS, 8)   \
+    X(SRC_UP, 2, 4, FORM_EXP_PAIRS, 16)  \
     X(SRC_UP, 2, 8, FORM_EXP, 16)        \
     X(SRC_UP, 2, 8, FORM_EXP, 8)         \
     X(SRC_UP, 2, 4, FORM_EXP, 8)         \

@@ -74,6 +74,7 @@ __global__ void noalloc_init_kernel(BatchDev *b, FrameWords f, Prefix p, int32_t
         b->mk_pre[0] = b->mk_pre[1] = 0;
         b->tl_flags[0] = b->tl_flags[1] = nullptr;   // plain filter kernels only: no tile flags
         b->tl_th[0] = b->tl_th[1] = 0;
+        b->tl_tw[0] = b->tl_tw[1] = 32;
     }
 }
 

@@ -149,6 +149,7 @@ struct FilterSel {
     int src = 0;         // TMA source kind
     int kp = 0;          // output rows per thread
     int nw = 8;          // warps per CTA (tile height = kp * nw)
+    int tile_w = 32;     // output tile (tile_w x tile_h pixels)
     int tile_h = 0;
     int occ = 1;         // resident CTAs per SM
     TmaKernelInfo info{};
@@ -280,6 +281,7 @@ std::vector<FilterSel> filter_candidates(const densify_params &p, int kind, int 
             s.kp = vs[i].kp;
             s.nw = vs[i].nw;
             jbf_tma_info(src, r, vs[i], form, &s.info);
+            s.tile_w = s.info.tile_w;
             s.tile_h = s.info.tile_h;
             out.push_back(s);
         }
@@ -293,8 +295,10 @@ std::vector<FilterSel> filter_candidates(const densify_params &p, int kind, int 
             const double log2e = 1.4426950408889634;
             const double kc = log2e / (2.0 * (double)st.sigma_c * (double)st.sigma_c);
             const double kp = log2e / (2.0 * (double)st.sigma_p * (double)st.sigma_p);
-            if (p.kernel_variant == 0 && kc * 3.0 * 128.0 * 128.0 + kp * 2.0 * r * r <= kExpRange)
+            if (p.kernel_variant == 0 && kc * 3.0 * 128.0 * 128.0 + kp * 2.0 * r * r <= kExpRange) {
+                add_tma(TMA_FORM_EXP_PAIRS);
                 add_tma(TMA_FORM_EXP);
+            }
             add_tma(TMA_FORM_FP32);
         }
     }
@@ -559,8 +563,8 @@ void fill_batch(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &tk) {
     const int r1 = c->p.stage[0].radius, r2 = nst == 2 ? c->p.stage[1].radius : 0;
     (void)r1;
     (void)r2;
-    const int th1 = c->sel[0].tile_h;
-    const int th2 = nst == 2 ? c->sel[1].tile_h : 1;
+    const int tw1 = c->sel[0].tile_w, th1 = c->sel[0].tile_h;
+    const int tw2 = nst == 2 ? c->sel[1].tile_w : 32, th2 = nst == 2 ? c->sel[1].tile_h : 1;
     for (int i = 0; i < n; ++i) {
         FrameRec &r = c->frames[tk[i]];
         const FrameDev &d = r.dev;
@@ -572,8 +576,8 @@ void fill_batch(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &tk) {
         }
         b.pool_pre[i + 1] = b.pool_pre[i] + (nst == 2 ? ceil_div(d.Wc, kPoolPerChunk) * d.Hc : 0);
         const int g1w = nst == 2 ? d.Wc : d.W, g1h = nst == 2 ? d.Hc : d.H;
-        b.t1_pre[i + 1] = b.t1_pre[i] + ceil_div(g1w, 32) * ceil_div(g1h, th1);
-        b.t2_pre[i + 1] = b.t2_pre[i] + (nst == 2 ? ceil_div(d.W, 32) * ceil_div(d.H, th2) : 0);
+        b.t1_pre[i + 1] = b.t1_pre[i] + ceil_div(g1w, tw1) * ceil_div(g1h, th1);
+        b.t2_pre[i + 1] = b.t2_pre[i] + (nst == 2 ? ceil_div(d.W, tw2) * ceil_div(d.H, th2) : 0);
         b.bp_pre[i + 1] = b.bp_pre[i] + (c->p.emit_points ? d.n_bp_chunks : 0);
         b.px_pre[i + 1] = b.px_pre[i] + d.n_px_chunks;
         b.oc_pre[i + 1] = b.oc_pre[i] + ceil_div(d.W, kOccTile) * ceil_div(d.H, kOccTile);
@@ -635,7 +639,7 @@ void cache_store(const std::string &key, const std::string &val) {
 }
 
 std::string cand_name(const FilterSel &f) {
-    static const char *forms[] = {"fp32", "fp16", "exp"};
+    static const char *forms[] = {"fp32", "fp16", "exp", "exp_pairs"};
     return std::string(f.tma ? "tma" : "plain") + ":kp" + std::to_string(f.kp) + ":nw" + std::to_string(f.nw) +
            (f.tma ? std::string(":") + forms[f.form] : std::string());
 }
@@ -737,6 +741,7 @@ densify_status prepare_tile_lists(densify_ctx *c, Slot &sl) {
     // filter's epilogue (two-stage path), the first (or only) stage's by the mark kernel
     for (int i = 0; i < 2; ++i) {
         const bool on = i < c->p.num_stages && c->sel[i].tma;
+        b.tl_tw[i] = on ? c->sel[i].tile_w : 32;
         b.tl_th[i] = on ? c->sel[i].tile_h : 0;
         b.tl_r[i] = on ? c->sel[i].radius : 0;
     }
@@ -1458,10 +1463,13 @@ int32_t densify_describe(densify_ctx *c, char *buf, int32_t cap) {
     auto one = [&](const FilterSel &f) {
         char tmp[256];
         std::snprintf(tmp, sizeof tmp,
-                      "{\"kernel\": \"%s\", \"kp\": %d, \"warps\": %d, \"tile\": [32, %d], \"fp16\": %s, "
+                      "{\"kernel\": \"%s\", \"kp\": %d, \"warps\": %d, \"tile\": [%d, %d], \"fp16\": %s, "
                       "\"form\": \"%s\", \"ctas_per_sm\": %d%s",
-                      f.tma ? "tma" : "plain", f.kp, f.nw, f.tile_h, f.half ? "true" : "false",
-                      f.half ? "fp16" : f.form == TMA_FORM_EXP ? "fp32_expanded" : "fp32",
+                      f.tma ? "tma" : "plain", f.kp, f.nw, f.tile_w, f.tile_h, f.half ? "true" : "false",
+                      f.half                          ? "fp16"
+                      : f.form == TMA_FORM_EXP_PAIRS ? "fp32_expanded_pairs"
+                      : f.form == TMA_FORM_EXP        ? "fp32_expanded"
+                                                      : "fp32",
                       f.occ,
                       f.tuned_us >= 0.0f ? "" : "}");
         std::string s(tmp);

@@ -30,8 +30,10 @@ struct TmaKernelInfo {
 // Arithmetic forms of the filter kernels: FP32 with colour differences, FP16
 // guide and weights with FP32 sums (full-resolution stages only), FP32 with the
 // squared colour distance expanded into a dot product (weights kept in range
-// only while kc * 3 * 128^2 + kp * 2 R^2 <= kExpRange, see jbf_tma.cuh).
-enum { TMA_FORM_FP32 = 0, TMA_FORM_FP16 = 1, TMA_FORM_EXP = 2 };
+// only while kc * 3 * 128^2 + kp * 2 R^2 <= kExpRange, see jbf_tma.cuh), and the
+// expanded form on pairs of output columns in packed two-lane FP32 arithmetic
+// (64-column tiles, see jbf_pair.cuh).
+enum { TMA_FORM_FP32 = 0, TMA_FORM_FP16 = 1, TMA_FORM_EXP = 2, TMA_FORM_EXP_PAIRS = 3 };
 constexpr double kExpRange = 100.0;
 
 // Instantiated variants of (source, radius, form).
@@ -41,7 +43,7 @@ cudaError_t jbf_tma_prepare(int src, int r, TmaVariant v, int form);
 cudaError_t launch_jbf_tma(int src, int r, TmaVariant v, int form, const BatchDev *b, const StageArgs &a, int grid,
                            cudaStream_t s);
 int occupancy_jbf_tma(int src, int r, TmaVariant v, int form);
-// Flag the tiles of the stage's grid (32 x th) that some observation within radius r
+// Flag the tiles of the stage's grid (tw x th) that some observation within radius r
 // reaches (the flags were zeroed by the batch's first kernel).
 cudaError_t launch_tile_mark(int src, const BatchDev *b, int stage, int th, int r, int grid, cudaStream_t s);
 

@@ -61,3 +61,36 @@ def test_tuned_equals_untuned_and_cache_is_reused(tmp_path, monkeypatch, precisi
     assert cache.read_text().splitlines() == lines
     for s1, s2 in zip(desc["stages"], desc2["stages"]):
         assert all(s1["chosen"][k] == s2["chosen"][k] for k in ("kernel", "kp", "warps", "form"))
+
+
+_FORM_TAG = {"fp32": "fp32", "fp16": "fp16", "fp32_expanded": "exp", "fp32_expanded_pairs": "exp_pairs"}
+
+
+def test_every_second_stage_candidate_matches_the_plain_kernel(tmp_path, monkeypatch):
+    """Each kernel the tuner may pick for the full-resolution stage, forced
+    through a tuning-cache entry, gives the plain kernel's integer decisions
+    and its depths within FP32 rounding (frames of three sizes in one batch:
+    tiles of every kind, ragged rows)."""
+    import torch
+    views = [scene.make_batch_view(78, r, i, 3) for i, r in enumerate(["1080p", "720p", "540p"])]
+    plain, _ = _run(views, torch, kernel_variant=1)
+    _, desc = _run(views, torch)
+    px = sum(v.rgb.shape[0] * v.rgb.shape[1] for v in views)
+    key = f"kind=2,r={STAGES[1][0]},half=0,px=2^{px.bit_length() - 1}"
+    tried = set()
+    for c in desc["stages"][1]["candidates"]:
+        if c["kernel"] != "tma":
+            continue
+        name = f"tma:kp{c['kp']}:nw{c['warps']}:{_FORM_TAG[c['form']]}"
+        cache = tmp_path / f"{name.replace(':', '_')}.txt"
+        cache.write_text(f"{key} {name}\n")
+        monkeypatch.setenv("DENSIFY_TUNE_CACHE", str(cache))
+        got, d = _run(views, torch, autotune=1)
+        ch = d["stages"][1]["chosen"]
+        assert (ch["kp"], ch["warps"], ch["form"]) == (c["kp"], c["warps"], c["form"])
+        for a, b in zip(got, plain):
+            for k in ("valid", "rgba"):
+                assert np.array_equal(a[k], b[k]), (name, k)
+            np.testing.assert_allclose(a["depth"], b["depth"], rtol=3e-5, err_msg=name)
+        tried.add(c["form"])
+    assert "fp32_expanded_pairs" in tried
