@@ -71,8 +71,12 @@ __device__ __forceinline__ __half2 h2exp2_approx(__half2 x) {
     return h2bits(y);
 }
 
+// Resident CTAs per SM the compiler is asked to fit (registers): 16 warps per SM, and 32 for
+// the paired form at two rows per thread, whose state fits 64 registers.
+constexpr int tma_min_ctas(int form, int kp, int nw) { return (form == FORM_EXP_PAIRS && kp == 2 ? 32 : 16) / nw; }
+
 template <int SRC, int R, int KP, int FORM = FORM_FP32, int NW = 8>
-__global__ void __launch_bounds__(NW * 32, 16 / NW) jbf_tma_kernel(const BatchDev *__restrict__ B,
+__global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_kernel(const BatchDev *__restrict__ B,
                                                                            const StageArgs a) {
     constexpr bool HALF = FORM == FORM_FP16, EXP = FORM == FORM_EXP;
     using G = TmaGeom<SRC, R, KP, NW, FORM>;
