@@ -92,8 +92,11 @@ __device__ __forceinline__ void pair_tile(const FrameDev &F, const StageArgs &a,
             r1[j] = q[0]; g1[j] = q[1]; b1[j] = q[2];
         }
     }
-    // byte b as an exact float minus bias: 2^23 + b has b in its low mantissa bits
-    auto bytef = [](uint32_t b, float bias) { return __uint_as_float(0x4B000000u | b) - (8388608.0f + bias); };
+    // bytes b, b' as exact floats minus 128: 2^23 + b has b in its low mantissa bits
+    auto bytes2 = [](uint32_t b, uint32_t b2) {
+        return __fadd2_rn(f2(__uint_as_float(0x4B000000u | b), __uint_as_float(0x4B000000u | b2)),
+                          f2(-8388736.0f, -8388736.0f));
+    };
     const float kc = a.kc;
 #pragma unroll
     for (int j = 0; j < NCONV; ++j) {
@@ -101,14 +104,13 @@ __device__ __forceinline__ void pair_tile(const FrameDev &F, const StageArgs &a,
         const bool o0 = (om0 >> j) & 1u, o1 = (om1 >> j) & 1u;
         if (i < SH * SP) {
             // centred colours (exact); an unobserved record keeps its colour with F = G = 0
-            const float2 r = f2(bytef(r0[j], 128.0f), bytef(r1[j], 128.0f));
-            const float2 g = f2(bytef(g0[j], 128.0f), bytef(g1[j], 128.0f));
-            const float2 b = f2(bytef(b0[j], 128.0f), bytef(b1[j], 128.0f));
-            const float f0 = o0 ? ex2_approx(-kc * fmaf(r.x, r.x, fmaf(g.x, g.x, b.x * b.x))) : 0.0f;
-            const float f1 = o1 ? ex2_approx(-kc * fmaf(r.y, r.y, fmaf(g.y, g.y, b.y * b.y))) : 0.0f;
+            const float2 r = bytes2(r0[j], r1[j]), g = bytes2(g0[j], g1[j]), b = bytes2(b0[j], b1[j]);
+            const float2 e = __fmul2_rn(f2(-kc, -kc), __ffma2_rn(r, r, __ffma2_rn(g, g, __fmul2_rn(b, b))));
+            const float f0 = o0 ? ex2_approx(e.x) : 0.0f, f1 = o1 ? ex2_approx(e.y) : 0.0f;
+            const float2 fd = __fmul2_rn(f2(f0, f1), f2(d0[j], d1[j]));
             sc[i] = make_float4(r.x, r.y, g.x, g.y);
             sb[i] = make_float4(b.x, b.y, f0, f1);
-            sg[i] = f2(o0 ? f0 * d0[j] : 0.0f, o1 ? f1 * d1[j] : 0.0f);   // an empty z-buffer cell holds +inf
+            sg[i] = f2(o0 ? fd.x : 0.0f, o1 ? fd.y : 0.0f);   // an empty z-buffer cell holds +inf
         }
         const uint32_t w0 = __ballot_sync(0xffffffffu, o0), w1 = __ballot_sync(0xffffffffu, o1);
         if (lane == 0) {

@@ -169,7 +169,12 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
     // filters, and every global result is used one tile after it was requested: the issuing
     // thread never waits on a load or on the counter, which a whole grid of CTAs shares. The
     // counter is only ever touched atomically (the descriptor's other fields are read-only here).
-    int n1 = total, f1 = 0, l1f = 0, l1x = 0, l1y = 0, n2raw = 0;
+    __shared__ int s_q[6];   // thread 0's queue state, kept out of every thread's registers
+    int &n1 = s_q[0], &f1 = s_q[1], &l1f = s_q[2], &l1x = s_q[3], &l1y = s_q[4], &n2raw = s_q[5];
+    if (threadIdx.x == 0) {
+        n1 = total;
+        f1 = l1f = l1x = l1y = n2raw = 0;
+    }
     auto request = [&]() { return atomicAdd(const_cast<int32_t *>(&B->tl_next[stage]), 1); };
     auto advance = [&]() {   // thread 0: n1 <- the counter's last reply; request the next one
         n1 = (int)gridDim.x + n2raw;
