@@ -38,7 +38,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "1080p dense-depth frames/s (3 merged LiDAR scans, two-stage JBF r=4@1/3 + r=2, coloured points)"
 UNIT = "frames/s"
-TAP_INSTR = 6          # issue slots of the minimal filter tap (see the roofline note below)
+# issue slots of one filter tap in each arithmetic form (see the roofline note below)
+TAP_INSTR = {"fp32": 10.0, "fp32_expanded": 6.0, "fp32_expanded_pairs": 3.5}
 STAGES = ((4, 5.0, 20.0), (2, 5.0, 20.0))
 L2_FLUSH_BYTES = 256 << 20
 
@@ -517,11 +518,13 @@ def ours_arm(a, rank, world, local_rank):
     except Exception:
         pass
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    # ALU peak of the filter: 152 SMs x 4 SMSPs x 32 lanes issue one instruction per clock; a tap needs at
-    # least 6 (with the squared colour distance expanded, 3 fma give the exponent, 1 ex2, 2 fma accumulate);
-    # the ex2 unit (32 lanes per SM) and the FP32 pipe (128 lanes, 5 fma a tap) bound it less tightly.
+    # ALU peak of the filter: 152 SMs x 4 SMSPs x 32 lanes issue one instruction per clock. A tap of the
+    # expanded form takes 6 (3 fma give the exponent, 1 ex2, 2 fma accumulate), the difference form 10; the
+    # paired form runs two taps in 3 two-lane fma, 2 ex2 and 2 two-lane fma: 3.5 a tap.
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak_gtap = sms * 128 / TAP_INSTR * sm_max * 1e6 / 1e9
+    form2 = kernel_choice["stages"][-1]["chosen"].get("form", "fp32_expanded")
+    tap_instr = TAP_INSTR.get(form2, 6.0)
+    peak_gtap = sms * 128 / tap_instr * sm_max * 1e6 / 1e9
     s2 = times.get("jbf_stage2", (0.0, 1))
     avg_us = s2[0] / max(1, s2[1])
     achieved = taps2 / (avg_us * 1e-6) / 1e9 if avg_us > 0 else 0.0
@@ -548,7 +551,8 @@ def ours_arm(a, rank, world, local_rank):
                      "unit": "Gtap/s", "frac": achieved / peak_gtap if peak_gtap else None,
                      "traffic": profiled_traffic("jbf_stage2", kernel_choice["stages"][-1]["chosen"]),
                      "traffic_unit": "bytes per launch (ncu capture of the same kernel variant)",
-                     "peak_basis": f"{sms} SMs x 128 lanes / {TAP_INSTR} instructions per tap x {sm_max:.0f} MHz",
+                     "peak_basis": f"{sms} SMs x 128 lanes / {tap_instr:g} instructions per tap ({form2}) x "
+                                   f"{sm_max:.0f} MHz",
                      "taps_per_launch": taps2, "avg_launch_us": avg_us},
         "kernels": ktable,
         "kernels_how": ("per-kernel CUDA events in a separate pass of 10 steps; the timed steps carry events "
