@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-fp16", action="store_true", help="skip the FP16-form measurement")
     ap.add_argument("--autotune", type=int, default=1, help="1: pick filter kernels on the first batch")
+    ap.add_argument("--kernels", default="",
+                    help="STAGE1,STAGE2 filter kernels to use instead of tuning (candidate names as in the "
+                         "tuning cache, e.g. tma:kp2:nw4:exp,tma:kp4:nw4:exp_pairs); for profiling runs")
     ap.add_argument("--kernel-timing", type=int, default=2,
                     help="events inside the timed steps: 2 around the full-resolution filter only (the "
                          "per-kernel table then comes from a separate untimed pass), 1 around every kernel")
@@ -362,9 +365,16 @@ def ours_arm(a, rank, world, local_rank):
     from paper_2601_01210_gb300.frames import FrameBuffers
 
     views = make_views(a.views, 1001, rank)   # before any CUDA call (spawn pool)
-    if "DENSIFY_TUNE_CACHE" not in os.environ:   # later contexts reuse the first one's kernel choices
+    if "DENSIFY_TUNE_CACHE" not in os.environ or a.kernels:   # later contexts reuse the first one's choices
         import tempfile
         os.environ["DENSIFY_TUNE_CACHE"] = os.path.join(tempfile.mkdtemp(prefix="densify_tune_"), "tune.txt")
+    if a.kernels:   # the tuner takes cached choices without timing: key = stage kind, radius, precision, pixel class
+        px = a.batch * 1920 * 1080
+        names = a.kernels.split(",")
+        with open(os.environ["DENSIFY_TUNE_CACHE"], "w") as f:
+            for (kind, st), name in zip(((1, STAGES[0]), (2, STAGES[1])), names):
+                f.write(f"kind={kind},r={st[0]},half=0,px=2^{px.bit_length() - 1} {name}\n")
+        a.autotune = 1
     mixed_views = make_mixed_views(16, 4004) if (not a.no_serve and rank == 0) else None
     build.build()
     torch.cuda.set_device(local_rank)
