@@ -16,12 +16,13 @@ pytestmark = pytest.mark.gpu
 STAGES = ((4, 5.0, 20.0), (2, 5.0, 20.0))
 
 
-def _run(views, torch, **params):
+def _run(views, torch, debug=False, **params):
     from paper_2601_01210_gb300 import Densifier, build
     from paper_2601_01210_gb300.frames import FrameBuffers
     build.build()
     with Densifier(dict(num_stages=2, stages=STAGES, launch_policy=1, max_batch=8, **params)) as d:
-        bufs = [FrameBuffers(v.camera, v.rgb, [(s.xyz, s.lidar_to_world) for s in v.scans]) for v in views]
+        bufs = [FrameBuffers(v.camera, v.rgb, [(s.xyz, s.lidar_to_world) for s in v.scans], debug=debug)
+                for v in views]
         ts = [d.submit(b.frame) for b in bufs]
         d.flush()
         for t in ts:
@@ -66,31 +67,36 @@ def test_tuned_equals_untuned_and_cache_is_reused(tmp_path, monkeypatch, precisi
 _FORM_TAG = {"fp32": "fp32", "fp16": "fp16", "fp32_expanded": "exp", "fp32_expanded_pairs": "exp_pairs"}
 
 
-def test_every_second_stage_candidate_matches_the_plain_kernel(tmp_path, monkeypatch):
-    """Each kernel the tuner may pick for the full-resolution stage, forced
-    through a tuning-cache entry, gives the plain kernel's integer decisions
-    and its depths within FP32 rounding (frames of three sizes in one batch:
-    tiles of every kind, ragged rows)."""
+@pytest.mark.parametrize("stage", [0, 1])
+def test_every_candidate_matches_the_plain_kernel(tmp_path, monkeypatch, stage):
+    """Each kernel the tuner may pick for a stage, forced through a tuning-cache
+    entry (the other stage runs the plain kernel), gives the plain kernel's
+    integer decisions and its depths within FP32 rounding (frames of three
+    sizes in one batch: tiles of every kind, ragged rows and columns)."""
     import torch
     views = [scene.make_batch_view(78, r, i, 3) for i, r in enumerate(["1080p", "720p", "540p"])]
-    plain, _ = _run(views, torch, kernel_variant=1)
+    plain, _ = _run(views, torch, debug=True, kernel_variant=1)
     _, desc = _run(views, torch)
     px = sum(v.rgb.shape[0] * v.rgb.shape[1] for v in views)
-    key = f"kind=2,r={STAGES[1][0]},half=0,px=2^{px.bit_length() - 1}"
+    keys = [f"kind={k},r={STAGES[i][0]},half=0,px=2^{px.bit_length() - 1}" for i, k in enumerate((1, 2))]
+    other = next(c for c in desc["stages"][1 - stage]["candidates"] if c["kernel"] == "plain")
+    other_name = f"plain:kp{other['kp']}:nw{other['warps']}"
     tried = set()
-    for c in desc["stages"][1]["candidates"]:
+    for c in desc["stages"][stage]["candidates"]:
         if c["kernel"] != "tma":
             continue
         name = f"tma:kp{c['kp']}:nw{c['warps']}:{_FORM_TAG[c['form']]}"
-        cache = tmp_path / f"{name.replace(':', '_')}.txt"
-        cache.write_text(f"{key} {name}\n")
+        cache = tmp_path / f"{stage}_{name.replace(':', '_')}.txt"
+        cache.write_text(f"{keys[stage]} {name}\n{keys[1 - stage]} {other_name}\n")
         monkeypatch.setenv("DENSIFY_TUNE_CACHE", str(cache))
-        got, d = _run(views, torch, autotune=1)
-        ch = d["stages"][1]["chosen"]
+        got, d = _run(views, torch, debug=True, autotune=1)
+        assert d["stages"][1 - stage]["chosen"]["kernel"] == "plain"
+        ch = d["stages"][stage]["chosen"]
         assert (ch["kp"], ch["warps"], ch["form"]) == (c["kp"], c["warps"], c["form"])
         for a, b in zip(got, plain):
-            for k in ("valid", "rgba"):
+            for k in ("valid", "coarse_valid", "rgba"):
                 assert np.array_equal(a[k], b[k]), (name, k)
             np.testing.assert_allclose(a["depth"], b["depth"], rtol=3e-5, err_msg=name)
+            np.testing.assert_allclose(a["coarse"], b["coarse"], rtol=3e-5, err_msg=name)
         tried.add(c["form"])
-    assert "fp32_expanded_pairs" in tried
+    assert "fp32_expanded" in tried
