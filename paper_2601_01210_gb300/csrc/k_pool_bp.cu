@@ -239,6 +239,17 @@ __global__ void __launch_bounds__(kThreads, 4) bp_write_kernel(const BatchDev *_
         uint32_t m[4];
         float4 zq[4];
         uint32_t cw[4][3];
+        int ys[4], xs[4];   // row and column of each step's first pixel (128 pixels apart)
+        row_col(wbase + lane * 4, W, iw, ys[0], xs[0]);
+#pragma unroll
+        for (int it = 1; it < 4; ++it) {
+            ys[it] = ys[it - 1];
+            xs[it] = xs[it - 1] + 128;
+            while (xs[it] >= W) {
+                xs[it] -= W;
+                ++ys[it];
+            }
+        }
 #pragma unroll
         for (int it = 0; it < 4; ++it) {
             const int64_t p0 = wbase + it * 128 + lane * 4;
@@ -247,9 +258,8 @@ __global__ void __launch_bounds__(kThreads, 4) bp_write_kernel(const BatchDev *_
             cw[it][0] = cw[it][1] = cw[it][2] = 0u;
             if (vdepth && rows4 && p0 + 4 <= n) {
                 zq[it] = *reinterpret_cast<const float4 *>(F.out_depth + p0);
-                int y, x;
-                row_col(p0, W, iw, y, x);
-                const uint32_t *cp = reinterpret_cast<const uint32_t *>(F.rgb + (int64_t)y * F.rgb_pitch + 3 * x);
+                const uint32_t *cp =
+                    reinterpret_cast<const uint32_t *>(F.rgb + (int64_t)ys[it] * F.rgb_pitch + 3 * xs[it]);
                 cw[it][0] = cp[0];
                 cw[it][1] = cp[1];
                 cw[it][2] = cp[2];
@@ -270,24 +280,23 @@ __global__ void __launch_bounds__(kThreads, 4) bp_write_kernel(const BatchDev *_
                 const int64_t p0 = wbase + it * 128 + lane * 4;
                 uint32_t j = incl - cnt;
                 if (vdepth && rows4 && p0 + 4 <= n) {
-                    // the 4 pixels share a row; colour bytes were loaded as 3 words
+                    // the 4 pixels share a row; colour bytes were loaded as 3 words. The point is
+                    // Z (R (u, v, 1)) + t with the ray (u, v) = ((x + 1/2 - cx) / fx, (y + 1/2 - cy) / fy),
+                    // so each pixel takes 3 fma for R's ray column and 3 for the point.
                     const float z[4] = {zq[it].x, zq[it].y, zq[it].z, zq[it].w};
                     const uint32_t w0 = cw[it][0], w1 = cw[it][1], w2 = cw[it][2];
                     const uint32_t col[4] = {w0 & 0xFFFFFFu, (w0 >> 24) | ((w1 & 0xFFFFu) << 8),
                                              (w1 >> 16) | ((w2 & 0xFFu) << 16), w2 >> 8};
-                    int y, x0;
-                    row_col(p0, W, iw, y, x0);
-                    const float Y = ((float)y + 0.5f - F.cy) * ify;
+                    const float v = ((float)ys[it] + 0.5f - F.cy) * ify;
+                    const float u0 = ((float)xs[it] + 0.5f - F.cx) * ifx;
+                    const float b0 = fmaf(r01, v, r02), b1 = fmaf(r11, v, r12), b2 = fmaf(r21, v, r22);
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         if (m[it] >> k & 1u) {
                             const float Z = z[k];
-                            const float X = ((float)(x0 + k) + 0.5f - F.cx) * Z * ifx;
-                            const float Yz = Y * Z;
-                            st[j++] = make_float4(fmaf(r00, X, fmaf(r01, Yz, fmaf(r02, Z, t0))),
-                                                  fmaf(r10, X, fmaf(r11, Yz, fmaf(r12, Z, t1))),
-                                                  fmaf(r20, X, fmaf(r21, Yz, fmaf(r22, Z, t2))),
-                                                  __uint_as_float(col[k] | 0xFF000000u));
+                            const float u = fmaf((float)k, ifx, u0);
+                            st[j++] = make_float4(fmaf(fmaf(r00, u, b0), Z, t0), fmaf(fmaf(r10, u, b1), Z, t1),
+                                                  fmaf(fmaf(r20, u, b2), Z, t2), __uint_as_float(col[k] | 0xFF000000u));
                         }
                     }
                 } else {
@@ -312,10 +321,10 @@ __global__ void __launch_bounds__(kThreads, 4) bp_write_kernel(const BatchDev *_
                 }
             }
             __syncwarp();
-            for (uint32_t i = lane; i < tot; i += 32) {
-                const int64_t pos = off + i;
-                if (pos < F.points_cap) F.out_points[pos] = st[i];
-            }
+            // the part's points from off on, as far as the caller's capacity goes
+            const uint32_t fit = (uint32_t)max((int64_t)0, min((int64_t)tot, F.points_cap - off));
+            float4 *dst = F.out_points + off;
+            for (uint32_t i = lane; i < fit; i += 32) dst[i] = st[i];
             __syncwarp();
             off += tot;
         }
