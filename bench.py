@@ -369,6 +369,31 @@ def valid_taps_stage1(cnt_pos, r=4):
     return int(correlate(cnt_pos.astype(np.float64), np.ones((2 * r + 1, 2 * r + 1)), mode="constant").sum())
 
 
+def step_work(b, view, pool=3):
+    """Algorithmic work of every kernel of the path for one frame (probe buffers with debug outputs):
+    bytes each HBM-bound kernel must move at least, observed taps of both filters."""
+    import numpy as np
+    W, H = b.W, b.H
+    Wc, Hc = -(-W // pool), -(-H // pool)
+    z = b.zbuf.cpu().numpy().view(np.uint32)
+    obs = z != 0x7F800000
+    zp = np.zeros((Hc * pool, Wc * pool), bool)
+    zp[:H, :W] = obs
+    cnt_pos = zp.reshape(Hc, pool, Wc, pool).any(axis=(1, 3))
+    npts = sum(s.xyz.shape[0] for s in view.scans)
+    nout = b.n_points()
+    return {
+        "prep_compose_clear": 4 * W * H,                      # z-buffer clear
+        "project_zbuf": 12 * npts + 4 * int(obs.sum()),       # point reads + one depth word per observed pixel
+        "pool3": 7 * W * H + 20 * Wc * Hc,                    # z-buffer + RGB in, guide + sums out
+        "tile_mark1": 4 * Wc * Hc,                            # one observation word per pooled pixel
+        "bp_count": W * H,                                    # validity bytes
+        "bp_write": 8 * W * H + 16 * nout,                    # validity, depth, colour in; points out
+        "taps1": valid_taps_stage1(cnt_pos),
+        "taps2": valid_taps_stage2(b.coarse_valid.cpu().numpy(), W, H),
+    }
+
+
 def host_link_gbps(dev, mb=256, reps=5):
     """Pinned host <-> device copy rates (GB/s), CUDA events."""
     import torch
@@ -450,6 +475,8 @@ def ours_arm(a, rank, world, local_rank):
         torch.cuda.synchronize()
         taps_view = [valid_taps_stage2(b.coarse_valid.cpu().numpy(), b.W, b.H) for b in probe]
         taps2 = sum(taps_view[i % len(views)] for i in range(B))
+        work_view = [step_work(b, views[i]) for i, b in enumerate(probe)]
+        work = {k: sum(work_view[i % len(views)][k] for i in range(B)) for k in work_view[0]}
         del probe
         d.reset_kernel_times()
         if world > 1:
@@ -572,6 +599,23 @@ def ours_arm(a, rank, world, local_rank):
     achieved = taps2 / (avg_us * 1e-6) / 1e9 if avg_us > 0 else 0.0
     ktable = {k: {"total_us": round(v[0], 2), "launches": v[1], "avg_us": round(v[0] / max(1, v[1]), 3)}
               for k, v in ktable_times.items()}
+    # each kernel's roofline time for the step's work (HBM-bound kernels at the measured copy rate,
+    # the filters at the ALU peak of their form), against its measured time; their sum is the path's roof
+    hbm = peaks.get("hbm_gbs", 6758.5) * 1e9
+    form1 = kernel_choice["stages"][0]["chosen"].get("form", "fp32_expanded")
+    alu = lambda form: sms * 128 / TAP_INSTR.get(form, 6.0) * sm_max * 1e6   # taps per second
+    roof_us = {k: work[k] / hbm * 1e6 for k in ("prep_compose_clear", "project_zbuf", "pool3", "tile_mark1",
+                                                "bp_count", "bp_write")}
+    roof_us["jbf_stage1"] = work["taps1"] / alu(form1) * 1e6
+    roof_us["jbf_stage2"] = work["taps2"] / alu(form2) * 1e6
+    kroof = {k: {"roof_us": round(r, 2), "measured_us": ktable[k]["avg_us"],
+                 "frac": round(r / ktable[k]["avg_us"], 3) if ktable.get(k, {}).get("avg_us") else None}
+             for k, r in roof_us.items() if k in ktable}
+    ideal = sum(v["roof_us"] for v in kroof.values())
+    path_roof = {"ideal_us_per_step": round(ideal, 2), "measured_us_per_step": round(1000.0 * total_ms / a.steps, 2),
+                 "frac": round(ideal / (1000.0 * total_ms / a.steps), 3),
+                 "basis": "sum over the path's kernels of algorithmic work / peak (HBM: measured copy rate; "
+                          "filters: ALU issue peak of their form)", "kernels": kroof}
     cpu = None
     if not a.no_cpu_baseline:
         rate, dt = cpu_oracle_rate(views, a.cpu_frames, a.cpu_procs)
@@ -598,6 +642,7 @@ def ours_arm(a, rank, world, local_rank):
                                    f"{sm_max:.0f} MHz",
                      "taps_per_launch": taps2, "avg_launch_us": avg_us},
         "kernels": ktable,
+        "path_roofline": path_roof,
         "kernels_how": ("per-kernel CUDA events in a separate pass of 10 steps; the timed steps carry events "
                         "around the full-resolution filter only" if a.kernel_timing != 1 else
                         "per-kernel CUDA events inside the timed steps"),
