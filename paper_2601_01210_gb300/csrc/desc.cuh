@@ -101,9 +101,12 @@ struct BatchDev {
     int32_t mk_pre[kMaxBatch + 1];                 // 32-pixel row segments of the observation grid
     // TMA filters (index 0: first or only filter, 1: second): one flag per tile of the stage
     // (in the order its prefix array counts them), nonzero when some observation reaches the
-    // tile; zeroed on the stream and set by tile_mark_kernel before every filter launch
+    // tile; zeroed by the batch's first kernel and set by the kernel in front of the filter (the
+    // pooling kernel for the first of two stages, the first filter for the second, tile_mark_kernel
+    // for a single stage)
     int32_t *tl_flags[2];
-    int32_t tl_next[2];                            // the filter's tile counter (reset before each filter launch)
+    int32_t tl_next[2];                            // the filter's tile counter (reset by the prep kernel; by the
+                                                   // mark kernel or a memset before a filter launched on its own)
     int32_t tl_tw[2];                              // tile width of a TMA filter stage (32 or 64)
     int32_t tl_th[2];                              // tile height of a TMA filter stage (0: no tile flags)
     int32_t tl_r[2];                               // its radius
@@ -131,20 +134,20 @@ struct StageArgs {
     float ex_sy[2 * kMaxR + 1];
 };
 
-// Flag the filter tiles (tw x th output pixels, row-major per frame) that an observation range
-// reaches: columns [ox0, ox1] and rows [oy0, oy1] of a grid f times coarser than the gw x gh
-// output grid, grown by the radius r. The lanes of one warp share the stores, plain stores of
-// the same value (no read first: the caller does not wait on a load).
+// Flag the filter tiles (tw x th output pixels, tw a power of two, row-major per frame) that an
+// observation range reaches: columns [ox0, ox1] and rows [oy0, oy1] of a grid f times coarser
+// than the gw x gh output grid, grown by the radius r. The lanes of one warp share the stores,
+// plain stores of the same value (no read first: the caller does not wait on a load).
 __device__ __forceinline__ void mark_reach(int32_t *flags, int tw, int th, int r, int f, int gw, int gh, int ox0,
                                            int ox1, int oy0, int oy1, int lane) {
     const int xlo = max(0, f * ox0 - r), xhi = min(gw - 1, f * ox1 + f - 1 + r);
     const int ylo = max(0, f * oy0 - r), yhi = min(gh - 1, f * oy1 + f - 1 + r);
     if (xlo > xhi || ylo > yhi) return;
-    const int tiles_x = (gw + tw - 1) / tw;
-    const int tx0 = xlo / tw, ntx = xhi / tw - tx0 + 1, ty0 = ylo / th, n = ntx * (yhi / th - ty0 + 1);
-    for (int j = lane; j < n; j += 32) {
-        flags[(ty0 + j / ntx) * tiles_x + tx0 + j % ntx] = 1;
-    }
+    const int sw = __ffs(tw) - 1;   // tile widths are powers of two
+    const int tiles_x = (gw + tw - 1) >> sw;
+    const int tx0 = xlo >> sw, tx1 = xhi >> sw, ty0 = ylo / th, ty1 = yhi / th;
+    for (int ty = ty0; ty <= ty1; ++ty)
+        for (int tx = tx0 + lane; tx <= tx1; tx += 32) flags[ty * tiles_x + tx] = 1;
 }
 
 // Largest i with pre[i] <= item (pre is non-decreasing, pre[0] = 0).

@@ -38,9 +38,10 @@ __device__ __forceinline__ double compose_entry(const double *c2w, const double 
 __global__ void __launch_bounds__(kThreads) prep_kernel(BatchDev *__restrict__ B) {
     const int nf = B->n_frames;
     const int total = B->zb_pre[nf];
-    // the TMA filters' tile flags (both stages, contiguous) start the batch cleared; the producers
-    // (pooling, first filter) and the mark kernel set them
+    // the TMA filters' tile flags (both stages, contiguous) and tile counters start the batch
+    // cleared; the producers (pooling, first filter) and the mark kernel set the flags
     if (B->tl_flags[0]) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) B->tl_next[0] = B->tl_next[1] = 0;   // the filters' tile counters
         const int nflags = B->t1_pre[nf] + B->t2_pre[nf];
         for (int i = blockIdx.x * kThreads + threadIdx.x; i < nflags; i += gridDim.x * kThreads) B->tl_flags[0][i] = 0;
     }

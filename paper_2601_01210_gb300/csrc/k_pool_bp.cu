@@ -31,9 +31,74 @@ __device__ __forceinline__ void pool_store(const FrameDev &F, int I, int J, floa
     F.cssum[o] = s;
 }
 
+// Pooled pixel (I, J): its guide and sums; cnt_out = its observation count.
+__device__ __forceinline__ void pool_one(const FrameDev &F, int I, int J, int f, float &cnt_out) {
+    const int x0 = I * f, y0 = J * f;
+    const int o = (9 * I) & 3;                            // first colour byte inside its word
+    const int64_t wb = 9 * (int64_t)I - o;                // byte offset of the first covering word
+    if (f == 3 && x0 + 3 <= F.W && y0 + 3 <= F.H && wb + 12 <= 3 * (int64_t)F.W && pool_words_ok(F)) {
+        uint32_t z[3][3], c[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+            const uint32_t *zr = F.zbuf + (int64_t)(y0 + r) * F.zpitch + x0;
+            const uint32_t *cw = reinterpret_cast<const uint32_t *>(F.rgb + (int64_t)(y0 + r) * F.rgb_pitch + wb);
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                z[r][j] = zr[j];
+                c[r][j] = cw[j];
+            }
+        }
+        float s = 0.0f, cnt = 0.0f;
+        uint32_t rs = 0u, gs = 0u, bs = 0u;
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+                if (z[r][j] != kEmpty) {
+                    s = __fadd_rn(s, __uint_as_float(z[r][j]));
+                    cnt += 1.0f;
+                }
+            }
+            // bytes c0 .. c8 of the row (r, g, b of 3 pixels) into a0 = c0..c3, a1 = c4..c7, a2 = c8..
+            const uint32_t a0 = __funnelshift_r(c[r][0], c[r][1], 8 * o);
+            const uint32_t a1 = __funnelshift_r(c[r][1], c[r][2], 8 * o);
+            const uint32_t a2 = c[r][2] >> (8 * o);
+            rs = __dp4a(__byte_perm(a0, a1, 0x0630), 0x00010101u, rs);   // c0 + c3 + c6
+            gs = __dp4a(__byte_perm(a0, a1, 0x0741), 0x00010101u, gs);   // c1 + c4 + c7
+            bs = __dp4a(__byte_perm(a0, a1, 0x0052), 0x00000101u, bs) + (a2 & 0xFFu);   // c2 + c5 + c8
+        }
+        pool_store(F, I, J, (float)rs, (float)gs, (float)bs, cnt, s, 9.0f);
+        cnt_out = cnt;
+    } else {
+        const int x1 = min(x0 + f, F.W), y1 = min(y0 + f, F.H);
+        float s = 0.0f, cnt = 0.0f, r = 0.0f, g = 0.0f, b = 0.0f;
+        for (int y = y0; y < y1; ++y) {
+            const uint32_t *zr = F.zbuf + (int64_t)y * F.zpitch;
+            const uint8_t *cr = F.rgb + (int64_t)y * F.rgb_pitch;
+            for (int x = x0; x < x1; ++x) {
+                const uint32_t zz = zr[x];
+                if (zz != kEmpty) {
+                    s = __fadd_rn(s, __uint_as_float(zz));
+                    cnt += 1.0f;
+                }
+                r += (float)cr[3 * x];
+                g += (float)cr[3 * x + 1];
+                b += (float)cr[3 * x + 2];
+            }
+        }
+        pool_store(F, I, J, r, g, b, cnt, s, (float)((x1 - x0) * (y1 - y0)));
+        cnt_out = cnt;
+    }
+}
+
+// With a TMA first-stage filter (tl_th[0] > 0) every warp also flags the first-stage tiles that
+// its observed pooled pixels reach (one ballot; a row segment of 32 pooled pixels grown by the
+// radius spans at most two tiles across and two down), so no mark kernel runs before that filter.
 __global__ void __launch_bounds__(kThreads) pool_kernel(const BatchDev *__restrict__ B, int f) {
     const int nf = B->n_frames;
     const int total = B->pool_pre[nf];
+    const int lane = threadIdx.x & 31;
+    const bool marks = B->tl_th[0] > 0;
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int fi = find_segment(B->pool_pre, nf, item);
         const FrameDev &F = B->f[fi];
@@ -41,63 +106,18 @@ __global__ void __launch_bounds__(kThreads) pool_kernel(const BatchDev *__restri
         const int t = item - B->pool_pre[fi];
         const int J = t / segs;
         const int I = (t - J * segs) * kPoolPerChunk + threadIdx.x;
-        if (I >= F.Wc) continue;
-        const int x0 = I * f, y0 = J * f;
-        const int o = (9 * I) & 3;                            // first colour byte inside its word
-        const int64_t wb = 9 * (int64_t)I - o;                // byte offset of the first covering word
-        if (f == 3 && x0 + 3 <= F.W && y0 + 3 <= F.H && wb + 12 <= 3 * (int64_t)F.W && pool_words_ok(F)) {
-            uint32_t z[3][3], c[3][3];
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-                const uint32_t *zr = F.zbuf + (int64_t)(y0 + r) * F.zpitch + x0;
-                const uint32_t *cw = reinterpret_cast<const uint32_t *>(F.rgb + (int64_t)(y0 + r) * F.rgb_pitch + wb);
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    z[r][j] = zr[j];
-                    c[r][j] = cw[j];
-                }
-            }
-            float s = 0.0f, cnt = 0.0f;
-            uint32_t rs = 0u, gs = 0u, bs = 0u;
-#pragma unroll
-            for (int r = 0; r < 3; ++r) {
-#pragma unroll
-                for (int j = 0; j < 3; ++j) {
-                    if (z[r][j] != kEmpty) {
-                        s = __fadd_rn(s, __uint_as_float(z[r][j]));
-                        cnt += 1.0f;
-                    }
-                }
-                // bytes c0 .. c8 of the row (r, g, b of 3 pixels) into a0 = c0..c3, a1 = c4..c7, a2 = c8..
-                const uint32_t a0 = __funnelshift_r(c[r][0], c[r][1], 8 * o);
-                const uint32_t a1 = __funnelshift_r(c[r][1], c[r][2], 8 * o);
-                const uint32_t a2 = c[r][2] >> (8 * o);
-                rs = __dp4a(__byte_perm(a0, a1, 0x0630), 0x00010101u, rs);   // c0 + c3 + c6
-                gs = __dp4a(__byte_perm(a0, a1, 0x0741), 0x00010101u, gs);   // c1 + c4 + c7
-                bs = __dp4a(__byte_perm(a0, a1, 0x0052), 0x00000101u, bs) + (a2 & 0xFFu);   // c2 + c5 + c8
-            }
-            pool_store(F, I, J, (float)rs, (float)gs, (float)bs, cnt, s, 9.0f);
-        } else {
-            const int x1 = min(x0 + f, F.W), y1 = min(y0 + f, F.H);
-            float s = 0.0f, cnt = 0.0f, r = 0.0f, g = 0.0f, b = 0.0f;
-            for (int y = y0; y < y1; ++y) {
-                const uint32_t *zr = F.zbuf + (int64_t)y * F.zpitch;
-                const uint8_t *cr = F.rgb + (int64_t)y * F.rgb_pitch;
-                for (int x = x0; x < x1; ++x) {
-                    const uint32_t zz = zr[x];
-                    if (zz != kEmpty) {
-                        s = __fadd_rn(s, __uint_as_float(zz));
-                        cnt += 1.0f;
-                    }
-                    r += (float)cr[3 * x];
-                    g += (float)cr[3 * x + 1];
-                    b += (float)cr[3 * x + 2];
-                }
-            }
-            pool_store(F, I, J, r, g, b, cnt, s, (float)((x1 - x0) * (y1 - y0)));
+        float cnt = 0.0f;
+        if (I < F.Wc) pool_one(F, I, J, f, cnt);
+        if (marks) {
+            const uint32_t m = __ballot_sync(0xffffffffu, cnt > 0.0f);
+            const int I0 = I - lane;
+            if (m)
+                mark_reach(B->tl_flags[0] + B->t1_pre[fi], B->tl_tw[0], B->tl_th[0], B->tl_r[0], 1, F.Wc, F.Hc,
+                           I0 + __ffs(m) - 1, I0 + 31 - __clz(m), J, J, lane);
         }
     }
 }
+
 
 cudaError_t launch_pool(const BatchDev *b, int pool, int grid, cudaStream_t s) {
     pool_kernel<<<grid, kThreads, 0, s>>>(b, pool);

@@ -737,8 +737,9 @@ densify_status prepare_tile_lists(densify_ctx *c, Slot &sl) {
     }
     b.tl_flags[0] = sl.d_tiles;
     b.tl_flags[1] = sl.d_tiles + b.t1_pre[n];
-    // tile geometry of the TMA stages: the second stage's tiles are flagged by the first
-    // filter's epilogue (two-stage path), the first (or only) stage's by the mark kernel
+    // tile geometry of the TMA stages: on the two-stage path the pooling kernel flags the first
+    // stage's tiles and the first filter's epilogue the second's; a single stage's are flagged by
+    // the mark kernel
     for (int i = 0; i < 2; ++i) {
         const bool on = i < c->p.num_stages && c->sel[i].tma;
         b.tl_tw[i] = on ? c->sel[i].tile_w : 32;
@@ -748,16 +749,21 @@ densify_status prepare_tile_lists(densify_ctx *c, Slot &sl) {
     return DENSIFY_OK;
 }
 
-// CUDA kernels of one filter launch (a TMA first or only stage: tile marks + filter).
-int filter_kernels(const densify_ctx *c, int i) { return c->sel[i].tma && i == 0 ? 2 : 1; }
+// The tiles of a TMA filter are flagged by the kernel in front of it: the pooling kernel for the
+// first of two stages, the first filter for the second; a single stage has a mark kernel of its own.
+bool tiles_marked_by_mark_kernel(const densify_ctx *c, int i) { return c->sel[i].tma && c->p.num_stages == 1; }
 
-// In front of a TMA filter: the tile mark kernel, which also resets the tile counter (first or
-// only stage), or the counter reset alone (second stage, whose tiles the first filter flags).
-// Nothing for the plain kernels.
+// CUDA kernels of one filter launch (a single TMA stage: tile marks + filter).
+int filter_kernels(const densify_ctx *c, int i) { return tiles_marked_by_mark_kernel(c, i) ? 2 : 1; }
+
+// In front of a TMA filter launched on its own (the autotuner's trials): the tile mark kernel,
+// which also resets the tile counter (single stage), or the counter reset alone (two-stage path,
+// whose batches reset both counters in the prep kernel). Nothing for the plain kernels.
 cudaError_t launch_filter_scan(densify_ctx *c, int i, const BatchDev *b, cudaStream_t s) {
     const FilterSel &f = c->sel[i];
     if (!f.tma) return cudaSuccess;
-    if (i == 1) return cudaMemsetAsync(const_cast<int32_t *>(&b->tl_next[i]), 0, sizeof(int32_t), s);
+    if (!tiles_marked_by_mark_kernel(c, i))
+        return cudaMemsetAsync(const_cast<int32_t *>(&b->tl_next[i]), 0, sizeof(int32_t), s);
     return launch_tile_mark(f.src, b, i, f.tile_h, f.radius, c->sms * 8, s);
 }
 
@@ -851,15 +857,12 @@ densify_status issue_kernels(densify_ctx *c, Slot &sl, cudaStream_t s, bool reco
         CU(mark(K_OCCLUSION), "event");
     }
     if (nst == 2) {
+        // the prep kernel reset both tile counters; pooling flags the first filter's tiles, the
+        // first filter the second's
         CU(launch_pool(b, c->p.pool, c->grid[K_POOL], s), "pool launch");
         CU(mark(K_POOL), "event");
-        if (c->sel[0].tma) {
-            CU(launch_filter_scan(c, 0, b, s), "stage-1 tile mark launch");
-            CU(mark(K_MARK1), "event");
-        }
         CU(launch_filter_kernel(c, 0, b, s), "stage-1 filter launch");
         CU(mark(K_JBF1), "event");
-        CU(launch_filter_scan(c, 1, b, s), "stage-2 tile counter reset");
         CU(start_last(), "event");
         CU(launch_filter_kernel(c, 1, b, s), "stage-2 filter launch");
         CU(mark(K_JBF2), "event");

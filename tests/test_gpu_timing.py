@@ -29,13 +29,12 @@ def _run(timing, batches=3):
 def test_timing_modes_and_launch_count():
     t1, n1, desc = _run(1)
     tma = [s["chosen"]["kernel"] == "tma" for s in desc["stages"]]
-    # prep, project, pool, (tile marks +) the first filter, the second filter (its tiles are
-    # flagged by the first filter), compaction count + scan + write
-    per_batch = 3 + (2 if tma[0] else 1) + 1 + 3
+    # prep, project, pool (which flags the first filter's tiles), the first filter, the second
+    # filter (its tiles are flagged by the first filter), compaction count + scan + write
+    assert tma[0]
+    per_batch = 3 + 1 + 1 + 3
     assert n1 == 3 * per_batch
     steps = {"prep_compose_clear", "project_zbuf", "pool3", "jbf_stage1", "jbf_stage2", "bp_count", "bp_write"}
-    if tma[0]:
-        steps.add("tile_mark1")
     assert set(t1) == steps
     assert all(n == 3 and us > 0.0 for us, n in t1.values())
     t2, n2, _ = _run(2)
