@@ -22,6 +22,7 @@ namespace dz {
     X(SRC_COARSE, 4, 2, FORM_EXP, 8)     \
     X(SRC_COARSE, 4, 2, FORM_EXP, 4)     \
     X(SRC_COARSE, 2, 4, FORM_EXP, 8)     \
+    X(SRC_ZBUF, 2, 4, FORM_EXP_PAIRS, 4) \
     X(SRC_ZBUF, 2, 8, FORM_EXP, 8)       \
     X(SRC_ZBUF, 4, 4, FORM_EXP, 8)       \
     X(SRC_ZBUF, 7, 4, FORM_EXP, 8)
