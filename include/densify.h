@@ -134,7 +134,9 @@ typedef struct densify_stage {
  *                 centred at 128; same sums, different rounding, within the
  *                 FP32 tolerance) where log2(e) / (2 sigma_c^2) * 3 * 128^2 +
  *                 log2(e) / (2 sigma_p^2) * 2 r^2 <= 100, else the difference
- *                 form. 1: the plain kernels everywhere (difference form,
+ *                 form; at radius 2 of a full-resolution stage also on pairs of
+ *                 output columns in two-lane FP32 instructions (same rounding
+ *                 as the scalar expanded form). 1: the plain kernels everywhere (difference form,
  *                 for comparison). 2: the TMA kernels in the difference form
  *                 only (the same bits as 1).
  *   autotune      1: on the first batch, time every kernel that can run each

@@ -163,7 +163,7 @@ __device__ __forceinline__ int find_segment(const int32_t *pre, int n, int item)
 // Kernel launchers. Grids are persistent: a multiple of the SM count.
 enum KernelId {
     K_PREP = 0, K_MOTION, K_DILATE, K_ERODE, K_PROJECT, K_OCCLUSION, K_POOL, K_JBF1, K_JBF2, K_CONTOUR,
-    K_BP_COUNT, K_BP_WRITE, K_MARK1, K_MARK2, K_COUNT
+    K_BP_COUNT, K_BP_WRITE, K_MARK1, K_COUNT
 };
 
 // Preprocessing / post-filtering (k_prepost.cu).

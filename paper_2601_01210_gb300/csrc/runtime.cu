@@ -44,7 +44,7 @@ namespace {
 const char *const kKernelNames[K_COUNT] = {"prep_compose_clear", "motion_mask", "motion_dilate", "motion_erode",
                                            "project_zbuf",       "occlusion",   "pool3",         "jbf_stage1",
                                            "jbf_stage2",         "contour",     "bp_count",      "bp_write",
-                                           "tile_mark1",         "tile_mark2"};
+                                           "tile_mark1"};
 
 constexpr uint64_t kAlign = 256;
 uint64_t align_up(uint64_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
