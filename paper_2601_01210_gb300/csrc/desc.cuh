@@ -145,7 +145,10 @@ __device__ __forceinline__ void mark_reach(int32_t *flags, int tw, int th, int r
     if (xlo > xhi || ylo > yhi) return;
     const int sw = __ffs(tw) - 1;   // tile widths are powers of two
     const int tiles_x = (gw + tw - 1) >> sw;
-    const int tx0 = xlo >> sw, tx1 = xhi >> sw, ty0 = ylo / th, ty1 = yhi / th;
+    const int tx0 = xlo >> sw, tx1 = xhi >> sw;
+    const int sh = __ffs(th) - 1;   // tile heights mostly are
+    const bool pow2 = th == 1 << sh;
+    const int ty0 = pow2 ? ylo >> sh : ylo / th, ty1 = pow2 ? yhi >> sh : yhi / th;
     for (int ty = ty0; ty <= ty1; ++ty)
         for (int tx = tx0 + lane; tx <= tx1; tx += 32) flags[ty * tiles_x + tx] = 1;
 }

@@ -148,28 +148,39 @@ __device__ __forceinline__ uint32_t valid_bits4(const uint8_t *v, int64_t p, int
     return m;
 }
 
-// One count per warp: valid pixels of its 512-pixel part of the chunk (16 per lane).
+// Valid pixels of 512-pixel parts: a warp takes kCountParts consecutive parts of a chunk, 16
+// pixels of each per lane, with all its loads in flight before any is used.
+constexpr int kCountParts = 4;
 __global__ void __launch_bounds__(kThreads) bp_count_kernel(const BatchDev *__restrict__ B) {
+    constexpr int kGroups = kBpWarps / kCountParts;   // part groups of a chunk
     const int nf = B->n_frames;
-    const int total = B->bp_pre[nf] * kBpWarps;
+    const int total = B->bp_pre[nf] * kGroups;
     const int lane = threadIdx.x & 31;
     for (int wi = blockIdx.x * kBpWarps + (threadIdx.x >> 5); wi < total; wi += gridDim.x * kBpWarps) {
-        const int item = wi / kBpWarps;
+        const int item = wi / kGroups;
         const int fi = find_segment(B->bp_pre, nf, item);
         const FrameDev &F = B->f[fi];
-        const int sub = (item - B->bp_pre[fi]) * kBpWarps + wi % kBpWarps;   // the frame's part index
+        const int sub0 = (item - B->bp_pre[fi]) * kBpWarps + (wi % kGroups) * kCountParts;   // the frame's first part
         const int64_t n = (int64_t)F.W * F.H;
-        const int64_t p = (int64_t)sub * kBpPart + lane * 16;
-        uint32_t cnt = 0;
-        if ((((uintptr_t)F.out_valid) & 15u) == 0 && p + 16 <= n) {
-            const uint4 w = *reinterpret_cast<const uint4 *>(F.out_valid + p);   // bytes are 0 or 1
-            cnt = __popc(w.x) + __popc(w.y) + __popc(w.z) + __popc(w.w);
-        } else {
-            for (int k = 0; k < 16; ++k) cnt += (p + k < n && F.out_valid[p + k]) ? 1u : 0u;
+        const bool vec = (((uintptr_t)F.out_valid) & 15u) == 0;
+        uint4 w[kCountParts];
+#pragma unroll
+        for (int j = 0; j < kCountParts; ++j) {
+            const int64_t p = (int64_t)(sub0 + j) * kBpPart + lane * 16;
+            w[j] = make_uint4(0u, 0u, 0u, 0u);
+            if (vec && p + 16 <= n) w[j] = *reinterpret_cast<const uint4 *>(F.out_valid + p);   // bytes are 0 or 1
         }
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
-        if (lane == 0) F.chunk_cnt[sub] = cnt;
+        for (int j = 0; j < kCountParts; ++j) {
+            const int64_t p = (int64_t)(sub0 + j) * kBpPart + lane * 16;
+            uint32_t cnt = __popc(w[j].x) + __popc(w[j].y) + __popc(w[j].z) + __popc(w[j].w);
+            if (!(vec && p + 16 <= n)) {
+                cnt = 0;
+                for (int k = 0; k < 16; ++k) cnt += (p + k < n && F.out_valid[p + k]) ? 1u : 0u;
+            }
+            cnt = __reduce_add_sync(0xffffffffu, cnt);
+            if (lane == 0) F.chunk_cnt[sub0 + j] = cnt;
+        }
     }
 }
 
