@@ -133,7 +133,9 @@ def test_ragged_sizes(torch_cuda, res, variant):
         pose = scene.make_lidar_pose(cam, (0.1 * s, 0.05, 0.02), 2.0 * s)
         scans.append(scene.Scan(scene.lidar_sweep(sc, pose, 48, 700 + s, rng), pose))
     v = scene.View(cam, rgb, scans, gt)
-    for stages, st in ((2, PAPER_STAGES), (1, ((3, 2.0, 15.0),)), (1, ((4, 3.0, 20.0),)), (1, ((2, 1.5, 10.0),))):
+    # (the single stage at r = 2, sigma_c = 20 runs the column-paired kernel by default)
+    for stages, st in ((2, PAPER_STAGES), (1, ((3, 2.0, 15.0),)), (1, ((4, 3.0, 20.0),)), (1, ((2, 1.5, 10.0),)),
+                       (1, ((2, 5.0, 20.0),))):
         g = run_gpu([v], stages, st, torch_cuda, kernel_variant=variant)[0]
         o = run_oracle(v, stages, st)
         compare(g, o, stages, f"{W}x{H} {stages}-stage")
