@@ -24,6 +24,8 @@
 // (' for the first staged column of the slot, '' for the second).
 #pragma once
 
+#include <type_traits>
+
 #include "jbf_core.cuh"
 #include "tma_common.cuh"
 
@@ -56,9 +58,11 @@ __device__ __forceinline__ void pair_tile(const FrameDev &F, const StageArgs &a,
     const float2 *craw = reinterpret_cast<const float2 *>(rawb);
     const uint32_t *zraw = reinterpret_cast<const uint32_t *>(rawb);
     auto rgb_at = [&](int sy, int sx) { return rgbraw + sy * G::RGB_BX + 3 * sx - 3 * R + G::RGB_LEAD; };
-    auto depth_of = [&](int sy, int sx, float &d) -> bool {
+    // a tile whose halo lies inside the image needs no bounds checks on its staged positions
+    const bool interior = x0 >= R && x0 + G::TW + R <= gw && y0 >= R && y0 + G::TH + R <= gh;
+    auto depth_of = [&](int sy, int sx, float &d, auto inside) -> bool {
         const int gx = x0 - R + sx, gy = y0 - R + sy;
-        if (gx < 0 || gx >= gw || gy < 0 || gy >= gh) return false;
+        if (!decltype(inside)::value && (gx < 0 || gx >= gw || gy < 0 || gy >= gh)) return false;
         if (SRC == SRC_UP) {
             const float2 c = craw[((int)((unsigned)gy / 3u) - cy0) * G::C_BX + ((int)((unsigned)gx / 3u) - cx0)];
             d = c.x;
@@ -74,24 +78,28 @@ __device__ __forceinline__ void pair_tile(const FrameDev &F, const StageArgs &a,
     uint32_t om0 = 0u, om1 = 0u;   // bit j: first / second column of slot j observed
     float d0[NCONV], d1[NCONV];
     uint32_t r0[NCONV], g0[NCONV], b0[NCONV], r1[NCONV], g1[NCONV], b1[NCONV];
+    auto load_slots = [&](auto inside) {
 #pragma unroll
-    for (int j = 0; j < NCONV; ++j) {
-        const int i = threadIdx.x + j * NT;
-        d0[j] = d1[j] = 0.0f;
-        r0[j] = g0[j] = b0[j] = r1[j] = g1[j] = b1[j] = 0u;
-        if (i < SH * SP) {
-            const int sy = i / SP, s = i - sy * SP;
-            float d = 0.0f;
-            if (depth_of(sy, s, d)) om0 |= 1u << j;
-            d0[j] = d;
-            d = 0.0f;
-            if (depth_of(sy, s + 32, d)) om1 |= 1u << j;
-            d1[j] = d;
-            const uint8_t *p = rgb_at(sy, s), *q = p + 96;
-            r0[j] = p[0]; g0[j] = p[1]; b0[j] = p[2];
-            r1[j] = q[0]; g1[j] = q[1]; b1[j] = q[2];
+        for (int j = 0; j < NCONV; ++j) {
+            const int i = threadIdx.x + j * NT;
+            d0[j] = d1[j] = 0.0f;
+            r0[j] = g0[j] = b0[j] = r1[j] = g1[j] = b1[j] = 0u;
+            if (i < SH * SP) {
+                const int sy = i / SP, s = i - sy * SP;
+                float d = 0.0f;
+                if (depth_of(sy, s, d, inside)) om0 |= 1u << j;
+                d0[j] = d;
+                d = 0.0f;
+                if (depth_of(sy, s + 32, d, inside)) om1 |= 1u << j;
+                d1[j] = d;
+                const uint8_t *p = rgb_at(sy, s), *q = p + 96;
+                r0[j] = p[0]; g0[j] = p[1]; b0[j] = p[2];
+                r1[j] = q[0]; g1[j] = q[1]; b1[j] = q[2];
+            }
         }
-    }
+    };
+    if (interior) load_slots(std::true_type{});
+    else load_slots(std::false_type{});
     // bytes b, b' as exact floats minus 128: 2^23 + b has b in its low mantissa bits
     auto bytes2 = [](uint32_t b, uint32_t b2) {
         return __fadd2_rn(f2(__uint_as_float(0x4B000000u | b), __uint_as_float(0x4B000000u | b2)),
@@ -192,11 +200,15 @@ __device__ __forceinline__ void pair_tile(const FrameDev &F, const StageArgs &a,
 
     // ---- outputs; a valid pixel whose weight sum is too small for the plain form (dominant
     // weight near the bottom of the FP32 range) is recomputed with shifted exponents
+    // the output pointers in registers: a store through them could alias the frame descriptor,
+    // which would make the compiler reload them after every store
+    float *const out_depth = F.flt_depth;
+    uint8_t *const out_valid = F.flt_valid;
     auto store = [&](int x, int y, float out, bool v) {
         if (x < gw && y < gh) {
             const int64_t o = (int64_t)y * gw + x;
-            F.flt_depth[o] = out;
-            F.flt_valid[o] = v;
+            out_depth[o] = out;
+            out_valid[o] = v;
         }
     };
     uint32_t slow = 0u;   // bit 2k + h: pixel (k, half h)
@@ -219,7 +231,7 @@ __device__ __forceinline__ void pair_tile(const FrameDev &F, const StageArgs &a,
             const uint8_t *p = rgb_at(sy, sx);
             const float dr = (float)p[0] - cr0, dg = (float)p[1] - cg0, db = (float)p[2] - cb0;
             wd = 0.0f;
-            const bool seen = depth_of(sy, sx, wd);
+            const bool seen = depth_of(sy, sx, wd, std::false_type{});
             const float n2 = fmaf(dr, dr, fmaf(dg, dg, db * db));
             const float s2 = (float)((dx - R) * (dx - R) + (dy - R) * (dy - R));
             arg = fmaf(n2, -a.kc, -s2 * a.kp);

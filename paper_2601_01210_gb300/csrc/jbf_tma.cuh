@@ -484,17 +484,23 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
             }
         }
         const int x = x0 + lane;
+        // the output pointers in registers: a store through them could alias the frame descriptor,
+        // which would make the compiler reload them after every store
+        float2 *const out_s1 = F.s1;
+        const int64_t cpitch = F.cpitch;
+        float *const out_coarse = F.out_coarse, *const out_depth = F.flt_depth;
+        uint8_t *const out_coarse_valid = F.out_coarse_valid, *const out_valid = F.flt_valid;
         auto store = [&](int k, float out, bool v) {
             const int y = y0 + rbase + k;
             if (x < gw && y < gh) {
                 const int64_t o = (int64_t)y * gw + x;
                 if (SRC == SRC_COARSE) {
-                    F.s1[(int64_t)y * F.cpitch + x] = make_float2(out, v ? 1.0f : 0.0f);
-                    if (F.out_coarse) F.out_coarse[o] = out;
-                    if (F.out_coarse_valid) F.out_coarse_valid[o] = v;
+                    out_s1[(int64_t)y * cpitch + x] = make_float2(out, v ? 1.0f : 0.0f);
+                    if (out_coarse) out_coarse[o] = out;
+                    if (out_coarse_valid) out_coarse_valid[o] = v;
                 } else {
-                    F.flt_depth[o] = out;
-                    F.flt_valid[o] = v;
+                    out_depth[o] = out;
+                    out_valid[o] = v;
                 }
             }
         };
