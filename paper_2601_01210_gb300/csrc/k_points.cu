@@ -76,20 +76,29 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(BatchDev *__restrict__ B
 // project: one work item = 1024 consecutive points of one (frame, scan);
 // each thread takes 4 points with 16-byte vector loads.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void project_one(const float (&M)[12], float x, float y, float z, const FrameDev &F,
-                                            uint32_t *zbuf, bool old_scan) {
+// The camera of a frame in registers: read once per work item (an atomic on the z-buffer could
+// alias the frame descriptor, so reading it per point would mean a reload after every atomic).
+struct ProjCam {
+    float fx, fy, cx, cy, w, h;
+    int W;
+    int64_t zpitch;
+    const uint8_t *motion;   // NULL unless afterimage removal applies to this scan
+};
+
+__device__ __forceinline__ void project_one(const float (&M)[12], float x, float y, float z, const ProjCam &C,
+                                            uint32_t *zbuf) {
     const float xc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[0], x), __fmul_rn(M[1], y)), __fmul_rn(M[2], z)), M[3]);
     const float yc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[4], x), __fmul_rn(M[5], y)), __fmul_rn(M[6], z)), M[7]);
     const float zc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[8], x), __fmul_rn(M[9], y)), __fmul_rn(M[10], z)), M[11]);
     if (!(zc > 0.0f) || !(zc < __int_as_float(0x7F800000))) return;
-    const float u = __fadd_rn(__fmul_rn(F.fx, __fdiv_rn(xc, zc)), F.cx);
-    const float v = __fadd_rn(__fmul_rn(F.fy, __fdiv_rn(yc, zc)), F.cy);
-    if (!(u >= 0.0f && u < (float)F.W && v >= 0.0f && v < (float)F.H)) return;
+    const float u = __fadd_rn(__fmul_rn(C.fx, __fdiv_rn(xc, zc)), C.cx);
+    const float v = __fadd_rn(__fmul_rn(C.fy, __fdiv_rn(yc, zc)), C.cy);
+    if (!(u >= 0.0f && u < C.w && v >= 0.0f && v < C.h)) return;
     const int i = __float2int_rz(u);   // u >= 0: truncation is floor
     const int j = __float2int_rz(v);
     // afterimage removal: points of older scans are dropped where the scene moved
-    if (old_scan && F.motion && F.motion[(int64_t)j * F.W + i]) return;
-    atomicMin(zbuf + (int64_t)j * F.zpitch + i, __float_as_uint(zc));
+    if (C.motion && C.motion[(int64_t)j * C.W + i]) return;
+    atomicMin(zbuf + (int64_t)j * C.zpitch + i, __float_as_uint(zc));
 }
 
 __global__ void __launch_bounds__(kThreads) project_kernel(const BatchDev *__restrict__ B) {
@@ -106,27 +115,30 @@ __global__ void __launch_bounds__(kThreads) project_kernel(const BatchDev *__res
         if (p0 >= S.count) continue;
         uint32_t *zbuf = F.zbuf_raw;
         const bool old_scan = (seg % kMaxScans) != F.newest_scan;
+        const ProjCam C{F.fx, F.fy, F.cx, F.cy, (float)F.W, (float)F.H, F.W, F.zpitch, old_scan ? F.motion : nullptr};
+        const int64_t count = S.count;
         if (S.stride_floats == 3) {
             if (p0 + 4 <= S.count) {
                 // 4 packed points = 48 bytes = 3 aligned float4 (base 16-byte aligned, p0 % 4 == 0)
                 const float4 *q = reinterpret_cast<const float4 *>(S.xyz + p0 * 3);
                 const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
-                project_one(M, a.x, a.y, a.z, F, zbuf, old_scan);
-                project_one(M, a.w, b.x, b.y, F, zbuf, old_scan);
-                project_one(M, b.z, b.w, c.x, F, zbuf, old_scan);
-                project_one(M, c.y, c.z, c.w, F, zbuf, old_scan);
+                project_one(M, a.x, a.y, a.z, C, zbuf);
+                project_one(M, a.w, b.x, b.y, C, zbuf);
+                project_one(M, b.z, b.w, c.x, C, zbuf);
+                project_one(M, c.y, c.z, c.w, C, zbuf);
             } else {
-                for (int64_t p = p0; p < S.count; ++p)
-                    project_one(M, __ldg(S.xyz + 3 * p), __ldg(S.xyz + 3 * p + 1), __ldg(S.xyz + 3 * p + 2), F, zbuf, old_scan);
+                const float *xyz = S.xyz;
+                for (int64_t p = p0; p < count; ++p)
+                    project_one(M, __ldg(xyz + 3 * p), __ldg(xyz + 3 * p + 1), __ldg(xyz + 3 * p + 2), C, zbuf);
             }
         } else {
             const float4 *q = reinterpret_cast<const float4 *>(S.xyz) + p0;
-            const int n = (int)(S.count - p0 < 4 ? S.count - p0 : 4);
+            const int n = (int)(count - p0 < 4 ? count - p0 : 4);
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
                 if (k < n) {
                     const float4 a = __ldg(q + k);
-                    project_one(M, a.x, a.y, a.z, F, zbuf, old_scan);
+                    project_one(M, a.x, a.y, a.z, C, zbuf);
                 }
             }
         }

@@ -27,8 +27,10 @@ __device__ __forceinline__ bool pool_words_ok(const FrameDev &F) {
 __device__ __forceinline__ void pool_store(const FrameDev &F, int I, int J, float rr, float gg, float bb, float cnt,
                                            float s, float npx) {
     const int64_t o = (int64_t)J * F.cpitch + I;
-    F.cguide[o] = make_float4(__fdiv_rn(rr, npx), __fdiv_rn(gg, npx), __fdiv_rn(bb, npx), cnt);
-    F.cssum[o] = s;
+    float4 *const guide = F.cguide;   // both pointers read before either store
+    float *const sums = F.cssum;
+    guide[o] = make_float4(__fdiv_rn(rr, npx), __fdiv_rn(gg, npx), __fdiv_rn(bb, npx), cnt);
+    sums[o] = s;
 }
 
 // Pooled pixel (I, J): its guide and sums; cnt_out = its observation count.
@@ -98,7 +100,10 @@ __global__ void __launch_bounds__(kThreads) pool_kernel(const BatchDev *__restri
     const int nf = B->n_frames;
     const int total = B->pool_pre[nf];
     const int lane = threadIdx.x & 31;
-    const bool marks = B->tl_th[0] > 0;
+    // the first filter's tile geometry, read before any store (a store could alias the descriptor)
+    const int mtw = B->tl_tw[0], mth = B->tl_th[0], mr = B->tl_r[0];
+    int32_t *const mflags = B->tl_flags[0];
+    const bool marks = mth > 0;
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int fi = find_segment(B->pool_pre, nf, item);
         const FrameDev &F = B->f[fi];
@@ -112,8 +117,8 @@ __global__ void __launch_bounds__(kThreads) pool_kernel(const BatchDev *__restri
             const uint32_t m = __ballot_sync(0xffffffffu, cnt > 0.0f);
             const int I0 = I - lane;
             if (m)
-                mark_reach(B->tl_flags[0] + B->t1_pre[fi], B->tl_tw[0], B->tl_th[0], B->tl_r[0], 1, F.Wc, F.Hc,
-                           I0 + __ffs(m) - 1, I0 + 31 - __clz(m), J, J, lane);
+                mark_reach(mflags + B->t1_pre[fi], mtw, mth, mr, 1, F.Wc, F.Hc, I0 + __ffs(m) - 1, I0 + 31 - __clz(m), J,
+                           J, lane);
         }
     }
 }
