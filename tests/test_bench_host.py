@@ -1,0 +1,92 @@
+"""Host-side pieces of bench.py that the reported numbers rest on: the observed-tap
+counts of both filter stages (the roofline's algorithmic work), each kernel's work for
+the path roofline, and the DRAM-traffic lookup keyed on the captured kernel's sources.
+Brute force on small random masks; no GPU."""
+import json
+import os
+import sys
+import types
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _brute_taps(obs, r):
+    """Sum over output pixels of the observed pixels in the (2r+1)^2 window."""
+    H, W = obs.shape
+    n = 0
+    for y in range(H):
+        for x in range(W):
+            n += int(obs[max(0, y - r):y + r + 1, max(0, x - r):x + r + 1].sum())
+    return n
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_stage1_taps_brute_force(seed):
+    rng = np.random.default_rng(seed)
+    obs = rng.random((11, 17)) < 0.25
+    assert bench.valid_taps_stage1(obs, r=4) == _brute_taps(obs, 4)
+
+
+@pytest.mark.parametrize("W,H", [(20, 13), (9, 9), (7, 4)])
+def test_stage2_taps_brute_force(W, H):
+    rng = np.random.default_rng(W * H)
+    Hc, Wc = -(-H // 3), -(-W // 3)
+    cv = (rng.random((Hc, Wc)) < 0.5).astype(np.uint8)
+    full = np.kron(cv, np.ones((3, 3), np.uint8))[:H, :W] > 0   # restored validity, cropped
+    assert bench.valid_taps_stage2(cv, W, H) == _brute_taps(full, 2)
+
+
+class _T:
+    def __init__(self, a):
+        self.a = a
+
+    def cpu(self):
+        return self
+
+    def numpy(self):
+        return self.a
+
+
+def test_step_work_counts():
+    W, H = 97, 50
+    z = np.full((H, W), 0x7F800000, np.uint32)
+    z[10, 10] = np.float32(1.0).view(np.uint32)
+    z[49, 96] = np.float32(2.0).view(np.uint32)
+    Hc, Wc = -(-H // 3), -(-W // 3)
+    cv = np.zeros((Hc, Wc), np.uint8)
+    cv[3, 3] = 1
+    probe = types.SimpleNamespace(W=W, H=H, zbuf=_T(z.view(np.int32)), coarse_valid=_T(cv), n_points=lambda: 25)
+    view = types.SimpleNamespace(scans=[types.SimpleNamespace(xyz=np.zeros((100, 3), np.float32))] * 2)
+    w = bench.step_work(probe, view)
+    assert w["prep_compose_clear"] == 4 * W * H
+    assert w["project_zbuf"] == 12 * 200 + 4 * 2
+    assert w["pool3"] == 7 * W * H + 20 * Wc * Hc
+    assert w["bp_count"] == W * H
+    assert w["bp_write"] == 8 * W * H + 16 * 25
+    # pooled observations at (3, 3) and (16, 32): a full 9 x 9 reach clipped by the grid edge,
+    # and the corner pixel's 5 x 5
+    assert w["taps1"] == 8 * 8 + 5 * 5
+    # the restored 3 x 3 block of pooled pixel (3, 3): 9 pixels, each in 25 windows
+    assert w["taps2"] == 9 * 25
+
+
+def test_traffic_record_follows_sources(tmp_path, monkeypatch):
+    src = tmp_path / "k.cuh"
+    src.write_text("kernel v1\n")
+    import hashlib
+    digest = hashlib.sha256(src.read_bytes()).hexdigest()[:16]
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    rec = {"kernel": "k", "variant": {"kp": 4, "warps": 8}, "dram_bytes_per_launch": 123,
+           "sources": {"k.cuh": digest}}
+    (prof / "traffic.json").write_text(json.dumps({"jbf_stage2": [rec]}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profiled_traffic("jbf_stage2", {"kp": 4, "warps": 8}) == 123
+    assert bench.profiled_traffic("jbf_stage2", {"kp": 4, "warps": 4}) is None   # another variant
+    src.write_text("kernel v2\n")
+    assert bench.profiled_traffic("jbf_stage2", {"kp": 4, "warps": 8}) is None   # sources changed
