@@ -394,6 +394,19 @@ def step_work(b, view, pool=3):
     }
 
 
+def host_link_bounds(link, h2d_bytes, d2h_bytes, frames, world=1):
+    """End-to-end rates the host link allows for a step of ``frames`` frames at the measured copy
+    rates: both directions at once (full duplex; the batch slots' copies in and out overlap),
+    and one direction at a time (serial)."""
+    t_in = h2d_bytes / (link["h2d_GBps"] * 1e9)
+    t_out = d2h_bytes / (link["d2h_GBps"] * 1e9)
+    return dict(link, bound_frames_per_s=round(frames / max(t_in, t_out) * world, 1),
+                serial_frames_per_s=round(frames / (t_in + t_out) * world, 1),
+                note="copy-engine rates, 256 MiB pinned <-> device, each direction measured alone; bound: both "
+                     "directions at once (the larger of bytes in / h2d rate and bytes out / d2h rate per step); "
+                     "serial: one direction after the other")
+
+
 def host_link_gbps(dev, mb=256, reps=5):
     """Pinned host <-> device copy rates (GB/s), CUDA events."""
     import torch
@@ -565,14 +578,10 @@ def ours_arm(a, rank, world, local_rank):
         h2d = sum(sum(x.numel() * 4 for x, _ in b.scans) + b.rgb.numel() for b in hb[0])
         d2h = sum(8 + b.n_points() * 16 for b in hb[0])
         link = host_link_gbps(dev)
-        # the step's bytes cross the host link one direction at a time at the measured copy rates
-        bound = B / (h2d / (link["h2d_GBps"] * 1e9) + d2h / (link["d2h_GBps"] * 1e9)) * world
         e2e = {"value": B * a.steps / dt * world, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h),
                "what": "pinned host points + RGB in, coloured points out (written by the GPU into pinned memory)",
-               "host_link": dict(link, bound_frames_per_s=round(bound, 1),
-                                 note="copy-engine rates, 256 MiB pinned <-> device; bound = bytes in / h2d rate + "
-                                      "bytes out / d2h rate per step")}
+               "host_link": host_link_bounds(link, h2d, d2h, B, world)}
     serving = None
     if not a.no_serve and rank == 0:
         serving = serve_measure(mixed_views, dev, stream, a.serve_seconds, 1, a.autotune)

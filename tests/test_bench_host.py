@@ -90,3 +90,12 @@ def test_traffic_record_follows_sources(tmp_path, monkeypatch):
     assert bench.profiled_traffic("jbf_stage2", {"kp": 4, "warps": 4}) is None   # another variant
     src.write_text("kernel v2\n")
     assert bench.profiled_traffic("jbf_stage2", {"kp": 4, "warps": 8}) is None   # sources changed
+
+
+def test_host_link_bounds():
+    link = {"h2d_GBps": 200.0, "d2h_GBps": 100.0}
+    b = bench.host_link_bounds(link, h2d_bytes=2e9, d2h_bytes=4e9, frames=8, world=2)
+    # 10 ms in, 40 ms out: both at once 40 ms a step, one after the other 50 ms
+    assert b["bound_frames_per_s"] == round(8 / 0.040 * 2, 1)
+    assert b["serial_frames_per_s"] == round(8 / 0.050 * 2, 1)
+    assert b["h2d_GBps"] == 200.0 and b["d2h_GBps"] == 100.0
