@@ -252,7 +252,10 @@ typedef struct densify_frame {
  * a 2 GiB budget and CUDA graphs on. */
 DENSIFY_API void densify_default_params(densify_params *p);
 
-/* Create a context on CUDA device `device`, issuing work on `cuda_stream`
+/* Sets up the per-viewpoint path of Sec. 2 (merge and projection of the
+ * scans, the joint bilateral filter of Eq. (1)-(4) in the two-stage schedule
+ * of Sec. 5, back-projection to coloured points) on one GPU.
+ * Create a context on CUDA device `device`, issuing work on `cuda_stream`
  * (a cudaStream_t; NULL: the context creates its own non-blocking stream).
  * Allocates the scratch arena (hbm_budget_bytes) and per-batch descriptors
  * up front; nothing is allocated per frame afterwards.
@@ -260,7 +263,9 @@ DENSIFY_API void densify_default_params(densify_params *p);
 DENSIFY_API densify_status densify_create(const densify_params *params, int device, void *cuda_stream,
                               densify_ctx **out);
 
-/* Admit one frame (non-blocking). Validates it, reserves its scratch in the
+/* One frame of one viewpoint: its camera image and the (up to three) LiDAR
+ * scans staggered in time that Sec. 2 merges into one depth image.
+ * Admit one frame (non-blocking). Validates it, reserves its scratch in the
  * arena and queues it; the frame goes to the GPU at once if a launch slot
  * is free, else with the next batch. The caller keeps every buffer alive and
  * unmodified until densify_poll() returns DENSIFY_OK (or an error) for the
@@ -269,31 +274,41 @@ DENSIFY_API densify_status densify_create(const densify_params *params, int devi
  * E_NOMEM (the frame can never fit the budget), E_CUDA. */
 DENSIFY_API densify_status densify_submit(densify_ctx *ctx, const densify_frame *frame, uint64_t *ticket);
 
-/* Send every queued frame to the GPU now, waiting (bounded by timeout_ns,
+/* Runs the queued frames' path (Sec. 2: projection and densification, done
+ * independently per viewpoint, here many viewpoints in one batched launch).
+ * Send every queued frame to the GPU now, waiting (bounded by timeout_ns,
  * <0: no bound) for a launch slot if all are busy. */
 DENSIFY_API densify_status densify_flush(densify_ctx *ctx, int64_t timeout_ns);
 
-/* Wait up to timeout_ns (0: just check; <0: no bound) for a ticket.
+/* Collects one frame's results: the dense depth and validity of Eq. (1)
+ * (after the two stages of Sec. 5) and its coloured points (Sec. 2).
+ * Wait up to timeout_ns (0: just check; <0: no bound) for a ticket.
  * Returns OK (results written; the ticket is collected and its scratch
  * freed), PENDING (timeout_ns == 0 and not done), E_TIMEOUT, E_TICKET or
  * E_CUDA. Polling also launches frames that were waiting for a slot. */
 DENSIFY_API densify_status densify_poll(densify_ctx *ctx, uint64_t ticket, int64_t timeout_ns);
 
-/* Wait (bounded: at most timeout_ns per outstanding batch, 10 s if <0) for
+/* Ends the per-viewpoint path of Sec. 2 set up by densify_create.
+ * Wait (bounded: at most timeout_ns per outstanding batch, 10 s if <0) for
  * in-flight work, then free every resource of the context. */
 DENSIFY_API densify_status densify_destroy(densify_ctx *ctx);
 
-/* Static string naming a status. */
+/* Static string naming a status. (No counterpart in the paper: Sec. 2
+ * describes no error reporting; the codes are this library's.) */
 DENSIFY_API const char *densify_status_str(densify_status s);
 
-/* The last error message of a context (empty if none). Valid until the next
+/* (No counterpart in the paper: error detail of this library's calls.)
+ * The last error message of a context (empty if none). Valid until the next
  * call on the context. ctx may be NULL: the last error of a failed create. */
 DENSIFY_API const char *densify_last_error(const densify_ctx *ctx);
 
-/* Device bytes one frame of this shape reserves from the arena. */
+/* Device bytes one frame of this shape reserves from the arena: the z-buffer
+ * (D and B of Algorithm 1), the pooled maps and first-stage result of the
+ * two-stage filter (Sec. 5) and the compaction counts. */
 DENSIFY_API uint64_t densify_frame_scratch_bytes(const densify_params *params, const densify_frame *frame);
 
-/* Per-kernel device time accumulated since the last reset, when the context
+/* (No counterpart in the paper: Table 1 reports only a per-frame total.)
+ * Per-kernel device time accumulated since the last reset, when the context
  * was created with timing = 1: for each kernel, its static name, the summed
  * CUDA-event duration in microseconds over all completed batches and the
  * number of launches. Times are read when batches are collected, so call
@@ -302,16 +317,19 @@ DENSIFY_API uint64_t densify_frame_scratch_bytes(const densify_params *params, c
 DENSIFY_API int32_t densify_kernel_times(densify_ctx *ctx, const char **names, double *total_us,
                              int64_t *launches, int32_t cap);
 
-/* Zero the accumulated kernel times and the kernel launch count. */
+/* Zero the accumulated kernel times and the kernel launch count. (No
+ * counterpart in the paper.) */
 DENSIFY_API void densify_reset_kernel_times(densify_ctx *ctx);
 
-/* Number of CUDA kernels launched by the context's completed batches since
+/* (No counterpart in the paper: launch accounting of this library.)
+ * Number of CUDA kernels launched by the context's completed batches since
  * creation or the last densify_reset_kernel_times (a replayed graph counts each
  * of its kernels; the autotuner's trial launches are not counted). With
  * timing = 1 or 0 alike. */
 DENSIFY_API int64_t densify_kernel_launches(densify_ctx *ctx);
 
-/* JSON text describing the filter kernels the context runs: per filter stage the
+/* The kernels that run the filter stages of Sec. 5 (Eq. (1)-(4) each).
+ * JSON text describing the filter kernels the context runs: per filter stage the
  * chosen kernel (TMA-staged or plain, rows per thread, tile, grid) and, after
  * autotuning, every candidate's measured time. Writes at most cap bytes
  * (NUL-terminated); returns the length of the full text. */
@@ -364,7 +382,8 @@ DENSIFY_API densify_status densify_frame_noalloc(const densify_params *params, c
 DENSIFY_API densify_status densify_sigma_grad(densify_ctx *ctx, const densify_frame *frame, const float *gt_depth,
                                               double *loss, double *grad, int64_t *n_pixels);
 
-/* ABI version of the loaded library (DENSIFY_ABI_VERSION). */
+/* ABI version of the loaded library (DENSIFY_ABI_VERSION). (No counterpart
+ * in the paper.) */
 DENSIFY_API int32_t densify_abi_version(void);
 
 #ifdef __cplusplus

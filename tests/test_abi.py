@@ -28,6 +28,27 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def _doc_comments():
+    """Map each declared function to the comment block directly in front of its declaration."""
+    src = open(HEADER).read()
+    out = {}
+    for m in re.finditer(r"/\*((?:[^*]|\*(?!/))*)\*/\s*DENSIFY_API\s+[\w\s\*]*?\b(densify_\w+)\s*\(", src):
+        out[m.group(2)] = " ".join(m.group(1).replace("*", " ").split())
+    return out
+
+
+def test_every_declaration_cites_its_passage():
+    """Each entry point's comment names the paper passage that defines what it runs (a section,
+    equation, algorithm or table), or states that the paper has no counterpart."""
+    docs = _doc_comments()
+    assert sorted(docs) == _declared(), "every declaration needs a comment block in front of it"
+    cite = re.compile(r"\b(Sec\. \d|Eq\. \(\d|Algorithm \d|Table \d)")
+    for name, doc in docs.items():
+        assert cite.search(doc) or "no counterpart" in doc.lower(), f"{name}: no passage cited"
+    for name in ("densify_create", "densify_submit", "densify_flush", "densify_poll", "densify_destroy"):
+        assert cite.search(docs[name]), f"{name}: the boundary call must cite a passage"
+
+
 def test_library_exports_every_declared_symbol(built):
     out = subprocess.run(["nm", "-D", "--defined-only", built], capture_output=True, text=True, check=True).stdout
     exported = sorted(set(re.findall(r"\bT (densify_\w+)", out)))
