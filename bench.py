@@ -631,6 +631,11 @@ def ours_arm(a, rank, world, local_rank):
         cpu = {"value": rate, "unit": UNIT, "cores": a.cpu_procs, "kind": "oracle",
                "sample": f"{a.cpu_frames} frames of the same workload, FP64, one single-threaded oracle process "
                          f"per core ({a.cpu_procs}), {dt:.1f} s"}
+        # the FP32 projection contract against a pure FP64 projection of the first view (untimed)
+        import oracle
+        v0 = views[0]
+        cpu["projection_fp32_vs_fp64"] = oracle.projection_precision_report(
+            v0.camera, [(s.xyz, s.lidar_to_world) for s in v0.scans])
     sorted_ms = sorted(step_ms)
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps, "warmup": a.warmup,

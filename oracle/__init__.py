@@ -121,6 +121,8 @@ def project(M32, xyz, W, H, fx, fy, cx, cy, zbuf=None):
 
 
 def project_fp64(M64, xyz, W, H, fx, fy, cx, cy, depth=None):
+    """Pure FP64 projection (FP64 matrix and arithmetic) into a nearest-depth
+    map of FP64 camera depths (+inf where empty); returns (depth, kept)."""
     xyz = np.ascontiguousarray(xyz, np.float32)
     if depth is None:
         depth = np.full(H * W, np.inf)
@@ -129,6 +131,41 @@ def project_fp64(M64, xyz, W, H, fx, fy, cx, cy, depth=None):
                                      xyz.reshape(-1) if n else np.zeros(4, np.float32), n,
                                      xyz.shape[1] if n else 3, W, H, fx, fy, cx, cy, depth)
     return depth, kept
+
+
+def projection_precision_report(cam, scans):
+    """How the FP32 projection contract differs from a pure FP64 projection of
+    the same points (Sec. 2: the merged scans projected into the camera view).
+
+    The FP32 z-buffer (``project``, pixel and depth decided in the kernel's
+    precision) is compared with ``project_fp64`` (FP64 matrix, FP64 arithmetic):
+    pixels observed in only one of the two, pixels observed in both whose
+    nearest point differs (relative depth difference above 1e-5, far above the
+    FP32 rounding of one point's depth), and the largest relative depth
+    difference where the same point wins."""
+    W, H = cam.width, cam.height
+    z32 = np.full(H * W, ZBUF_EMPTY, np.uint32)
+    d64 = np.full(H * W, np.inf)
+    n_points = 0
+    for xyz, l2w in scans:
+        M64, M32 = compose(cam.cam_to_world, l2w)
+        project(M32, xyz, W, H, cam.fx, cam.fy, cam.cx, cam.cy, z32)
+        project_fp64(M64, xyz, W, H, cam.fx, cam.fy, cam.cx, cam.cy, d64)
+        n_points += int(np.asarray(xyz).shape[0])
+    o32 = z32 != ZBUF_EMPTY
+    o64 = np.isfinite(d64)
+    both = o32 & o64
+    d32 = z32[both].view(np.float32).astype(np.float64)
+    rel = np.abs(d32 - d64[both]) / d64[both]
+    other = rel > 1e-5
+    return {
+        "points": n_points,
+        "observed_fp32": int(o32.sum()), "observed_fp64": int(o64.sum()),
+        "only_fp32": int((o32 & ~o64).sum()), "only_fp64": int((o64 & ~o32).sum()),
+        "other_nearest_point": int(other.sum()),
+        "pixels_assigned_differently": int((o32 ^ o64).sum() + other.sum()),
+        "max_rel_depth_same_point": float(rel[~other].max()) if (~other).any() else 0.0,
+    }
 
 
 def zbuf_to_depth(zbuf):

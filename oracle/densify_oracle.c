@@ -17,7 +17,8 @@
  *                         the depth image D and mask B of Algorithm 1).
  *                         The pixel index and stored depth are decided in the
  *                         kernel's precision (FP32), emulated exactly here.
- *   oracle_project_fp64   the same projection in pure FP64 (informational)
+ *   oracle_project_fp64   the same projection in pure FP64 (compared with the
+ *                         FP32 contract: how many pixels it assigns differently)
  *   oracle_pool           1/3 pooling of depth, mask and guide (Sec. 5,
  *                         two-stage filtering)
  *   oracle_jbf_gather     Eq. (1)-(4), gather form, plain or shifted exponent

@@ -148,6 +148,91 @@ def test_projection_matches_numpy_float32(oracle_mod):
     assert np.array_equal(zb, ref)
 
 
+def test_fp64_projection_known_pixels(oracle_mod):
+    """Pure FP64 projection: points at pixel centres land on their pixels with their exact depth;
+    a non-square image and distinct row and column targets catch a u/v swap."""
+    W, H, f, cx, cy = 16, 12, 64.0, 8.0, 6.0
+    jj, ii = np.mgrid[0:H, 0:W]
+    ii, jj = ii.ravel().astype(float), jj.ravel().astype(float)
+    pts = _pixel_centre_points(ii, jj, 4.0, f, cx, cy)
+    I = np.eye(4)
+    M64, _ = oracle_mod.compose(I, I)
+    depth, kept = oracle_mod.project_fp64(M64, pts, W, H, f, f, cx, cy)
+    assert kept == W * H and np.all(depth == 4.0)
+    for k in _rng(5).permutation(W * H)[:40]:
+        d, kept = oracle_mod.project_fp64(M64, pts[k:k + 1], W, H, f, f, cx, cy)
+        assert kept == 1
+        assert np.flatnonzero(np.isfinite(d)).tolist() == [int(jj[k]) * W + int(ii[k])]
+    # nearest wins, rejections as in the FP32 contract
+    a = _pixel_centre_points(np.array([3.0]), np.array([5.0]), 4.0, f, cx, cy)
+    b = _pixel_centre_points(np.array([3.0]), np.array([5.0]), 2.0, f, cx, cy)
+    junk = np.array([[0.1, 0.1, -1.0], [100.0, 0.0, 1.0], [np.nan, 0.0, 1.0], [0.0, 0.0, 0.0]], np.float32)
+    d, kept = oracle_mod.project_fp64(M64, np.concatenate([a, junk, b]), W, H, f, f, cx, cy)
+    assert kept == 2 and np.flatnonzero(np.isfinite(d)).tolist() == [5 * W + 3] and d[5 * W + 3] == 2.0
+
+
+def test_fp64_projection_matches_numpy_float64(oracle_mod):
+    """Pure FP64 projection re-evaluated with numpy float64 on random rigid poses."""
+    rng = _rng(6)
+    W, H = 96, 64
+    fx, fy, cx, cy = 70.3, 69.1, 47.7, 31.2
+    for _ in range(3):
+        C, L = _rigid(rng), _rigid(rng)
+        M64, _ = oracle_mod.compose(C, L)
+        pts_c = np.stack([rng.uniform(-2, 2, 4000), rng.uniform(-1.5, 1.5, 4000), rng.uniform(-1, 6, 4000)], 1)
+        pts = ((np.linalg.inv(L) @ C @ np.c_[pts_c, np.ones(4000)].T).T[:, :3]).astype(np.float32)
+        depth, kept = oracle_mod.project_fp64(M64, pts, W, H, fx, fy, cx, cy)
+        c = pts.astype(np.float64) @ M64[:, :3].T + M64[:, 3]
+        with np.errstate(all="ignore"):
+            u = fx * (c[:, 0] / c[:, 2]) + cx
+            v = fy * (c[:, 1] / c[:, 2]) + cy
+            ok = (c[:, 2] > 0) & (u >= 0) & (u < W) & (v >= 0) & (v < H)
+        ref = np.full(W * H, np.inf)
+        np.minimum.at(ref, (np.floor(v[ok]) * W + np.floor(u[ok])).astype(np.int64), c[ok, 2])
+        assert kept == int(ok.sum()) and kept > 400
+        assert np.array_equal(np.isfinite(depth), np.isfinite(ref))
+        m = np.isfinite(ref)
+        np.testing.assert_allclose(depth[m], ref[m], rtol=1e-13, atol=0)
+
+
+def test_fp64_projection_decides_edges_exactly(oracle_mod):
+    """A point whose exact image coordinate lies one FP32 ulp below a pixel edge: the FP32 contract
+    (numpy float32 agrees) rounds it onto the next pixel, the FP64 projection keeps it on the pixel
+    the exact value lies in. With fx = z = 3 and cx = 0 the exact u is x itself."""
+    I = np.eye(4)
+    M64, M32 = oracle_mod.compose(I, I)
+    three = np.float32(3.0)
+    found = 0
+    W, H = 4096, 8
+    for k in range(1, W):
+        x = np.nextafter(np.float32(k), np.float32(0))          # largest float32 below k
+        u32 = three * (x / three)
+        if u32 < k:
+            continue                                            # FP32 keeps it below the edge too
+        y = np.float32(4.5)                                     # row 4 in both precisions
+        p = np.array([[x, y, 3.0]], np.float32)
+        zb, _ = oracle_mod.project(M32, p, W, H, 3.0, 3.0, 0.0, 0.0)
+        d, _ = oracle_mod.project_fp64(M64, p, W, H, 3.0, 3.0, 0.0, 0.0)
+        assert np.flatnonzero(zb != EMPTY).tolist() == [4 * W + k]        # FP32: rounded onto pixel k
+        assert np.flatnonzero(np.isfinite(d)).tolist() == [4 * W + k - 1]  # exact: pixel k - 1
+        found += 1
+    assert found > 100
+
+
+def test_fp32_contract_against_fp64_projection_1080p(oracle_mod):
+    """The FP32 projection contract against pure FP64 on the 1080p three-scan workload: the same
+    observed pixels up to a handful moved across a pixel edge, the same nearest point elsewhere,
+    depths within FP32 rounding."""
+    import scene
+    v = scene.make_view(1001, res="1080p", scene_kind="room", n_scans=3, beams=128, az_steps=1024,
+                        view_index=0, n_views=7)
+    rep = oracle_mod.projection_precision_report(v.camera, [(s.xyz, s.lidar_to_world) for s in v.scans])
+    print(rep)
+    assert rep["observed_fp32"] > 50000
+    assert rep["pixels_assigned_differently"] <= 1e-3 * rep["observed_fp32"]
+    assert rep["max_rel_depth_same_point"] < 1e-6
+
+
 def test_merge_order_independent(oracle_mod, small_view):
     v = small_view
     cam = v.camera
