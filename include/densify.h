@@ -328,10 +328,23 @@ DENSIFY_API void densify_reset_kernel_times(densify_ctx *ctx);
  * timing = 1 or 0 alike. */
 DENSIFY_API int64_t densify_kernel_launches(densify_ctx *ctx);
 
+/* (No counterpart in the paper: a test hook for this library's error path.)
+ * Makes the next batch launched on the context report what its kernels report
+ * when a bounded wait on tile copies gives up: the host sets bit 0 of the
+ * batch's device status word on the batch's stream, after its kernels and
+ * before the status is read back (no wait on the GPU actually runs out).
+ * Collecting that batch's tickets then returns DENSIFY_E_CUDA with the
+ * bounded-wait message in densify_last_error(), and the context stays
+ * unusable (every later call returns DENSIFY_E_CUDA), as after a real
+ * timeout. Errors: E_INVALID (ctx NULL), E_CUDA (context already failed). */
+DENSIFY_API densify_status densify_inject_wait_failure(densify_ctx *ctx);
+
 /* The kernels that run the filter stages of Sec. 5 (Eq. (1)-(4) each).
  * JSON text describing the filter kernels the context runs: per filter stage the
  * chosen kernel (TMA-staged or plain, rows per thread, tile, grid) and, after
- * autotuning, every candidate's measured time. Writes at most cap bytes
+ * autotuning, every candidate's measured time; then the number of batches
+ * launched and the most batches in flight at once (launched, not yet
+ * complete). Writes at most cap bytes
  * (NUL-terminated); returns the length of the full text. */
 DENSIFY_API int32_t densify_describe(densify_ctx *ctx, char *buf, int32_t cap);
 
@@ -358,7 +371,10 @@ DENSIFY_API int32_t densify_describe(densify_ctx *ctx, char *buf, int32_t cap);
  * the GPU (two streams, or two host threads) race on it; serialise them.
  * The first call on a device looks up the array's device address and the SM
  * count (once per device, with that device current); make that first call
- * before any stream capture. No cudaMalloc, cudaFree or other allocating call
+ * before any stream capture, and before the device-memory footprint is
+ * frozen: like the first launch of any kernel under lazy module loading, it
+ * may load the library's kernel code into device memory. Later calls leave the
+ * device's free memory unchanged. No cudaMalloc, cudaFree or other allocating call
  * is made. Errors: E_INVALID (bad argument or too large), E_CUDA (a launch
  * failed); the message is in densify_last_error(NULL). */
 DENSIFY_API densify_status densify_frame_noalloc(const densify_params *params, const densify_frame *frame,

@@ -84,6 +84,14 @@ struct alignas(64) FrameDev {
     int64_t *points_n;
     float *out_coarse;       // optional first-stage depth copy
     uint8_t *out_coarse_valid;
+    // TMA filters (index 0: first or only filter, 1: second): one flag per tile of the stage,
+    // row-major over the frame's tiles, nonzero when some observation reaches the tile; both
+    // stages' flags are one block of ntflags words of the frame's scratch, zeroed by the batch's
+    // first kernel and set by the kernel in front of the filter (the pooling kernel for the first
+    // of two stages, the first filter for the second, tile_mark_kernel for a single stage)
+    int32_t *tflags[2];
+    int32_t ntflags;
+    int32_t pad1;
 };
 
 struct BatchDev {
@@ -99,12 +107,10 @@ struct BatchDev {
     int32_t px_pre[kMaxBatch + 1];                 // pixel chunks of the motion / contour kernels
     int32_t oc_pre[kMaxBatch + 1];                 // tiles of the occlusion kernel
     int32_t mk_pre[kMaxBatch + 1];                 // 32-pixel row segments of the observation grid
-    // TMA filters (index 0: first or only filter, 1: second): one flag per tile of the stage
-    // (in the order its prefix array counts them), nonzero when some observation reaches the
-    // tile; zeroed by the batch's first kernel and set by the kernel in front of the filter (the
-    // pooling kernel for the first of two stages, the first filter for the second, tile_mark_kernel
-    // for a single stage)
-    int32_t *tl_flags[2];
+    // TMA filters (index 0: first or only filter, 1: second); the tile flags are per frame
+    // (FrameDev::tflags)
+    int32_t tl_on;                                 // some stage runs a TMA filter: frames carry tile flags
+    int32_t tl_pad;
     int32_t tl_next[2];                            // the filter's tile counter (reset by the prep kernel; by the
                                                    // mark kernel or a memset before a filter launched on its own)
     int32_t tl_tw[2];                              // tile width of a TMA filter stage (32 or 64)

@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(256) jbf_kernel(const BatchDev *__restrict__ B
                 }
             }
             if (cols)
-                mark_reach(B->tl_flags[1] + B->t2_pre[fi], B->tl_tw[1], B->tl_th[1], B->tl_r[1], a.pool, F.W, F.H,
+                mark_reach(F.tflags[1], B->tl_tw[1], B->tl_th[1], B->tl_r[1], a.pool, F.W, F.H,
                            x0 + __ffs(cols) - 1, x0 + 31 - __clz(cols), y0 + rbase + kf, y0 + rbase + kl, lane);
         }
     }

@@ -98,7 +98,6 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
     const int32_t *pre = stage ? B->t2_pre : B->t1_pre;
     const int nf = B->n_frames;
     const int total = pre[nf];
-    const int32_t *flags = B->tl_flags[stage];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 
     // Tiles are handed out dynamically: a CTA starts with tile blockIdx.x and takes every further
@@ -179,8 +178,8 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
     auto advance = [&]() {   // thread 0: n1 <- the counter's last reply; request the next one
         n1 = (int)gridDim.x + n2raw;
         if (n1 < total) {
-            f1 = flags[n1];
             locate(n1, l1f, l1x, l1y);
+            f1 = B->f[l1f].tflags[stage][n1 - pre[l1f]];
             n2raw = request();
             asm volatile("" ::"r"(f1));   // wait for the flag here, in warp 0's filter phase, not at the next issue
         }
@@ -190,7 +189,7 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
         if (t0 < total) {
             int fi, x0, y0;
             locate(t0, fi, x0, y0);
-            const int f0 = flags[t0];
+            const int f0 = B->f[fi].tflags[stage][t0 - pre[fi]];
             issue(t0, f0, fi, x0, y0, 0);
             if (f0) inflight |= 1u;
             n2raw = request();
@@ -517,7 +516,7 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
                 }
             }
             if (cols)
-                mark_reach(B->tl_flags[1] + B->t2_pre[fi], B->tl_tw[1], B->tl_th[1], B->tl_r[1], a.pool, F.W, F.H,
+                mark_reach(F.tflags[1], B->tl_tw[1], B->tl_th[1], B->tl_r[1], a.pool, F.W, F.H,
                            x0 + __ffs(cols) - 1, x0 + 31 - __clz(cols), y0 + rbase + kf, y0 + rbase + kl, lane);
         }
         uint32_t slow = 0u;   // bit k: valid pixel whose weight sum is too small for the plain form
@@ -615,7 +614,6 @@ template <int SRC>
 __global__ void __launch_bounds__(kMarkThreads) tile_mark_kernel(BatchDev *__restrict__ B, int stage, int th, int r) {
     constexpr int kWarps = kMarkThreads / 32;
     if (blockIdx.x == 0 && threadIdx.x == 0) B->tl_next[stage] = 0;
-    const int32_t *tpre = stage ? B->t2_pre : B->t1_pre;
     const int32_t *mpre = B->mk_pre;
     const int nf = B->n_frames;
     const int total = mpre[nf];
@@ -649,7 +647,7 @@ __global__ void __launch_bounds__(kMarkThreads) tile_mark_kernel(BatchDev *__res
         const int ox0 = sx0 + __ffs(cols) - 1, ox1 = sx0 + 31 - __clz(cols);
         const int oy1 = oy0 + 31 - __clz(all), oyf = oy0 + __ffs(all) - 1;
         const int f = SRC == SRC_UP ? 3 : 1;   // output pixels per observation pixel and axis
-        mark_reach(B->tl_flags[stage] + tpre[fi], B->tl_tw[stage], th, r, f, gw, gh, ox0, ox1, oyf, oy1, lane);
+        mark_reach(F.tflags[stage], B->tl_tw[stage], th, r, f, gw, gh, ox0, ox1, oyf, oy1, lane);
     }
 }
 

@@ -38,12 +38,15 @@ __device__ __forceinline__ double compose_entry(const double *c2w, const double 
 __global__ void __launch_bounds__(kThreads) prep_kernel(BatchDev *__restrict__ B) {
     const int nf = B->n_frames;
     const int total = B->zb_pre[nf];
-    // the TMA filters' tile flags (both stages, contiguous) and tile counters start the batch
-    // cleared; the producers (pooling, first filter) and the mark kernel set the flags
-    if (B->tl_flags[0]) {
+    // the TMA filters' tile flags (each frame's block of both stages) and tile counters start the
+    // batch cleared; the producers (pooling, first filter) and the mark kernel set the flags
+    if (B->tl_on) {
         if (blockIdx.x == 0 && threadIdx.x == 0) B->tl_next[0] = B->tl_next[1] = 0;   // the filters' tile counters
-        const int nflags = B->t1_pre[nf] + B->t2_pre[nf];
-        for (int i = blockIdx.x * kThreads + threadIdx.x; i < nflags; i += gridDim.x * kThreads) B->tl_flags[0][i] = 0;
+        for (int f = 0; f < nf; ++f) {
+            int32_t *const fl = B->f[f].tflags[0];
+            const int n = B->f[f].ntflags;
+            for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) fl[i] = 0;
+        }
     }
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int f = find_segment(B->zb_pre, nf, item);

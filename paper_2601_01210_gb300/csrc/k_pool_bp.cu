@@ -102,7 +102,6 @@ __global__ void __launch_bounds__(kThreads) pool_kernel(const BatchDev *__restri
     const int lane = threadIdx.x & 31;
     // the first filter's tile geometry, read before any store (a store could alias the descriptor)
     const int mtw = B->tl_tw[0], mth = B->tl_th[0], mr = B->tl_r[0];
-    int32_t *const mflags = B->tl_flags[0];
     const bool marks = mth > 0;
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int fi = find_segment(B->pool_pre, nf, item);
@@ -117,7 +116,7 @@ __global__ void __launch_bounds__(kThreads) pool_kernel(const BatchDev *__restri
             const uint32_t m = __ballot_sync(0xffffffffu, cnt > 0.0f);
             const int I0 = I - lane;
             if (m)
-                mark_reach(mflags + B->t1_pre[fi], mtw, mth, mr, 1, F.Wc, F.Hc, I0 + __ffs(m) - 1, I0 + 31 - __clz(m), J,
+                mark_reach(F.tflags[0], mtw, mth, mr, 1, F.Wc, F.Hc, I0 + __ffs(m) - 1, I0 + 31 - __clz(m), J,
                            J, lane);
         }
     }

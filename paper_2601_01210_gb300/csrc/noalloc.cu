@@ -72,7 +72,7 @@ __global__ void noalloc_init_kernel(BatchDev *b, FrameWords f, Prefix p, int32_t
         b->bp_pre[0] = 0;
         b->bp_pre[1] = p.bp;
         b->mk_pre[0] = b->mk_pre[1] = 0;
-        b->tl_flags[0] = b->tl_flags[1] = nullptr;   // plain filter kernels only: no tile flags
+        b->tl_on = 0;   // plain filter kernels only: no tile flags
         b->tl_th[0] = b->tl_th[1] = 0;
         b->tl_tw[0] = b->tl_tw[1] = 32;
     }

@@ -106,6 +106,7 @@ struct Layout {
     int64_t rgb_pitch = 0;   // pitch of the staged RGB copy (0: the caller's frame is used in place)
     float4 *points_direct = nullptr;    // device view of a page-locked host point buffer
     int64_t *count_direct = nullptr;    // device view of a page-locked host count
+    uint64_t tflags = 0;                // tile flags of the TMA filters (both stages)
     uint64_t total = 0;
     bool own_depth = false, own_valid = false;
 };
@@ -134,8 +135,6 @@ struct Slot {
     cudaGraphExec_t exec = nullptr;
     bool busy = false;
     std::vector<uint64_t> tickets;
-    int32_t *d_tiles = nullptr;  // tile lists of the TMA filters (both stages)
-    int64_t tiles_cap = 0;
     int nkern = 0;               // CUDA kernels one batch of this slot launches
 };
 
@@ -216,6 +215,9 @@ struct densify_ctx {
     double t_us[K_COUNT] = {};
     int64_t t_n[K_COUNT] = {};
     int64_t kernel_launches = 0;   // CUDA kernels of completed batches
+    bool inject_wait_failure = false;   // densify_inject_wait_failure: armed for the next batch
+    int64_t batches = 0;                // batches launched
+    int max_busy = 0;                   // most batches on the GPU at once
 };
 
 namespace {
@@ -430,6 +432,21 @@ T *mapped_host(void *p) {
     return at.type == cudaMemoryTypeHost && at.devicePointer ? static_cast<T *>(at.devicePointer) : nullptr;
 }
 
+// Tile flags one frame needs (both stages): the most any TMA candidate of a stage needs, so that
+// the frame's reservation holds whichever kernel the autotuner picks; 0 without a TMA stage.
+int64_t tile_flag_words(const densify_params &p, int64_t W, int64_t H) {
+    int64_t words = 0;
+    for (int i = 0; i < p.num_stages; ++i) {
+        const int kind = p.num_stages == 1 ? 0 : (i == 0 ? 1 : 2);
+        const int64_t gw = kind == 1 ? (W + p.pool - 1) / p.pool : W, gh = kind == 1 ? (H + p.pool - 1) / p.pool : H;
+        int64_t most = 0;
+        for (const FilterSel &s : filter_candidates(p, kind, p.stage[i].radius))
+            if (s.tma) most = std::max<int64_t>(most, ((gw + s.tile_w - 1) / s.tile_w) * ((gh + s.tile_h - 1) / s.tile_h));
+        words += most;
+    }
+    return words;
+}
+
 Layout layout_of(const densify_params &p, const densify_frame *f) {
     Layout L;
     const int64_t W = f->K.width, H = f->K.height, npx = W * H;
@@ -463,6 +480,7 @@ Layout layout_of(const densify_params &p, const densify_frame *f) {
         if (host && f->out_coarse_valid) L.coarse_valid = take(Wc * Hc);
     }
     L.chunk = take(((npx + kBpChunk - 1) / kBpChunk) * kBpWarps * 4);
+    if (const int64_t tw = tile_flag_words(p, W, H)) L.tflags = take((uint64_t)tw * 4);
     L.own_depth = host || !f->out_depth;
     L.own_valid = host || !f->out_valid;
     if (L.own_depth) L.depth = take(npx * 4);
@@ -540,6 +558,18 @@ void build_frame_dev(densify_ctx *c, FrameRec &r) {
             host ? (f->out_coarse_valid ? (uint8_t *)(base + L.coarse_valid) : nullptr) : f->out_coarse_valid;
     }
     d.chunk_cnt = (uint32_t *)(base + L.chunk);
+    if (L.tflags) {   // the chosen kernels' tile counts (at most what the layout reserved)
+        int64_t n[2] = {0, 0};
+        for (int i = 0; i < c->p.num_stages; ++i) {
+            const FilterSel &s = c->sel[i];
+            if (!s.tma) continue;
+            const int gw = s.kind == 1 ? d.Wc : d.W, gh = s.kind == 1 ? d.Hc : d.H;
+            n[i] = (int64_t)ceil_div(gw, s.tile_w) * ceil_div(gh, s.tile_h);
+        }
+        d.tflags[0] = (int32_t *)(base + L.tflags);
+        d.tflags[1] = d.tflags[0] + n[0];
+        d.ntflags = (int32_t)(n[0] + n[1]);
+    }
     d.out_depth = L.own_depth ? (float *)(base + L.depth) : f->out_depth;
     d.out_valid = L.own_valid ? (uint8_t *)(base + L.valid) : f->out_valid;
     const bool contour = c->p.contour_threshold > 0.0f;
@@ -718,26 +748,11 @@ densify_status autotune(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &t
     return st;
 }
 
-// Tile flags of the batch's TMA filters: one word per tile of both stages
-// (contiguous, stage 1 first), pointers in the host descriptor (uploaded with it).
+// Tile geometry of the batch's TMA filters. The flags (one word per tile of both stages) are part
+// of each frame's scratch, reserved at admission, so a batch allocates nothing.
 densify_status prepare_tile_lists(densify_ctx *c, Slot &sl) {
     BatchDev &b = *sl.h;
-    const int n = b.n_frames;
-    const int64_t need = (int64_t)b.t1_pre[n] + b.t2_pre[n];
-    if (need > sl.tiles_cap) {
-        if (sl.d_tiles) {
-            CU(cudaStreamSynchronize(sl.stream), "tile list");
-            cudaFree(sl.d_tiles);
-            sl.d_tiles = nullptr;
-            sl.tiles_cap = 0;
-        }
-        const int64_t cap = std::max<int64_t>(need + need / 2, 4096);
-        CU(cudaMalloc(&sl.d_tiles, (size_t)cap * sizeof(int32_t)), "tile list allocation");
-        sl.tiles_cap = cap;
-    }
-    b.tl_flags[0] = sl.d_tiles;
-    b.tl_flags[1] = sl.d_tiles + b.t1_pre[n];
-    // tile geometry of the TMA stages: on the two-stage path the pooling kernel flags the first
+    // the flags themselves live in each frame's scratch (FrameDev::tflags); tile geometry of the TMA stages: on the two-stage path the pooling kernel flags the first
     // stage's tiles and the first filter's epilogue the second's; a single stage's are flagged by
     // the mark kernel
     for (int i = 0; i < 2; ++i) {
@@ -746,6 +761,7 @@ densify_status prepare_tile_lists(densify_ctx *c, Slot &sl) {
         b.tl_th[i] = on ? c->sel[i].tile_h : 0;
         b.tl_r[i] = on ? c->sel[i].radius : 0;
     }
+    b.tl_on = b.tl_th[0] > 0 || b.tl_th[1] > 0;
     return DENSIFY_OK;
 }
 
@@ -888,6 +904,25 @@ densify_status issue_kernels(densify_ctx *c, Slot &sl, cudaStream_t s, bool reco
     return DENSIFY_OK;
 }
 
+// Capture a slot's kernel sequence (its own device descriptor) into a graph, instantiate it and
+// upload it to the device ahead of its first launch.
+densify_status capture_slot(densify_ctx *c, Slot &sl) {
+    CU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+    densify_status st = issue_kernels(c, sl, c->cap_stream, c->p.timing != 0);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (st != DENSIFY_OK) {
+        if (g) cudaGraphDestroy(g);
+        return st;
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
+    e = cudaGraphInstantiate(&sl.exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+    CU(cudaGraphUpload(sl.exec, sl.stream), "graph upload");
+    return DENSIFY_OK;
+}
+
 densify_status launch_batch(densify_ctx *c, int si) {
     Slot &sl = c->slots[si];
     std::vector<uint64_t> tk;
@@ -946,19 +981,12 @@ densify_status launch_batch(densify_ctx *c, int si) {
            "rgb staging");
     }
     if (c->p.use_graphs) {
-        if (!sl.exec) {
-            CU(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal), "begin capture");
-            densify_status st = issue_kernels(c, sl, c->cap_stream, c->p.timing != 0);
-            cudaGraph_t g = nullptr;
-            cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
-            if (st != DENSIFY_OK) {
-                if (g) cudaGraphDestroy(g);
-                return st;
-            }
-            if (e != cudaSuccess) return cuda_fail(c, e, "end capture");
-            e = cudaGraphInstantiate(&sl.exec, g, 0);
-            cudaGraphDestroy(g);
-            if (e != cudaSuccess) return cuda_fail(c, e, "graph instantiate");
+        // the first batch captures, instantiates and uploads every slot's graph (the kernel sequence
+        // is fixed once the filter kernels are chosen), so no later batch pays for a capture
+        for (auto &other : c->slots) {
+            if (other.exec) continue;
+            densify_status st = capture_slot(c, other);
+            if (st != DENSIFY_OK) return st;
         }
         CU(cudaGraphLaunch(sl.exec, sl.stream), "graph launch");
     } else {
@@ -1006,6 +1034,10 @@ densify_status launch_batch(densify_ctx *c, int si) {
         if (c->p.emit_points && !r.L.count_direct)
             CU(cudaMemcpyAsync(r.fr.out_points_n, r.dev.points_n, 8, cudaMemcpyDeviceToHost, sl.stream), "count copy");
     }
+    if (c->inject_wait_failure) {   // test hook: the status a kernel sets when a bounded wait gives up (bit 0)
+        CU(cudaMemsetAsync(sl.d_status, 1, 1, sl.stream), "status injection");
+        c->inject_wait_failure = false;
+    }
     CU(cudaMemcpyAsync(sl.h_status, sl.d_status, sizeof(int32_t), cudaMemcpyDeviceToHost, sl.stream), "status copy");
     CU(cudaEventRecord(sl.done, sl.stream), "event record");
     for (uint64_t t : tk) {
@@ -1015,6 +1047,10 @@ densify_status launch_batch(densify_ctx *c, int si) {
     }
     sl.tickets = tk;
     sl.busy = true;
+    ++c->batches;
+    int busy = 0;
+    for (const auto &other : c->slots) busy += other.busy;
+    c->max_busy = std::max(c->max_busy, busy);
     return DENSIFY_OK;
 }
 
@@ -1109,7 +1145,6 @@ void destroy_resources(densify_ctx *c) {
         if (sl.d) cudaFree(sl.d);
         if (sl.h) cudaFreeHost(sl.h);
         if (sl.d_status) cudaFree(sl.d_status);
-        if (sl.d_tiles) cudaFree(sl.d_tiles);
         if (sl.h_status) cudaFreeHost(sl.h_status);
     }
     c->slots.clear();
@@ -1411,9 +1446,8 @@ densify_status densify_sigma_grad(densify_ctx *c, const densify_frame *frame, co
     const int64_t Wc = (frame->K.width + pool - 1) / pool, Hc = (frame->K.height + pool - 1) / pool;
     const uint64_t off_g1 = r.L.total;
     const uint64_t off_part = off_g1 + align_up((uint64_t)((Wc + 3) & ~3) * Hc * 8);
-    const uint64_t off_out = off_part + align_up((uint64_t)grid * 6 * 8);
     const uint64_t hdr = offsetof(BatchDev, f) + sizeof(FrameDev);
-    const uint64_t off_batch = off_out + 256;
+    const uint64_t off_batch = off_part + align_up((uint64_t)grid * 6 * 4);
     const uint64_t total = off_batch + align_up(hdr);
     if (total > c->arena.size()) return fail(c, DENSIFY_E_NOMEM, "frame scratch exceeds hbm_budget_bytes");
     if (!c->arena.alloc(total, &r.off)) return fail(c, DENSIFY_E_AGAIN, "scratch arena full");
@@ -1444,16 +1478,20 @@ densify_status densify_sigma_grad(densify_ctx *c, const densify_frame *frame, co
     }
     cudaStream_t s = c->slots[0].stream;
     BatchDev *bd = (BatchDev *)(base + off_batch);
-    double host_out[6] = {0, 0, 0, 0, 0, 0};
+    std::vector<float> host_part((size_t)grid * 6);
     cudaError_t e = cudaMemcpyAsync(bd, hb, hdr, cudaMemcpyHostToDevice, s);
     if (e == cudaSuccess) e = launch_prep(bd, c->grid[K_PREP], s);
     if (e == cudaSuccess) e = launch_project(bd, c->grid[K_PROJECT], s);
     if (e == cudaSuccess && ga.two_stage) e = launch_pool(bd, pool, c->grid[K_POOL], s);
-    if (e == cudaSuccess) e = launch_grad(bd, ga, gt, (double *)(base + off_part), grid, (double *)(base + off_out), s);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(host_out, base + off_out, sizeof(host_out), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = launch_grad(bd, ga, gt, (float *)(base + off_part), grid, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(host_part.data(), base + off_part, host_part.size() * sizeof(float), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     c->arena.release(r.off, total);
     if (e != cudaSuccess) return cuda_fail(c, e, "sigma gradient");
+    double host_out[6] = {0, 0, 0, 0, 0, 0};   // the blocks' FP32 partial sums, added on the host in FP64
+    for (int b = 0; b < grid; ++b)
+        for (int k = 0; k < 6; ++k) host_out[k] += (double)host_part[(size_t)b * 6 + k];
     const double n = host_out[1];
     *loss = n > 0 ? host_out[0] / n : 0.0;
     for (int k = 0; k < 4; ++k) grad[k] = n > 0 ? host_out[2 + k] / n : 0.0;
@@ -1492,7 +1530,8 @@ int32_t densify_describe(densify_ctx *c, char *buf, int32_t cap) {
         }
         out += "]}";
     }
-    out += "]}";
+    out += "], \"batches\": {\"launched\": " + std::to_string(c->batches) +
+           ", \"max_in_flight\": " + std::to_string(c->max_busy) + "}}";
     if (buf && cap > 0) {
         const size_t n = std::min<size_t>(out.size(), (size_t)cap - 1);
         std::memcpy(buf, out.data(), n);
@@ -1508,6 +1547,13 @@ void densify_reset_kernel_times(densify_ctx *c) {
         c->t_n[k] = 0;
     }
     c->kernel_launches = 0;
+}
+
+densify_status densify_inject_wait_failure(densify_ctx *c) {
+    if (!c) return fail(nullptr, DENSIFY_E_INVALID, "ctx is NULL");
+    if (c->dead) return DENSIFY_E_CUDA;
+    c->inject_wait_failure = true;
+    return DENSIFY_OK;
 }
 
 int64_t densify_kernel_launches(densify_ctx *c) {

@@ -123,6 +123,7 @@ _SIGS = {
     "densify_sigma_grad": ([C.c_void_p, C.POINTER(densify_frame), C.c_void_p, C.POINTER(C.c_double),
                             C.POINTER(C.c_double), C.POINTER(C.c_int64)], C.c_int),
     "densify_frame_noalloc": ([C.POINTER(densify_params), C.POINTER(densify_frame), C.c_void_p], C.c_int),
+    "densify_inject_wait_failure": ([C.c_void_p], C.c_int),
 }
 EXPORTED = tuple(_SIGS)
 
@@ -240,6 +241,11 @@ def densify_frame_noalloc(params: densify_params, frame: densify_frame, stream: 
     """Enqueue one frame on ``stream`` using the library's fixed device scratch
     (no allocation); returns the status."""
     return lib().densify_frame_noalloc(C.byref(params), C.byref(frame), C.c_void_p(stream or 0))
+
+
+def densify_inject_wait_failure(ctx) -> int:
+    """Test hook: the next batch reports a bounded wait that gave up (DENSIFY_E_CUDA)."""
+    return lib().densify_inject_wait_failure(ctx)
 
 
 # ---------------------------------------------------------------------------

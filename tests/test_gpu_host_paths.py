@@ -56,3 +56,31 @@ def test_two_batches_in_flight_on_own_streams():
     two = _run(views, torch, memory=1, batches_in_flight=2)
     for a, b in zip(one, two):
         _same(a, b, ("depth", "valid", "xyz", "rgba", "n"))
+
+
+def test_bounded_wait_failure_reaches_the_caller():
+    """The error path of a kernel's bounded wait, injected on the host: the batch's status word is
+    set (bit 0, as the kernels set it) and collecting its ticket returns DENSIFY_E_CUDA with the
+    bounded-wait message; the context stays failed. No wait on the GPU runs out."""
+    import torch
+    from paper_2601_01210_gb300 import Densifier, build
+    from paper_2601_01210_gb300 import densify as D
+    from paper_2601_01210_gb300.frames import FrameBuffers
+    build.build()
+    v = _views()[2]
+    with Densifier(dict(num_stages=2, stages=STAGES, launch_policy=1, max_batch=2, max_inflight=4)) as d:
+        b = FrameBuffers(v.camera, v.rgb, [(s.xyz, s.lidar_to_world) for s in v.scans])
+        t = d.submit(b.frame)
+        d.flush()
+        assert d.poll(t, -1) == 0                       # a healthy batch first
+        assert D.densify_inject_wait_failure(d.ctx) == D.DENSIFY_OK
+        t = d.submit(b.frame)
+        d.flush()
+        st = D.densify_poll(d.ctx, t, -1)
+        assert st == D.DENSIFY_E_CUDA
+        assert "bounded wait" in D.densify_last_error(d.ctx)
+        st, _ = D.densify_submit(d.ctx, b.frame)
+        assert st == D.DENSIFY_E_CUDA                   # the context stays failed
+        torch.cuda.synchronize()
+        assert D.densify_destroy(d.ctx) == D.DENSIFY_OK   # and still tears down cleanly
+        d.ctx = None
