@@ -17,9 +17,9 @@ struct GradArgs {
     int32_t pool;
 };
 
-// grid: persistent CTAs; part: grid x 6 doubles of scratch; out: 6 doubles
-// (squared-error sum, pixel count, gradient sums for sp1, sc1, sp2, sc2).
-cudaError_t launch_grad(const BatchDev *b, const GradArgs &ga, const float *gt, double *part, int grid, double *out,
+// grid: persistent CTAs; part: grid x 6 floats, one row per block (squared-error
+// sum, pixel count, gradient sums for sp1, sc1, sp2, sc2), added by the caller.
+cudaError_t launch_grad(const BatchDev *b, const GradArgs &ga, const float *gt, float *part, int grid,
                         cudaStream_t s);
 
 }  // namespace dz

@@ -10,8 +10,9 @@
 // first-stage result, so d out2 / d theta1 = sum w2 beta2 d out1(c(q)) / d theta1
 // / sum w2 beta2 with c(q) the pooled pixel under q. Every pixel's window is
 // evaluated with exponents shifted by their maximum (the factor cancels).
-// Per-pixel terms are FP32; every block sums its pixels and writes one row of
-// partial sums, which a single block adds in FP64 in block order.
+// Everything on the device is FP32: per-pixel terms, each thread's running
+// sums, a pairwise (shuffle-tree) sum per warp and per block; every block
+// writes one row of partial sums, which the host adds in FP64.
 #include "desc.cuh"
 #include "grad.h"
 
@@ -111,7 +112,7 @@ __global__ void __launch_bounds__(kThreads) grad_coarse_kernel(const BatchDev *_
 // Full-resolution stage (the second of two, or the only one): per pixel with
 // ground truth, the squared error and its gradient; per-block partial sums.
 __global__ void __launch_bounds__(kThreads) grad_full_kernel(const BatchDev *__restrict__ B, const GradArgs ga,
-                                                             const float *__restrict__ gt, double *__restrict__ part) {
+                                                             const float *__restrict__ gt, float *__restrict__ part) {
     __shared__ float red[kThreads / 32][6];
     float acc[6] = {0, 0, 0, 0, 0, 0};   // loss, n, d/d(sp1, sc1, sp2, sc2) -- or (sp, sc, 0, 0) single
     const int nf = B->n_frames;
@@ -183,22 +184,19 @@ __global__ void __launch_bounds__(kThreads) grad_full_kernel(const BatchDev *__r
     if (lane == 0)
         for (int j = 0; j < 6; ++j) red[warp][j] = acc[j];
     __syncthreads();
-    if (threadIdx.x < 6) {
-        double s = 0.0;
-        for (int w = 0; w < kThreads / 32; ++w) s += (double)red[w][threadIdx.x];
-        part[(int64_t)blockIdx.x * 6 + threadIdx.x] = s;
+    if (threadIdx.x < 6) {   // pairwise over the block's warps
+        float v[kThreads / 32];
+#pragma unroll
+        for (int w = 0; w < kThreads / 32; ++w) v[w] = red[w][threadIdx.x];
+#pragma unroll
+        for (int h = kThreads / 64; h > 0; h >>= 1)
+#pragma unroll
+            for (int w = 0; w < h; ++w) v[w] += v[w + h];
+        part[(int64_t)blockIdx.x * 6 + threadIdx.x] = v[0];
     }
 }
 
-__global__ void grad_reduce_kernel(const double *__restrict__ part, int nblocks, double *__restrict__ out) {
-    if (threadIdx.x < 6) {
-        double s = 0.0;
-        for (int b = 0; b < nblocks; ++b) s += part[(int64_t)b * 6 + threadIdx.x];
-        out[threadIdx.x] = s;
-    }
-}
-
-cudaError_t launch_grad(const BatchDev *b, const GradArgs &ga, const float *gt, double *part, int grid, double *out,
+cudaError_t launch_grad(const BatchDev *b, const GradArgs &ga, const float *gt, float *part, int grid,
                         cudaStream_t s) {
     if (ga.two_stage) {
         grad_coarse_kernel<<<grid, kThreads, 0, s>>>(b, ga);
@@ -206,9 +204,6 @@ cudaError_t launch_grad(const BatchDev *b, const GradArgs &ga, const float *gt, 
         if (e != cudaSuccess) return e;
     }
     grad_full_kernel<<<grid, kThreads, 0, s>>>(b, ga, gt, part);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return e;
-    grad_reduce_kernel<<<1, 32, 0, s>>>(part, grid, out);
     return cudaGetLastError();
 }
 
