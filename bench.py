@@ -38,8 +38,10 @@ sys.path.insert(0, ROOT)
 
 METRIC = "1080p dense-depth frames/s (3 merged LiDAR scans, two-stage JBF r=4@1/3 + r=2, coloured points)"
 UNIT = "frames/s"
-# issue slots of one filter tap in each arithmetic form (see the roofline note below)
+# issue slots of one filter tap in each arithmetic form: the last-resort peak model, used only when
+# neither the committed nor a live measurement of the instruction rates is available
 TAP_INSTR = {"fp32": 10.0, "fp32_expanded": 6.0, "fp32_expanded_pairs": 3.5}
+ALU_PEAKS = os.path.join(ROOT, "profiles", "alu_peaks.json")
 STAGES = ((4, 5.0, 20.0), (2, 5.0, 20.0))
 L2_FLUSH_BYTES = 256 << 20
 
@@ -67,7 +69,7 @@ def parse():
     ap.add_argument("--kernel-timing", type=int, default=2,
                     help="events inside the timed steps: 2 around the full-resolution filter only (the "
                          "per-kernel table then comes from a separate untimed pass), 1 around every kernel")
-    ap.add_argument("--serve-seconds", type=float, default=10.0,
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="duration of the paper-rate serving run (16 viewpoints x 30 fps)")
     return ap.parse_args()
 
@@ -100,10 +102,13 @@ def make_mixed_views(n, seed0):
         return list(ex.map(_gen_mixed, jobs))
 
 
-def serve_measure(views, dev, stream, seconds, precision, autotune=1):
-    """Frames/s and p50/p99 latency of the serving loop: single-frame launches
-    against continuous batching, at the paper's load (16 viewpoints x 30 fps,
-    Poisson-jittered) and at a saturating load."""
+def serve_measure(views, dev, seconds, autotune=1):
+    """Frames/s and p50/p99 latency of the serving loop at the paper's load (16 viewpoints x 30 fps,
+    Poisson-jittered, ``seconds`` long) and at a saturating load, in three modes: single-frame
+    launches in FP32, continuous batching in FP32 and continuous batching in FP16 (so that the
+    effect of batching and the effect of precision are measured apart). Each context owns its
+    streams (two batches in flight overlap on the GPU). The loop is a host Python busy-poll, so
+    the latencies include its turn time."""
     from paper_2601_01210_gb300 import Densifier
     from paper_2601_01210_gb300.frames import FrameBuffers
     from paper_2601_01210_gb300.serve import ServeLoop, poisson_arrivals
@@ -112,21 +117,22 @@ def serve_measure(views, dev, stream, seconds, precision, autotune=1):
     frames = [[b.frame for b in r] for r in ring]
     modes = {
         "single_frame_fp32": dict(max_batch=1, batches_in_flight=1, precision=0),
-        "batched_fp16" if precision else "batched_fp32": dict(max_batch=16, batches_in_flight=2,
-                                                              precision=precision),
+        "batched_fp32": dict(max_batch=16, batches_in_flight=2, precision=0),
+        "batched_fp16": dict(max_batch=16, batches_in_flight=2, precision=1),
     }
     loads = {"paper_rate_30fps": (30.0, seconds), "saturating_1000fps": (1000.0, 2.0)}
     out = {}
     for mname, extra in modes.items():
         params = dict(num_stages=2, stages=STAGES, max_inflight=32, launch_policy=0, autotune=autotune,
                       hbm_budget_bytes=4 << 30, **extra)
-        with Densifier(params, device=dev.index, stream=stream.cuda_stream) as d:
-            # warm-up (graph capture, first-touch)
-            ServeLoop(d, frames).run(poisson_arrivals(len(views), 200.0, 0.1, seed=9), 0.1)
+        with Densifier(params, device=dev.index) as d:
+            # warm-up: the first batch tunes the filters and captures every slot's graph; then a
+            # saturating burst sends batches of every size through both slots
+            ServeLoop(d, frames).run(poisson_arrivals(len(views), 1000.0, 0.2, seed=9), 0.2)
             for lname, (fps, dur) in loads.items():
                 arr = poisson_arrivals(len(views), fps, dur, seed=11)
                 st = ServeLoop(d, frames).run(arr, dur, drain_s=10.0)
-                out[f"{mname}/{lname}"] = st.summary()
+                out[f"{mname}/{lname}"] = dict(st.summary(), batches=d.describe()["batches"])
     return out
 
 
@@ -584,7 +590,7 @@ def ours_arm(a, rank, world, local_rank):
                "host_link": host_link_bounds(link, h2d, d2h, B, world)}
     serving = None
     if not a.no_serve and rank == 0:
-        serving = serve_measure(mixed_views, dev, stream, a.serve_seconds, 1, a.autotune)
+        serving = serve_measure(mixed_views, dev, a.serve_seconds, a.autotune)
     fp16 = None
     if not a.no_fp16:
         fp16 = fp16_measure(a, bufs, params, dev, stream, flush_buf, taps2)
@@ -596,13 +602,37 @@ def ours_arm(a, rank, world, local_rank):
     except Exception:
         pass
     sm_max = peaks.get("sm_max_mhz", 2070.0)
-    # ALU peak of the filter: 152 SMs x 4 SMSPs x 32 lanes issue one instruction per clock. A tap of the
-    # expanded form takes 6 (3 fma give the exponent, 1 ex2, 2 fma accumulate), the difference form 10; the
-    # paired form runs two taps in 3 two-lane fma, 2 ex2 and 2 two-lane fma: 3.5 a tap.
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    form1 = kernel_choice["stages"][0]["chosen"].get("form", "fp32_expanded")
     form2 = kernel_choice["stages"][-1]["chosen"].get("form", "fp32_expanded")
-    tap_instr = TAP_INSTR.get(form2, 6.0)
-    peak_gtap = sms * 128 / tap_instr * sm_max * 1e6 / 1e9
+    # ALU peak of the filters: the measured instruction rates (profiles/alu_peaks.json, the microbenchmark
+    # of the filter forms' arithmetic on this GPU model) give each form's tap peak as the least of the
+    # issue, FMA-pipe and ex2 bounds; a live run of the same microbenchmark is reported beside it
+    alu_file = alu_live = None
+    try:
+        alu_file = json.load(open(ALU_PEAKS))
+    except Exception:
+        pass
+    try:
+        from paper_2601_01210_gb300 import alu_peaks
+        alu_live = alu_peaks.measure(local_rank)
+    except Exception as ex:   # the bench still reports against the committed measurement
+        alu_live = {"error": str(ex)[:200]}
+    alu_src = alu_file if alu_file else (alu_live if "tap_peaks" in (alu_live or {}) else None)
+
+    def tap_peak(form):
+        """(taps/s, basis) of a filter form."""
+        if alu_src and form in alu_src["tap_peaks"]:
+            t = alu_src["tap_peaks"][form]
+            return t["taps_per_s"], (f"{'profiles/alu_peaks.json' if alu_file else 'live microbenchmark'}: "
+                                     f"{t['taps_per_sm_clk']:.2f} taps per SM clock ({t['binds']} bound of "
+                                     f"{t['bounds_taps_per_sm_clk']}) x {alu_src['sms']} SMs x "
+                                     f"{alu_src['sm_mhz_median'] or alu_src['sm_max_mhz']:.0f} MHz, measured")
+        ti = TAP_INSTR.get(form, 6.0)
+        return sms * 128 / ti * sm_max * 1e6, f"{sms} SMs x 128 lanes / {ti:g} instructions per tap x {sm_max:.0f} MHz (model)"
+
+    peak2, basis2 = tap_peak(form2)
+    peak_gtap = peak2 / 1e9
     s2 = times.get("jbf_stage2", (0.0, 1))
     avg_us = s2[0] / max(1, s2[1])
     achieved = taps2 / (avg_us * 1e-6) / 1e9 if avg_us > 0 else 0.0
@@ -611,8 +641,7 @@ def ours_arm(a, rank, world, local_rank):
     # each kernel's roofline time for the step's work (HBM-bound kernels at the measured copy rate,
     # the filters at the ALU peak of their form), against its measured time; their sum is the path's roof
     hbm = peaks.get("hbm_gbs", 6758.5) * 1e9
-    form1 = kernel_choice["stages"][0]["chosen"].get("form", "fp32_expanded")
-    alu = lambda form: sms * 128 / TAP_INSTR.get(form, 6.0) * sm_max * 1e6   # taps per second
+    alu = lambda form: tap_peak(form)[0]   # taps per second
     roof_us = {k: work[k] / hbm * 1e6 for k in ("prep_compose_clear", "project_zbuf", "pool3", "tile_mark1",
                                                 "bp_count", "bp_write")}
     roof_us["jbf_stage1"] = work["taps1"] / alu(form1) * 1e6
@@ -624,7 +653,7 @@ def ours_arm(a, rank, world, local_rank):
     path_roof = {"ideal_us_per_step": round(ideal, 2), "measured_us_per_step": round(1000.0 * total_ms / a.steps, 2),
                  "frac": round(ideal / (1000.0 * total_ms / a.steps), 3),
                  "basis": "sum over the path's kernels of algorithmic work / peak (HBM: measured copy rate; "
-                          "filters: ALU issue peak of their form)", "kernels": kroof}
+                          "filters: measured tap peak of their form)", "kernels": kroof}
     cpu = None
     if not a.no_cpu_baseline:
         rate, dt = cpu_oracle_rate(views, a.cpu_frames, a.cpu_procs)
@@ -652,8 +681,8 @@ def ours_arm(a, rank, world, local_rank):
                      "unit": "Gtap/s", "frac": achieved / peak_gtap if peak_gtap else None,
                      "traffic": profiled_traffic("jbf_stage2", kernel_choice["stages"][-1]["chosen"]),
                      "traffic_unit": "bytes per launch (ncu capture of the same kernel variant)",
-                     "peak_basis": f"{sms} SMs x 128 lanes / {tap_instr:g} instructions per tap ({form2}) x "
-                                   f"{sm_max:.0f} MHz",
+                     "peak_basis": f"{form2}: {basis2}",
+                     "peak_live": (alu_live or {}).get("tap_peaks", {}).get(form2, alu_live),
                      "taps_per_launch": taps2, "avg_launch_us": avg_us},
         "kernels": ktable,
         "path_roofline": path_roof,
@@ -667,7 +696,10 @@ def ours_arm(a, rank, world, local_rank):
         "cpu_baseline": cpu,
         "fp16": fp16 and {"precision": "full-resolution stage: FP16 guide and weights, FP32 sums", **fp16},
         "serving": serving and {"viewpoints": "16 (1080p/720p/540p mixed, 1-3 sweeps each)",
-                                "note": "frames/s and latency from submit-arrival to completion seen by the loop",
+                                "paper_rate_seconds": a.serve_seconds,
+                                "note": "frames/s and latency from arrival to completion seen by the loop (a host "
+                                        "Python busy-poll: its turn time is part of every latency); batches: "
+                                        "launched so far by the context and the most in flight at once",
                                 **serving},
     }
     print(json.dumps(out), flush=True)

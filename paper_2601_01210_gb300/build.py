@@ -49,8 +49,29 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
+PEAKS_SRC = os.path.join(PKG, "peaks", "alu_peaks.cu")
+PEAKS_LIB = os.path.join(PKG, "libalupeaks.so")
+
+
+def build_peaks(force: bool = False) -> str:
+    """The instruction-rate microbenchmark (libalupeaks.so), a library of its own: it is not part of
+    the densification ABI."""
+    if not force and os.path.exists(PEAKS_LIB) and os.path.getmtime(PEAKS_LIB) >= max(
+            os.path.getmtime(PEAKS_SRC), os.path.getmtime(os.path.abspath(__file__))):
+        return PEAKS_LIB
+    tmp = PEAKS_LIB + f".tmp{os.getpid()}"
+    cmd = [nvcc(), "-shared", PEAKS_SRC, "-o", tmp] + ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
+                                                             "-Xcompiler", "-fvisibility=hidden"]
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc failed on {PEAKS_SRC}:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, PEAKS_LIB)
+    return PEAKS_LIB
+
+
 def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -> str:
     if not force and up_to_date():
+        build_peaks()
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
@@ -72,7 +93,9 @@ def build(force: bool = False, verbose: bool = False, jobs: int | None = None) -
 
     srcs = _sources()
     with cf.ThreadPoolExecutor(max_workers=jobs or min(8, os.cpu_count() or 4)) as ex:
+        peaks = ex.submit(build_peaks, force)
         objs = list(ex.map(compile_one, srcs))
+        peaks.result()
     tmp = LIB + f".tmp{os.getpid()}"
     cmd = [cc, "-shared", "-o", tmp] + objs + ARCH + ["-Xlinker", "--version-script=" + os.path.join(CSRC, "densify.map")]
     r = subprocess.run(cmd, capture_output=True, text=True)

@@ -99,3 +99,26 @@ def test_host_link_bounds():
     assert b["bound_frames_per_s"] == round(8 / 0.040 * 2, 1)
     assert b["serial_frames_per_s"] == round(8 / 0.050 * 2, 1)
     assert b["h2d_GBps"] == 200.0 and b["d2h_GBps"] == 100.0
+
+
+def test_tap_peaks_take_the_binding_bound():
+    """The filter forms' tap peaks are the least of the issue, FMA-pipe and ex2 bounds of the
+    measured per-SM-per-clock rates."""
+    from paper_2601_01210_gb300 import alu_peaks
+    rates = {"ffma": 128.0, "ffma2": 64.0, "ex2_f32": 32.0, "ex2_f16x2": 32.0, "tap_paired": 20.0}
+    p = alu_peaks.tap_peaks(rates)
+    # paired: issue 128 / 3.5 = 36.6, two-lane FMA 64 / 2.5 = 25.6, ex2 32 / 1 = 32
+    assert p["fp32_expanded_pairs"]["binds"] == "fma_pipe"
+    assert abs(p["fp32_expanded_pairs"]["taps_per_sm_clk"] - 25.6) < 1e-9
+    # expanded: issue 128 / 6 = 21.3, FMA 128 / 5 = 25.6, ex2 32
+    assert p["fp32_expanded"]["binds"] == "issue"
+    rates["ex2_f32"] = 16.0
+    assert alu_peaks.tap_peaks(rates)["fp32_expanded_pairs"]["binds"] == "ex2"
+
+
+def test_alu_microbenchmark_library_builds():
+    import subprocess
+    from paper_2601_01210_gb300 import build
+    lib = build.build_peaks()
+    out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True, check=True).stdout
+    assert " T alu_peak_run" in out
