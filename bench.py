@@ -62,6 +62,8 @@ def parse():
                     help="oracle worker processes (one single-threaded oracle per host core)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-fp16", action="store_true", help="skip the FP16-form measurement")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the 320x240 single-stage (FP32, FP16) and uneven 12-view workloads")
     ap.add_argument("--autotune", type=int, default=1, help="1: pick filter kernels on the first batch")
     ap.add_argument("--kernels", default="",
                     help="STAGE1,STAGE2 filter kernels to use instead of tuning (candidate names as in the "
@@ -171,6 +173,171 @@ def fp16_measure(a, bufs, params, dev, stream, flush_buf, taps2):
     return {"value": B * a.steps / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms / a.steps,
             "jbf_stage2_avg_us": avg, "jbf_stage2_gtap_s": taps2 / (avg * 1e-6) / 1e9 if avg > 0 else None,
             "kernels": {k: round(v[0] / max(1, v[1]), 3) for k, v in kt.items()}, "filter_kernels": choice}
+
+
+# ---------------------------------------------------------------------------
+# the other workloads: 320x240 single stage (FP32 and FP16) and the uneven 12-view batch
+# ---------------------------------------------------------------------------
+QVGA_STAGES = ((4, 3.0, 20.0),)          # 9x9 window, sigma_p 3 px, sigma_c 20
+UNEVEN_RES = ["1080p"] * 4 + ["720p"] * 4 + ["540p"] * 4
+
+
+def _gen_qvga(seed):
+    import scene
+    return scene.make_workload("qvga_1scan", seed)
+
+
+def _gen_uneven(args):
+    import scene
+    seed, i = args
+    return scene.make_batch_view(seed, UNEVEN_RES[i], i, len(UNEVEN_RES))
+
+
+def make_config_views(n_qvga=16, seed_qvga=1000, seed_uneven=1003):
+    """Distinct views of the 320x240 workload and the 12 uneven views (spawn pool, before CUDA)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    with cf.ProcessPoolExecutor(max(1, min(12, (os.cpu_count() or 2) - 1)), mp_context=mp.get_context("spawn")) as ex:
+        qvga = list(ex.map(_gen_qvga, [seed_qvga + i for i in range(n_qvga)]))
+        uneven = list(ex.map(_gen_uneven, [(seed_uneven, i) for i in range(len(UNEVEN_RES))]))
+    return {"qvga": qvga, "uneven": uneven}
+
+
+EXTRA_CONFIGS = {
+    # BASELINE configs 0 / 2: one viewpoint at 320x240, one 32x256 sweep, single-stage 9x9 window
+    "qvga_1scan_single_stage_fp32": dict(views="qvga", stages=QVGA_STAGES, precision=0, batch=32),
+    "qvga_1scan_single_stage_fp16": dict(views="qvga", stages=QVGA_STAGES, precision=1, batch=32),
+    # config 3: 12 uneven views in one batched, graph-captured launch sequence, FP16, autotuned
+    "uneven_12view_two_stage_fp16": dict(views="uneven", stages=STAGES, precision=1, batch=12),
+    # the 1080p three-scan views with the single-stage alternative: one 15x15 window at full resolution
+    "1080p_3scan_single_stage_15x15_fp32": dict(views="main", stages=((7, 5.0, 20.0),), precision=0, batch=4),
+}
+
+
+def config_measure(name, cfg, views, a, dev, stream, flush_buf, tap_peak, hbm):
+    """Device frames/s of one workload (same method as the headline: inputs resident, L2 flushed before
+    every step, CUDA events around the launch), per-kernel times from a separate pass, the path roofline,
+    and the probe outputs (depth, validity) of each distinct view for the CPU leg's error report."""
+    import torch
+    from paper_2601_01210_gb300 import Densifier
+    from paper_2601_01210_gb300.frames import FrameBuffers
+    stages, B, ns = cfg["stages"], cfg["batch"], len(cfg["stages"])
+
+    def fb(v, **kw):
+        return FrameBuffers(v.camera, v.rgb, [(s.xyz, s.lidar_to_world) for s in v.scans], device=dev,
+                            num_stages=ns, **kw)
+
+    bufs = [fb(views[i % len(views)]) for i in range(B)]
+    # max_batch above the step's frames: the batch leaves at the flush, between the step's events
+    params = dict(num_stages=ns, stages=stages, precision=cfg["precision"], max_batch=min(64, 2 * B),
+                  max_inflight=max(B, 16),
+                  launch_policy=1, timing=2, autotune=a.autotune, batches_in_flight=1,
+                  hbm_budget_bytes=max(2 << 30, B * 48 << 20))
+
+    def run(d, frames, k, ev=None):
+        ts = [d.submit(f.frame) for f in frames]
+        flush_buf.fill_(k)
+        if ev:
+            ev[0].record(stream)
+        d.flush(-1)
+        if ev:
+            ev[1].record(stream)
+        for t in ts:
+            d.poll(t, -1)
+
+    with Densifier(params, device=dev.index, stream=stream.cuda_stream) as d:
+        for k in range(max(3, a.warmup)):
+            run(d, bufs, k)
+        torch.cuda.synchronize()
+        d.reset_kernel_times()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+        for k in range(a.steps):
+            run(d, bufs, k, evs[k])
+        torch.cuda.synchronize()
+        step_ms = [s_.elapsed_time(e_) for s_, e_ in evs]
+        choice = d.describe()
+        launches = d.kernel_launches()
+        probe = [fb(v, debug=True) for v in views[:min(len(views), 16)]]
+        run(d, probe, 0)
+        torch.cuda.synchronize()
+    with Densifier(dict(params, timing=1), device=dev.index, stream=stream.cuda_stream) as d3:
+        for k in range(3 + 10):
+            if k == 3:
+                torch.cuda.synchronize()
+                d3.reset_kernel_times()
+            run(d3, bufs, k)
+        torch.cuda.synchronize()
+        kt = d3.kernel_times()
+    ktable = {k: {"avg_us": round(v[0] / max(1, v[1]), 3), "launches": v[1]} for k, v in kt.items()}
+    # algorithmic work of one step: the batch cycles through the probed views
+    works = [step_work(b, v, single_radius=stages[0][0] if ns == 1 else None) for b, v in zip(probe, views)]
+    work = {k: sum(works[i % len(works)][k] for i in range(B)) for k in works[0]}
+    forms = [st["chosen"].get("form", "fp32") for st in choice["stages"]]
+    roof = {k: work[k] / hbm * 1e6 for k in ("prep_compose_clear", "project_zbuf", "pool3", "tile_mark1", "bp_count",
+                                              "bp_write") if k in work}
+    roof["jbf_stage1"] = work["taps1"] / tap_peak(forms[0])[0] * 1e6
+    if ns == 2:
+        roof["jbf_stage2"] = work["taps2"] / tap_peak(forms[1])[0] * 1e6
+    kroof = {k: {"roof_us": round(r, 2), "measured_us": ktable[k]["avg_us"],
+                 "frac": round(r / ktable[k]["avg_us"], 3) if ktable[k]["avg_us"] else None}
+             for k, r in roof.items() if k in ktable}
+    ms = sum(step_ms) / len(step_ms)
+    ideal = sum(v["roof_us"] for v in kroof.values())
+    sizes = sorted({f"{v.camera.width}x{v.camera.height}" for v in views})
+    out = {
+        "config": {"workload": name, "frames_per_step": B, "distinct_views": len(views), "resolutions": sizes,
+                   "stages": [list(st) for st in stages], "precision": "fp16" if cfg["precision"] else "fp32",
+                   "l2": "flushed (256 MiB write) before every step", "launch": "batched CUDA graph"},
+        "value": B / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms,
+        "latency_ms_per_step": {"p50": sorted(step_ms)[len(step_ms) // 2], "max": max(step_ms)},
+        "gpu_launches": launches,
+        "kernels": ktable,
+        "path_roofline": {"ideal_us_per_step": round(ideal, 2), "measured_us_per_step": round(1000 * ms, 2),
+                          "frac": round(ideal / (1000 * ms), 3), "kernels": kroof},
+        "filter_kernels": choice,
+    }
+    outputs = [{"depth": b.depth.cpu().numpy(), "valid": b.valid.cpu().numpy()} for b in probe]
+    return out, outputs
+
+
+def config_cpu_leg(name, cfg, views, outputs, procs):
+    """The oracle on the config's distinct views: its rate on the host cores and, per view, the GPU depth
+    against it (valid masks compared exactly; max and p99 absolute error, max relative error)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    import numpy as np
+    n = len(outputs)
+    t0 = time.perf_counter()
+    with cf.ProcessPoolExecutor(max(1, min(procs, n)), mp_context=mp.get_context("spawn")) as ex:
+        refs = list(ex.map(_oracle_config_frame, [(views[i], cfg["stages"]) for i in range(n)]))
+    dt = time.perf_counter() - t0
+    per_view = []
+    for v, g, (depth, valid) in zip(views, outputs, refs):
+        m = valid.astype(bool)
+        err = np.abs(g["depth"].astype(np.float64) - depth)[m] if m.any() else np.zeros(1)
+        rel = err / depth[m] if m.any() else np.zeros(1)
+        bound = np.maximum(1e-3, 1e-3 * depth[m]) if cfg["precision"] else 1e-4 * depth[m]
+        per_view.append({"view": f"{v.camera.width}x{v.camera.height}", "valid_mask_exact": bool(
+            np.array_equal(g["valid"], valid)), "max_abs_m": float(err.max()), "p99_abs_m": float(np.percentile(err, 99)),
+            "max_rel": float(rel.max()), "pixels_over_bar": int((err > bound).sum()) if m.any() else 0})
+    return {"value": n / dt, "unit": UNIT, "cores": min(procs, n), "kind": "oracle",
+            "sample": f"{n} distinct views of the workload, FP64, one single-threaded oracle process per view "
+                      f"(start-up included), {dt:.1f} s",
+            "error_vs_oracle": {"bar": "valid masks exact; depth within 1e-4 relative (FP32) or 1 mm absolute / "
+                                       "1e-3 relative (FP16)", "per_view": per_view,
+                                "all_masks_exact": all(p["valid_mask_exact"] for p in per_view),
+                                "pixels_over_bar": sum(p["pixels_over_bar"] for p in per_view),
+                                "max_abs_m": max(p["max_abs_m"] for p in per_view),
+                                "max_rel": max(p["max_rel"] for p in per_view)}}
+
+
+def _oracle_config_frame(args):
+    import oracle
+    v, stages = args
+    oracle.build()
+    o = oracle.densify_view(v, num_stages=len(stages), stages=stages, emit_points=False)
+    return o["depth"], o["valid"]
 
 
 def make_views(n, seed0, rank=0):
@@ -375,11 +542,24 @@ def valid_taps_stage1(cnt_pos, r=4):
     return int(correlate(cnt_pos.astype(np.float64), np.ones((2 * r + 1, 2 * r + 1)), mode="constant").sum())
 
 
-def step_work(b, view, pool=3):
+def step_work(b, view, pool=3, single_radius=None):
     """Algorithmic work of every kernel of the path for one frame (probe buffers with debug outputs):
-    bytes each HBM-bound kernel must move at least, observed taps of both filters."""
+    bytes each HBM-bound kernel must move at least, observed taps of the filters. single_radius:
+    the single-stage form at that radius (no pooling; the mark kernel reads the z-buffer)."""
     import numpy as np
     W, H = b.W, b.H
+    if single_radius is not None:
+        z = b.zbuf.cpu().numpy().view(np.uint32)
+        obs = z != 0x7F800000
+        npts = sum(s.xyz.shape[0] for s in view.scans)
+        return {
+            "prep_compose_clear": 4 * W * H,
+            "project_zbuf": 12 * npts + 4 * int(obs.sum()),
+            "tile_mark1": 4 * W * H,
+            "bp_count": W * H,
+            "bp_write": 8 * W * H + 16 * b.n_points(),
+            "taps1": valid_taps_stage1(obs, single_radius),
+        }
     Wc, Hc = -(-W // pool), -(-H // pool)
     z = b.zbuf.cpu().numpy().view(np.uint32)
     obs = z != 0x7F800000
@@ -452,6 +632,7 @@ def ours_arm(a, rank, world, local_rank):
                 f.write(f"kind={kind},r={st[0]},half=0,px=2^{px.bit_length() - 1} {name}\n")
         a.autotune = 1
     mixed_views = make_mixed_views(16, 4004) if (not a.no_serve and rank == 0) else None
+    config_views = make_config_views() if (not a.no_configs and rank == 0) else None
     build.build()
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
@@ -654,8 +835,18 @@ def ours_arm(a, rank, world, local_rank):
                  "frac": round(ideal / (1000.0 * total_ms / a.steps), 3),
                  "basis": "sum over the path's kernels of algorithmic work / peak (HBM: measured copy rate; "
                           "filters: measured tap peak of their form)", "kernels": kroof}
+    configs, config_outputs = {}, {}
+    cviews = lambda cfg: views if cfg["views"] == "main" else config_views[cfg["views"]]
+    if config_views:
+        for cname, cfg in EXTRA_CONFIGS.items():
+            configs[cname], config_outputs[cname] = config_measure(
+                cname, cfg, cviews(cfg), a, dev, stream, flush_buf, tap_peak, hbm)
     cpu = None
     if not a.no_cpu_baseline:
+        for cname, cfg in EXTRA_CONFIGS.items():   # each workload's oracle rate and error report
+            if cname in configs:
+                configs[cname]["cpu_baseline"] = config_cpu_leg(cname, cfg, cviews(cfg), config_outputs[cname],
+                                                                a.cpu_procs)
         rate, dt = cpu_oracle_rate(views, a.cpu_frames, a.cpu_procs)
         cpu = {"value": rate, "unit": UNIT, "cores": a.cpu_procs, "kind": "oracle",
                "sample": f"{a.cpu_frames} frames of the same workload, FP64, one single-threaded oracle process "
@@ -695,6 +886,7 @@ def ours_arm(a, rank, world, local_rank):
         "e2e": e2e,
         "cpu_baseline": cpu,
         "fp16": fp16 and {"precision": "full-resolution stage: FP16 guide and weights, FP32 sums", **fp16},
+        "configs": configs or None,
         "serving": serving and {"viewpoints": "16 (1080p/720p/540p mixed, 1-3 sweeps each)",
                                 "paper_rate_seconds": a.serve_seconds,
                                 "note": "frames/s and latency from arrival to completion seen by the loop (a host "

@@ -136,7 +136,12 @@ typedef struct densify_stage {
  *                 log2(e) / (2 sigma_p^2) * 2 r^2 <= 100, else the difference
  *                 form; at radius 2 of a full-resolution stage also on pairs of
  *                 output columns in two-lane FP32 instructions (same rounding
- *                 as the scalar expanded form). 1: the plain kernels everywhere (difference form,
+ *                 as the scalar expanded form). For a single stage on the
+ *                 z-buffer the autotuner also weighs Algorithm 1's scatter
+ *                 form: every observed neighbour adds its weighted depth and
+ *                 weight into the sums of the pixels its window reaches (same
+ *                 weights up to a per-pixel factor that cancels; the sums are
+ *                 added in a fixed order, so results repeat exactly). 1: the plain kernels everywhere (difference form,
  *                 for comparison). 2: the TMA kernels in the difference form
  *                 only (the same bits as 1).
  *   autotune      1: on the first batch, time every kernel that can run each

@@ -30,13 +30,17 @@ import time
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libalupeaks.so")
 
-OPS = {"ffma": 0, "ffma2": 1, "ex2_f32": 2, "ex2_f16x2": 3, "tap_paired": 4, "red_shared_f32": 5}
+OPS = {"ffma": 0, "ffma2": 1, "ex2_f32": 2, "ex2_f16x2": 3, "tap_paired": 4, "red_shared_f32": 5, "hfma2": 6,
+       "tap_fp16": 7}
 ISSUE_PER_SM_CLK = 128.0   # 4 schedulers x one 32-lane warp instruction per clock
 # per tap of each filter form: (FP32 FMA-pipe thread-instructions, of which two-lane, ex2 thread-instructions)
 FORMS = {
     "fp32": {"fma": 9.0, "fma2": 0.0, "ex2": 1.0},                 # difference form: 3 sub, 3 fma, 1 fma, 2 fma
     "fp32_expanded": {"fma": 5.0, "fma2": 0.0, "ex2": 1.0},        # 3 fma exponent, 2 fma sums
     "fp32_expanded_pairs": {"fma": 0.0, "fma2": 2.5, "ex2": 1.0},  # per tap: 1.5 + 1 two-lane fma
+    # scatter (Algorithm 1): 3 fma + 1 add exponent, 2 mul (weight times depth, times count), one load of
+    # the target colour, two adds into shared memory
+    "fp32_scatter": {"fma": 6.0, "fma2": 0.0, "ex2": 1.0, "lds": 1.0, "red": 2.0},
 }
 
 
@@ -94,12 +98,22 @@ class _Clocks:
 
 
 def tap_peaks(rates_per_sm_clk):
-    """Tap bounds per SM and clock of each filter form from the measured per-SM-per-clock rates."""
+    """Tap bounds per SM and clock of each filter form from the measured per-SM-per-clock rates.
+    The FP16 form mixes half2, conversion and FP32 instructions whose pipes are not all measured
+    apart: its peak is the measured rate of its own tap loop."""
     out = {}
+    if "tap_fp16" in rates_per_sm_clk:
+        out["fp16"] = {"taps_per_sm_clk": rates_per_sm_clk["tap_fp16"], "binds": "measured_tap_loop",
+                       "bounds_taps_per_sm_clk": {"measured_tap_loop": round(rates_per_sm_clk["tap_fp16"], 3)},
+                       "thread_instructions_per_tap": None}
     for form, k in FORMS.items():
-        instr = k["fma"] + k["fma2"] + k["ex2"]
+        instr = k["fma"] + k["fma2"] + k["ex2"] + k.get("lds", 0.0) + k.get("red", 0.0)
         bounds = {"issue": ISSUE_PER_SM_CLK / instr,
                   "ex2": rates_per_sm_clk["ex2_f32"] / k["ex2"]}
+        if k.get("red"):
+            if "red_shared_f32" not in rates_per_sm_clk:
+                continue
+            bounds["smem_atomic"] = rates_per_sm_clk["red_shared_f32"] / k["red"]
         if k["fma"]:
             bounds["fma_pipe"] = rates_per_sm_clk["ffma"] / k["fma"]
         if k["fma2"]:

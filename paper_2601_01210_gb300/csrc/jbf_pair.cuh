@@ -133,6 +133,7 @@ __device__ __forceinline__ void pair_tile(const FrameDev &F, const StageArgs &a,
     const int rbase = warp * KP;
     bool val0[KP], val1[KP];
     bool any_val = false;
+    uint32_t rows_warp;   // bit iy: some lane of the warp has an observation in its window of staged row rbase + iy
     {
         uint32_t rows0 = 0u, rows1 = 0u;   // bit iy: an observation in staged row rbase + iy, slots lane .. lane + 2R
 #pragma unroll
@@ -149,6 +150,7 @@ __device__ __forceinline__ void pair_tile(const FrameDev &F, const StageArgs &a,
             val1[k] = ((rows1 >> k) & TMASK) != 0;
             any_val |= val0[k] || val1[k];
         }
+        rows_warp = __reduce_or_sync(0xffffffffu, rows0 | rows1);
     }
 
     // ---- taps
@@ -169,6 +171,8 @@ __device__ __forceinline__ void pair_tile(const FrameDev &F, const StageArgs &a,
         }
 #pragma unroll
         for (int iy = 0; iy < KP + 2 * R; ++iy) {
+            // a staged row no lane's window observes adds exact zeros (F = G = 0): skip it
+            if (!((rows_warp >> iy) & 1u)) continue;
             float2 dd[KP];
 #pragma unroll
             for (int k = 0; k < KP; ++k) {

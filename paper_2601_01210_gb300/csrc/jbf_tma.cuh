@@ -49,6 +49,7 @@
 
 #include "jbf_core.cuh"
 #include "jbf_pair.cuh"
+#include "jbf_scatter.cuh"
 #include "tma_common.cuh"
 
 namespace dz {
@@ -71,9 +72,20 @@ __device__ __forceinline__ __half2 h2exp2_approx(__half2 x) {
     return h2bits(y);
 }
 
-// Resident CTAs per SM the compiler is asked to fit (registers): 16 warps per SM, and 32 for
-// the paired form at two rows per thread, whose state fits 64 registers.
-constexpr int tma_min_ctas(int form, int kp, int nw) { return (form == FORM_EXP_PAIRS && kp == 2 ? 32 : 16) / nw; }
+// Resident CTAs per SM the compiler is asked to fit (registers): 16 warps per SM, 32 for the
+// paired form at two rows per thread, whose state fits 64 registers, and 8 for the paired form
+// at eight rows per thread, whose state needs more than 128.
+constexpr int tma_min_ctas(int form, int kp, int nw) {
+    return (form == FORM_EXP_PAIRS && kp == 2 ? 32 : form == FORM_EXP_PAIRS && kp == 8 ? 8 : 16) / nw;
+}
+
+// FP16 form: bound on the relative error of a weight (2^(e) with e = -kc |dc|^2 + spatial term
+// evaluated in half precision: roundings of kc, of the squared distance and of e, about 2^-10.4 of
+// |e| each, for |e| <= 24, plus the ex2.approx.f16 error), and the weighted standard deviation of a
+// window's depths, as a fraction of the pixel's depth, above which the pixel is recomputed in FP32
+// (kHalfWeightErr * kHalfStdFrac = 5e-4, half the 1e-3 relative bar).
+constexpr float kHalfWeightErr = 0.02f;
+constexpr float kHalfStdFrac = 5e-4f / kHalfWeightErr;
 
 template <int SRC, int R, int KP, int FORM = FORM_FP32, int NW = 8>
 __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_kernel(const BatchDev *__restrict__ B,
@@ -250,6 +262,54 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
             __syncthreads();   // staged records / raw[buf] are reused by the next tile
             continue;
         }
+        if constexpr (G::SCATTER) {
+            static_assert(SRC != SRC_UP, "scatter form: the sparse stages");
+            const int x = x0 + lane;
+            // the output pointers in registers (stores through them could alias the frame descriptor)
+            float2 *const out_s1 = F.s1;
+            const int64_t cpitch = F.cpitch;
+            float *const out_coarse = F.out_coarse, *const out_depth = F.flt_depth;
+            uint8_t *const out_coarse_valid = F.out_coarse_valid, *const out_valid = F.flt_valid;
+            const int rb = warp * KP;
+            auto store = [&](int k, float out, bool v) {
+                const int y = y0 + rb + k;
+                if (x < gw && y < gh) {
+                    const int64_t o = (int64_t)y * gw + x;
+                    if (SRC == SRC_COARSE) {
+                        out_s1[(int64_t)y * cpitch + x] = make_float2(out, v ? 1.0f : 0.0f);
+                        if (out_coarse) out_coarse[o] = out;
+                        if (out_coarse_valid) out_coarse_valid[o] = v;
+                    } else {
+                        out_depth[o] = out;
+                        out_valid[o] = v;
+                    }
+                }
+            };
+            auto mark_rows = [&](const bool *val, int rbase) {   // flag the second-stage tiles valid pixels reach
+                if (SRC == SRC_COARSE && B->tl_th[1] > 0) {
+                    uint32_t cols = 0u;
+                    int kf = KP, kl = -1;
+#pragma unroll
+                    for (int k = 0; k < KP; ++k) {
+                        const uint32_t m = __ballot_sync(0xffffffffu, val[k] && x < gw && y0 + rbase + k < gh);
+                        cols |= m;
+                        if (m) {
+                            kf = min(kf, k);
+                            kl = k;
+                        }
+                    }
+                    if (cols)
+                        mark_reach(F.tflags[1], B->tl_tw[1], B->tl_th[1], B->tl_r[1], a.pool, F.W, F.H,
+                                   x0 + __ffs(cols) - 1, x0 + 31 - __clz(cols), y0 + rbase + kf, y0 + rbase + kl,
+                                   lane);
+                }
+            };
+            scatter_tile<SRC, R, KP, NW>(F, a, x0, y0, gw, gh, rawA(buf), rawB(buf), smem, [&]() {
+                if (threadIdx.x == 0 && n1 < total) advance();   // off the path of the CTA's barriers
+            }, store, mark_rows);
+            __syncthreads();   // lists, accumulators and raw[buf] are reused by the next tile
+            continue;
+        }
         const uint8_t *rgbraw = rawA(buf);
         const float4 *cg = reinterpret_cast<const float4 *>(rawA(buf));
         const float *cs = reinterpret_cast<const float *>(rawB(buf));
@@ -350,6 +410,7 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
         // ---- filter: thread owns column lane, rows rbase .. rbase + KP - 1 of the tile
         const int rbase = warp * KP;
         float cr[KP], cgr[KP], cb[KP], num[KP], den[KP];
+        float sq[HALF ? KP : 1];   // FP16 form: weighted sum of squared depths (the error bound below)
         bool val[KP];
         bool any_val = false;
 #pragma unroll
@@ -363,7 +424,9 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
             }
             num[k] = 0.0f;
             den[k] = 0.0f;
+            if (HALF) sq[k] = 0.0f;
         }
+        uint32_t rows_warp;   // bit iy: some lane's window of staged row rbase + iy holds an observation
         {
             uint32_t rows = 0;   // bit iy: an observation in staged row rbase + iy, columns lane .. lane + 2R
 #pragma unroll
@@ -377,6 +440,7 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
                 val[k] = ((rows >> k) & ((1u << T) - 1u)) != 0;
                 any_val |= val[k];
             }
+            rows_warp = __reduce_or_sync(0xffffffffu, rows);
         }
         if (HALF && __any_sync(0xffffffffu, any_val)) {
             // centre colours of row pairs (2j, 2j+1) as half2
@@ -396,7 +460,7 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
                 for (int dx = 0; dx < T; ++dx) {
                     const uint4 q = staged_h[(rbase + iy) * SW + lane + dx];
                     const __half2 qr = h2bits(q.x), qg = h2bits(q.y), qb = h2bits(q.z);
-                    const float qd = __uint_as_float(q.w);
+                    const float qd = __uint_as_float(q.w), qd2 = qd * qd;
 #pragma unroll
                     for (int j = 0; j < KP / 2; ++j) {
                         const int d = iy - 2 * j;   // row offset of the pair's first pixel
@@ -407,8 +471,10 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
                             const float2 w = __half22float2(w2);
                             num[2 * j] = fmaf(w.x, qd, num[2 * j]);
                             den[2 * j] += w.x;
+                            sq[2 * j] = fmaf(w.x, qd2, sq[2 * j]);
                             num[2 * j + 1] = fmaf(w.y, qd, num[2 * j + 1]);
                             den[2 * j + 1] += w.y;
+                            sq[2 * j + 1] = fmaf(w.y, qd2, sq[2 * j + 1]);
                         }
                     }
                 }
@@ -427,6 +493,8 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
             }
 #pragma unroll
             for (int iy = 0; iy < KP + 2 * R; ++iy) {
+                // a staged row no lane's window observes adds exact zeros (F q = 0): skip it
+                if (!((rows_warp >> iy) & 1u)) continue;
                 float dd[KP];
 #pragma unroll
                 for (int k = 0; k < KP; ++k) {
@@ -526,7 +594,20 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
                 slow |= 1u << k;
                 continue;
             }
-            store(k, val[k] ? __fdividef(num[k], den[k]) : 0.0f, val[k]);
+            const float out = val[k] ? __fdividef(num[k], den[k]) : 0.0f;
+            if (HALF && val[k]) {
+                // FP16 weights carry a relative error of at most kHalfWeightErr (exponents rounded in
+                // half precision); the depth error is then at most kHalfWeightErr times the weighted
+                // standard deviation of the window's depths (Cauchy-Schwarz over the weights). Where that
+                // bound could exceed half of 1e-3 of the depth, the pixel is recomputed in FP32.
+                const float var = __fdividef(sq[k], den[k]) - out * out;
+                const float lim = kHalfStdFrac * out;
+                if (var > lim * lim) {
+                    slow |= 1u << k;
+                    continue;
+                }
+            }
+            store(k, out, val[k]);
         }
         // shifted recomputation in FP32 (rare): largest exponent of the window first
         while (slow) {

@@ -13,6 +13,7 @@ namespace dz {
     X(SRC_UP, 2, 2, FORM_EXP_PAIRS, 8)   \
     X(SRC_UP, 2, 4, FORM_EXP_PAIRS, 4)   \
     X(SRC_UP, 2, 4, FORM_EXP_PAIRS, 16)  \
+    X(SRC_UP, 2, 8, FORM_EXP_PAIRS, 4)   \
     X(SRC_UP, 2, 8, FORM_EXP, 16)        \
     X(SRC_UP, 2, 8, FORM_EXP, 8)         \
     X(SRC_UP, 2, 4, FORM_EXP, 8)         \

@@ -36,8 +36,17 @@ __device__ __forceinline__ double compose_entry(const double *c2w, const double 
 }
 
 __global__ void __launch_bounds__(kThreads) prep_kernel(BatchDev *__restrict__ B) {
+    // the batch's clear prefix and each frame's z-buffer in shared memory: a work item then starts
+    // its stores without a chain of dependent global loads
+    __shared__ int32_t s_pre[kMaxBatch + 1];
+    __shared__ uint32_t *s_z[kMaxBatch];
+    __shared__ int64_t s_n[kMaxBatch];
     const int nf = B->n_frames;
-    const int total = B->zb_pre[nf];
+    for (int i = threadIdx.x; i <= nf; i += kThreads) s_pre[i] = B->zb_pre[i];
+    for (int i = threadIdx.x; i < nf; i += kThreads) {
+        s_z[i] = B->f[i].zbuf_raw;
+        s_n[i] = (int64_t)B->f[i].zpitch * B->f[i].H;
+    }
     // the TMA filters' tile flags (each frame's block of both stages) and tile counters start the
     // batch cleared; the producers (pooling, first filter) and the mark kernel set the flags
     if (B->tl_on) {
@@ -48,11 +57,13 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(BatchDev *__restrict__ B
             for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) fl[i] = 0;
         }
     }
+    __syncthreads();
+    const int total = s_pre[nf];
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
-        const int f = find_segment(B->zb_pre, nf, item);
-        FrameDev &F = B->f[f];
-        const int c = item - B->zb_pre[f];
+        const int f = find_segment(s_pre, nf, item);
+        const int c = item - s_pre[f];
         if (c == 0) {
+            FrameDev &F = B->f[f];
             const int t = threadIdx.x;
             if (t < F.num_scans * 12) {
                 const int s = t / 12, e = t % 12;
@@ -62,22 +73,26 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(BatchDev *__restrict__ B
                 F.c2w32[e] = __double2float_rn(F.c2w[(e / 4) * 4 + (e % 4)]);
             }
         }
-        const int64_t n = (int64_t)F.zpitch * F.H;
+        const int64_t n = s_n[f];
         const int64_t w0 = (int64_t)c * kZbWordsPerChunk;
         const int64_t w1 = min(n, w0 + kZbWordsPerChunk);
-        uint32_t *z = F.zbuf_raw;
-        // arena buffers are 256-byte aligned and w0 is a multiple of 4
+        uint32_t *z = s_z[f];
+        // arena buffers are 256-byte aligned and w0 is a multiple of 4; every thread's stores of the
+        // chunk are issued together
         const int64_t v1 = w0 + ((w1 - w0) & ~int64_t(3));
         const uint4 e4 = make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
-        for (int64_t w = w0 + 4 * threadIdx.x; w < v1; w += 4 * kThreads)
-            *reinterpret_cast<uint4 *>(z + w) = e4;
+#pragma unroll
+        for (int k = 0; k < kZbWordsPerChunk / (4 * kThreads); ++k) {
+            const int64_t w = w0 + 4 * (threadIdx.x + k * kThreads);
+            if (w < v1) *reinterpret_cast<uint4 *>(z + w) = e4;
+        }
         for (int64_t w = v1 + threadIdx.x; w < w1; w += kThreads) z[w] = kEmpty;
     }
 }
 
 // ---------------------------------------------------------------------------
-// project: one work item = 1024 consecutive points of one (frame, scan);
-// each thread takes 4 points with 16-byte vector loads.
+// project: one work item = kPtsPerChunk consecutive points of one (frame, scan);
+// each thread takes kPtsPerThread points with 16-byte vector loads.
 // ---------------------------------------------------------------------------
 // The camera of a frame in registers: read once per work item (an atomic on the z-buffer could
 // alias the frame descriptor, so reading it per point would mean a reload after every atomic).
@@ -105,30 +120,37 @@ __device__ __forceinline__ void project_one(const float (&M)[12], float x, float
 }
 
 __global__ void __launch_bounds__(kThreads) project_kernel(const BatchDev *__restrict__ B) {
+    __shared__ int32_t s_pre[kMaxBatch * kMaxScans + 1];   // point-chunk prefix, searched per work item
     const int nseg = B->n_frames * kMaxScans;
-    const int total = B->pt_pre[nseg];
+    for (int i = threadIdx.x; i <= nseg; i += kThreads) s_pre[i] = B->pt_pre[i];
+    __syncthreads();
+    const int total = s_pre[nseg];
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
-        const int seg = find_segment(B->pt_pre, nseg, item);
+        const int seg = find_segment(s_pre, nseg, item);
         const FrameDev &F = B->f[seg / kMaxScans];
         const ScanDev &S = F.scans[seg % kMaxScans];
         float M[12];
 #pragma unroll
         for (int e = 0; e < 12; ++e) M[e] = S.M[e];
-        const int64_t p0 = (int64_t)(item - B->pt_pre[seg]) * kPtsPerChunk + (int64_t)threadIdx.x * kPtsPerThread;
+        const int64_t p0 = (int64_t)(item - s_pre[seg]) * kPtsPerChunk + (int64_t)threadIdx.x * kPtsPerThread;
         if (p0 >= S.count) continue;
         uint32_t *zbuf = F.zbuf_raw;
         const bool old_scan = (seg % kMaxScans) != F.newest_scan;
         const ProjCam C{F.fx, F.fy, F.cx, F.cy, (float)F.W, (float)F.H, F.W, F.zpitch, old_scan ? F.motion : nullptr};
         const int64_t count = S.count;
         if (S.stride_floats == 3) {
-            if (p0 + 4 <= S.count) {
-                // 4 packed points = 48 bytes = 3 aligned float4 (base 16-byte aligned, p0 % 4 == 0)
+            if (p0 + kPtsPerThread <= S.count) {
+                // kPtsPerThread packed points = 3 kPtsPerThread / 4 aligned float4 (base 16-byte
+                // aligned, p0 % 4 == 0), all loaded before any is used
                 const float4 *q = reinterpret_cast<const float4 *>(S.xyz + p0 * 3);
-                const float4 a = __ldg(q), b = __ldg(q + 1), c = __ldg(q + 2);
-                project_one(M, a.x, a.y, a.z, C, zbuf);
-                project_one(M, a.w, b.x, b.y, C, zbuf);
-                project_one(M, b.z, b.w, c.x, C, zbuf);
-                project_one(M, c.y, c.z, c.w, C, zbuf);
+                float v[3 * kPtsPerThread];
+#pragma unroll
+                for (int k = 0; k < 3 * kPtsPerThread / 4; ++k) {
+                    const float4 a = __ldg(q + k);
+                    v[4 * k] = a.x; v[4 * k + 1] = a.y; v[4 * k + 2] = a.z; v[4 * k + 3] = a.w;
+                }
+#pragma unroll
+                for (int k = 0; k < kPtsPerThread; ++k) project_one(M, v[3 * k], v[3 * k + 1], v[3 * k + 2], C, zbuf);
             } else {
                 const float *xyz = S.xyz;
                 for (int64_t p = p0; p < count; ++p)
@@ -136,14 +158,14 @@ __global__ void __launch_bounds__(kThreads) project_kernel(const BatchDev *__res
             }
         } else {
             const float4 *q = reinterpret_cast<const float4 *>(S.xyz) + p0;
-            const int n = (int)(count - p0 < 4 ? count - p0 : 4);
+            const int n = (int)(count - p0 < kPtsPerThread ? count - p0 : kPtsPerThread);
+            float4 a[kPtsPerThread];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (k < n) {
-                    const float4 a = __ldg(q + k);
-                    project_one(M, a.x, a.y, a.z, C, zbuf);
-                }
-            }
+            for (int k = 0; k < kPtsPerThread; ++k)
+                if (k < n) a[k] = __ldg(q + k);
+#pragma unroll
+            for (int k = 0; k < kPtsPerThread; ++k)
+                if (k < n) project_one(M, a[k].x, a[k].y, a[k].z, C, zbuf);
         }
     }
 }

@@ -3,8 +3,10 @@
 // (ex2.approx.ftz.f32, ex2.approx.f16x2) and the mixed loop of one filter tap
 // pair in the paired expanded form (three two-lane FMA for the exponents of two
 // output pixels, one ex2 per pixel, two two-lane FMA into numerator and weight
-// sum: 3.5 instructions a tap), and FP32 adds into shared memory (the
-// scatter form's accumulation). Its measured rates are the peaks the filter
+// sum: 3.5 instructions a tap), FP32 adds into shared memory (the scatter
+// form's accumulation), half2 FMA (fma.rn.f16x2) and the FP16 form's tap pair
+// (half2 colour differences, squared distance and exponent for two output
+// rows, one ex2.approx.f16x2, the weights widened to FP32 and accumulated). Its measured rates are the peaks the filter
 // rooflines divide by.
 //
 // Every thread runs kChains independent dependency chains, unrolled, so that
@@ -13,6 +15,7 @@
 // chains feed every result back into the next exponent: values run to +inf
 // after a few steps and stay there (the instruction's rate does not depend on
 // its operand).
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -22,7 +25,10 @@ constexpr int kThreads = 256;
 constexpr int kChains = 8;
 constexpr int kUnroll = 16;
 
-enum Op { OP_FFMA = 0, OP_FFMA2 = 1, OP_EX2 = 2, OP_EX2_H2 = 3, OP_TAP_PAIRED = 4, OP_RED_SHARED = 5, OP_COUNT = 6 };
+enum Op {
+    OP_FFMA = 0, OP_FFMA2 = 1, OP_EX2 = 2, OP_EX2_H2 = 3, OP_TAP_PAIRED = 4, OP_RED_SHARED = 5, OP_HFMA2 = 6,
+    OP_TAP_FP16 = 7, OP_COUNT = 8
+};
 
 __device__ __forceinline__ float ex2f(float x) {
     float y;
@@ -90,6 +96,53 @@ __global__ void __launch_bounds__(kThreads, 6) rate_kernel(float *__restrict__ o
         }
 #pragma unroll
         for (int c = 0; c < kChains; ++c) sink += __uint_as_float(a[c] & 0x3FFFFFFFu);
+    } else if (OP == OP_HFMA2) {
+        __half2 a[kChains];
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) a[c] = __floats2half2_rn(0.5f + 0.01f * c, 0.25f + 1e-3f * (tid & 15));
+        const __half2 m = __floats2half2_rn(0.99f * s, 0.98f), k = __floats2half2_rn(1e-3f, 2e-3f);
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+                for (int c = 0; c < kChains; ++c) a[c] = __hfma2(a[c], m, k);
+        }
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) sink += __low2float(a[c]) + __high2float(a[c]);
+    } else if (OP == OP_TAP_FP16) {   // the FP16 form's tap pair: two output rows of one column, one neighbour
+        constexpr int P = kChains / 2;
+        __half2 q[P];
+        float num[2 * P], den[2 * P];
+#pragma unroll
+        for (int c = 0; c < P; ++c) {
+            q[c] = __floats2half2_rn(3.0f + c, 5.0f + 1e-3f * (tid & 7));
+            num[2 * c] = num[2 * c + 1] = den[2 * c] = den[2 * c + 1] = 0.0f;
+        }
+        const __half2 cr = __floats2half2_rn(1.0f * s, 2.0f), cg = __floats2half2_rn(3.0f, 1.0f),
+                      cb = __floats2half2_rn(2.0f, 4.0f), kc2 = __floats2half2_rn(-0.01f, -0.01f),
+                      sp = __floats2half2_rn(-0.1f, -0.2f);
+        const float qd = 2.5f * s;
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+#pragma unroll
+                for (int c = 0; c < P; ++c) {
+                    const __half2 dr = __hsub2(q[c], cr), dg = __hsub2(q[c], cg), db = __hsub2(q[c], cb);
+                    const __half2 n2 = __hfma2(dr, dr, __hfma2(dg, dg, __hmul2(db, db)));
+                    uint32_t wb;
+                    const __half2 e = __hfma2(n2, kc2, sp);
+                    asm("ex2.approx.f16x2 %0, %1;" : "=r"(wb) : "r"(*reinterpret_cast<const uint32_t *>(&e)));
+                    const float2 w = __half22float2(*reinterpret_cast<const __half2 *>(&wb));
+                    num[2 * c] = fmaf(w.x, qd, num[2 * c]);
+                    den[2 * c] += w.x;
+                    num[2 * c + 1] = fmaf(w.y, qd, num[2 * c + 1]);
+                    den[2 * c + 1] += w.y;
+                    q[c] = dr;   // the next neighbour depends on this one (nothing to hoist, no extra instruction)
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 2 * P; ++c) sink += num[c] + den[c];
     } else if (OP == OP_RED_SHARED) {   // FP32 add to shared memory, no return value, distinct words per lane
         __shared__ float acc[kChains][kThreads];
 #pragma unroll
@@ -147,7 +200,9 @@ double units_per_iteration(int op) {
     case OP_FFMA2:
     case OP_EX2:
     case OP_EX2_H2:
-    case OP_RED_SHARED: return (double)kUnroll * kChains;
+    case OP_RED_SHARED:
+    case OP_HFMA2: return (double)kUnroll * kChains;
+    case OP_TAP_FP16: return (double)kUnroll * (kChains / 2) * 2;   // two taps per pair
     case OP_TAP_PAIRED: return (double)kUnroll * (kChains / 2) * 2;   // two taps per pair
     default: return 0.0;
     }
@@ -161,6 +216,8 @@ cudaError_t launch(int op, int blocks, int iters, float *out, cudaStream_t st) {
     case OP_EX2_H2: rate_kernel<OP_EX2_H2><<<blocks, kThreads, 0, st>>>(out, iters, 1.0f); break;
     case OP_TAP_PAIRED: rate_kernel<OP_TAP_PAIRED><<<blocks, kThreads, 0, st>>>(out, iters, 1.0f); break;
     case OP_RED_SHARED: rate_kernel<OP_RED_SHARED><<<blocks, kThreads, 0, st>>>(out, iters, 1.0f); break;
+    case OP_HFMA2: rate_kernel<OP_HFMA2><<<blocks, kThreads, 0, st>>>(out, iters, 1.0f); break;
+    case OP_TAP_FP16: rate_kernel<OP_TAP_FP16><<<blocks, kThreads, 0, st>>>(out, iters, 1.0f); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -122,3 +122,53 @@ def test_alu_microbenchmark_library_builds():
     lib = build.build_peaks()
     out = subprocess.run(["nm", "-D", "--defined-only", lib], capture_output=True, text=True, check=True).stdout
     assert " T alu_peak_run" in out
+
+
+def test_config_cpu_leg_reports_errors_against_the_oracle():
+    """The CPU leg of the extra workloads: the oracle's own outputs score zero error and exact masks,
+    a perturbed depth map is reported with its error."""
+    import numpy as np
+
+    import bench
+    import oracle
+    import scene
+    oracle.build()
+    views = [scene.make_workload("qvga_1scan", 1000 + i) for i in range(2)]
+    cfg = bench.EXTRA_CONFIGS["qvga_1scan_single_stage_fp32"]
+    outs = []
+    for v in views:
+        o = oracle.densify_view(v, num_stages=1, stages=cfg["stages"], emit_points=False)
+        outs.append({"depth": o["depth"].astype(np.float32), "valid": o["valid"]})
+    rep = bench.config_cpu_leg("qvga", cfg, views, outs, 2)
+    e = rep["error_vs_oracle"]
+    assert e["all_masks_exact"] and e["max_rel"] < 1e-7
+    outs[1]["depth"] = outs[1]["depth"] * np.float32(1.001)
+    e = bench.config_cpu_leg("qvga", cfg, views, outs, 2)["error_vs_oracle"]
+    assert abs(e["max_rel"] - 1e-3) < 1e-5
+
+
+def test_single_stage_work_counts_observed_taps():
+    """Observed taps of the single-stage filter: a lone observation in a 9x9 window reaches 81 output
+    pixels; at the image corner only 25."""
+    import numpy as np
+    import torch
+
+    import bench
+
+    class Buf:
+        W, H = 20, 16
+
+        def __init__(self, cells):
+            z = np.full((16, 20), 0x7F800000, np.uint32)
+            for (y, x) in cells:
+                z[y, x] = np.float32(2.0).view(np.uint32)
+            self.zbuf = torch.from_numpy(z.view(np.int32))
+
+        def n_points(self):
+            return 0
+
+    class View:
+        scans = []
+
+    assert bench.step_work(Buf([(8, 10)]), View, single_radius=4)["taps1"] == 81
+    assert bench.step_work(Buf([(0, 0)]), View, single_radius=4)["taps1"] == 25

@@ -64,7 +64,8 @@ def test_tuned_equals_untuned_and_cache_is_reused(tmp_path, monkeypatch, precisi
         assert all(s1["chosen"][k] == s2["chosen"][k] for k in ("kernel", "kp", "warps", "form"))
 
 
-_FORM_TAG = {"fp32": "fp32", "fp16": "fp16", "fp32_expanded": "exp", "fp32_expanded_pairs": "exp_pairs"}
+_FORM_TAG = {"fp32": "fp32", "fp16": "fp16", "fp32_expanded": "exp", "fp32_expanded_pairs": "exp_pairs",
+             "fp32_scatter": "scatter"}
 
 
 @pytest.mark.parametrize("stage", [0, 1])
@@ -100,3 +101,49 @@ def test_every_candidate_matches_the_plain_kernel(tmp_path, monkeypatch, stage):
             np.testing.assert_allclose(a["coarse"], b["coarse"], rtol=3e-5, err_msg=name)
         tried.add(c["form"])
     assert "fp32_expanded" in tried
+
+
+@pytest.mark.parametrize("radius", [2, 4, 7])
+def test_every_single_stage_candidate_matches_the_plain_kernel(tmp_path, monkeypatch, radius):
+    """The single stage on the z-buffer: each candidate the tuner may pick (the gather forms and
+    Algorithm 1's scatter form), forced through a tuning-cache entry, gives the plain kernel's
+    integer decisions and its depths within FP32 rounding (frames of three sizes, ragged edges)."""
+    import torch
+    from paper_2601_01210_gb300 import Densifier, build
+    from paper_2601_01210_gb300.frames import FrameBuffers
+    build.build()
+    views = [scene.make_batch_view(79, r, i, 3) for i, r in enumerate(["720p", "540p", "qvga"])]
+    st = ((radius, 5.0, 20.0),)
+
+    def run(**params):
+        with Densifier(dict(num_stages=1, stages=st, launch_policy=1, max_batch=8, **params)) as d:
+            bufs = [FrameBuffers(v.camera, v.rgb, [(s.xyz, s.lidar_to_world) for s in v.scans], debug=True,
+                                 num_stages=1) for v in views]
+            ts = [d.submit(b.frame) for b in bufs]
+            d.flush()
+            for t in ts:
+                assert d.poll(t, -1) == 0
+            torch.cuda.synchronize()
+            return [b.results() for b in bufs], d.describe()
+
+    plain, _ = run(kernel_variant=1)
+    _, desc = run()
+    px = sum(v.rgb.shape[0] * v.rgb.shape[1] for v in views)
+    key = f"kind=0,r={radius},half=0,px=2^{px.bit_length() - 1}"
+    tried = set()
+    for c in desc["stages"][0]["candidates"]:
+        if c["kernel"] != "tma":
+            continue
+        name = f"tma:kp{c['kp']}:nw{c['warps']}:{_FORM_TAG[c['form']]}"
+        cache = tmp_path / f"{radius}_{name.replace(':', '_')}.txt"
+        cache.write_text(f"{key} {name}\n")
+        monkeypatch.setenv("DENSIFY_TUNE_CACHE", str(cache))
+        got, d = run(autotune=1)
+        ch = d["stages"][0]["chosen"]
+        assert (ch["kp"], ch["warps"], ch["form"]) == (c["kp"], c["warps"], c["form"])
+        for a, b in zip(got, plain):
+            for k in ("zbuf", "valid", "rgba"):
+                assert np.array_equal(a[k], b[k]), (name, k)
+            np.testing.assert_allclose(a["depth"], b["depth"], rtol=3e-5, err_msg=name)
+        tried.add(c["form"])
+    assert "fp32_scatter" in tried

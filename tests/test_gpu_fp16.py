@@ -57,13 +57,26 @@ def test_fp16_1080p_two_stage():
 
 
 def test_fp16_qvga_single_stage():
+    """Sixteen views of the 320x240 workload (far ground at grazing angles, box edges: windows whose
+    depths spread widely, where FP16 weight errors matter most)."""
     import torch
     import oracle
-    v = scene.make_workload("qvga_1scan", 1000)
     st = ((4, 3.0, 20.0),)
-    g = _run(v, st, 1, torch)
-    o = oracle.densify_view(v, num_stages=1, stages=st)
-    _check(g, o, "qvga 9x9")
+    for seed in range(1000, 1016):
+        v = scene.make_workload("qvga_1scan", seed)
+        g = _run(v, st, 1, torch)
+        o = oracle.densify_view(v, num_stages=1, stages=st)
+        _check(g, o, f"qvga 9x9 seed {seed}")
+
+
+def test_fp16_uneven_views_two_stage():
+    import torch
+    import oracle
+    for i, res in enumerate(["1080p", "720p", "540p"]):
+        v = scene.make_batch_view(1003, res, 4 * i, 12)
+        g = _run(v, PAPER_STAGES, 1, torch)
+        o = oracle.densify_view(v, num_stages=2, stages=PAPER_STAGES)
+        _check(g, o, f"{res} two-stage")
 
 
 def test_fp16_rejected_where_unavailable():

@@ -51,6 +51,31 @@ int check(const char *name) {
     if (G::OFF_STAGED % 16 || G::OFF_G % 16 || G::OFF_OBS % 4 || G::OFF_BAR % 8) rep.fail("layout alignment", G::OFF_STAGED, G::OFF_G, G::OFF_OBS);
     if (G::SMEM > 232448) rep.fail("shared memory", G::SMEM, 232448, 0);
     if (G::NCONV * G::NT < G::SH * G::SP) rep.fail("conversion coverage", G::NCONV, G::NT, G::SH * G::SP);
+    if (G::SCATTER) {
+        // every staged row belongs to one warp's list, whose room holds a source per position of its rows
+        if (G::NW * G::RPW < G::SH) rep.fail("scatter rows", G::NW, G::RPW, G::SH);
+        if (G::TW != 32 || G::SW > 64) rep.fail("scatter tile / row mask", G::TW, G::SW, 0);
+        if (G::OFF_TGT % 16 || G::OFF_ACC % 16 || G::OFF_ROWS % 16) rep.fail("scatter layout", G::OFF_TGT, G::OFF_ACC, G::OFF_ROWS);
+        for (int warp = 0; warp < G::NW; ++warp) {
+            int rows = 0;
+            for (int sy = warp; sy < G::SH; sy += G::NW) ++rows;
+            if (rows > G::RPW) rep.fail("scatter list room", warp, rows, G::RPW);
+            if (2 * G::NW * G::RPW * G::SW * 16 > G::STAGED) rep.fail("scatter list", warp, G::RPW, G::SW);
+        }
+        // every source (sy, sx) and offset (ox, oy): a target inside the tile indexes the tile's arrays
+        for (int sy = 0; sy < G::SH; ++sy)
+            for (int sx = 0; sx < G::SW; ++sx)
+                for (int oy = -R; oy <= R; ++oy)
+                    for (int ox = -R; ox <= R; ++ox) {
+                        const int ty = sy - R + oy, tx = sx - R + ox;
+                        if (ty < 0 || ty >= G::TH || tx < 0 || tx >= G::TW) continue;
+                        const int i = (ty * G::TWP + sx - R) + ox;
+                        if (i < 0 || G::TH * G::TWP + i >= G::ACC / 4 || i >= G::TGT / 16) rep.fail("scatter target", sy, sx, ox);
+                    }
+        // epilogue row masks: rows ty .. ty + 2R of every output row
+        for (int ty = 0; ty < G::TH; ++ty)
+            if (ty + 2 * R >= G::ROWS / 8) rep.fail("scatter row mask", ty, R, G::ROWS);
+    }
     // ---- taps, validity words and centres of every thread (the same for every tile)
     for (int warp = 0; warp < NW; ++warp)
         for (int lane = 0; lane < 32; ++lane) {
