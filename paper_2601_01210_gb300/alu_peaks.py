@@ -38,9 +38,10 @@ FORMS = {
     "fp32": {"fma": 9.0, "fma2": 0.0, "ex2": 1.0},                 # difference form: 3 sub, 3 fma, 1 fma, 2 fma
     "fp32_expanded": {"fma": 5.0, "fma2": 0.0, "ex2": 1.0},        # 3 fma exponent, 2 fma sums
     "fp32_expanded_pairs": {"fma": 0.0, "fma2": 2.5, "ex2": 1.0},  # per tap: 1.5 + 1 two-lane fma
-    # scatter (Algorithm 1): 3 fma + 1 add exponent, 2 mul (weight times depth, times count), one load of
-    # the target colour, two adds into shared memory
-    "fp32_scatter": {"fma": 6.0, "fma2": 0.0, "ex2": 1.0, "lds": 1.0, "red": 2.0},
+    # sparse (a warp walks the observed positions of its block's footprint; per evaluated pixel and
+    # position): row offset, squared distance, 4 fma exponent, 2 sums, half the column terms of the
+    # two pixels a lane owns; window test (max, compare); half of the position's loads and loop work
+    "fp32_sparse": {"fma": 9.0, "fma2": 0.0, "ex2": 1.0, "other": 5.0},
 }
 
 
@@ -107,7 +108,7 @@ def tap_peaks(rates_per_sm_clk):
                        "bounds_taps_per_sm_clk": {"measured_tap_loop": round(rates_per_sm_clk["tap_fp16"], 3)},
                        "thread_instructions_per_tap": None}
     for form, k in FORMS.items():
-        instr = k["fma"] + k["fma2"] + k["ex2"] + k.get("lds", 0.0) + k.get("red", 0.0)
+        instr = k["fma"] + k["fma2"] + k["ex2"] + k.get("lds", 0.0) + k.get("red", 0.0) + k.get("other", 0.0)
         bounds = {"issue": ISSUE_PER_SM_CLK / instr,
                   "ex2": rates_per_sm_clk["ex2_f32"] / k["ex2"]}
         if k.get("red"):

@@ -21,8 +21,8 @@ constexpr uint32_t kEmpty = 0x7F800000u;   // z-buffer cell with no depth (+inf)
 
 // Work-item granularity of the non-filter kernels.
 constexpr int kThreads = 256;
-constexpr int kPtsPerThread = 8;
-constexpr int kPtsPerChunk = kThreads * kPtsPerThread;        // 2048 points
+constexpr int kPtsPerThread = 4;
+constexpr int kPtsPerChunk = kThreads * kPtsPerThread;        // 1024 points
 constexpr int kZbWordsPerChunk = 8192;                        // z-buffer clear: 8 uint4 stores a thread
 constexpr int kPoolPerChunk = kThreads;                       // coarse pixels (one coarse row segment)
 constexpr int kBpChunk = 4096;                                // compaction: 8 warps x 512 px

@@ -49,7 +49,7 @@
 
 #include "jbf_core.cuh"
 #include "jbf_pair.cuh"
-#include "jbf_scatter.cuh"
+#include "jbf_sparse.cuh"
 #include "tma_common.cuh"
 
 namespace dz {
@@ -262,52 +262,23 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
             __syncthreads();   // staged records / raw[buf] are reused by the next tile
             continue;
         }
-        if constexpr (G::SCATTER) {
-            static_assert(SRC != SRC_UP, "scatter form: the sparse stages");
-            const int x = x0 + lane;
+        if constexpr (G::SPARSE) {
+            static_assert(SRC == SRC_ZBUF, "sparse form: the single stage on the z-buffer");
             // the output pointers in registers (stores through them could alias the frame descriptor)
-            float2 *const out_s1 = F.s1;
-            const int64_t cpitch = F.cpitch;
-            float *const out_coarse = F.out_coarse, *const out_depth = F.flt_depth;
-            uint8_t *const out_coarse_valid = F.out_coarse_valid, *const out_valid = F.flt_valid;
-            const int rb = warp * KP;
-            auto store = [&](int k, float out, bool v) {
-                const int y = y0 + rb + k;
+            float *const out_depth = F.flt_depth;
+            uint8_t *const out_valid = F.flt_valid;
+            auto store = [&](int tx, int ty, float out, bool v) {
+                const int x = x0 + tx, y = y0 + ty;
                 if (x < gw && y < gh) {
                     const int64_t o = (int64_t)y * gw + x;
-                    if (SRC == SRC_COARSE) {
-                        out_s1[(int64_t)y * cpitch + x] = make_float2(out, v ? 1.0f : 0.0f);
-                        if (out_coarse) out_coarse[o] = out;
-                        if (out_coarse_valid) out_coarse_valid[o] = v;
-                    } else {
-                        out_depth[o] = out;
-                        out_valid[o] = v;
-                    }
+                    out_depth[o] = out;
+                    out_valid[o] = v;
                 }
             };
-            auto mark_rows = [&](const bool *val, int rbase) {   // flag the second-stage tiles valid pixels reach
-                if (SRC == SRC_COARSE && B->tl_th[1] > 0) {
-                    uint32_t cols = 0u;
-                    int kf = KP, kl = -1;
-#pragma unroll
-                    for (int k = 0; k < KP; ++k) {
-                        const uint32_t m = __ballot_sync(0xffffffffu, val[k] && x < gw && y0 + rbase + k < gh);
-                        cols |= m;
-                        if (m) {
-                            kf = min(kf, k);
-                            kl = k;
-                        }
-                    }
-                    if (cols)
-                        mark_reach(F.tflags[1], B->tl_tw[1], B->tl_th[1], B->tl_r[1], a.pool, F.W, F.H,
-                                   x0 + __ffs(cols) - 1, x0 + 31 - __clz(cols), y0 + rbase + kf, y0 + rbase + kl,
-                                   lane);
-                }
-            };
-            scatter_tile<SRC, R, KP, NW>(F, a, x0, y0, gw, gh, rawA(buf), rawB(buf), smem, [&]() {
+            sparse_tile<R, KP, NW>(a, x0, y0, gw, gh, rawA(buf), rawB(buf), smem, [&]() {
                 if (threadIdx.x == 0 && n1 < total) advance();   // off the path of the CTA's barriers
-            }, store, mark_rows);
-            __syncthreads();   // lists, accumulators and raw[buf] are reused by the next tile
+            }, store);
+            __syncthreads();   // records and raw[buf] are reused by the next tile
             continue;
         }
         const uint8_t *rgbraw = rawA(buf);

@@ -39,24 +39,24 @@ DZ_TMA_LOOKUPS(DZ_TMA_CASES, base)
 int jbf_tma_variants(int src, int r, int form, TmaVariant *out, int cap) {
     int n = base_variants(src, r, form, out, cap);
     n += jbf_tma_exp_variants(src, r, form, out + n, cap - n);
-    return n + jbf_tma_sc_variants(src, r, form, out + n, cap - n);
+    return n + jbf_tma_sp_variants(src, r, form, out + n, cap - n);
 }
 
 bool jbf_tma_info(int src, int r, TmaVariant v, int form, TmaKernelInfo *out) {
     *out = TmaKernelInfo{};
     return base_info(src, r, v, form, out) || jbf_tma_exp_info(src, r, v, form, out) ||
-           jbf_tma_sc_info(src, r, v, form, out);
+           jbf_tma_sp_info(src, r, v, form, out);
 }
 
 cudaError_t jbf_tma_prepare(int src, int r, TmaVariant v, int form) {
-    return form == TMA_FORM_SCATTER ? jbf_tma_sc_prepare(src, r, v, form)
+    return form == TMA_FORM_SPARSE ? jbf_tma_sp_prepare(src, r, v, form)
            : form >= TMA_FORM_EXP   ? jbf_tma_exp_prepare(src, r, v, form)
                                     : base_prepare(src, r, v, form);
 }
 
 cudaError_t launch_jbf_tma(int src, int r, TmaVariant v, int form, const BatchDev *b, const StageArgs &a, int grid,
                            cudaStream_t s) {
-    return form == TMA_FORM_SCATTER ? jbf_tma_sc_launch(src, r, v, form, b, a, grid, s)
+    return form == TMA_FORM_SPARSE ? jbf_tma_sp_launch(src, r, v, form, b, a, grid, s)
            : form >= TMA_FORM_EXP   ? jbf_tma_exp_launch(src, r, v, form, b, a, grid, s)
                                     : base_launch(src, r, v, form, b, a, grid, s);
 }
@@ -70,7 +70,7 @@ cudaError_t launch_tile_mark(int src, const BatchDev *b, int stage, int th, int 
 }
 
 int occupancy_jbf_tma(int src, int r, TmaVariant v, int form) {
-    const int n = form == TMA_FORM_SCATTER ? jbf_tma_sc_occupancy(src, r, v, form)
+    const int n = form == TMA_FORM_SPARSE ? jbf_tma_sp_occupancy(src, r, v, form)
                   : form >= TMA_FORM_EXP   ? jbf_tma_exp_occupancy(src, r, v, form)
                                            : base_occupancy(src, r, v, form);
     return n > 0 ? n : 1;

@@ -298,10 +298,11 @@ std::vector<FilterSel> filter_candidates(const densify_params &p, int kind, int 
             const double kc = log2e / (2.0 * (double)st.sigma_c * (double)st.sigma_c);
             const double kp = log2e / (2.0 * (double)st.sigma_p * (double)st.sigma_p);
             if (p.kernel_variant == 0 && kc * 3.0 * 128.0 * 128.0 + kp * 2.0 * r * r <= kExpRange) {
+                // the single stage on the z-buffer (a few percent of the pixels observed): the sparse
+                // form first, whose work follows the observations; then the gather forms
+                if (kind == 0) add_tma(TMA_FORM_SPARSE);
                 add_tma(TMA_FORM_EXP_PAIRS);
                 add_tma(TMA_FORM_EXP);
-                // the single stage on the sparse z-buffer: Algorithm 1's scatter form, for the tuner
-                if (kind == 0) add_tma(TMA_FORM_SCATTER);
             }
             add_tma(TMA_FORM_FP32);
         }
@@ -671,7 +672,7 @@ void cache_store(const std::string &key, const std::string &val) {
 }
 
 std::string cand_name(const FilterSel &f) {
-    static const char *forms[] = {"fp32", "fp16", "exp", "exp_pairs", "scatter"};
+    static const char *forms[] = {"fp32", "fp16", "exp", "exp_pairs", "sparse"};
     return std::string(f.tma ? "tma" : "plain") + ":kp" + std::to_string(f.kp) + ":nw" + std::to_string(f.nw) +
            (f.tma ? std::string(":") + forms[f.form] : std::string());
 }
@@ -1510,7 +1511,7 @@ int32_t densify_describe(densify_ctx *c, char *buf, int32_t cap) {
                       "\"form\": \"%s\", \"ctas_per_sm\": %d%s",
                       f.tma ? "tma" : "plain", f.kp, f.nw, f.tile_w, f.tile_h, f.half ? "true" : "false",
                       f.half                          ? "fp16"
-                      : f.form == TMA_FORM_SCATTER   ? "fp32_scatter"
+                      : f.form == TMA_FORM_SPARSE    ? "fp32_sparse"
                       : f.form == TMA_FORM_EXP_PAIRS ? "fp32_expanded_pairs"
                       : f.form == TMA_FORM_EXP        ? "fp32_expanded"
                                                       : "fp32",

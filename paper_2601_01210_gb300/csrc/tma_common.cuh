@@ -67,18 +67,17 @@ constexpr int ceil_to(int x, int m) { return (x + m - 1) / m * m; }
 
 // Tile geometry shared by the kernel and the host (tensor-map boxes).
 // Arithmetic forms of the kernels (the host's TMA_FORM_* values).
-enum { FORM_FP32 = 0, FORM_FP16 = 1, FORM_EXP = 2, FORM_EXP_PAIRS = 3, FORM_SCATTER = 4 };
+enum { FORM_FP32 = 0, FORM_FP16 = 1, FORM_EXP = 2, FORM_EXP_PAIRS = 3, FORM_SPARSE = 4 };
 
 // Tile geometry shared by the kernels and the host (tensor-map boxes). The
 // paired form filters 64-column tiles, a thread taking columns c and c + 32;
 // its staged records are slots of SP = 32 + 2R per staged row, slot s holding
-// staged columns s and s + 32 side by side. The scatter form (jbf_scatter.cuh)
-// keeps per-warp source lists (32 bytes a source, room for every position of the
-// warp's RPW staged rows), the tile's target colours, its accumulators and one
-// 64-bit observation mask per staged row.
+// staged columns s and s + 32 side by side. The sparse form (jbf_sparse.cuh)
+// keeps a 32-byte record per staged position (written for the observed ones)
+// and one 64-bit observation mask per staged row.
 template <int SRC, int R, int KP, int NW_ = 8, int FORM = FORM_FP32>
 struct TmaGeom {
-    static constexpr bool EXP = FORM == FORM_EXP, PAIRS = FORM == FORM_EXP_PAIRS, SCATTER = FORM == FORM_SCATTER;
+    static constexpr bool EXP = FORM == FORM_EXP, PAIRS = FORM == FORM_EXP_PAIRS, SPARSE = FORM == FORM_SPARSE;
     static constexpr int TW = PAIRS ? 64 : 32, NW = NW_, TH = NW * KP, SW = TW + 2 * R, SH = TH + 2 * R;
     static constexpr int SP = PAIRS ? 32 + 2 * R : SW;   // staged records per staged row
     // RGB bytes: box starts at byte 3*x0 - RGB_LEAD (x0 is a multiple of 32, so 3*x0 of 16)
@@ -108,22 +107,17 @@ struct TmaGeom {
     static constexpr int TX_BYTES = SRC == SRC_COARSE ? G_BX * G_BY * 4 + S_BX * S_BY * 4
                                     : SRC == SRC_UP   ? RGB_BX * RGB_BY + C_BX * C_BY * 8
                                                       : RGB_BX * RGB_BY + Z_BX * Z_BY * 4;
-    // scatter form: staged rows per warp (warp w lists rows w, w + NW, ...)
+    // sparse form: staged rows per warp in the record pass (warp w scans rows w, w + NW, ...)
     static constexpr int RPW = (SH + NW - 1) / NW;
-    // staged records: float4 per position (two float4 per slot in the paired form; two per source
-    // in the scatter form's lists)
-    static constexpr int STAGED = SCATTER ? NW * RPW * SW * 32
+    // staged records: float4 per position (two float4 per slot in the paired form, two per
+    // position in the sparse form)
+    static constexpr int STAGED = SPARSE ? 2 * SH * SW * 16
                                   : PAIRS ? 2 * SH * SP * 16
                                   : SRC == SRC_COARSE && !EXP ? 0 : SH * SW * 16;
     // expanded forms: F_q times depth (float per position, float2 per slot)
     static constexpr int STAGED_G = PAIRS ? SH * SP * 8 : EXP ? ceil_to(SH * SW * 4, 16) : 0;
-    // scatter form: target colours (float4), numerator and weight-sum accumulators (two float
-    // arrays) and row masks (uint64); a tile row is TWP = TW + 1 elements apart, so that the lanes'
-    // targets, which lie in different rows of the same column as often as not, spread over the banks
-    static constexpr int TWP = TW + 1;
-    static constexpr int TGT = SCATTER ? TH * TWP * 16 : 0;
-    static constexpr int ACC = SCATTER ? ceil_to(2 * TH * TWP * 4, 16) : 0;
-    static constexpr int ROWS = SCATTER ? ceil_to(SH * 8, 16) : 0;
+    // sparse form: one observation mask (uint64) per staged row
+    static constexpr int ROWS = SPARSE ? ceil_to(SH * 8, 16) : 0;
     // observation bitmap: bit i = staged record i observed; one word per 32 records for every
     // record the conversion loop visits, plus a zero guard word (the paired form keeps one
     // bitmap per half of its slots)
@@ -135,9 +129,7 @@ struct TmaGeom {
     static constexpr int OFF_RAW = 0;
     static constexpr int OFF_STAGED = OFF_RAW + 2 * (RAW_A + RAW_B);
     static constexpr int OFF_G = OFF_STAGED + STAGED;
-    static constexpr int OFF_TGT = OFF_G + STAGED_G;
-    static constexpr int OFF_ACC = OFF_TGT + TGT;
-    static constexpr int OFF_ROWS = OFF_ACC + ACC;
+    static constexpr int OFF_ROWS = OFF_G + STAGED_G;
     static constexpr int OFF_OBS = OFF_ROWS + ROWS;
     static constexpr int OFF_HOR = OFF_OBS + OBS;
     static constexpr int OFF_BAR = ceil_to(OFF_HOR + HOR, 16);

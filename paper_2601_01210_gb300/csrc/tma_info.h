@@ -32,9 +32,10 @@ struct TmaKernelInfo {
 // squared colour distance expanded into a dot product (weights kept in range
 // only while kc * 3 * 128^2 + kp * 2 R^2 <= kExpRange, see jbf_tma.cuh), the
 // expanded form on pairs of output columns in packed two-lane FP32 arithmetic
-// (64-column tiles, see jbf_pair.cuh), and Algorithm 1's scatter form on the same
-// expanded weights (work per observed tap; sparse inputs, see jbf_scatter.cuh).
-enum { TMA_FORM_FP32 = 0, TMA_FORM_FP16 = 1, TMA_FORM_EXP = 2, TMA_FORM_EXP_PAIRS = 3, TMA_FORM_SCATTER = 4 };
+// (64-column tiles, see jbf_pair.cuh), and the sparse form on the same weights (a warp
+// walks only the observed positions of its block's footprint; the single stage on the
+// z-buffer, see jbf_sparse.cuh).
+enum { TMA_FORM_FP32 = 0, TMA_FORM_FP16 = 1, TMA_FORM_EXP = 2, TMA_FORM_EXP_PAIRS = 3, TMA_FORM_SPARSE = 4 };
 constexpr double kExpRange = 100.0;
 
 // Instantiated variants of (source, radius, form).
@@ -56,12 +57,12 @@ cudaError_t jbf_tma_exp_launch(int src, int r, TmaVariant v, int form, const Bat
                                int grid, cudaStream_t s);
 int jbf_tma_exp_occupancy(int src, int r, TmaVariant v, int form);
 
-// the scatter form's instantiations (k_jbf_scatter.cu)
-int jbf_tma_sc_variants(int src, int r, int form, TmaVariant *out, int cap);
-bool jbf_tma_sc_info(int src, int r, TmaVariant v, int form, TmaKernelInfo *out);
-cudaError_t jbf_tma_sc_prepare(int src, int r, TmaVariant v, int form);
-cudaError_t jbf_tma_sc_launch(int src, int r, TmaVariant v, int form, const BatchDev *b, const StageArgs &a,
+// the sparse form's instantiations (k_jbf_sparse.cu)
+int jbf_tma_sp_variants(int src, int r, int form, TmaVariant *out, int cap);
+bool jbf_tma_sp_info(int src, int r, TmaVariant v, int form, TmaKernelInfo *out);
+cudaError_t jbf_tma_sp_prepare(int src, int r, TmaVariant v, int form);
+cudaError_t jbf_tma_sp_launch(int src, int r, TmaVariant v, int form, const BatchDev *b, const StageArgs &a,
                               int grid, cudaStream_t s);
-int jbf_tma_sc_occupancy(int src, int r, TmaVariant v, int form);
+int jbf_tma_sp_occupancy(int src, int r, TmaVariant v, int form);
 
 }  // namespace dz

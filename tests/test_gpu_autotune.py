@@ -65,7 +65,7 @@ def test_tuned_equals_untuned_and_cache_is_reused(tmp_path, monkeypatch, precisi
 
 
 _FORM_TAG = {"fp32": "fp32", "fp16": "fp16", "fp32_expanded": "exp", "fp32_expanded_pairs": "exp_pairs",
-             "fp32_scatter": "scatter"}
+             "fp32_sparse": "sparse"}
 
 
 @pytest.mark.parametrize("stage", [0, 1])
@@ -105,8 +105,8 @@ def test_every_candidate_matches_the_plain_kernel(tmp_path, monkeypatch, stage):
 
 @pytest.mark.parametrize("radius", [2, 4, 7])
 def test_every_single_stage_candidate_matches_the_plain_kernel(tmp_path, monkeypatch, radius):
-    """The single stage on the z-buffer: each candidate the tuner may pick (the gather forms and
-    Algorithm 1's scatter form), forced through a tuning-cache entry, gives the plain kernel's
+    """The single stage on the z-buffer: each candidate the tuner may pick (the sparse form and the
+    gather forms), forced through a tuning-cache entry, gives the plain kernel's
     integer decisions and its depths within FP32 rounding (frames of three sizes, ragged edges)."""
     import torch
     from paper_2601_01210_gb300 import Densifier, build
@@ -146,4 +146,4 @@ def test_every_single_stage_candidate_matches_the_plain_kernel(tmp_path, monkeyp
                 assert np.array_equal(a[k], b[k]), (name, k)
             np.testing.assert_allclose(a["depth"], b["depth"], rtol=3e-5, err_msg=name)
         tried.add(c["form"])
-    assert "fp32_scatter" in tried
+    assert "fp32_sparse" in tried

@@ -17,7 +17,7 @@ CSRC = os.path.join(ROOT, "paper_2601_01210_gb300", "csrc")
 
 def variants():
     out = []
-    for fn in ("k_jbf_tma.cu", "k_jbf_tma_exp.cu", "k_jbf_scatter.cu"):
+    for fn in ("k_jbf_tma.cu", "k_jbf_tma_exp.cu", "k_jbf_sparse.cu"):
         text = open(os.path.join(CSRC, fn)).read()
         out += re.findall(r"X\((SRC_\w+),\s*(\d+),\s*(\d+),\s*(FORM_\w+),\s*(\d+)\)", text)
     return out
@@ -26,7 +26,7 @@ def variants():
 def test_variant_lists_parse():
     v = variants()
     assert len(v) >= 20 and ("SRC_UP", "2", "4", "FORM_EXP_PAIRS", "4") in v
-    assert ("SRC_ZBUF", "7", "4", "FORM_SCATTER", "8") in v
+    assert ("SRC_ZBUF", "7", "4", "FORM_SPARSE", "8") in v
 
 
 def test_every_variant_stays_in_bounds(tmp_path):

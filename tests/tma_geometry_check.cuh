@@ -51,30 +51,23 @@ int check(const char *name) {
     if (G::OFF_STAGED % 16 || G::OFF_G % 16 || G::OFF_OBS % 4 || G::OFF_BAR % 8) rep.fail("layout alignment", G::OFF_STAGED, G::OFF_G, G::OFF_OBS);
     if (G::SMEM > 232448) rep.fail("shared memory", G::SMEM, 232448, 0);
     if (G::NCONV * G::NT < G::SH * G::SP) rep.fail("conversion coverage", G::NCONV, G::NT, G::SH * G::SP);
-    if (G::SCATTER) {
-        // every staged row belongs to one warp's list, whose room holds a source per position of its rows
-        if (G::NW * G::RPW < G::SH) rep.fail("scatter rows", G::NW, G::RPW, G::SH);
-        if (G::TW != 32 || G::SW > 64) rep.fail("scatter tile / row mask", G::TW, G::SW, 0);
-        if (G::OFF_TGT % 16 || G::OFF_ACC % 16 || G::OFF_ROWS % 16) rep.fail("scatter layout", G::OFF_TGT, G::OFF_ACC, G::OFF_ROWS);
-        for (int warp = 0; warp < G::NW; ++warp) {
-            int rows = 0;
-            for (int sy = warp; sy < G::SH; sy += G::NW) ++rows;
-            if (rows > G::RPW) rep.fail("scatter list room", warp, rows, G::RPW);
-            if (2 * G::NW * G::RPW * G::SW * 16 > G::STAGED) rep.fail("scatter list", warp, G::RPW, G::SW);
-        }
-        // every source (sy, sx) and offset (ox, oy): a target inside the tile indexes the tile's arrays
-        for (int sy = 0; sy < G::SH; ++sy)
-            for (int sx = 0; sx < G::SW; ++sx)
-                for (int oy = -R; oy <= R; ++oy)
-                    for (int ox = -R; ox <= R; ++ox) {
-                        const int ty = sy - R + oy, tx = sx - R + ox;
-                        if (ty < 0 || ty >= G::TH || tx < 0 || tx >= G::TW) continue;
-                        const int i = (ty * G::TWP + sx - R) + ox;
-                        if (i < 0 || G::TH * G::TWP + i >= G::ACC / 4 || i >= G::TGT / 16) rep.fail("scatter target", sy, sx, ox);
+    if (G::SPARSE) {
+        constexpr int FW = 8 + 2 * R;
+        if (G::TW != 32 || G::TH % 8 || G::SW > 64) rep.fail("sparse tile / row mask", G::TW, G::TH, G::SW);
+        if (G::NW * G::RPW < G::SH) rep.fail("sparse record rows", G::NW, G::RPW, G::SH);
+        if (G::STAGED < 2 * G::SH * G::SW * 16) rep.fail("sparse records", G::STAGED, G::SH, G::SW);
+        if (G::OFF_ROWS % 16 || G::ROWS < G::SH * 8) rep.fail("sparse row masks", G::OFF_ROWS, G::ROWS, G::SH);
+        // every block's footprint: staged rows and the bits of its row masks
+        for (int by = 0; by < G::TH; by += 8)
+            for (int bx = 0; bx < G::TW; bx += 8) {
+                if (by + 7 + 2 * R >= G::SH) rep.fail("sparse footprint rows", bx, by, R);
+                if (bx + FW > G::SW || bx + FW > 64) rep.fail("sparse footprint columns", bx, by, R);
+                for (int ly = 0; ly < 8; ++ly)
+                    for (int lx = 0; lx < 8; ++lx) {   // a pixel's window for the shifted recomputation
+                        const int px = bx + lx, py = by + ly;
+                        if (py + 2 * R >= G::SH || px + 2 * R >= G::SW) rep.fail("sparse window", px, py, R);
                     }
-        // epilogue row masks: rows ty .. ty + 2R of every output row
-        for (int ty = 0; ty < G::TH; ++ty)
-            if (ty + 2 * R >= G::ROWS / 8) rep.fail("scatter row mask", ty, R, G::ROWS);
+            }
     }
     // ---- taps, validity words and centres of every thread (the same for every tile)
     for (int warp = 0; warp < NW; ++warp)
