@@ -62,6 +62,9 @@ def parse():
                     help="oracle worker processes (one single-threaded oracle per host core)")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving measurement")
     ap.add_argument("--no-fp16", action="store_true", help="skip the FP16-form measurement")
+    ap.add_argument("--no-live-peaks", action="store_true",
+                    help="skip the live instruction-rate microbenchmark (profiling runs: its kernels stay out of "
+                         "the launch list; the committed measurement is used)")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the 320x240 single-stage (FP32, FP16) and uneven 12-view workloads")
     ap.add_argument("--autotune", type=int, default=1, help="1: pick filter kernels on the first batch")
@@ -586,18 +589,26 @@ def host_link_bounds(link, h2d_bytes, d2h_bytes, frames, world=1):
     and one direction at a time (serial)."""
     t_in = h2d_bytes / (link["h2d_GBps"] * 1e9)
     t_out = d2h_bytes / (link["d2h_GBps"] * 1e9)
+    both = link.get("both_GBps")
+    extra = {}
+    if both:   # both directions at once at the measured combined rate
+        extra["duplex_frames_per_s"] = round(frames / max(t_in, t_out, (h2d_bytes + d2h_bytes) / (both * 1e9)) * world, 1)
     return dict(link, bound_frames_per_s=round(frames / max(t_in, t_out) * world, 1),
-                serial_frames_per_s=round(frames / (t_in + t_out) * world, 1),
-                note="copy-engine rates, 256 MiB pinned <-> device, each direction measured alone; bound: both "
-                     "directions at once (the larger of bytes in / h2d rate and bytes out / d2h rate per step); "
-                     "serial: one direction after the other")
+                serial_frames_per_s=round(frames / (t_in + t_out) * world, 1), **extra,
+                note="copy-engine rates, 256 MiB pinned <-> device, each direction alone and both at once; "
+                     "bound: both directions at once at their separate rates (the larger of bytes in / h2d rate "
+                     "and bytes out / d2h rate per step); duplex: the same, also held to the measured combined "
+                     "rate of both directions at once; serial: one direction after the other")
 
 
 def host_link_gbps(dev, mb=256, reps=5):
-    """Pinned host <-> device copy rates (GB/s), CUDA events."""
+    """Pinned host <-> device copy rates (GB/s), CUDA events: each direction alone, and both at once
+    (two streams; the sum of the two directions' bytes over the common time)."""
     import torch
     h = torch.empty(mb << 20, dtype=torch.uint8, pin_memory=True)
     d = torch.empty(mb << 20, dtype=torch.uint8, device=dev)
+    h2 = torch.empty(mb << 20, dtype=torch.uint8, pin_memory=True)
+    d2 = torch.empty(mb << 20, dtype=torch.uint8, device=dev)
     out = {}
     for name, fn in (("h2d_GBps", lambda: d.copy_(h, non_blocking=True)),
                      ("d2h_GBps", lambda: h.copy_(d, non_blocking=True))):
@@ -610,6 +621,17 @@ def host_link_gbps(dev, mb=256, reps=5):
         e1.record()
         torch.cuda.synchronize()
         out[name] = round(reps * (mb << 20) / (e0.elapsed_time(e1) / 1e3) / 1e9, 1)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(s1):
+        for _ in range(reps):
+            d.copy_(h, non_blocking=True)
+    with torch.cuda.stream(s2):
+        for _ in range(reps):
+            h2.copy_(d2, non_blocking=True)
+    torch.cuda.synchronize()
+    out["both_GBps"] = round(2 * reps * (mb << 20) / (time.perf_counter() - t0) / 1e9, 1)
     return out
 
 
@@ -740,20 +762,23 @@ def ours_arm(a, rank, world, local_rank):
     # slots on the context's own streams so that one batch's copies overlap the next batch's kernels
     e2e = None
     if not a.no_e2e:
-        hb = [[fb(i, memory=DENSIFY_MEM_HOST, depth_out=False) for i in range(B)] for _ in range(2)]
-        pe = dict(params, timing=0, batches_in_flight=2, max_batch=B, max_inflight=4 * B,
-                  hbm_budget_bytes=max(2 << 30, 2 * B * 64 << 20))
+        # three batches in flight (three sets of page-locked buffers): while one batch's points travel to
+        # the host, the next one's inputs travel to the device and a third one computes
+        NB = 3
+        hb = [[fb(i, memory=DENSIFY_MEM_HOST, depth_out=False) for i in range(B)] for _ in range(NB)]
+        pe = dict(params, timing=0, batches_in_flight=NB, max_batch=B, max_inflight=(NB + 1) * B,
+                  hbm_budget_bytes=max(2 << 30, NB * B * 64 << 20))
         with Densifier(pe, device=local_rank) as d2:
             def e2e_steps(n):
-                prev = None
+                pending = []
                 for k in range(n):
-                    ts = [d2.submit(b.frame) for b in hb[k % 2]]   # the B-th submit launches the batch
-                    if prev:
-                        for t in prev:
+                    pending.append([d2.submit(b.frame) for b in hb[k % NB]])   # the B-th submit launches it
+                    if len(pending) == NB:   # collect the oldest batch before its buffers are reused
+                        for t in pending.pop(0):
                             d2.poll(t, -1)
-                    prev = ts
-                for t in prev or []:
-                    d2.poll(t, -1)
+                for ts in pending:
+                    for t in ts:
+                        d2.poll(t, -1)
 
             e2e_steps(3)
             if world > 1:
@@ -795,8 +820,11 @@ def ours_arm(a, rank, world, local_rank):
     except Exception:
         pass
     try:
-        from paper_2601_01210_gb300 import alu_peaks
-        alu_live = alu_peaks.measure(local_rank)
+        if a.no_live_peaks:
+            alu_live = {"skipped": "--no-live-peaks"}
+        else:
+            from paper_2601_01210_gb300 import alu_peaks
+            alu_live = alu_peaks.measure(local_rank)
     except Exception as ex:   # the bench still reports against the committed measurement
         alu_live = {"error": str(ex)[:200]}
     alu_src = alu_file if alu_file else (alu_live if "tap_peaks" in (alu_live or {}) else None)

@@ -113,7 +113,12 @@ typedef struct densify_stage {
  *                 launch (continuous batching).
  *   hbm_budget_bytes   device memory the context may use for per-frame
  *                 scratch (z-buffers, coarse maps, staging of host frames);
- *                 admission fails with DENSIFY_E_AGAIN when it is full.
+ *                 admission fails with DENSIFY_E_AGAIN when it is full. In the
+ *                 two-stage form with stage2_input 0 and no occlusion removal, a
+ *                 quarter of it holds z-buffers that are kept empty between
+ *                 frames (the pooling kernel empties the cells it read, so no
+ *                 frame needs a clear), used by every frame that does not ask
+ *                 for out_zbuf.
  *   use_graphs    1: replay each batch slot's launch sequence as a CUDA graph.
  *   timing        1: record CUDA events around every kernel of every batch and
  *                 accumulate per-kernel device time (densify_kernel_times);

@@ -91,7 +91,12 @@ struct alignas(64) FrameDev {
     // of two stages, the first filter for the second, tile_mark_kernel for a single stage)
     int32_t *tflags[2];
     int32_t ntflags;
-    int32_t pad1;
+    // z-buffer upkeep: zclear = the batch's first kernel clears it; zrestore = it comes from the
+    // context's pool of clean z-buffers and the pooling kernel, its last reader, writes the empty
+    // pattern back into the cells it finds observed
+    uint8_t zclear;
+    uint8_t zrestore;
+    uint8_t pad1[2];
 };
 
 struct BatchDev {
@@ -191,6 +196,8 @@ int occupancy_prepost(KernelId k);
 constexpr int kOccTile = 32;   // occlusion kernel output tile (32 x 32)
 
 cudaError_t launch_prep(const BatchDev *b, int grid, cudaStream_t s);
+// every word of [p, p + n) set to the empty z-buffer cell
+cudaError_t launch_fill_empty(uint32_t *p, uint64_t n, cudaStream_t s);
 cudaError_t launch_project(const BatchDev *b, int grid, cudaStream_t s);
 cudaError_t launch_pool(const BatchDev *b, int pool, int grid, cudaStream_t s);
 cudaError_t launch_bp_count(const BatchDev *b, int grid, cudaStream_t s);

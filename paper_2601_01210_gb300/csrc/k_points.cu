@@ -35,6 +35,7 @@ __device__ __forceinline__ double compose_entry(const double *c2w, const double 
     return s;
 }
 
+// The batch's first kernel: calibration compose, tile flags and counters, z-buffer clear.
 __global__ void __launch_bounds__(kThreads) prep_kernel(BatchDev *__restrict__ B) {
     // the batch's clear prefix and each frame's z-buffer in shared memory: a work item then starts
     // its stores without a chain of dependent global loads
@@ -57,22 +58,24 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(BatchDev *__restrict__ B
             for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) fl[i] = 0;
         }
     }
+    // calibration compose: block f takes frame f
+    for (int f = blockIdx.x; f < nf; f += gridDim.x) {
+        FrameDev &F = B->f[f];
+        const int t = threadIdx.x;
+        if (t < F.num_scans * 12) {
+            const int s = t / 12, e = t % 12;
+            F.scans[s].M[e] = __double2float_rn(compose_entry(F.c2w, F.scans[s].l2w, e / 4, e % 4));
+        } else if (t >= 64 && t < 76) {
+            const int e = t - 64;
+            F.c2w32[e] = __double2float_rn(F.c2w[(e / 4) * 4 + (e % 4)]);
+        }
+    }
     __syncthreads();
+    // z-buffer clear: the chunks of the frames that clear (a frame from the clean pool has none)
     const int total = s_pre[nf];
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int f = find_segment(s_pre, nf, item);
         const int c = item - s_pre[f];
-        if (c == 0) {
-            FrameDev &F = B->f[f];
-            const int t = threadIdx.x;
-            if (t < F.num_scans * 12) {
-                const int s = t / 12, e = t % 12;
-                F.scans[s].M[e] = __double2float_rn(compose_entry(F.c2w, F.scans[s].l2w, e / 4, e % 4));
-            } else if (t >= 64 && t < 76) {
-                const int e = t - 64;
-                F.c2w32[e] = __double2float_rn(F.c2w[(e / 4) * 4 + (e % 4)]);
-            }
-        }
         const int64_t n = s_n[f];
         const int64_t w0 = (int64_t)c * kZbWordsPerChunk;
         const int64_t w1 = min(n, w0 + kZbWordsPerChunk);
@@ -168,6 +171,18 @@ __global__ void __launch_bounds__(kThreads) project_kernel(const BatchDev *__res
                 if (k < n) project_one(M, a[k].x, a[k].y, a[k].z, C, zbuf);
         }
     }
+}
+
+__global__ void fill_empty_kernel(uint32_t *__restrict__ p, uint64_t n) {
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        p[i] = kEmpty;
+}
+
+cudaError_t launch_fill_empty(uint32_t *p, uint64_t n, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const uint64_t blocks = (n + kThreads - 1) / kThreads;
+    fill_empty_kernel<<<(unsigned)(blocks < 4096 ? blocks : 4096), kThreads, 0, s>>>(p, n);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_prep(const BatchDev *b, int grid, cudaStream_t s) {

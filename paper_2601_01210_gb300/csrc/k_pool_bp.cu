@@ -24,12 +24,14 @@ __device__ __forceinline__ bool pool_words_ok(const FrameDev &F) {
     return ((((uintptr_t)F.zbuf) | ((uintptr_t)F.rgb)) & 3u) == 0 && (F.rgb_pitch & 3) == 0;
 }
 
+// The guide is the colour sum times the reciprocal of the block's pixel count (within one rounding
+// of the quotient; the filter's tolerance covers it).
 __device__ __forceinline__ void pool_store(const FrameDev &F, int I, int J, float rr, float gg, float bb, float cnt,
-                                           float s, float npx) {
+                                           float s, float inv_npx) {
     const int64_t o = (int64_t)J * F.cpitch + I;
     float4 *const guide = F.cguide;   // both pointers read before either store
     float *const sums = F.cssum;
-    guide[o] = make_float4(__fdiv_rn(rr, npx), __fdiv_rn(gg, npx), __fdiv_rn(bb, npx), cnt);
+    guide[o] = make_float4(rr * inv_npx, gg * inv_npx, bb * inv_npx, cnt);
     sums[o] = s;
 }
 
@@ -52,6 +54,9 @@ __device__ __forceinline__ void pool_one(const FrameDev &F, int I, int J, int f,
         }
         float s = 0.0f, cnt = 0.0f;
         uint32_t rs = 0u, gs = 0u, bs = 0u;
+        uint32_t *const zb = F.zbuf;   // read before any store (a store could alias the descriptor)
+        const int64_t zp = F.zpitch;
+        const bool restore = F.zrestore;
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
 #pragma unroll
@@ -59,6 +64,7 @@ __device__ __forceinline__ void pool_one(const FrameDev &F, int I, int J, int f,
                 if (z[r][j] != kEmpty) {
                     s = __fadd_rn(s, __uint_as_float(z[r][j]));
                     cnt += 1.0f;
+                    if (restore) zb[(int64_t)(y0 + r) * zp + x0 + j] = kEmpty;   // the clean pool's invariant
                 }
             }
             // bytes c0 .. c8 of the row (r, g, b of 3 pixels) into a0 = c0..c3, a1 = c4..c7, a2 = c8..
@@ -69,26 +75,29 @@ __device__ __forceinline__ void pool_one(const FrameDev &F, int I, int J, int f,
             gs = __dp4a(__byte_perm(a0, a1, 0x0741), 0x00010101u, gs);   // c1 + c4 + c7
             bs = __dp4a(__byte_perm(a0, a1, 0x0052), 0x00000101u, bs) + (a2 & 0xFFu);   // c2 + c5 + c8
         }
-        pool_store(F, I, J, (float)rs, (float)gs, (float)bs, cnt, s, 9.0f);
+        pool_store(F, I, J, (float)rs, (float)gs, (float)bs, cnt, s, 1.0f / 9.0f);
         cnt_out = cnt;
     } else {
         const int x1 = min(x0 + f, F.W), y1 = min(y0 + f, F.H);
         float s = 0.0f, cnt = 0.0f, r = 0.0f, g = 0.0f, b = 0.0f;
+        uint32_t *const zb = F.zbuf;
+        const bool restore = F.zrestore;
         for (int y = y0; y < y1; ++y) {
-            const uint32_t *zr = F.zbuf + (int64_t)y * F.zpitch;
+            uint32_t *zr = zb + (int64_t)y * F.zpitch;
             const uint8_t *cr = F.rgb + (int64_t)y * F.rgb_pitch;
             for (int x = x0; x < x1; ++x) {
                 const uint32_t zz = zr[x];
                 if (zz != kEmpty) {
                     s = __fadd_rn(s, __uint_as_float(zz));
                     cnt += 1.0f;
+                    if (restore) zr[x] = kEmpty;
                 }
                 r += (float)cr[3 * x];
                 g += (float)cr[3 * x + 1];
                 b += (float)cr[3 * x + 2];
             }
         }
-        pool_store(F, I, J, r, g, b, cnt, s, (float)((x1 - x0) * (y1 - y0)));
+        pool_store(F, I, J, r, g, b, cnt, s, 1.0f / (float)((x1 - x0) * (y1 - y0)));
         cnt_out = cnt;
     }
 }
@@ -157,14 +166,17 @@ __device__ __forceinline__ uint32_t valid_bits4(const uint8_t *v, int64_t p, int
 constexpr int kCountParts = 4;
 __global__ void __launch_bounds__(kThreads) bp_count_kernel(const BatchDev *__restrict__ B) {
     constexpr int kGroups = kBpWarps / kCountParts;   // part groups of a chunk
+    __shared__ int32_t s_pre[kMaxBatch + 1];          // chunk prefix, searched per work item
     const int nf = B->n_frames;
-    const int total = B->bp_pre[nf] * kGroups;
+    for (int i = threadIdx.x; i <= nf; i += kThreads) s_pre[i] = B->bp_pre[i];
+    __syncthreads();
+    const int total = s_pre[nf] * kGroups;
     const int lane = threadIdx.x & 31;
     for (int wi = blockIdx.x * kBpWarps + (threadIdx.x >> 5); wi < total; wi += gridDim.x * kBpWarps) {
         const int item = wi / kGroups;
-        const int fi = find_segment(B->bp_pre, nf, item);
+        const int fi = find_segment(s_pre, nf, item);
         const FrameDev &F = B->f[fi];
-        const int sub0 = (item - B->bp_pre[fi]) * kBpWarps + (wi % kGroups) * kCountParts;   // the frame's first part
+        const int sub0 = (item - s_pre[fi]) * kBpWarps + (wi % kGroups) * kCountParts;   // the frame's first part
         const int64_t n = (int64_t)F.W * F.H;
         const bool vec = (((uintptr_t)F.out_valid) & 15u) == 0;
         uint4 w[kCountParts];
@@ -250,13 +262,16 @@ __device__ __forceinline__ void row_col(int64_t p, int W, float inv_w, int &y, i
 
 __global__ void __launch_bounds__(kThreads, 4) bp_write_kernel(const BatchDev *__restrict__ B) {
     __shared__ float4 stage[kThreads / 32][128];
+    __shared__ int32_t s_pre[kMaxBatch + 1];          // chunk prefix, searched per work item
     const int nf = B->n_frames;
-    const int total = B->bp_pre[nf];
+    for (int i = threadIdx.x; i <= nf; i += kThreads) s_pre[i] = B->bp_pre[i];
+    __syncthreads();
+    const int total = s_pre[nf];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
-        const int fi = find_segment(B->bp_pre, nf, item);
+        const int fi = find_segment(s_pre, nf, item);
         const FrameDev &F = B->f[fi];
-        const int c = item - B->bp_pre[fi];
+        const int c = item - s_pre[fi];
         const int W = F.W;
         const int64_t n = (int64_t)W * F.H;
         const bool vvalid = (((uintptr_t)F.out_valid) & 3u) == 0;
@@ -269,6 +284,9 @@ __global__ void __launch_bounds__(kThreads, 4) bp_write_kernel(const BatchDev *_
         const float r20 = c2w[8], r21 = c2w[9], r22 = c2w[10], t2 = c2w[11];
         const float ifx = 1.0f / F.fx, ify = 1.0f / F.fy, iw = 1.0f / (float)W;
         float4 *st = stage[warp];
+        // staged point j sits at j ^ ((j >> 2) & 7): a lane's four consecutive points and the read-back's
+        // eight consecutive points of a quarter warp then fall on distinct 16-byte bank groups
+        auto sw = [](uint32_t j) { return j ^ ((j >> 2) & 7u); };
         // all loads of the four steps (validity, depth, colour) are issued before any is used:
         // one memory round trip per chunk; depth and colour lines are mostly needed anyway
         uint32_t m[4];
@@ -330,8 +348,8 @@ __global__ void __launch_bounds__(kThreads, 4) bp_write_kernel(const BatchDev *_
                         if (m[it] >> k & 1u) {
                             const float Z = z[k];
                             const float u = fmaf((float)k, ifx, u0);
-                            st[j++] = make_float4(fmaf(fmaf(r00, u, b0), Z, t0), fmaf(fmaf(r10, u, b1), Z, t1),
-                                                  fmaf(fmaf(r20, u, b2), Z, t2), __uint_as_float(col[k] | 0xFF000000u));
+                            st[sw(j++)] = make_float4(fmaf(fmaf(r00, u, b0), Z, t0), fmaf(fmaf(r10, u, b1), Z, t1),
+                                                      fmaf(fmaf(r20, u, b2), Z, t2), __uint_as_float(col[k] | 0xFF000000u));
                         }
                     }
                 } else {
@@ -347,7 +365,7 @@ __global__ void __launch_bounds__(kThreads, 4) bp_write_kernel(const BatchDev *_
                             const float Z = F.out_depth[p];
                             const float X = ((float)x + 0.5f - F.cx) * Z * ifx;
                             const float Yz = ((float)y + 0.5f - F.cy) * ify * Z;
-                            st[j++] = make_float4(fmaf(r00, X, fmaf(r01, Yz, fmaf(r02, Z, t0))),
+                            st[sw(j++)] = make_float4(fmaf(r00, X, fmaf(r01, Yz, fmaf(r02, Z, t0))),
                                                   fmaf(r10, X, fmaf(r11, Yz, fmaf(r12, Z, t1))),
                                                   fmaf(r20, X, fmaf(r21, Yz, fmaf(r22, Z, t2))),
                                                   __uint_as_float(rgba));
@@ -359,7 +377,7 @@ __global__ void __launch_bounds__(kThreads, 4) bp_write_kernel(const BatchDev *_
             // the part's points from off on, as far as the caller's capacity goes
             const uint32_t fit = (uint32_t)max((int64_t)0, min((int64_t)tot, F.points_cap - off));
             float4 *dst = F.out_points + off;
-            for (uint32_t i = lane; i < fit; i += 32) dst[i] = st[i];
+            for (uint32_t i = lane; i < fit; i += 32) dst[i] = st[sw(i)];
             __syncwarp();
             off += tot;
         }

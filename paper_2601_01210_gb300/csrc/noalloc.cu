@@ -190,6 +190,7 @@ extern "C" DENSIFY_API densify_status densify_frame_noalloc(const densify_params
     d.rgb_pitch = f->rgb_pitch;
     d.zbuf = reinterpret_cast<uint32_t *>(base + off_zbuf);
     d.zbuf_raw = d.zbuf;
+    d.zclear = 1;   // the static scratch holds whatever the last call left: cleared every call
     d.newest_scan = -1;
     if (params->num_stages == 2) {
         d.cguide = reinterpret_cast<float4 *>(base + off_cg);

@@ -107,6 +107,8 @@ struct Layout {
     float4 *points_direct = nullptr;    // device view of a page-locked host point buffer
     int64_t *count_direct = nullptr;    // device view of a page-locked host count
     uint64_t tflags = 0;                // tile flags of the TMA filters (both stages)
+    bool zpooled = false;               // z-buffer from the context's pool of clean z-buffers
+    uint64_t zbytes = 0;                // its size (not part of total)
     uint64_t total = 0;
     bool own_depth = false, own_valid = false;
 };
@@ -115,6 +117,7 @@ struct FrameRec {
     densify_frame fr;
     Layout L;
     uint64_t off = 0;
+    uint64_t zoff = 0;       // offset of a pooled z-buffer
     int state = 0;   // 0 queued, 1 on the GPU, 2 finished
     int slot = -1;
     FrameDev dev;
@@ -200,6 +203,10 @@ struct densify_ctx {
     PrepostArgs pp{};
     void *arena_base = nullptr;
     Arena arena;
+    // clean z-buffers (two-stage contexts whose pooling kernel is the z-buffer's last reader): a free
+    // region of this pool is all empty cells, so a frame's z-buffer needs no clear
+    void *zpool_base = nullptr;
+    Arena zpool;
     std::vector<Slot> slots;
     std::deque<uint64_t> queue;
     std::map<uint64_t, FrameRec> frames;
@@ -218,6 +225,7 @@ struct densify_ctx {
     bool inject_wait_failure = false;   // densify_inject_wait_failure: armed for the next batch
     int64_t batches = 0;                // batches launched
     int max_busy = 0;                   // most batches on the GPU at once
+    bool grids_fixed = false;           // the kernel grids were settled by the first batch
 };
 
 namespace {
@@ -450,7 +458,15 @@ int64_t tile_flag_words(const densify_params &p, int64_t W, int64_t H) {
     return words;
 }
 
-Layout layout_of(const densify_params &p, const densify_frame *f) {
+// The pooling kernel is the last reader of the z-buffer: two stages with the restored first stage
+// as the second stage's only input, no occluded-point removal (which rewrites the z-buffer).
+bool zpool_applies(const densify_params &p) {
+    return p.num_stages == 2 && p.stage2_input == 0 && p.occlusion_radius <= 0;
+}
+
+// allow_zpool: the frame may take its z-buffer from the context's clean pool (not when the caller
+// wants the z-buffer itself, which is copied out after the pooling kernel has emptied it).
+Layout layout_of(const densify_params &p, const densify_frame *f, bool allow_zpool = true) {
     Layout L;
     const int64_t W = f->K.width, H = f->K.height, npx = W * H;
     const bool host = f->memory == DENSIFY_MEM_HOST;
@@ -461,7 +477,9 @@ Layout layout_of(const densify_params &p, const densify_frame *f) {
         return at;
     };
     const int64_t zp = (W + 3) & ~int64_t(3);
-    L.zbuf = take(zp * H * 4);
+    L.zpooled = allow_zpool && zpool_applies(p) && !f->out_zbuf;
+    if (L.zpooled) L.zbytes = align_up((uint64_t)zp * H * 4);
+    else L.zbuf = take(zp * H * 4);
     if (p.occlusion_radius > 0) L.zbuf_raw = take(zp * H * 4);
     L.has_motion = p.motion_threshold > 0.0f && f->prev_rgb;
     if (L.has_motion) {
@@ -542,7 +560,9 @@ void build_frame_dev(densify_ctx *c, FrameRec &r) {
     d.rgb = L.rgb_pitch ? (const uint8_t *)(base + L.rgb) : f->rgb;
     d.rgb_pitch = L.rgb_pitch ? L.rgb_pitch : f->rgb_pitch;
     d.zpitch = (d.W + 3) & ~3;
-    d.zbuf = (uint32_t *)(base + L.zbuf);
+    d.zbuf = L.zpooled ? (uint32_t *)((char *)c->zpool_base + r.zoff) : (uint32_t *)(base + L.zbuf);
+    d.zclear = !L.zpooled;
+    d.zrestore = L.zpooled;
     d.zbuf_raw = c->p.occlusion_radius > 0 ? (uint32_t *)(base + L.zbuf_raw) : d.zbuf;
     d.newest_scan = f->newest_scan;
     d.n_px_chunks = ceil_div((int64_t)d.W * d.H, kPxChunk);
@@ -602,7 +622,7 @@ void fill_batch(densify_ctx *c, Slot &sl, const std::vector<uint64_t> &tk) {
         FrameRec &r = c->frames[tk[i]];
         const FrameDev &d = r.dev;
         b.f[i] = d;
-        b.zb_pre[i + 1] = b.zb_pre[i] + ceil_div((int64_t)d.zpitch * d.H, kZbWordsPerChunk);
+        b.zb_pre[i + 1] = b.zb_pre[i] + (d.zclear ? ceil_div((int64_t)d.zpitch * d.H, kZbWordsPerChunk) : 0);
         for (int s = 0; s < kMaxScans; ++s) {
             const int k = i * kMaxScans + s;
             b.pt_pre[k + 1] = b.pt_pre[k] + ceil_div(d.scans[s].count, kPtsPerChunk);
@@ -901,10 +921,25 @@ densify_status issue_kernels(densify_ctx *c, Slot &sl, cudaStream_t s, bool reco
     if (c->p.emit_points) {
         CU(launch_bp_count(b, c->grid[K_BP_COUNT], s), "compaction count launch");
         CU(mark(K_BP_COUNT), "event");
-        CU(launch_bp_write(b, c->grid[K_BP_WRITE], s), "compaction write launch");
+        CU(launch_bp_write(b, c->grid[K_BP_WRITE], s), "compaction write launch");   // see settle_grids
         CU(mark(K_BP_WRITE), "event");
     }
     return DENSIFY_OK;
+}
+
+// The first batch settles the kernel grids (they are part of every slot's graph). A compaction
+// write whose points go straight into page-locked host memory runs at the host link's rate, about
+// a millisecond for eight 1080p frames; with the persistent grid on every SM it would hold them all
+// that long, and the next batch's kernels (on another slot's stream) could not start. When every
+// frame of the first batch writes its points that way, the compaction write gets a quarter of the
+// SMs, which still outpace the link, and the rest run the next batch.
+void settle_grids(densify_ctx *c, const std::vector<uint64_t> &tk) {
+    if (c->grids_fixed) return;
+    c->grids_fixed = true;
+    // (only a context with its own streams overlaps its slots' batches)
+    bool host_points = c->p.emit_points && c->own_stream && c->slots.size() > 1 && !tk.empty();
+    for (uint64_t t : tk) host_points &= c->frames[t].L.points_direct != nullptr;
+    if (host_points) c->grid[K_BP_WRITE] = std::max(1, c->grid[K_BP_WRITE] / 4);
 }
 
 // Capture a slot's kernel sequence (its own device descriptor) into a graph, instantiate it and
@@ -938,6 +973,7 @@ densify_status launch_batch(densify_ctx *c, int si) {
         densify_status st = autotune(c, sl, tk);
         if (st != DENSIFY_OK) return st;
     }
+    settle_grids(c, tk);
     for (uint64_t t : tk) {
         build_frame_dev(c, c->frames[t]);
         const std::string e = encode_maps(c, c->frames[t].dev);
@@ -1153,6 +1189,8 @@ void destroy_resources(densify_ctx *c) {
     c->slots.clear();
     if (c->arena_base) cudaFree(c->arena_base);
     c->arena_base = nullptr;
+    if (c->zpool_base) cudaFree(c->zpool_base);
+    c->zpool_base = nullptr;
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     if (c->d2h_stream) cudaStreamDestroy(c->d2h_stream);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -1206,7 +1244,8 @@ void densify_default_params(densify_params *p) {
 
 uint64_t densify_frame_scratch_bytes(const densify_params *params, const densify_frame *frame) {
     if (!params || !frame) return 0;
-    return layout_of(*params, frame).total;
+    const Layout L = layout_of(*params, frame);
+    return L.total + L.zbytes;
 }
 
 densify_status densify_create(const densify_params *params, int device, void *cuda_stream, densify_ctx **out) {
@@ -1239,11 +1278,25 @@ densify_status densify_create(const densify_params *params, int device, void *cu
     if ((e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking)) != cudaSuccess ||
         (e = cudaStreamCreateWithFlags(&c->d2h_stream, cudaStreamNonBlocking)) != cudaSuccess)
         return bail(DENSIFY_E_CUDA, std::string("stream: ") + cudaGetErrorString(e));
-    if ((e = cudaMalloc(&c->arena_base, params->hbm_budget_bytes)) != cudaSuccess) {
+    // a quarter of the budget holds the clean z-buffers where they apply (a 1080p frame's z-buffer is
+    // about a quarter of its scratch), the rest the other scratch
+    const uint64_t zpool_bytes = zpool_applies(*params) ? (params->hbm_budget_bytes / 4) & ~(kAlign - 1) : 0;
+    const uint64_t arena_bytes = params->hbm_budget_bytes - zpool_bytes;
+    if ((e = cudaMalloc(&c->arena_base, arena_bytes)) != cudaSuccess) {
         cudaGetLastError();
         return bail(DENSIFY_E_NOMEM, std::string("arena: ") + cudaGetErrorString(e));
     }
-    c->arena.init(params->hbm_budget_bytes);
+    c->arena.init(arena_bytes);
+    if (zpool_bytes) {
+        if ((e = cudaMalloc(&c->zpool_base, zpool_bytes)) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(DENSIFY_E_NOMEM, std::string("z-buffer pool: ") + cudaGetErrorString(e));
+        }
+        if ((e = launch_fill_empty((uint32_t *)c->zpool_base, zpool_bytes / 4, c->stream)) != cudaSuccess ||
+            (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+            return bail(DENSIFY_E_CUDA, std::string("z-buffer pool: ") + cudaGetErrorString(e));
+        c->zpool.init(zpool_bytes);
+    }
     c->slots.resize(params->batches_in_flight);
     for (auto &sl : c->slots) {
         // a context that owns its streams gives every slot its own, so that one batch's host copies
@@ -1328,8 +1381,13 @@ densify_status densify_submit(densify_ctx *c, const densify_frame *frame, uint64
     FrameRec r;
     r.fr = *frame;
     r.L = layout_of(c->p, frame);
-    if (r.L.total > c->arena.size()) return fail(c, DENSIFY_E_NOMEM, "frame scratch exceeds hbm_budget_bytes");
+    if (r.L.total > c->arena.size() || r.L.zbytes > c->zpool.size())
+        return fail(c, DENSIFY_E_NOMEM, "frame scratch exceeds hbm_budget_bytes");
     if (!c->arena.alloc(r.L.total, &r.off)) return fail(c, DENSIFY_E_AGAIN, "scratch arena full");
+    if (r.L.zpooled && !c->zpool.alloc(r.L.zbytes, &r.zoff)) {
+        c->arena.release(r.off, r.L.total);
+        return fail(c, DENSIFY_E_AGAIN, "z-buffer pool full");
+    }
     const uint64_t t = c->next_ticket++;
     c->frames.emplace(t, r);
     c->queue.push_back(t);
@@ -1367,6 +1425,7 @@ densify_status densify_poll(densify_ctx *c, uint64_t ticket, int64_t timeout_ns)
         if (r.state == 2) {
             st = finalize(c, r);
             c->arena.release(r.off, r.L.total);
+            if (r.L.zpooled) c->zpool.release(r.zoff, r.L.zbytes);
             c->frames.erase(ticket);
             c->admitted--;
             return st;
@@ -1443,7 +1502,7 @@ densify_status densify_sigma_grad(densify_ctx *c, const densify_frame *frame, co
     FrameRec r;
     r.fr = *frame;
     r.fr.out_zbuf = nullptr;
-    r.L = layout_of(p, &r.fr);
+    r.L = layout_of(p, &r.fr, false);   // its z-buffer in the main arena, cleared by the prep kernel
     const int grid = c->sms * 4;
     const int pool = p.num_stages == 2 ? p.pool : 1;
     const int64_t Wc = (frame->K.width + pool - 1) / pool, Hc = (frame->K.height + pool - 1) / pool;

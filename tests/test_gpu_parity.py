@@ -207,3 +207,35 @@ def test_variants_agree_bit_for_bit(torch_cuda):
     np.testing.assert_allclose(a["coarse"], b["coarse"], rtol=2e-6)
     np.testing.assert_allclose(e["depth"], b["depth"], rtol=3e-5)
     np.testing.assert_allclose(e["coarse"], b["coarse"], rtol=3e-5)
+
+
+def test_clean_zbuffer_pool_over_many_batches(torch_cuda):
+    """Two-stage frames that do not ask for the z-buffer take it from the context's pool of clean
+    z-buffers, and the pooling kernel empties the cells it found observed. Rounds of frames of
+    different sizes through one context, each round's z-buffers on regions earlier rounds used: every
+    frame matches the oracle, so no frame sees another frame's observations."""
+    from paper_2601_01210_gb300 import Densifier
+    from paper_2601_01210_gb300.frames import FrameBuffers
+    res = ["1080p", "720p", "540p", "qvga", "540p", "720p"]
+    views = [scene.make_batch_view(55, r, i, len(res)) for i, r in enumerate(res)]
+    ref = {}
+    with Densifier(dict(num_stages=2, stages=PAPER_STAGES, launch_policy=1, max_batch=4, max_inflight=8,
+                        hbm_budget_bytes=512 << 20)) as d:
+        for rnd in range(4):
+            pick = [(rnd + k) % len(views) for k in range(4)]
+            bufs = [FrameBuffers(views[i].camera, views[i].rgb,
+                                 [(s.xyz, s.lidar_to_world) for s in views[i].scans]) for i in pick]
+            ts = [d.submit(b.frame) for b in bufs]
+            d.flush()
+            for t in ts:
+                assert d.poll(t, -1) == 0
+            torch_cuda.cuda.synchronize()
+            for i, b in zip(pick, bufs):
+                if i not in ref:
+                    ref[i] = run_oracle(views[i], 2, PAPER_STAGES)
+                g, o = b.results(), ref[i]
+                assert np.array_equal(g["valid"], o["valid"]), (rnd, i)
+                m = o["valid"].astype(bool)
+                rel = np.abs(g["depth"][m] - o["depth"][m]) / o["depth"][m]
+                assert rel.max() <= RTOL, (rnd, i, rel.max())
+                assert g["n"] == int(m.sum())
