@@ -22,6 +22,11 @@
 // counterpart): slot records are
 //   sc = {r', r'', g', g''},  sb = {b', b'', F', F''},  sg = {G', G''}
 // (' for the first staged column of the slot, '' for the second).
+//
+// A tile takes two steps: pair_convert writes the slot records and
+// observation bitmaps from the raw boxes (every thread of the CTA), then
+// pair_filter computes the outputs of KP rows of the tile from those records
+// (one warp per KP rows).
 #pragma once
 
 #include <type_traits>
@@ -33,104 +38,118 @@ namespace dz {
 
 __device__ __forceinline__ float2 f2(float lo, float hi) { return make_float2(lo, hi); }
 
-// after_conversion() runs right after the barrier that publishes the staged records
-// (the kernel's thread 0 advances its tile queue there); the caller ends the tile with
-// a barrier before the staged records or the raw boxes are rewritten.
-template <int SRC, int R, int KP, int NW, class AfterConversion>
-__device__ __forceinline__ void pair_tile(const FrameDev &F, const StageArgs &a, int x0, int y0, int gw, int gh,
-                                          const uint8_t *rgbraw, const uint8_t *rawb, uint8_t *smem,
-                                          AfterConversion &&after_conversion) {
-    using G = TmaGeom<SRC, R, KP, NW, FORM_EXP_PAIRS>;
-    static_assert(SRC != SRC_COARSE, "paired form: full-resolution stages");
-    constexpr int SP = G::SP, SH = G::SH, T = 2 * R + 1, NT = G::NT, NCONV = G::NCONV;
-    constexpr uint32_t TMASK = (1u << T) - 1u;
-    float4 *sc = reinterpret_cast<float4 *>(smem + G::OFF_STAGED);
-    float4 *sb = sc + SH * SP;
-    float2 *sg = reinterpret_cast<float2 *>(smem + G::OFF_G);
-    uint32_t *obs0 = reinterpret_cast<uint32_t *>(smem + G::OFF_OBS);   // first column of each slot
-    uint32_t *obs1 = obs0 + G::OBS_ONE / 4;                              // second column
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// One set of slot records and observation bitmaps in shared memory (bit i of
+// obs0 / obs1: the first / second staged column of slot i holds an observation;
+// each bitmap ends in a zero guard word).
+struct PairRecords {
+    float4 *sc, *sb;
+    float2 *sg;
+    uint32_t *obs0, *obs1;
+};
 
-    // staged position (sy, sx) <-> image pixel (x0 - R + sx, y0 - R + sy): colour bytes in the
-    // raw RGB box, depth and observation in the raw first-stage box (restored by x / 3, y / 3)
-    // or the raw z-buffer box
-    const int cx0 = floor_div3(x0 - R) & ~1, cy0 = floor_div3(y0 - R);
-    const float2 *craw = reinterpret_cast<const float2 *>(rawb);
-    const uint32_t *zraw = reinterpret_cast<const uint32_t *>(rawb);
+// Staged position (sy, sx) <-> image pixel (x0 - R + sx, y0 - R + sy): depth and
+// observation in the raw first-stage box (restored by x / 3, y / 3) or the raw
+// z-buffer box. G gives the boxes' geometry.
+template <int SRC, int R, class G, bool INSIDE>
+__device__ __forceinline__ bool pair_raw_depth(const uint8_t *rawb, int x0, int y0, int gw, int gh, int sy, int sx,
+                                               float &d) {
+    const int gx = x0 - R + sx, gy = y0 - R + sy;
+    if (!INSIDE && (gx < 0 || gx >= gw || gy < 0 || gy >= gh)) return false;
+    if (SRC == SRC_UP) {
+        const int cx0 = floor_div3(x0 - R) & ~1, cy0 = floor_div3(y0 - R);
+        const float2 c = reinterpret_cast<const float2 *>(
+            rawb)[((int)((unsigned)gy / 3u) - cy0) * G::C_BX + ((int)((unsigned)gx / 3u) - cx0)];
+        d = c.x;
+        return c.y > 0.0f;
+    }
+    const uint32_t z = reinterpret_cast<const uint32_t *>(rawb)[sy * G::Z_BX + sx - R + G::Z_LEAD];
+    d = __uint_as_float(z);
+    return z != kEmpty;
+}
+
+// Slot records of a tile: the NCT converting threads take slots t, t + NCT, ... (t their index
+// among them, consecutive within each warp), in groups of up to 8 per thread: all raw loads of a
+// group first, then its records; one ballot per half gives a word of each observation bitmap.
+template <int SRC, int R, class G, int NCT>
+__device__ __forceinline__ void pair_convert(const StageArgs &a, int x0, int y0, int gw, int gh, const uint8_t *rgbraw,
+                                             const uint8_t *rawb, const PairRecords st, int t) {
+    static_assert(SRC != SRC_COARSE, "paired form: full-resolution stages");
+    constexpr int SP = G::SP, SH = G::SH, NCONV = (SH * SP + NCT - 1) / NCT;
+    constexpr int CH = NCONV <= 8 ? NCONV : 4;   // slots of a thread per group
+    const int lane = t & 31;
     auto rgb_at = [&](int sy, int sx) { return rgbraw + sy * G::RGB_BX + 3 * sx - 3 * R + G::RGB_LEAD; };
     // a tile whose halo lies inside the image needs no bounds checks on its staged positions
     const bool interior = x0 >= R && x0 + G::TW + R <= gw && y0 >= R && y0 + G::TH + R <= gh;
-    auto depth_of = [&](int sy, int sx, float &d, auto inside) -> bool {
-        const int gx = x0 - R + sx, gy = y0 - R + sy;
-        if (!decltype(inside)::value && (gx < 0 || gx >= gw || gy < 0 || gy >= gh)) return false;
-        if (SRC == SRC_UP) {
-            const float2 c = craw[((int)((unsigned)gy / 3u) - cy0) * G::C_BX + ((int)((unsigned)gx / 3u) - cx0)];
-            d = c.x;
-            return c.y > 0.0f;
-        }
-        const uint32_t z = zraw[sy * G::Z_BX + sx - R + G::Z_LEAD];
-        d = __uint_as_float(z);
-        return z != kEmpty;
-    };
-
-    // ---- conversion: every thread takes slots threadIdx.x + j * NT, all raw loads first,
-    // then the records; one ballot per half gives a word of each observation bitmap
-    uint32_t om0 = 0u, om1 = 0u;   // bit j: first / second column of slot j observed
-    float d0[NCONV], d1[NCONV];
-    uint32_t r0[NCONV], g0[NCONV], b0[NCONV], r1[NCONV], g1[NCONV], b1[NCONV];
-    auto load_slots = [&](auto inside) {
-#pragma unroll
-        for (int j = 0; j < NCONV; ++j) {
-            const int i = threadIdx.x + j * NT;
-            d0[j] = d1[j] = 0.0f;
-            r0[j] = g0[j] = b0[j] = r1[j] = g1[j] = b1[j] = 0u;
-            if (i < SH * SP) {
-                const int sy = i / SP, s = i - sy * SP;
-                float d = 0.0f;
-                if (depth_of(sy, s, d, inside)) om0 |= 1u << j;
-                d0[j] = d;
-                d = 0.0f;
-                if (depth_of(sy, s + 32, d, inside)) om1 |= 1u << j;
-                d1[j] = d;
-                const uint8_t *p = rgb_at(sy, s), *q = p + 96;
-                r0[j] = p[0]; g0[j] = p[1]; b0[j] = p[2];
-                r1[j] = q[0]; g1[j] = q[1]; b1[j] = q[2];
-            }
-        }
-    };
-    if (interior) load_slots(std::true_type{});
-    else load_slots(std::false_type{});
     // bytes b, b' as exact floats minus 128: 2^23 + b has b in its low mantissa bits
     auto bytes2 = [](uint32_t b, uint32_t b2) {
         return __fadd2_rn(f2(__uint_as_float(0x4B000000u | b), __uint_as_float(0x4B000000u | b2)),
                           f2(-8388736.0f, -8388736.0f));
     };
     const float kc = a.kc;
+#pragma unroll 1
+    for (int j0 = 0; j0 < NCONV; j0 += CH) {
+        uint32_t om0 = 0u, om1 = 0u;   // bit j: first / second column of slot j of the group observed
+        float d0[CH], d1[CH];
+        uint32_t r0[CH], g0[CH], b0[CH], r1[CH], g1[CH], b1[CH];
+        auto load_slots = [&](auto inside) {
+            constexpr bool IN = decltype(inside)::value;
 #pragma unroll
-    for (int j = 0; j < NCONV; ++j) {
-        const int i = threadIdx.x + j * NT;
-        const bool o0 = (om0 >> j) & 1u, o1 = (om1 >> j) & 1u;
-        if (i < SH * SP) {
-            // centred colours (exact); an unobserved record keeps its colour with F = G = 0
-            const float2 r = bytes2(r0[j], r1[j]), g = bytes2(g0[j], g1[j]), b = bytes2(b0[j], b1[j]);
-            const float2 e = __fmul2_rn(f2(-kc, -kc), __ffma2_rn(r, r, __ffma2_rn(g, g, __fmul2_rn(b, b))));
-            const float f0 = o0 ? ex2_approx(e.x) : 0.0f, f1 = o1 ? ex2_approx(e.y) : 0.0f;
-            const float2 fd = __fmul2_rn(f2(f0, f1), f2(d0[j], d1[j]));
-            sc[i] = make_float4(r.x, r.y, g.x, g.y);
-            sb[i] = make_float4(b.x, b.y, f0, f1);
-            sg[i] = f2(o0 ? fd.x : 0.0f, o1 ? fd.y : 0.0f);   // an empty z-buffer cell holds +inf
-        }
-        const uint32_t w0 = __ballot_sync(0xffffffffu, o0), w1 = __ballot_sync(0xffffffffu, o1);
-        if (lane == 0) {
-            obs0[(threadIdx.x + j * NT) >> 5] = w0;
-            obs1[(threadIdx.x + j * NT) >> 5] = w1;
+            for (int j = 0; j < CH; ++j) {
+                const int i = t + (j0 + j) * NCT;
+                d0[j] = d1[j] = 0.0f;
+                r0[j] = g0[j] = b0[j] = r1[j] = g1[j] = b1[j] = 0u;
+                if (j0 + j < NCONV && i < SH * SP) {
+                    const int sy = i / SP, s = i - sy * SP;
+                    float d = 0.0f;
+                    if (pair_raw_depth<SRC, R, G, IN>(rawb, x0, y0, gw, gh, sy, s, d)) om0 |= 1u << j;
+                    d0[j] = d;
+                    d = 0.0f;
+                    if (pair_raw_depth<SRC, R, G, IN>(rawb, x0, y0, gw, gh, sy, s + 32, d)) om1 |= 1u << j;
+                    d1[j] = d;
+                    const uint8_t *p = rgb_at(sy, s), *q = p + 96;
+                    r0[j] = p[0]; g0[j] = p[1]; b0[j] = p[2];
+                    r1[j] = q[0]; g1[j] = q[1]; b1[j] = q[2];
+                }
+            }
+        };
+        if (interior) load_slots(std::true_type{});
+        else load_slots(std::false_type{});
+#pragma unroll
+        for (int j = 0; j < CH; ++j) {
+            if (j0 + j >= NCONV) break;
+            const int i = t + (j0 + j) * NCT;
+            const bool o0 = (om0 >> j) & 1u, o1 = (om1 >> j) & 1u;
+            if (i < SH * SP) {
+                // centred colours (exact); an unobserved record keeps its colour with F = G = 0
+                const float2 r = bytes2(r0[j], r1[j]), g = bytes2(g0[j], g1[j]), b = bytes2(b0[j], b1[j]);
+                const float2 e = __fmul2_rn(f2(-kc, -kc), __ffma2_rn(r, r, __ffma2_rn(g, g, __fmul2_rn(b, b))));
+                const float f0 = o0 ? ex2_approx(e.x) : 0.0f, f1 = o1 ? ex2_approx(e.y) : 0.0f;
+                const float2 fd = __fmul2_rn(f2(f0, f1), f2(d0[j], d1[j]));
+                st.sc[i] = make_float4(r.x, r.y, g.x, g.y);
+                st.sb[i] = make_float4(b.x, b.y, f0, f1);
+                st.sg[i] = f2(o0 ? fd.x : 0.0f, o1 ? fd.y : 0.0f);   // an empty z-buffer cell holds +inf
+            }
+            const uint32_t w0 = __ballot_sync(0xffffffffu, o0), w1 = __ballot_sync(0xffffffffu, o1);
+            if (lane == 0) {
+                st.obs0[i >> 5] = w0;
+                st.obs1[i >> 5] = w1;
+            }
         }
     }
-    __syncthreads();
-    after_conversion();
+}
+
+// Outputs of tile rows rbase .. rbase + KP - 1 (one warp) from the tile's slot records.
+// raw_at(sy, sx, r, g, b, d) gives the colour bytes and the depth of staged position (sy, sx)
+// and whether it holds an observation, for the shifted recomputation of a valid pixel whose
+// weight sum is too small for the plain form (dominant weight near the bottom of the FP32 range).
+template <int SRC, int R, int KP, class G, class RawAt>
+__device__ __forceinline__ void pair_filter(const FrameDev &F, const StageArgs &a, int x0, int y0, int gw, int gh,
+                                            const PairRecords st, int rbase, int lane, RawAt &&raw_at) {
+    constexpr int SP = G::SP, T = 2 * R + 1;
+    constexpr uint32_t TMASK = (1u << T) - 1u;
+    const float kc = a.kc;
 
     // ---- validity: an output pixel is valid when its window holds an observation
-    const int rbase = warp * KP;
     bool val0[KP], val1[KP];
     bool any_val = false;
     uint32_t rows_warp;   // bit iy: some lane of the warp has an observation in its window of staged row rbase + iy
@@ -139,8 +158,8 @@ __device__ __forceinline__ void pair_tile(const FrameDev &F, const StageArgs &a,
 #pragma unroll
         for (int iy = 0; iy < KP + 2 * R; ++iy) {
             const int bit = (rbase + iy) * SP + lane;   // the window never leaves its row
-            const uint32_t w0 = __funnelshift_r(obs0[bit >> 5], obs0[(bit >> 5) + 1], bit & 31);
-            const uint32_t w1 = __funnelshift_r(obs1[bit >> 5], obs1[(bit >> 5) + 1], bit & 31);
+            const uint32_t w0 = __funnelshift_r(st.obs0[bit >> 5], st.obs0[(bit >> 5) + 1], bit & 31);
+            const uint32_t w1 = __funnelshift_r(st.obs1[bit >> 5], st.obs1[(bit >> 5) + 1], bit & 31);
             rows0 |= ((w0 & TMASK) != 0 ? 1u : 0u) << iy;
             rows1 |= ((w1 & TMASK) != 0 ? 1u : 0u) << iy;
         }
@@ -163,7 +182,7 @@ __device__ __forceinline__ void pair_tile(const FrameDev &F, const StageArgs &a,
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
             const int o = (rbase + k + R) * SP + lane + R;
-            const float4 c = sc[o], b = sb[o];
+            const float4 c = st.sc[o], b = st.sb[o];
             ar[k] = f2(kc2 * c.x, kc2 * c.y);
             ag[k] = f2(kc2 * c.z, kc2 * c.w);
             ab[k] = f2(kc2 * b.x, kc2 * b.y);
@@ -182,8 +201,8 @@ __device__ __forceinline__ void pair_tile(const FrameDev &F, const StageArgs &a,
 #pragma unroll
             for (int dx = 0; dx < T; ++dx) {
                 const int o = (rbase + iy) * SP + lane + dx;
-                const float4 qc = sc[o], qb = sb[o];
-                const float2 qg = sg[o];
+                const float4 qc = st.sc[o], qb = st.sb[o];
+                const float2 qg = st.sg[o];
                 const float2 ex = f2(a.ex_sx[dx], a.ex_sx[dx]);
                 const float2 fx = __fmul2_rn(f2(qb.z, qb.w), ex), gx = __fmul2_rn(qg, ex);
 #pragma unroll
@@ -202,8 +221,8 @@ __device__ __forceinline__ void pair_tile(const FrameDev &F, const StageArgs &a,
         }
     }
 
-    // ---- outputs; a valid pixel whose weight sum is too small for the plain form (dominant
-    // weight near the bottom of the FP32 range) is recomputed with shifted exponents
+    // ---- outputs, through one pair of pointers for the warp's rows (row k at k * gw); columns
+    // and rows outside the grid are left alone
     // the output pointers in registers: a store through them could alias the frame descriptor,
     // which would make the compiler reload them after every store
     float *const out_depth = F.flt_depth;
@@ -216,26 +235,41 @@ __device__ __forceinline__ void pair_tile(const FrameDev &F, const StageArgs &a,
         }
     };
     uint32_t slow = 0u;   // bit 2k + h: pixel (k, half h)
+    {
+        const int64_t o0 = (int64_t)(y0 + rbase) * gw + x0 + lane;
+        float *const dp = out_depth + o0;
+        uint8_t *const vp = out_valid + o0;
+        const bool in0 = x0 + lane < gw, in1 = x0 + 32 + lane < gw;
+        const int rows_in = gh - (y0 + rbase);
 #pragma unroll
-    for (int k = 0; k < KP; ++k) {
-        const int y = y0 + rbase + k;
-        if (val0[k] && !(den[k].x >= 0x1p-60f)) slow |= 1u << (2 * k);
-        else store(x0 + lane, y, val0[k] ? __fdividef(num[k].x, den[k].x) : 0.0f, val0[k]);
-        if (val1[k] && !(den[k].y >= 0x1p-60f)) slow |= 2u << (2 * k);
-        else store(x0 + 32 + lane, y, val1[k] ? __fdividef(num[k].y, den[k].y) : 0.0f, val1[k]);
+        for (int k = 0; k < KP; ++k) {
+            if (k >= rows_in) break;
+            const int64_t ok = (int64_t)k * gw;
+            if (val0[k] && !(den[k].x >= 0x1p-60f)) {
+                slow |= 1u << (2 * k);
+            } else if (in0) {
+                dp[ok] = val0[k] ? __fdividef(num[k].x, den[k].x) : 0.0f;
+                vp[ok] = val0[k];
+            }
+            if (val1[k] && !(den[k].y >= 0x1p-60f)) {
+                slow |= 2u << (2 * k);
+            } else if (in1) {
+                dp[ok + 32] = val1[k] ? __fdividef(num[k].y, den[k].y) : 0.0f;
+                vp[ok + 32] = val1[k];
+            }
+        }
     }
-    while (slow) {   // rare: from the raw boxes, largest exponent of the window first
+    while (slow) {   // rare: largest exponent of the window first
         const int bit = __ffs(slow) - 1;
         slow &= slow - 1u;
         const int k = bit >> 1, cx = lane + 32 * (bit & 1);   // staged column of the pixel, minus R
-        const uint8_t *pc = rgb_at(rbase + k + R, cx + R);
-        const float cr0 = (float)pc[0], cg0 = (float)pc[1], cb0 = (float)pc[2];
+        float cr0, cg0, cb0, cd;
+        raw_at(rbase + k + R, cx + R, cr0, cg0, cb0, cd);
         auto tap = [&](int dy, int dx, float &arg, float &wd) -> bool {
-            const int sy = rbase + k + dy, sx = cx + dx;
-            const uint8_t *p = rgb_at(sy, sx);
-            const float dr = (float)p[0] - cr0, dg = (float)p[1] - cg0, db = (float)p[2] - cb0;
+            float r, g, b;
             wd = 0.0f;
-            const bool seen = depth_of(sy, sx, wd, std::false_type{});
+            const bool seen = raw_at(rbase + k + dy, cx + dx, r, g, b, wd);
+            const float dr = r - cr0, dg = g - cg0, db = b - cb0;
             const float n2 = fmaf(dr, dr, fmaf(dg, dg, db * db));
             const float s2 = (float)((dx - R) * (dx - R) + (dy - R) * (dy - R));
             arg = fmaf(n2, -a.kc, -s2 * a.kp);
@@ -263,6 +297,38 @@ __device__ __forceinline__ void pair_tile(const FrameDev &F, const StageArgs &a,
             }
         store(x0 + cx, y0 + rbase + k, nn / dn, true);
     }
+}
+
+// One tile with all NW warps of the CTA: conversion, a barrier, then each warp's KP rows.
+// A warp with bad set (its copies did not land) skips the conversion; the barrier ORs the
+// flag and the function then returns true at once, for the caller to leave. Otherwise
+// after_conversion() runs right after the barrier that publishes the slot records (the
+// kernel's thread 0 advances its tile queue there) and the function returns false; the
+// caller ends the tile with a barrier before the records or the raw boxes are rewritten.
+template <int SRC, int R, int KP, int NW, class AfterConversion>
+__device__ __forceinline__ bool pair_tile(const FrameDev &F, const StageArgs &a, int x0, int y0, int gw, int gh,
+                                          const uint8_t *rgbraw, const uint8_t *rawb, uint8_t *smem, bool bad,
+                                          AfterConversion &&after_conversion) {
+    using G = TmaGeom<SRC, R, KP, NW, FORM_EXP_PAIRS>;
+    PairRecords st;
+    st.sc = reinterpret_cast<float4 *>(smem + G::OFF_STAGED);
+    st.sb = st.sc + G::SH * G::SP;
+    st.sg = reinterpret_cast<float2 *>(smem + G::OFF_G);
+    st.obs0 = reinterpret_cast<uint32_t *>(smem + G::OFF_OBS);
+    st.obs1 = st.obs0 + G::OBS_ONE / 4;
+    if (!bad) pair_convert<SRC, R, G, G::NT>(a, x0, y0, gw, gh, rgbraw, rawb, st, threadIdx.x);
+    if (__syncthreads_or(bad)) return true;
+    after_conversion();
+    // the shifted recomputation reads the raw boxes, which stay in place until the tile ends
+    auto raw_at = [&](int sy, int sx, float &r, float &g, float &b, float &d) -> bool {
+        const uint8_t *p = rgbraw + sy * G::RGB_BX + 3 * sx - 3 * R + G::RGB_LEAD;
+        r = (float)p[0];
+        g = (float)p[1];
+        b = (float)p[2];
+        return pair_raw_depth<SRC, R, G, false>(rawb, x0, y0, gw, gh, sy, sx, d);
+    };
+    pair_filter<SRC, R, KP, G>(F, a, x0, y0, gw, gh, st, (threadIdx.x >> 5) * KP, threadIdx.x & 31, raw_at);
+    return false;
 }
 
 }  // namespace dz

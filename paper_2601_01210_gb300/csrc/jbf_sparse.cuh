@@ -33,11 +33,13 @@
 
 namespace dz {
 
-// store(x, y, depth, valid) takes tile-relative pixel coordinates.
+// store(x, y, depth, valid) takes tile-relative pixel coordinates. A warp with bad set (its copies
+// did not land) skips the records; the barrier after them ORs the flag and the function then
+// returns true at once, for the caller to leave (false once the tile is done).
 template <int R, int KP, int NW, class AfterRecords, class Store>
-__device__ __forceinline__ void sparse_tile(const StageArgs &a, int x0, int y0, int gw, int gh, const uint8_t *rgbraw,
-                                            const uint8_t *rawb, uint8_t *smem, AfterRecords &&after_records,
-                                            Store &&store) {
+__device__ __forceinline__ bool sparse_tile(const StageArgs &a, int x0, int y0, int gw, int gh, const uint8_t *rgbraw,
+                                            const uint8_t *rawb, uint8_t *smem, bool bad,
+                                            AfterRecords &&after_records, Store &&store) {
     using G = TmaGeom<SRC_ZBUF, R, KP, NW, FORM_SPARSE>;
     constexpr int TW = G::TW, TH = G::TH, SW = G::SW, SH = G::SH, RPW = G::RPW;
     constexpr int FW = 8 + 2 * R;                      // footprint of a block: columns bx .. bx + FW - 1 staged
@@ -55,7 +57,7 @@ __device__ __forceinline__ void sparse_tile(const StageArgs &a, int x0, int y0, 
 
     // ---- records of the observed positions; warp w scans staged rows w, w + NW, ...
 #pragma unroll 1
-    for (int i = 0; i < RPW; ++i) {
+    for (int i = 0; i < (bad ? 0 : RPW); ++i) {
         const int sy = warp + NW * i;
         if (sy >= SH) break;
         uint64_t mask = 0;
@@ -79,7 +81,7 @@ __device__ __forceinline__ void sparse_tile(const StageArgs &a, int x0, int y0, 
         }
         if (lane == 0) rowmask[sy] = mask;
     }
-    __syncthreads();
+    if (__syncthreads_or(bad)) return true;
     after_records();
 
     // ---- blocks of 8 x 8 pixels: lane (lx, ly) owns pixels (bx + lx, by + ly) and (bx + lx, by + ly + 4)
@@ -161,6 +163,7 @@ __device__ __forceinline__ void sparse_tile(const StageArgs &a, int x0, int y0, 
             store(px, py, out, hit[k]);
         }
     }
+    return false;
 }
 
 }  // namespace dz

@@ -120,12 +120,23 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
     // tile index or -1 when there is none) in s_tile[buffer] for the other threads, so the start of
     // a tile waits on no global load. A tile no observation reaches gets no copies.
     __shared__ int s_tile[2][5];
+    // The stage's tile prefix and each frame's tiles per row and tile flags, read into shared
+    // memory once: locating a tile then waits on no global load. A wait in thread 0's queue work
+    // would hold up warp 0, and with it every warp of the CTA at the tile's closing barrier.
+    __shared__ int32_t s_pre[kMaxBatch + 1];
+    __shared__ int32_t s_tx[kMaxBatch];
+    __shared__ const int32_t *s_fl[kMaxBatch];
+    for (int i = threadIdx.x; i <= nf; i += NT) s_pre[i] = pre[i];
+    for (int i = threadIdx.x; i < nf; i += NT) {
+        const FrameDev &F = B->f[i];
+        s_tx[i] = ((SRC == SRC_COARSE ? F.Wc : F.W) + TW - 1) / TW;
+        s_fl[i] = F.tflags[stage];
+    }
+    __syncthreads();
     auto locate = [&](int item, int &fi, int &x0, int &y0) {
-        fi = find_segment(pre, nf, item);
-        const FrameDev &F = B->f[fi];
-        const int gw = SRC == SRC_COARSE ? F.Wc : F.W;
-        const int tiles_x = (gw + TW - 1) / TW;
-        const int t = item - pre[fi];
+        fi = find_segment(s_pre, nf, item);
+        const int tiles_x = s_tx[fi];
+        const int t = item - s_pre[fi];
         x0 = (t % tiles_x) * TW;
         y0 = (t / tiles_x) * TH;
     };
@@ -177,23 +188,25 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
     // Thread 0 keeps the next tile n1 ready (its flag f1 requested and its coordinates located)
     // and the counter's reply for the tile after it (n2raw) requested. At the top of a tile it
     // only issues n1's copies; the queue advances after the conversion barrier, while the CTA
-    // filters, and every global result is used one tile after it was requested: the issuing
-    // thread never waits on a load or on the counter, which a whole grid of CTAs shares. The
-    // counter is only ever touched atomically (the descriptor's other fields are read-only here).
-    __shared__ int s_q[6];   // thread 0's queue state, kept out of every thread's registers
-    int &n1 = s_q[0], &f1 = s_q[1], &l1f = s_q[2], &l1x = s_q[3], &l1y = s_q[4], &n2raw = s_q[5];
+    // filters, and every global result is used one tile after it was requested: the flag load
+    // and the counter's reply land in registers (a store of either to shared memory would wait
+    // for it), so the issuing thread never waits on a load or on the counter, which a whole grid
+    // of CTAs shares. The counter is only ever touched atomically (the descriptor's other fields
+    // are read-only here).
+    __shared__ int s_q[4];   // thread 0's queue state, kept out of every thread's registers
+    int &n1 = s_q[0], &l1f = s_q[1], &l1x = s_q[2], &l1y = s_q[3];
+    int f1 = 0, n2raw = 0;
     if (threadIdx.x == 0) {
         n1 = total;
-        f1 = l1f = l1x = l1y = n2raw = 0;
+        l1f = l1x = l1y = 0;
     }
     auto request = [&]() { return atomicAdd(const_cast<int32_t *>(&B->tl_next[stage]), 1); };
     auto advance = [&]() {   // thread 0: n1 <- the counter's last reply; request the next one
         n1 = (int)gridDim.x + n2raw;
         if (n1 < total) {
             locate(n1, l1f, l1x, l1y);
-            f1 = B->f[l1f].tflags[stage][n1 - pre[l1f]];
+            f1 = load_issue(s_fl[l1f] + (n1 - s_pre[l1f]));
             n2raw = request();
-            asm volatile("" ::"r"(f1));   // wait for the flag here, in warp 0's filter phase, not at the next issue
         }
     };
     if (threadIdx.x == 0) {
@@ -201,7 +214,7 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
         if (t0 < total) {
             int fi, x0, y0;
             locate(t0, fi, x0, y0);
-            const int f0 = B->f[fi].tflags[stage][t0 - pre[fi]];
+            const int f0 = s_fl[fi][t0 - s_pre[fi]];
             issue(t0, f0, fi, x0, y0, 0);
             if (f0) inflight |= 1u;
             n2raw = request();
@@ -219,19 +232,26 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
             if (n1 < total && f1) inflight |= 1u << (buf ^ 1);
         }
         const bool copied = s_tile[buf][3] != 0;   // the same for every thread of the CTA
+        // A wait that gives up makes its warp skip the conversion; the barrier that publishes the
+        // staged records ORs the warps' failures, and on a failure the CTA leaves there (leave()).
+        // No barrier sits between the tiles' copies and the conversion.
+        bool bad = false;
         if (copied) {
             const bool ok = mbar_wait_bounded(&bar[buf], (phase >> buf) & 1u);
-            if (__syncthreads_or(!ok)) {
-                if (threadIdx.x == 0) {
-                    atomicOr(B->status, 1);
-                    for (int b = 0; b < 2; ++b)
-                        if ((inflight >> b) & 1u) mbar_wait_bounded(&bar[b], (phase >> b) & 1u);
-                }
-                return;
+            bad = !__all_sync(0xffffffffu, ok);
+            if (ok) {
+                phase ^= 1u << buf;
+                inflight &= ~(1u << buf);
             }
-            phase ^= 1u << buf;
-            inflight &= ~(1u << buf);
         }
+        // after a failed wait: record it and let the CTA's own copies land before it returns
+        auto leave = [&]() {
+            if (threadIdx.x == 0) {
+                atomicOr(B->status, 1);
+                for (int b = 0; b < 2; ++b)
+                    if ((inflight >> b) & 1u) mbar_wait_bounded(&bar[b], (phase >> b) & 1u);
+            }
+        };
 
         const int fi = s_tile[buf][0], x0 = s_tile[buf][1], y0 = s_tile[buf][2];
         const FrameDev &F = B->f[fi];
@@ -256,9 +276,12 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
             continue;
         }
         if constexpr (G::PAIRS) {
-            pair_tile<SRC, R, KP, NW>(F, a, x0, y0, gw, gh, rawA(buf), rawB(buf), smem, [&]() {
-                if (threadIdx.x == 0 && n1 < total) advance();   // off the path of the CTA's barriers
-            });
+            if (pair_tile<SRC, R, KP, NW>(F, a, x0, y0, gw, gh, rawA(buf), rawB(buf), smem, bad, [&]() {
+                    if (threadIdx.x == 0 && n1 < total) advance();   // off the path of the CTA's barriers
+                })) {
+                leave();
+                return;
+            }
             __syncthreads();   // staged records / raw[buf] are reused by the next tile
             continue;
         }
@@ -275,9 +298,12 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
                     out_valid[o] = v;
                 }
             };
-            sparse_tile<R, KP, NW>(a, x0, y0, gw, gh, rawA(buf), rawB(buf), smem, [&]() {
-                if (threadIdx.x == 0 && n1 < total) advance();   // off the path of the CTA's barriers
-            }, store);
+            if (sparse_tile<R, KP, NW>(a, x0, y0, gw, gh, rawA(buf), rawB(buf), smem, bad, [&]() {
+                    if (threadIdx.x == 0 && n1 < total) advance();   // off the path of the CTA's barriers
+                }, store)) {
+                leave();
+                return;
+            }
             __syncthreads();   // records and raw[buf] are reused by the next tile
             continue;
         }
@@ -308,73 +334,78 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
         // load of its positions (raw boxes; shared-memory stores in between would keep the compiler
         // from overlapping them), then the records; a warp's ballot gives one word of the
         // observation bitmap.
-        uint32_t omask = 0u;                     // bit j: position j observed
-        float dq[G::NCONV];                      // depth (SRC_UP / SRC_ZBUF) or depth sum (SRC_COARSE)
-        uint32_t c0[G::NCONV], c1[G::NCONV], c2[G::NCONV];   // colour bytes, or guide bits (SRC_COARSE)
-        float cw[G::NCONV];                      // pooled count (SRC_COARSE)
-#pragma unroll
-        for (int j = 0; j < G::NCONV; ++j) {
-            const int i = threadIdx.x + j * NT;
-            dq[j] = 0.0f;
-            c0[j] = c1[j] = c2[j] = 0u;
-            cw[j] = 0.0f;
-            if (i < SH * SW) {
-                const int sy = i / SW, sx = i - sy * SW;
-                if (SRC != SRC_COARSE) {
-                    float d = 0.0f;
-                    if (depth_of(sy, sx, d)) omask |= 1u << j;
-                    dq[j] = d;
-                    const uint8_t *p = rgb_at(sy, sx);
-                    c0[j] = p[0];
-                    c1[j] = p[1];
-                    c2[j] = p[2];
-                } else {
-                    const float4 q = cg[i];
-                    c0[j] = __float_as_uint(q.x);
-                    c1[j] = __float_as_uint(q.y);
-                    c2[j] = __float_as_uint(q.z);
-                    cw[j] = q.w;
-                    if (q.w > 0.0f) omask |= 1u << j;
-                    if (EXP) dq[j] = cs[sy * G::S_BX + sx - R + G::S_LEAD];
-                }
-            }
-        }
-        // byte b as an exact float minus bias: 2^23 + b has b in its low mantissa bits
-        auto bytef = [](uint32_t b, float bias) { return __uint_as_float(0x4B000000u | b) - (8388608.0f + bias); };
-#pragma unroll
-        for (int j = 0; j < G::NCONV; ++j) {
-            const int i = threadIdx.x + j * NT;
-            const bool o = (omask >> j) & 1u;
-            if (i < SH * SW) {
-                if (SRC != SRC_COARSE) {
-                    const float d = dq[j];
-                    if (HALF) {
-                        staged_h[i] = o ? make_uint4(h2u(__float2half2_rn(bytef(c0[j], 0.0f))),
-                                                     h2u(__float2half2_rn(bytef(c1[j], 0.0f))),
-                                                     h2u(__float2half2_rn(bytef(c2[j], 0.0f))), __float_as_uint(d))
-                                        : make_uint4(h2u(__float2half2_rn(65504.0f)), 0u, 0u, 0u);
-                    } else if (EXP) {
-                        // centred colour (exact), F_q = 2^(-kc |c'_q|^2); unobserved: F_q = 0
-                        const float rr = bytef(c0[j], 128.0f), gg = bytef(c1[j], 128.0f), bb = bytef(c2[j], 128.0f);
-                        const float f = o ? ex2_approx(-a.kc * fmaf(rr, rr, fmaf(gg, gg, bb * bb))) : 0.0f;
-                        staged[i] = o ? make_float4(rr, gg, bb, f) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                        staged_g[i] = o ? f * d : 0.0f;   // an empty z-buffer cell holds +inf
+        if (!bad) {   // (a warp whose copies did not land skips its conversion)
+            uint32_t omask = 0u;                     // bit j: position j observed
+            float dq[G::NCONV];                      // depth (SRC_UP / SRC_ZBUF) or depth sum (SRC_COARSE)
+            uint32_t c0[G::NCONV], c1[G::NCONV], c2[G::NCONV];   // colour bytes, or guide bits (SRC_COARSE)
+            float cw[G::NCONV];                      // pooled count (SRC_COARSE)
+    #pragma unroll
+            for (int j = 0; j < G::NCONV; ++j) {
+                const int i = threadIdx.x + j * NT;
+                dq[j] = 0.0f;
+                c0[j] = c1[j] = c2[j] = 0u;
+                cw[j] = 0.0f;
+                if (i < SH * SW) {
+                    const int sy = i / SW, sx = i - sy * SW;
+                    if (SRC != SRC_COARSE) {
+                        float d = 0.0f;
+                        if (depth_of(sy, sx, d)) omask |= 1u << j;
+                        dq[j] = d;
+                        const uint8_t *p = rgb_at(sy, sx);
+                        c0[j] = p[0];
+                        c1[j] = p[1];
+                        c2[j] = p[2];
                     } else {
-                        staged[i] = o ? make_float4(bytef(c0[j], 0.0f), bytef(c1[j], 0.0f), bytef(c2[j], 0.0f), d)
-                                      : make_float4(kSentinel, 0.0f, 0.0f, 0.0f);
+                        const float4 q = cg[i];
+                        c0[j] = __float_as_uint(q.x);
+                        c1[j] = __float_as_uint(q.y);
+                        c2[j] = __float_as_uint(q.z);
+                        cw[j] = q.w;
+                        if (q.w > 0.0f) omask |= 1u << j;
+                        if (EXP) dq[j] = cs[sy * G::S_BX + sx - R + G::S_LEAD];
                     }
-                } else if (EXP) {   // pooled guide: F_q times the count and times the depth sum (count 0: weight 0)
-                    const float rr = __uint_as_float(c0[j]) - 128.0f, gg = __uint_as_float(c1[j]) - 128.0f,
-                                bb = __uint_as_float(c2[j]) - 128.0f;
-                    const float f = ex2_approx(-a.kc * fmaf(rr, rr, fmaf(gg, gg, bb * bb)));
-                    staged[i] = make_float4(rr, gg, bb, f * cw[j]);
-                    staged_g[i] = f * dq[j];
                 }
             }
-            const uint32_t bits = __ballot_sync(0xffffffffu, o);
-            if (lane == 0) obsw[(threadIdx.x + j * NT) >> 5] = bits;
+            // byte b as an exact float minus bias: 2^23 + b has b in its low mantissa bits
+            auto bytef = [](uint32_t b, float bias) { return __uint_as_float(0x4B000000u | b) - (8388608.0f + bias); };
+    #pragma unroll
+            for (int j = 0; j < G::NCONV; ++j) {
+                const int i = threadIdx.x + j * NT;
+                const bool o = (omask >> j) & 1u;
+                if (i < SH * SW) {
+                    if (SRC != SRC_COARSE) {
+                        const float d = dq[j];
+                        if (HALF) {
+                            staged_h[i] = o ? make_uint4(h2u(__float2half2_rn(bytef(c0[j], 0.0f))),
+                                                         h2u(__float2half2_rn(bytef(c1[j], 0.0f))),
+                                                         h2u(__float2half2_rn(bytef(c2[j], 0.0f))), __float_as_uint(d))
+                                            : make_uint4(h2u(__float2half2_rn(65504.0f)), 0u, 0u, 0u);
+                        } else if (EXP) {
+                            // centred colour (exact), F_q = 2^(-kc |c'_q|^2); unobserved: F_q = 0
+                            const float rr = bytef(c0[j], 128.0f), gg = bytef(c1[j], 128.0f), bb = bytef(c2[j], 128.0f);
+                            const float f = o ? ex2_approx(-a.kc * fmaf(rr, rr, fmaf(gg, gg, bb * bb))) : 0.0f;
+                            staged[i] = o ? make_float4(rr, gg, bb, f) : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                            staged_g[i] = o ? f * d : 0.0f;   // an empty z-buffer cell holds +inf
+                        } else {
+                            staged[i] = o ? make_float4(bytef(c0[j], 0.0f), bytef(c1[j], 0.0f), bytef(c2[j], 0.0f), d)
+                                          : make_float4(kSentinel, 0.0f, 0.0f, 0.0f);
+                        }
+                    } else if (EXP) {   // pooled guide: F_q times the count and times the depth sum (count 0: weight 0)
+                        const float rr = __uint_as_float(c0[j]) - 128.0f, gg = __uint_as_float(c1[j]) - 128.0f,
+                                    bb = __uint_as_float(c2[j]) - 128.0f;
+                        const float f = ex2_approx(-a.kc * fmaf(rr, rr, fmaf(gg, gg, bb * bb)));
+                        staged[i] = make_float4(rr, gg, bb, f * cw[j]);
+                        staged_g[i] = f * dq[j];
+                    }
+                }
+                const uint32_t bits = __ballot_sync(0xffffffffu, o);
+                if (lane == 0) obsw[(threadIdx.x + j * NT) >> 5] = bits;
+            }
         }
-        __syncthreads();
+        if (__syncthreads_or(bad)) {
+            leave();
+            return;
+        }
 
         if (threadIdx.x == 0 && n1 < total) advance();   // off the path of the CTA's barriers
 

@@ -37,24 +37,33 @@ __device__ __forceinline__ double compose_entry(const double *c2w, const double 
 
 // The batch's first kernel: calibration compose, tile flags and counters, z-buffer clear.
 __global__ void __launch_bounds__(kThreads) prep_kernel(BatchDev *__restrict__ B) {
-    // the batch's clear prefix and each frame's z-buffer in shared memory: a work item then starts
-    // its stores without a chain of dependent global loads
+    // the batch's clear prefix, each frame's z-buffer and tile-flag block in shared memory, all read
+    // at once: the stores below then wait on no chain of dependent global loads (a store through a
+    // pointer read from the descriptor could alias the descriptor, which would order the next read
+    // after it)
     __shared__ int32_t s_pre[kMaxBatch + 1];
     __shared__ uint32_t *s_z[kMaxBatch];
     __shared__ int64_t s_n[kMaxBatch];
+    __shared__ int32_t *s_fl[kMaxBatch];
+    __shared__ int32_t s_nfl[kMaxBatch];
+    __shared__ int32_t s_tl_on;
     const int nf = B->n_frames;
+    if (threadIdx.x == 0) s_tl_on = B->tl_on;
     for (int i = threadIdx.x; i <= nf; i += kThreads) s_pre[i] = B->zb_pre[i];
     for (int i = threadIdx.x; i < nf; i += kThreads) {
         s_z[i] = B->f[i].zbuf_raw;
         s_n[i] = (int64_t)B->f[i].zpitch * B->f[i].H;
+        s_fl[i] = B->f[i].tflags[0];
+        s_nfl[i] = B->f[i].ntflags;
     }
+    __syncthreads();
     // the TMA filters' tile flags (each frame's block of both stages) and tile counters start the
     // batch cleared; the producers (pooling, first filter) and the mark kernel set the flags
-    if (B->tl_on) {
+    if (s_tl_on) {
         if (blockIdx.x == 0 && threadIdx.x == 0) B->tl_next[0] = B->tl_next[1] = 0;   // the filters' tile counters
         for (int f = 0; f < nf; ++f) {
-            int32_t *const fl = B->f[f].tflags[0];
-            const int n = B->f[f].ntflags;
+            int32_t *const fl = s_fl[f];
+            const int n = s_nfl[f];
             for (int i = blockIdx.x * kThreads + threadIdx.x; i < n; i += gridDim.x * kThreads) fl[i] = 0;
         }
     }
@@ -70,7 +79,6 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(BatchDev *__restrict__ B
             F.c2w32[e] = __double2float_rn(F.c2w[(e / 4) * 4 + (e % 4)]);
         }
     }
-    __syncthreads();
     // z-buffer clear: the chunks of the frames that clear (a frame from the clean pool has none)
     const int total = s_pre[nf];
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
@@ -97,17 +105,24 @@ __global__ void __launch_bounds__(kThreads) prep_kernel(BatchDev *__restrict__ B
 // project: one work item = kPtsPerChunk consecutive points of one (frame, scan);
 // each thread takes kPtsPerThread points with 16-byte vector loads.
 // ---------------------------------------------------------------------------
-// The camera of a frame in registers: read once per work item (an atomic on the z-buffer could
-// alias the frame descriptor, so reading it per point would mean a reload after every atomic).
-struct ProjCam {
+// A (frame, scan) of the batch as the projection reads it. Every block copies the batch's table
+// into shared memory once, all entries at once, so that a work item starts its point loads
+// without first waiting on the descriptor (an atomic on the z-buffer could alias the descriptor,
+// so the compiler would reload it from global memory after every atomic).
+struct ProjSeg {
+    float M[12];
     float fx, fy, cx, cy, w, h;
-    int W;
-    int64_t zpitch;
+    const float *xyz;
+    uint32_t *zbuf;
     const uint8_t *motion;   // NULL unless afterimage removal applies to this scan
+    int64_t count;
+    int64_t zpitch;
+    int32_t W;
+    int32_t stride_floats;
 };
 
-__device__ __forceinline__ void project_one(const float (&M)[12], float x, float y, float z, const ProjCam &C,
-                                            uint32_t *zbuf) {
+__device__ __forceinline__ void project_one(const ProjSeg &C, float x, float y, float z) {
+    const float *M = C.M;
     const float xc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[0], x), __fmul_rn(M[1], y)), __fmul_rn(M[2], z)), M[3]);
     const float yc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[4], x), __fmul_rn(M[5], y)), __fmul_rn(M[6], z)), M[7]);
     const float zc = __fadd_rn(__fadd_rn(__fadd_rn(__fmul_rn(M[8], x), __fmul_rn(M[9], y)), __fmul_rn(M[10], z)), M[11]);
@@ -119,33 +134,49 @@ __device__ __forceinline__ void project_one(const float (&M)[12], float x, float
     const int j = __float2int_rz(v);
     // afterimage removal: points of older scans are dropped where the scene moved
     if (C.motion && C.motion[(int64_t)j * C.W + i]) return;
-    atomicMin(zbuf + (int64_t)j * C.zpitch + i, __float_as_uint(zc));
+    atomicMin(C.zbuf + (int64_t)j * C.zpitch + i, __float_as_uint(zc));
 }
 
 __global__ void __launch_bounds__(kThreads) project_kernel(const BatchDev *__restrict__ B) {
     __shared__ int32_t s_pre[kMaxBatch * kMaxScans + 1];   // point-chunk prefix, searched per work item
+    __shared__ ProjSeg s_seg[kMaxBatch * kMaxScans];
     const int nseg = B->n_frames * kMaxScans;
     for (int i = threadIdx.x; i <= nseg; i += kThreads) s_pre[i] = B->pt_pre[i];
+    for (int i = threadIdx.x; i < nseg; i += kThreads) {
+        // a scan slot past the frame's num_scans has no chunks and is never read
+        const FrameDev &F = B->f[i / kMaxScans];
+        const int sc = i % kMaxScans;
+        const ScanDev &S = F.scans[sc];
+        ProjSeg &D = s_seg[i];
+#pragma unroll
+        for (int e = 0; e < 12; ++e) D.M[e] = S.M[e];
+        D.fx = F.fx;
+        D.fy = F.fy;
+        D.cx = F.cx;
+        D.cy = F.cy;
+        D.w = (float)F.W;
+        D.h = (float)F.H;
+        D.xyz = S.xyz;
+        D.zbuf = F.zbuf_raw;
+        D.motion = sc != F.newest_scan ? F.motion : nullptr;
+        D.count = S.count;
+        D.zpitch = F.zpitch;
+        D.W = F.W;
+        D.stride_floats = S.stride_floats;
+    }
     __syncthreads();
     const int total = s_pre[nseg];
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int seg = find_segment(s_pre, nseg, item);
-        const FrameDev &F = B->f[seg / kMaxScans];
-        const ScanDev &S = F.scans[seg % kMaxScans];
-        float M[12];
-#pragma unroll
-        for (int e = 0; e < 12; ++e) M[e] = S.M[e];
+        const ProjSeg &C = s_seg[seg];
         const int64_t p0 = (int64_t)(item - s_pre[seg]) * kPtsPerChunk + (int64_t)threadIdx.x * kPtsPerThread;
-        if (p0 >= S.count) continue;
-        uint32_t *zbuf = F.zbuf_raw;
-        const bool old_scan = (seg % kMaxScans) != F.newest_scan;
-        const ProjCam C{F.fx, F.fy, F.cx, F.cy, (float)F.W, (float)F.H, F.W, F.zpitch, old_scan ? F.motion : nullptr};
-        const int64_t count = S.count;
-        if (S.stride_floats == 3) {
-            if (p0 + kPtsPerThread <= S.count) {
+        const int64_t count = C.count;
+        if (p0 >= count) continue;
+        if (C.stride_floats == 3) {
+            if (p0 + kPtsPerThread <= count) {
                 // kPtsPerThread packed points = 3 kPtsPerThread / 4 aligned float4 (base 16-byte
                 // aligned, p0 % 4 == 0), all loaded before any is used
-                const float4 *q = reinterpret_cast<const float4 *>(S.xyz + p0 * 3);
+                const float4 *q = reinterpret_cast<const float4 *>(C.xyz + p0 * 3);
                 float v[3 * kPtsPerThread];
 #pragma unroll
                 for (int k = 0; k < 3 * kPtsPerThread / 4; ++k) {
@@ -153,14 +184,14 @@ __global__ void __launch_bounds__(kThreads) project_kernel(const BatchDev *__res
                     v[4 * k] = a.x; v[4 * k + 1] = a.y; v[4 * k + 2] = a.z; v[4 * k + 3] = a.w;
                 }
 #pragma unroll
-                for (int k = 0; k < kPtsPerThread; ++k) project_one(M, v[3 * k], v[3 * k + 1], v[3 * k + 2], C, zbuf);
+                for (int k = 0; k < kPtsPerThread; ++k) project_one(C, v[3 * k], v[3 * k + 1], v[3 * k + 2]);
             } else {
-                const float *xyz = S.xyz;
+                const float *xyz = C.xyz;
                 for (int64_t p = p0; p < count; ++p)
-                    project_one(M, __ldg(xyz + 3 * p), __ldg(xyz + 3 * p + 1), __ldg(xyz + 3 * p + 2), C, zbuf);
+                    project_one(C, __ldg(xyz + 3 * p), __ldg(xyz + 3 * p + 1), __ldg(xyz + 3 * p + 2));
             }
         } else {
-            const float4 *q = reinterpret_cast<const float4 *>(S.xyz) + p0;
+            const float4 *q = reinterpret_cast<const float4 *>(C.xyz) + p0;
             const int n = (int)(count - p0 < kPtsPerThread ? count - p0 : kPtsPerThread);
             float4 a[kPtsPerThread];
 #pragma unroll
@@ -168,7 +199,7 @@ __global__ void __launch_bounds__(kThreads) project_kernel(const BatchDev *__res
                 if (k < n) a[k] = __ldg(q + k);
 #pragma unroll
             for (int k = 0; k < kPtsPerThread; ++k)
-                if (k < n) project_one(M, a[k].x, a[k].y, a[k].z, C, zbuf);
+                if (k < n) project_one(C, a[k].x, a[k].y, a[k].z);
         }
     }
 }

@@ -20,23 +20,36 @@ namespace dz {
 // shifted into place, each channel's 3 bytes gathered by a byte permute and
 // summed by dp4a: integer sums, exactly the FP32 sums of the bytes. Blocks at
 // the image border, other factors and layouts use plain loads.
-__device__ __forceinline__ bool pool_words_ok(const FrameDev &F) {
+// A frame as the pooling kernel reads it. Every block copies the batch's frames into shared
+// memory once, all at once, so that a work item starts its loads without first waiting on the
+// frame descriptor (a store could alias the descriptor, so the compiler would otherwise reload
+// its fields from global memory after every store).
+struct PoolFrame {
+    uint32_t *zbuf;
+    const uint8_t *rgb;
+    float4 *cguide;
+    float *cssum;
+    int32_t *tflags;
+    int64_t rgb_pitch, zpitch, cpitch;
+    int32_t W, H, Wc, Hc, segs;
+    int32_t zrestore;
+};
+
+__device__ __forceinline__ bool pool_words_ok(const PoolFrame &F) {
     return ((((uintptr_t)F.zbuf) | ((uintptr_t)F.rgb)) & 3u) == 0 && (F.rgb_pitch & 3) == 0;
 }
 
 // The guide is the colour sum times the reciprocal of the block's pixel count (within one rounding
 // of the quotient; the filter's tolerance covers it).
-__device__ __forceinline__ void pool_store(const FrameDev &F, int I, int J, float rr, float gg, float bb, float cnt,
+__device__ __forceinline__ void pool_store(const PoolFrame &F, int I, int J, float rr, float gg, float bb, float cnt,
                                            float s, float inv_npx) {
     const int64_t o = (int64_t)J * F.cpitch + I;
-    float4 *const guide = F.cguide;   // both pointers read before either store
-    float *const sums = F.cssum;
-    guide[o] = make_float4(rr * inv_npx, gg * inv_npx, bb * inv_npx, cnt);
-    sums[o] = s;
+    F.cguide[o] = make_float4(rr * inv_npx, gg * inv_npx, bb * inv_npx, cnt);
+    F.cssum[o] = s;
 }
 
 // Pooled pixel (I, J): its guide and sums; cnt_out = its observation count.
-__device__ __forceinline__ void pool_one(const FrameDev &F, int I, int J, int f, float &cnt_out) {
+__device__ __forceinline__ void pool_one(const PoolFrame &F, int I, int J, int f, float &cnt_out) {
     const int x0 = I * f, y0 = J * f;
     const int o = (9 * I) & 3;                            // first colour byte inside its word
     const int64_t wb = 9 * (int64_t)I - o;                // byte offset of the first covering word
@@ -54,9 +67,6 @@ __device__ __forceinline__ void pool_one(const FrameDev &F, int I, int J, int f,
         }
         float s = 0.0f, cnt = 0.0f;
         uint32_t rs = 0u, gs = 0u, bs = 0u;
-        uint32_t *const zb = F.zbuf;   // read before any store (a store could alias the descriptor)
-        const int64_t zp = F.zpitch;
-        const bool restore = F.zrestore;
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
 #pragma unroll
@@ -64,7 +74,7 @@ __device__ __forceinline__ void pool_one(const FrameDev &F, int I, int J, int f,
                 if (z[r][j] != kEmpty) {
                     s = __fadd_rn(s, __uint_as_float(z[r][j]));
                     cnt += 1.0f;
-                    if (restore) zb[(int64_t)(y0 + r) * zp + x0 + j] = kEmpty;   // the clean pool's invariant
+                    if (F.zrestore) F.zbuf[(int64_t)(y0 + r) * F.zpitch + x0 + j] = kEmpty;   // the clean pool's invariant
                 }
             }
             // bytes c0 .. c8 of the row (r, g, b of 3 pixels) into a0 = c0..c3, a1 = c4..c7, a2 = c8..
@@ -80,17 +90,15 @@ __device__ __forceinline__ void pool_one(const FrameDev &F, int I, int J, int f,
     } else {
         const int x1 = min(x0 + f, F.W), y1 = min(y0 + f, F.H);
         float s = 0.0f, cnt = 0.0f, r = 0.0f, g = 0.0f, b = 0.0f;
-        uint32_t *const zb = F.zbuf;
-        const bool restore = F.zrestore;
         for (int y = y0; y < y1; ++y) {
-            uint32_t *zr = zb + (int64_t)y * F.zpitch;
+            uint32_t *zr = F.zbuf + (int64_t)y * F.zpitch;
             const uint8_t *cr = F.rgb + (int64_t)y * F.rgb_pitch;
             for (int x = x0; x < x1; ++x) {
                 const uint32_t zz = zr[x];
                 if (zz != kEmpty) {
                     s = __fadd_rn(s, __uint_as_float(zz));
                     cnt += 1.0f;
-                    if (restore) zr[x] = kEmpty;
+                    if (F.zrestore) zr[x] = kEmpty;
                 }
                 r += (float)cr[3 * x];
                 g += (float)cr[3 * x + 1];
@@ -106,27 +114,52 @@ __device__ __forceinline__ void pool_one(const FrameDev &F, int I, int J, int f,
 // its observed pooled pixels reach (one ballot; a row segment of 32 pooled pixels grown by the
 // radius spans at most two tiles across and two down), so no mark kernel runs before that filter.
 __global__ void __launch_bounds__(kThreads) pool_kernel(const BatchDev *__restrict__ B, int f) {
+    __shared__ int32_t s_pre[kMaxBatch + 1];   // pooling chunk prefix, searched per work item
+    __shared__ PoolFrame s_f[kMaxBatch];
+    __shared__ int32_t s_geo[3];               // the first filter's tile width, height and radius
     const int nf = B->n_frames;
-    const int total = B->pool_pre[nf];
+    for (int i = threadIdx.x; i <= nf; i += kThreads) s_pre[i] = B->pool_pre[i];
+    for (int i = threadIdx.x; i < nf; i += kThreads) {
+        const FrameDev &F = B->f[i];
+        PoolFrame &P = s_f[i];
+        P.zbuf = F.zbuf;
+        P.rgb = F.rgb;
+        P.cguide = F.cguide;
+        P.cssum = F.cssum;
+        P.tflags = F.tflags[0];
+        P.rgb_pitch = F.rgb_pitch;
+        P.zpitch = F.zpitch;
+        P.cpitch = F.cpitch;
+        P.W = F.W;
+        P.H = F.H;
+        P.Wc = F.Wc;
+        P.Hc = F.Hc;
+        P.segs = (F.Wc + kPoolPerChunk - 1) / kPoolPerChunk;
+        P.zrestore = F.zrestore;
+    }
+    if (threadIdx.x == 0) {
+        s_geo[0] = B->tl_tw[0];
+        s_geo[1] = B->tl_th[0];
+        s_geo[2] = B->tl_r[0];
+    }
+    __syncthreads();
+    const int total = s_pre[nf];
     const int lane = threadIdx.x & 31;
-    // the first filter's tile geometry, read before any store (a store could alias the descriptor)
-    const int mtw = B->tl_tw[0], mth = B->tl_th[0], mr = B->tl_r[0];
+    const int mtw = s_geo[0], mth = s_geo[1], mr = s_geo[2];
     const bool marks = mth > 0;
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
-        const int fi = find_segment(B->pool_pre, nf, item);
-        const FrameDev &F = B->f[fi];
-        const int segs = (F.Wc + kPoolPerChunk - 1) / kPoolPerChunk;
-        const int t = item - B->pool_pre[fi];
-        const int J = t / segs;
-        const int I = (t - J * segs) * kPoolPerChunk + threadIdx.x;
+        const int fi = find_segment(s_pre, nf, item);
+        const PoolFrame &F = s_f[fi];
+        const int t = item - s_pre[fi];
+        const int J = t / F.segs;
+        const int I = (t - J * F.segs) * kPoolPerChunk + threadIdx.x;
         float cnt = 0.0f;
         if (I < F.Wc) pool_one(F, I, J, f, cnt);
         if (marks) {
             const uint32_t m = __ballot_sync(0xffffffffu, cnt > 0.0f);
             const int I0 = I - lane;
             if (m)
-                mark_reach(F.tflags[0], mtw, mth, mr, 1, F.Wc, F.Hc, I0 + __ffs(m) - 1, I0 + 31 - __clz(m), J,
-                           J, lane);
+                mark_reach(F.tflags, mtw, mth, mr, 1, F.Wc, F.Hc, I0 + __ffs(m) - 1, I0 + 31 - __clz(m), J, J, lane);
         }
     }
 }
@@ -166,25 +199,35 @@ __device__ __forceinline__ uint32_t valid_bits4(const uint8_t *v, int64_t p, int
 constexpr int kCountParts = 4;
 __global__ void __launch_bounds__(kThreads) bp_count_kernel(const BatchDev *__restrict__ B) {
     constexpr int kGroups = kBpWarps / kCountParts;   // part groups of a chunk
-    __shared__ int32_t s_pre[kMaxBatch + 1];          // chunk prefix, searched per work item
+    // the chunk prefix and each frame's validity map, pixel count and part counts, read at once:
+    // a work item then starts its loads without first waiting on the frame descriptor
+    __shared__ int32_t s_pre[kMaxBatch + 1];
+    __shared__ const uint8_t *s_valid[kMaxBatch];
+    __shared__ uint32_t *s_cnt[kMaxBatch];
+    __shared__ int64_t s_n[kMaxBatch];
     const int nf = B->n_frames;
     for (int i = threadIdx.x; i <= nf; i += kThreads) s_pre[i] = B->bp_pre[i];
+    for (int i = threadIdx.x; i < nf; i += kThreads) {
+        s_valid[i] = B->f[i].out_valid;
+        s_cnt[i] = B->f[i].chunk_cnt;
+        s_n[i] = (int64_t)B->f[i].W * B->f[i].H;
+    }
     __syncthreads();
     const int total = s_pre[nf] * kGroups;
     const int lane = threadIdx.x & 31;
     for (int wi = blockIdx.x * kBpWarps + (threadIdx.x >> 5); wi < total; wi += gridDim.x * kBpWarps) {
         const int item = wi / kGroups;
         const int fi = find_segment(s_pre, nf, item);
-        const FrameDev &F = B->f[fi];
+        const uint8_t *const valid = s_valid[fi];
         const int sub0 = (item - s_pre[fi]) * kBpWarps + (wi % kGroups) * kCountParts;   // the frame's first part
-        const int64_t n = (int64_t)F.W * F.H;
-        const bool vec = (((uintptr_t)F.out_valid) & 15u) == 0;
+        const int64_t n = s_n[fi];
+        const bool vec = (((uintptr_t)valid) & 15u) == 0;
         uint4 w[kCountParts];
 #pragma unroll
         for (int j = 0; j < kCountParts; ++j) {
             const int64_t p = (int64_t)(sub0 + j) * kBpPart + lane * 16;
             w[j] = make_uint4(0u, 0u, 0u, 0u);
-            if (vec && p + 16 <= n) w[j] = *reinterpret_cast<const uint4 *>(F.out_valid + p);   // bytes are 0 or 1
+            if (vec && p + 16 <= n) w[j] = *reinterpret_cast<const uint4 *>(valid + p);   // bytes are 0 or 1
         }
 #pragma unroll
         for (int j = 0; j < kCountParts; ++j) {
@@ -192,10 +235,10 @@ __global__ void __launch_bounds__(kThreads) bp_count_kernel(const BatchDev *__re
             uint32_t cnt = __popc(w[j].x) + __popc(w[j].y) + __popc(w[j].z) + __popc(w[j].w);
             if (!(vec && p + 16 <= n)) {
                 cnt = 0;
-                for (int k = 0; k < 16; ++k) cnt += (p + k < n && F.out_valid[p + k]) ? 1u : 0u;
+                for (int k = 0; k < 16; ++k) cnt += (p + k < n && valid[p + k]) ? 1u : 0u;
             }
             cnt = __reduce_add_sync(0xffffffffu, cnt);
-            if (lane == 0) F.chunk_cnt[sub0 + j] = cnt;
+            if (lane == 0) s_cnt[fi][sub0 + j] = cnt;
         }
     }
 }
@@ -260,29 +303,64 @@ __device__ __forceinline__ void row_col(int64_t p, int W, float inv_w, int &y, i
     x = (int)r;
 }
 
+// A frame as the compaction write reads it (copied into shared memory once per block, all frames
+// at once, for the same reason as PoolFrame).
+struct BpFrame {
+    const uint8_t *valid;
+    const float *depth;
+    const uint8_t *rgb;
+    const uint32_t *cnt;
+    float4 *points;
+    int64_t rgb_pitch, cap;
+    float c2w[12];
+    float ifx, ify, cx, cy, iw;
+    int32_t W, H;
+};
+
 __global__ void __launch_bounds__(kThreads, 4) bp_write_kernel(const BatchDev *__restrict__ B) {
     __shared__ float4 stage[kThreads / 32][128];
     __shared__ int32_t s_pre[kMaxBatch + 1];          // chunk prefix, searched per work item
+    __shared__ BpFrame s_f[kMaxBatch];
     const int nf = B->n_frames;
     for (int i = threadIdx.x; i <= nf; i += kThreads) s_pre[i] = B->bp_pre[i];
+    for (int i = threadIdx.x; i < nf; i += kThreads) {
+        const FrameDev &F = B->f[i];
+        BpFrame &P = s_f[i];
+        P.valid = F.out_valid;
+        P.depth = F.out_depth;
+        P.rgb = F.rgb;
+        P.cnt = F.chunk_cnt;
+        P.points = F.out_points;
+        P.rgb_pitch = F.rgb_pitch;
+        P.cap = F.points_cap;
+#pragma unroll
+        for (int e = 0; e < 12; ++e) P.c2w[e] = F.c2w32[e];
+        P.ifx = 1.0f / F.fx;
+        P.ify = 1.0f / F.fy;
+        P.cx = F.cx;
+        P.cy = F.cy;
+        P.iw = 1.0f / (float)F.W;
+        P.W = F.W;
+        P.H = F.H;
+    }
     __syncthreads();
     const int total = s_pre[nf];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
         const int fi = find_segment(s_pre, nf, item);
-        const FrameDev &F = B->f[fi];
+        const BpFrame &F = s_f[fi];
         const int c = item - s_pre[fi];
         const int W = F.W;
         const int64_t n = (int64_t)W * F.H;
-        const bool vvalid = (((uintptr_t)F.out_valid) & 3u) == 0;
-        const bool vdepth = (((uintptr_t)F.out_depth) & 15u) == 0;
+        const bool vvalid = (((uintptr_t)F.valid) & 3u) == 0;
+        const bool vdepth = (((uintptr_t)F.depth) & 15u) == 0;
         const bool rows4 = (W & 3) == 0 && (F.rgb_pitch & 3) == 0 && (((uintptr_t)F.rgb) & 3u) == 0;
         const int64_t wbase = (int64_t)c * kBpChunk + warp * 512;
-        const float *c2w = F.c2w32;
+        const float *c2w = F.c2w;
         const float r00 = c2w[0], r01 = c2w[1], r02 = c2w[2], t0 = c2w[3];
         const float r10 = c2w[4], r11 = c2w[5], r12 = c2w[6], t1 = c2w[7];
         const float r20 = c2w[8], r21 = c2w[9], r22 = c2w[10], t2 = c2w[11];
-        const float ifx = 1.0f / F.fx, ify = 1.0f / F.fy, iw = 1.0f / (float)W;
+        const float ifx = F.ifx, ify = F.ify, iw = F.iw;
         float4 *st = stage[warp];
         // staged point j sits at j ^ ((j >> 2) & 7): a lane's four consecutive points and the read-back's
         // eight consecutive points of a quarter warp then fall on distinct 16-byte bank groups
@@ -306,11 +384,11 @@ __global__ void __launch_bounds__(kThreads, 4) bp_write_kernel(const BatchDev *_
 #pragma unroll
         for (int it = 0; it < 4; ++it) {
             const int64_t p0 = wbase + it * 128 + lane * 4;
-            m[it] = valid_bits4(F.out_valid, p0, n, vvalid);
+            m[it] = valid_bits4(F.valid, p0, n, vvalid);
             zq[it] = make_float4(0.f, 0.f, 0.f, 0.f);
             cw[it][0] = cw[it][1] = cw[it][2] = 0u;
             if (vdepth && rows4 && p0 + 4 <= n) {
-                zq[it] = *reinterpret_cast<const float4 *>(F.out_depth + p0);
+                zq[it] = *reinterpret_cast<const float4 *>(F.depth + p0);
                 const uint32_t *cp =
                     reinterpret_cast<const uint32_t *>(F.rgb + (int64_t)ys[it] * F.rgb_pitch + 3 * xs[it]);
                 cw[it][0] = cp[0];
@@ -318,7 +396,7 @@ __global__ void __launch_bounds__(kThreads, 4) bp_write_kernel(const BatchDev *_
                 cw[it][2] = cp[2];
             }
         }
-        int64_t off = F.chunk_cnt[c * kBpWarps + warp];   // exclusive prefix of the part counts (bp_scan_kernel)
+        int64_t off = F.cnt[c * kBpWarps + warp];   // exclusive prefix of the part counts (bp_scan_kernel)
 #pragma unroll
         for (int it = 0; it < 4; ++it) {
             const uint32_t cnt = __popc(m[it]);
@@ -362,7 +440,7 @@ __global__ void __launch_bounds__(kThreads, 4) bp_write_kernel(const BatchDev *_
                             const uint8_t *cb = F.rgb + (int64_t)y * F.rgb_pitch + 3 * x;
                             const uint32_t rgba = (uint32_t)cb[0] | ((uint32_t)cb[1] << 8) | ((uint32_t)cb[2] << 16) |
                                                   0xFF000000u;
-                            const float Z = F.out_depth[p];
+                            const float Z = F.depth[p];
                             const float X = ((float)x + 0.5f - F.cx) * Z * ifx;
                             const float Yz = ((float)y + 0.5f - F.cy) * ify * Z;
                             st[sw(j++)] = make_float4(fmaf(r00, X, fmaf(r01, Yz, fmaf(r02, Z, t0))),
@@ -375,8 +453,8 @@ __global__ void __launch_bounds__(kThreads, 4) bp_write_kernel(const BatchDev *_
             }
             __syncwarp();
             // the part's points from off on, as far as the caller's capacity goes
-            const uint32_t fit = (uint32_t)max((int64_t)0, min((int64_t)tot, F.points_cap - off));
-            float4 *dst = F.out_points + off;
+            const uint32_t fit = (uint32_t)max((int64_t)0, min((int64_t)tot, F.cap - off));
+            float4 *dst = F.points + off;
             for (uint32_t i = lane; i < fit; i += 32) dst[i] = st[sw(i)];
             __syncwarp();
             off += tot;

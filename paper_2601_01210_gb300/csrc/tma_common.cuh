@@ -49,6 +49,14 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     return true;
 }
 
+// A global load issued here and waited for only where its value is first used (the compiler may
+// not move a volatile asm, so the load is not sunk to its use).
+__device__ __forceinline__ int load_issue(const int32_t *p) {
+    int v;
+    asm volatile("ld.global.b32 %0, [%1];" : "=r"(v) : "l"(p));
+    return v;
+}
+
 __device__ __forceinline__ void tmap_acquire(const CUtensorMap *m) {
     asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"((uint64_t)m) : "memory");
 }
