@@ -143,8 +143,9 @@ __device__ __forceinline__ void pair_convert(const StageArgs &a, int x0, int y0,
 // and whether it holds an observation, for the shifted recomputation of a valid pixel whose
 // weight sum is too small for the plain form (dominant weight near the bottom of the FP32 range).
 template <int SRC, int R, int KP, class G, class RawAt>
-__device__ __forceinline__ void pair_filter(const FrameDev &F, const StageArgs &a, int x0, int y0, int gw, int gh,
-                                            const PairRecords st, int rbase, int lane, RawAt &&raw_at) {
+__device__ __forceinline__ void pair_filter(float *out_depth, uint8_t *out_valid, const StageArgs &a, int x0, int y0,
+                                            int gw, int gh, const PairRecords st, int rbase, int lane,
+                                            RawAt &&raw_at) {
     constexpr int SP = G::SP, T = 2 * R + 1;
     constexpr uint32_t TMASK = (1u << T) - 1u;
     const float kc = a.kc;
@@ -223,10 +224,6 @@ __device__ __forceinline__ void pair_filter(const FrameDev &F, const StageArgs &
 
     // ---- outputs, through one pair of pointers for the warp's rows (row k at k * gw); columns
     // and rows outside the grid are left alone
-    // the output pointers in registers: a store through them could alias the frame descriptor,
-    // which would make the compiler reload them after every store
-    float *const out_depth = F.flt_depth;
-    uint8_t *const out_valid = F.flt_valid;
     auto store = [&](int x, int y, float out, bool v) {
         if (x < gw && y < gh) {
             const int64_t o = (int64_t)y * gw + x;
@@ -306,7 +303,8 @@ __device__ __forceinline__ void pair_filter(const FrameDev &F, const StageArgs &
 // kernel's thread 0 advances its tile queue there) and the function returns false; the
 // caller ends the tile with a barrier before the records or the raw boxes are rewritten.
 template <int SRC, int R, int KP, int NW, class AfterConversion>
-__device__ __forceinline__ bool pair_tile(const FrameDev &F, const StageArgs &a, int x0, int y0, int gw, int gh,
+__device__ __forceinline__ bool pair_tile(float *out_depth, uint8_t *out_valid, const StageArgs &a, int x0, int y0,
+                                          int gw, int gh,
                                           const uint8_t *rgbraw, const uint8_t *rawb, uint8_t *smem, bool bad,
                                           AfterConversion &&after_conversion) {
     using G = TmaGeom<SRC, R, KP, NW, FORM_EXP_PAIRS>;
@@ -327,7 +325,8 @@ __device__ __forceinline__ bool pair_tile(const FrameDev &F, const StageArgs &a,
         b = (float)p[2];
         return pair_raw_depth<SRC, R, G, false>(rawb, x0, y0, gw, gh, sy, sx, d);
     };
-    pair_filter<SRC, R, KP, G>(F, a, x0, y0, gw, gh, st, (threadIdx.x >> 5) * KP, threadIdx.x & 31, raw_at);
+    pair_filter<SRC, R, KP, G>(out_depth, out_valid, a, x0, y0, gw, gh, st, (threadIdx.x >> 5) * KP, threadIdx.x & 31,
+                               raw_at);
     return false;
 }
 

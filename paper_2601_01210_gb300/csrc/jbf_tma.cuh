@@ -87,6 +87,20 @@ constexpr int tma_min_ctas(int form, int kp, int nw) {
 constexpr float kHalfWeightErr = 0.02f;
 constexpr float kHalfStdFrac = 5e-4f / kHalfWeightErr;
 
+// A frame's outputs as the filter writes them, copied into shared memory once per CTA: the outputs
+// of a tile then wait on no read of the frame descriptor.
+struct TileOut {
+    float *depth;      // full-resolution output depth and validity
+    uint8_t *valid;
+    float2 *s1;        // first of two stages: pooled result and validity, and its optional copies
+    float *cdepth;
+    uint8_t *cvalid;
+    int32_t *flags2;   // first of two stages: the second stage's tile flags
+    int64_t cpitch;
+    int32_t gw, gh;    // the stage's grid
+    int32_t W, H;      // full resolution
+};
+
 template <int SRC, int R, int KP, int FORM = FORM_FP32, int NW = 8>
 __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_kernel(const BatchDev *__restrict__ B,
                                                                            const StageArgs a) {
@@ -123,14 +137,36 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
     // The stage's tile prefix and each frame's tiles per row and tile flags, read into shared
     // memory once: locating a tile then waits on no global load. A wait in thread 0's queue work
     // would hold up warp 0, and with it every warp of the CTA at the tile's closing barrier.
+    // The same holds for each frame's outputs and the second stage's tile geometry (s_mk: width,
+    // height, radius; height 0: no flags to set).
     __shared__ int32_t s_pre[kMaxBatch + 1];
     __shared__ int32_t s_tx[kMaxBatch];
     __shared__ const int32_t *s_fl[kMaxBatch];
+    __shared__ TileOut s_out[kMaxBatch];
+    __shared__ int32_t s_mk[3];
     for (int i = threadIdx.x; i <= nf; i += NT) s_pre[i] = pre[i];
     for (int i = threadIdx.x; i < nf; i += NT) {
         const FrameDev &F = B->f[i];
-        s_tx[i] = ((SRC == SRC_COARSE ? F.Wc : F.W) + TW - 1) / TW;
+        const int gw = SRC == SRC_COARSE ? F.Wc : F.W, gh = SRC == SRC_COARSE ? F.Hc : F.H;
+        s_tx[i] = (gw + TW - 1) / TW;
         s_fl[i] = F.tflags[stage];
+        TileOut &O = s_out[i];
+        O.depth = F.flt_depth;
+        O.valid = F.flt_valid;
+        O.s1 = F.s1;
+        O.cdepth = F.out_coarse;
+        O.cvalid = F.out_coarse_valid;
+        O.flags2 = F.tflags[1];
+        O.cpitch = F.cpitch;
+        O.gw = gw;
+        O.gh = gh;
+        O.W = F.W;
+        O.H = F.H;
+    }
+    if (threadIdx.x == 0) {
+        s_mk[0] = B->tl_tw[1];
+        s_mk[1] = SRC == SRC_COARSE ? B->tl_th[1] : 0;
+        s_mk[2] = B->tl_r[1];
     }
     __syncthreads();
     auto locate = [&](int item, int &fi, int &x0, int &y0) {
@@ -254,9 +290,8 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
         };
 
         const int fi = s_tile[buf][0], x0 = s_tile[buf][1], y0 = s_tile[buf][2];
-        const FrameDev &F = B->f[fi];
-        const int gw = SRC == SRC_COARSE ? F.Wc : F.W;
-        const int gh = SRC == SRC_COARSE ? F.Hc : F.H;
+        const TileOut &O = s_out[fi];
+        const int gw = O.gw, gh = O.gh;
         if (!copied) {   // no observation reaches the tile: every output is (0, invalid)
             if (threadIdx.x == 0 && n1 < total) advance();
             for (int i = threadIdx.x; i < TW * TH; i += NT) {
@@ -264,19 +299,19 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
                 if (x >= gw || y >= gh) continue;
                 const int64_t o = (int64_t)y * gw + x;
                 if (SRC == SRC_COARSE) {
-                    F.s1[(int64_t)y * F.cpitch + x] = make_float2(0.0f, 0.0f);
-                    if (F.out_coarse) F.out_coarse[o] = 0.0f;
-                    if (F.out_coarse_valid) F.out_coarse_valid[o] = 0;
+                    O.s1[(int64_t)y * O.cpitch + x] = make_float2(0.0f, 0.0f);
+                    if (O.cdepth) O.cdepth[o] = 0.0f;
+                    if (O.cvalid) O.cvalid[o] = 0;
                 } else {
-                    F.flt_depth[o] = 0.0f;
-                    F.flt_valid[o] = 0;
+                    O.depth[o] = 0.0f;
+                    O.valid[o] = 0;
                 }
             }
             __syncthreads();   // s_tile[buf] is rewritten for the tile after next
             continue;
         }
         if constexpr (G::PAIRS) {
-            if (pair_tile<SRC, R, KP, NW>(F, a, x0, y0, gw, gh, rawA(buf), rawB(buf), smem, bad, [&]() {
+            if (pair_tile<SRC, R, KP, NW>(O.depth, O.valid, a, x0, y0, gw, gh, rawA(buf), rawB(buf), smem, bad, [&]() {
                     if (threadIdx.x == 0 && n1 < total) advance();   // off the path of the CTA's barriers
                 })) {
                 leave();
@@ -287,9 +322,8 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
         }
         if constexpr (G::SPARSE) {
             static_assert(SRC == SRC_ZBUF, "sparse form: the single stage on the z-buffer");
-            // the output pointers in registers (stores through them could alias the frame descriptor)
-            float *const out_depth = F.flt_depth;
-            uint8_t *const out_valid = F.flt_valid;
+            float *const out_depth = O.depth;
+            uint8_t *const out_valid = O.valid;
             auto store = [&](int tx, int ty, float out, bool v) {
                 const int x = x0 + tx, y = y0 + ty;
                 if (x < gw && y < gh) {
@@ -553,12 +587,10 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
             }
         }
         const int x = x0 + lane;
-        // the output pointers in registers: a store through them could alias the frame descriptor,
-        // which would make the compiler reload them after every store
-        float2 *const out_s1 = F.s1;
-        const int64_t cpitch = F.cpitch;
-        float *const out_coarse = F.out_coarse, *const out_depth = F.flt_depth;
-        uint8_t *const out_coarse_valid = F.out_coarse_valid, *const out_valid = F.flt_valid;
+        float2 *const out_s1 = O.s1;
+        const int64_t cpitch = O.cpitch;
+        float *const out_coarse = O.cdepth, *const out_depth = O.depth;
+        uint8_t *const out_coarse_valid = O.cvalid, *const out_valid = O.valid;
         auto store = [&](int k, float out, bool v) {
             const int y = y0 + rbase + k;
             if (x < gw && y < gh) {
@@ -573,7 +605,7 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
                 }
             }
         };
-        if (SRC == SRC_COARSE && B->tl_th[1] > 0) {   // flag the second-stage tiles the valid pixels reach
+        if (SRC == SRC_COARSE && s_mk[1] > 0) {   // flag the second-stage tiles the valid pixels reach
             uint32_t cols = 0u;
             int kf = KP, kl = -1;
 #pragma unroll
@@ -586,8 +618,8 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
                 }
             }
             if (cols)
-                mark_reach(F.tflags[1], B->tl_tw[1], B->tl_th[1], B->tl_r[1], a.pool, F.W, F.H,
-                           x0 + __ffs(cols) - 1, x0 + 31 - __clz(cols), y0 + rbase + kf, y0 + rbase + kl, lane);
+                mark_reach(O.flags2, s_mk[0], s_mk[1], s_mk[2], a.pool, O.W, O.H, x0 + __ffs(cols) - 1,
+                           x0 + 31 - __clz(cols), y0 + rbase + kf, y0 + rbase + kl, lane);
         }
         uint32_t slow = 0u;   // bit k: valid pixel whose weight sum is too small for the plain form
 #pragma unroll

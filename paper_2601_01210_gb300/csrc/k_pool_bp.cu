@@ -254,13 +254,17 @@ __global__ void __launch_bounds__(kScanBlock) bp_scan_kernel(const BatchDev *__r
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int fi = blockIdx.x; fi < B->n_frames; fi += gridDim.x) {
         const FrameDev &F = B->f[fi];
+        // the frame's fields in registers before any store (a store through them could alias the
+        // descriptor, which would make every later access reload them)
+        uint32_t *const cnt = F.chunk_cnt;
+        int64_t *const total = F.points_n;
         const int nparts = F.n_bp_chunks * kBpWarps;
-        if (nparts == 0 || !F.points_n) continue;
+        if (nparts == 0 || !total) continue;
         const int E = (nparts + kScanBlock - 1) / kScanBlock;
         const int c0 = threadIdx.x * E, c1 = min(nparts, c0 + E);
         uint32_t run = 0;
 #pragma unroll 4
-        for (int c = c0; c < c1; ++c) run += F.chunk_cnt[c];
+        for (int c = c0; c < c1; ++c) run += cnt[c];
         uint32_t incl = run;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -278,13 +282,14 @@ __global__ void __launch_bounds__(kScanBlock) bp_scan_kernel(const BatchDev *__r
                 if (lane >= o) w += u;
             }
             wsum[lane] = w - v;                                  // exclusive over warps
-            if (lane == 31 && threadIdx.x == 31) *F.points_n = (int64_t)w;   // the frame's total
+            if (lane == 31 && threadIdx.x == 31) *total = (int64_t)w;   // the frame's total
         }
         __syncthreads();
         uint32_t before = wsum[warp] + incl - run;
+#pragma unroll 4
         for (int c = c0; c < c1; ++c) {
-            const uint32_t v = F.chunk_cnt[c];
-            F.chunk_cnt[c] = before;
+            const uint32_t v = cnt[c];
+            cnt[c] = before;
             before += v;
         }
         __syncthreads();                                         // wsum is reused by the next frame
