@@ -145,6 +145,32 @@ def test_ragged_sizes(torch_cuda, res, variant):
         compare(g, o, stages, f"{W}x{H} {stages}-stage")
 
 
+@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("res", [(16384, 64), (64, 16384)])
+def test_largest_width_and_height(torch_cuda, res, variant):
+    """Frames at the largest width and height the boundary accepts (16384), as strips: pixel
+    indices, tile counts, pooled grids and compaction chunks at their largest per row or column.
+    The intrinsics spread 90 x 40 degrees over the strip, so the sweeps cover it."""
+    W, H = res
+    rng = np.random.default_rng(W + 3 * H)
+    sc = scene.make_scene(9, "room")
+    fx = (W / 2.0) / np.tan(np.radians(45.0))
+    fy = (H / 2.0) / np.tan(np.radians(20.0))
+    cam = scene.make_camera(W, H, fx, fy, W / 2.0, H / 2.0, (0.0, 0.0, 1.5))
+    rgb, gt = scene.render_rgb(sc, cam, rng)
+    scans = []
+    for s in range(2):
+        pose = scene.make_lidar_pose(cam, (0.1 * s, 0.05, 0.02), 2.0 * s)
+        scans.append(scene.Scan(scene.lidar_sweep(sc, pose, 64, 2048 + s, rng), pose))
+    v = scene.View(cam, rgb, scans, gt)
+    for stages, st in ((2, PAPER_STAGES), (1, ((2, 5.0, 20.0),))):
+        g = run_gpu([v], stages, st, torch_cuda, kernel_variant=variant)[0]
+        o = run_oracle(v, stages, st)
+        m = compare(g, o, stages, f"{W}x{H} {stages}-stage")
+        assert m.sum() > 1000, "the sweeps should cover the strip"
+        check_points(g, o, cam)
+
+
 def test_empty_and_degenerate_scans(torch_cuda):
     v = scene.make_view(3, res="qvga", scene_kind="room", n_scans=2, beams=16, az_steps=128)
     # no scans at all, an empty scan, and a scan entirely behind the camera
