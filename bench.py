@@ -214,7 +214,24 @@ EXTRA_CONFIGS = {
     "uneven_12view_two_stage_fp16": dict(views="uneven", stages=STAGES, precision=1, batch=12),
     # the 1080p three-scan views with the single-stage alternative: one 15x15 window at full resolution
     "1080p_3scan_single_stage_15x15_fp32": dict(views="main", stages=((7, 5.0, 20.0),), precision=0, batch=4),
+    # the headline workload with the preprocessing of Sec. 4.1 (afterimage removal against a previous frame
+    # in which a block of the image changed; occluded-point removal) and the contour removal of Sec. 5
+    "1080p_3scan_two_stage_prepost_fp32": dict(views="main", stages=STAGES, precision=0, batch=8, moved=True,
+                                               prepost=dict(occlusion_radius=5, occlusion_margin=0.3,
+                                                            motion_threshold=40.0, motion_close_radius=2,
+                                                            contour_threshold=0.05)),
 }
+
+
+def moved_frame(view, seed=0):
+    """A previous RGB frame of the view in which a block of the image differed (something moved there)."""
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    prev = view.rgb.copy()
+    H, W = prev.shape[:2]
+    y0, x0 = H // 3, W // 3
+    prev[y0:y0 + H // 4, x0:x0 + W // 4] = rng.integers(0, 256, 3, dtype=np.uint8)
+    return prev
 
 
 def config_measure(name, cfg, views, a, dev, stream, flush_buf, tap_peak, hbm):
@@ -225,17 +242,19 @@ def config_measure(name, cfg, views, a, dev, stream, flush_buf, tap_peak, hbm):
     from paper_2601_01210_gb300 import Densifier
     from paper_2601_01210_gb300.frames import FrameBuffers
     stages, B, ns = cfg["stages"], cfg["batch"], len(cfg["stages"])
+    prev = [moved_frame(v, i) for i, v in enumerate(views)] if cfg.get("moved") else [None] * len(views)
 
-    def fb(v, **kw):
+    def fb(i, **kw):
+        v = views[i]
         return FrameBuffers(v.camera, v.rgb, [(s.xyz, s.lidar_to_world) for s in v.scans], device=dev,
-                            num_stages=ns, **kw)
+                            num_stages=ns, prev_rgb=prev[i], **kw)
 
-    bufs = [fb(views[i % len(views)]) for i in range(B)]
+    bufs = [fb(i % len(views)) for i in range(B)]
     # max_batch above the step's frames: the batch leaves at the flush, between the step's events
     params = dict(num_stages=ns, stages=stages, precision=cfg["precision"], max_batch=min(64, 2 * B),
                   max_inflight=max(B, 16),
                   launch_policy=1, timing=2, autotune=a.autotune, batches_in_flight=1,
-                  hbm_budget_bytes=max(2 << 30, B * 48 << 20))
+                  hbm_budget_bytes=max(2 << 30, B * 48 << 20), **cfg.get("prepost", {}))
 
     def run(d, frames, k, ev=None):
         ts = [d.submit(f.frame) for f in frames]
@@ -260,7 +279,7 @@ def config_measure(name, cfg, views, a, dev, stream, flush_buf, tap_peak, hbm):
         step_ms = [s_.elapsed_time(e_) for s_, e_ in evs]
         choice = d.describe()
         launches = d.kernel_launches()
-        probe = [fb(v, debug=True) for v in views[:min(len(views), 16)]]
+        probe = [fb(i, debug=True) for i in range(min(len(views), 16))]
         run(d, probe, 0)
         torch.cuda.synchronize()
     with Densifier(dict(params, timing=1), device=dev.index, stream=stream.cuda_stream) as d3:
@@ -273,11 +292,13 @@ def config_measure(name, cfg, views, a, dev, stream, flush_buf, tap_peak, hbm):
         kt = d3.kernel_times()
     ktable = {k: {"avg_us": round(v[0] / max(1, v[1]), 3), "launches": v[1]} for k, v in kt.items()}
     # algorithmic work of one step: the batch cycles through the probed views
-    works = [step_work(b, v, single_radius=stages[0][0] if ns == 1 else None) for b, v in zip(probe, views)]
+    works = [step_work(b, v, single_radius=stages[0][0] if ns == 1 else None, prepost=cfg.get("prepost"))
+             for b, v in zip(probe, views)]
     work = {k: sum(works[i % len(works)][k] for i in range(B)) for k in works[0]}
     forms = [st["chosen"].get("form", "fp32") for st in choice["stages"]]
-    roof = {k: work[k] / hbm * 1e6 for k in ("prep_compose_clear", "project_zbuf", "pool3", "tile_mark1", "bp_count",
-                                              "bp_write") if k in work}
+    roof = {k: work[k] / hbm * 1e6 for k in ("prep_compose_clear", "motion_mask", "motion_dilate", "motion_erode",
+                                              "project_zbuf", "occlusion", "pool3", "tile_mark1", "contour",
+                                              "bp_count", "bp_write") if k in work}
     roof["jbf_stage1"] = work["taps1"] / tap_peak(forms[0])[0] * 1e6
     if ns == 2:
         roof["jbf_stage2"] = work["taps2"] / tap_peak(forms[1])[0] * 1e6
@@ -288,9 +309,11 @@ def config_measure(name, cfg, views, a, dev, stream, flush_buf, tap_peak, hbm):
     ideal = sum(v["roof_us"] for v in kroof.values())
     sizes = sorted({f"{v.camera.width}x{v.camera.height}" for v in views})
     out = {
-        "config": {"workload": name, "frames_per_step": B, "distinct_views": len(views), "resolutions": sizes,
-                   "stages": [list(st) for st in stages], "precision": "fp16" if cfg["precision"] else "fp32",
-                   "l2": "flushed (256 MiB write) before every step", "launch": "batched CUDA graph"},
+        "config": dict({"workload": name, "frames_per_step": B, "distinct_views": len(views), "resolutions": sizes,
+                        "stages": [list(st) for st in stages], "precision": "fp16" if cfg["precision"] else "fp32",
+                        "l2": "flushed (256 MiB write) before every step", "launch": "batched CUDA graph"},
+                       **({"prepost": cfg["prepost"], "previous_frame": "a block of the image changed"}
+                          if cfg.get("prepost") else {})),
         "value": B / (ms / 1000.0), "unit": UNIT, "ms_per_step": ms,
         "latency_ms_per_step": {"p50": sorted(step_ms)[len(step_ms) // 2], "max": max(step_ms)},
         "gpu_launches": launches,
@@ -312,17 +335,21 @@ def config_cpu_leg(name, cfg, views, outputs, procs):
     import numpy as np
     n = len(outputs)
     t0 = time.perf_counter()
+    extra = dict(cfg.get("prepost", {}))
+    jobs = [(views[i], cfg["stages"], dict(extra, prev_rgb=moved_frame(views[i], i)) if cfg.get("moved") else extra)
+            for i in range(n)]
     with cf.ProcessPoolExecutor(max(1, min(procs, n)), mp_context=mp.get_context("spawn")) as ex:
-        refs = list(ex.map(_oracle_config_frame, [(views[i], cfg["stages"]) for i in range(n)]))
+        refs = list(ex.map(_oracle_config_frame, jobs))
     dt = time.perf_counter() - t0
     per_view = []
     for v, g, (depth, valid) in zip(views, outputs, refs):
-        m = valid.astype(bool)
+        m = valid.astype(bool) & g["valid"].astype(bool)   # depth where both are valid (masks reported apart)
         err = np.abs(g["depth"].astype(np.float64) - depth)[m] if m.any() else np.zeros(1)
         rel = err / depth[m] if m.any() else np.zeros(1)
         bound = np.maximum(1e-3, 1e-3 * depth[m]) if cfg["precision"] else 1e-4 * depth[m]
         per_view.append({"view": f"{v.camera.width}x{v.camera.height}", "valid_mask_exact": bool(
-            np.array_equal(g["valid"], valid)), "max_abs_m": float(err.max()), "p99_abs_m": float(np.percentile(err, 99)),
+            np.array_equal(g["valid"], valid)), "mask_differences_px": int((g["valid"] != valid).sum()),
+            "max_abs_m": float(err.max()), "p99_abs_m": float(np.percentile(err, 99)),
             "max_rel": float(rel.max()), "pixels_over_bar": int((err > bound).sum()) if m.any() else 0})
     return {"value": n / dt, "unit": UNIT, "cores": min(procs, n), "kind": "oracle",
             "sample": f"{n} distinct views of the workload, FP64, one single-threaded oracle process per view "
@@ -330,6 +357,10 @@ def config_cpu_leg(name, cfg, views, outputs, procs):
             "error_vs_oracle": {"bar": "valid masks exact; depth within 1e-4 relative (FP32) or 1 mm absolute / "
                                        "1e-3 relative (FP16)", "per_view": per_view,
                                 "all_masks_exact": all(p["valid_mask_exact"] for p in per_view),
+                                **({"masks_note": "contour decisions are taken on the FP32 filtered map; pixels "
+                                                  "whose relative step is within rounding of the threshold may "
+                                                  "decide differently from the FP64 oracle"}
+                                   if extra.get("contour_threshold") else {}),
                                 "pixels_over_bar": sum(p["pixels_over_bar"] for p in per_view),
                                 "max_abs_m": max(p["max_abs_m"] for p in per_view),
                                 "max_rel": max(p["max_rel"] for p in per_view)}}
@@ -337,9 +368,9 @@ def config_cpu_leg(name, cfg, views, outputs, procs):
 
 def _oracle_config_frame(args):
     import oracle
-    v, stages = args
+    v, stages, extra = args
     oracle.build()
-    o = oracle.densify_view(v, num_stages=len(stages), stages=stages, emit_points=False)
+    o = oracle.densify_view(v, num_stages=len(stages), stages=stages, emit_points=False, **extra)
     return o["depth"], o["valid"]
 
 
@@ -545,12 +576,23 @@ def valid_taps_stage1(cnt_pos, r=4):
     return int(correlate(cnt_pos.astype(np.float64), np.ones((2 * r + 1, 2 * r + 1)), mode="constant").sum())
 
 
-def step_work(b, view, pool=3, single_radius=None):
+def step_work(b, view, pool=3, single_radius=None, prepost=None):
     """Algorithmic work of every kernel of the path for one frame (probe buffers with debug outputs):
     bytes each HBM-bound kernel must move at least, observed taps of the filters. single_radius:
-    the single-stage form at that radius (no pooling; the mark kernel reads the z-buffer)."""
+    the single-stage form at that radius (no pooling; the mark kernel reads the z-buffer). prepost:
+    the preprocessing and post-filter parameters, whose kernels' bytes are added."""
     import numpy as np
     W, H = b.W, b.H
+    extra = {}
+    if prepost:
+        if prepost.get("motion_threshold"):
+            extra["motion_mask"] = 7 * W * H          # RGB and previous RGB in, mask out
+            extra["motion_dilate"] = 2 * W * H        # mask in, mask out
+            extra["motion_erode"] = 2 * W * H
+        if prepost.get("occlusion_radius"):
+            extra["occlusion"] = 8 * W * H            # merged z-buffer in, kept z-buffer out
+        if prepost.get("contour_threshold"):
+            extra["contour"] = 10 * W * H             # filtered depth and validity in, outputs out
     if single_radius is not None:
         z = b.zbuf.cpu().numpy().view(np.uint32)
         obs = z != 0x7F800000
@@ -562,6 +604,7 @@ def step_work(b, view, pool=3, single_radius=None):
             "bp_count": W * H,
             "bp_write": 8 * W * H + 16 * b.n_points(),
             "taps1": valid_taps_stage1(obs, single_radius),
+            **extra,
         }
     Wc, Hc = -(-W // pool), -(-H // pool)
     z = b.zbuf.cpu().numpy().view(np.uint32)
@@ -580,6 +623,7 @@ def step_work(b, view, pool=3, single_radius=None):
         "bp_write": 8 * W * H + 16 * nout,                    # validity, depth, colour in; points out
         "taps1": valid_taps_stage1(cnt_pos),
         "taps2": valid_taps_stage2(b.coarse_valid.cpu().numpy(), W, H),
+        **extra,
     }
 
 

@@ -69,7 +69,7 @@ struct alignas(64) FrameDev {
     const uint8_t *prev_rgb;     // previous RGB frame (afterimage removal)
     int64_t prev_pitch;
     uint8_t *motion;             // H x W motion mask after the closing
-    uint8_t *motion_tmp;         // H x W raw mask, then the dilation
+    uint8_t *motion_tmp;         // the raw mask, then its dilation, bit-packed (rows of ceil(W / 32) words)
     uint32_t *zbuf_raw;          // projection target when occluded points are removed into zbuf
     int32_t newest_scan;         // scan kept inside the motion mask
     int32_t n_px_chunks;         // ceil(W H / kPxChunk)

@@ -16,151 +16,398 @@
 //   contour_kernel  contours: a valid pixel with a valid 4-neighbour whose
 //                   depth differs by more than t times its own depth is dropped
 //                   (FP32 on the filtered map).
+//
+// Every kernel copies the fields it needs of each frame into shared memory once
+// per block, so that no work item waits on a read of the frame descriptor (a
+// store through a pointer read from the descriptor could alias it, which would
+// make the compiler read the descriptor again after every store). The motion mask
+// and its closing work on bit-packed rows, a warp per 32 x 32 tile; the occlusion
+// window on 32 x 32 tiles staged in shared memory, one pass along the rows and
+// one along the columns; the contour test takes 4 consecutive pixels a thread.
 #include "desc.cuh"
 
 namespace dz {
 
 namespace {
 
-template <typename F>
-__device__ __forceinline__ void for_px(const BatchDev *B, F &&body) {
-    const int nf = B->n_frames;
-    const int total = B->px_pre[nf];
-    for (int item = blockIdx.x; item < total; item += gridDim.x) {
-        const int fi = find_segment(B->px_pre, nf, item);
-        const FrameDev &Fr = B->f[fi];
-        const int64_t n = (int64_t)Fr.W * Fr.H;
-        const int64_t p0 = (int64_t)(item - B->px_pre[fi]) * kPxChunk + threadIdx.x;
+constexpr int kPxPerThread = kPxChunk / kThreads;   // 4 consecutive pixels
+static_assert(kPxPerThread == 4, "per-pixel kernels: 4 consecutive pixels a thread");
+
+// (row, column) of pixel p of a W-wide image (p < 2^28)
+__device__ __forceinline__ void px_row_col(int p, int W, int &y, int &x) {
+    y = p / W;
+    x = p - y * W;
+}
+
+// The 3 colour bytes of pixel k (0..3) of 4 consecutive pixels whose 12 bytes are the words w0..w2,
+// as the low three bytes r, g, b of one word (the top byte is not specified).
+__device__ __forceinline__ uint32_t rgb_of(uint32_t w0, uint32_t w1, uint32_t w2, int k) {
+    switch (k) {
+        case 0: return __byte_perm(w0, 0u, 0x0210);
+        case 1: return __byte_perm(w0, w1, 0x0543);
+        case 2: return __byte_perm(w1, w2, 0x0432);
+        default: return __byte_perm(w2, 0u, 0x0321);
+    }
+}
+
+// Stage count elements into shared memory: each thread loads up to kStagePer of them (i = threadIdx.x,
+// threadIdx.x + kThreads, ...) before storing any, so that its global loads are in flight together.
+constexpr int kStagePer = 8;
+template <typename T, typename Load, typename Store>
+__device__ __forceinline__ void stage(int count, Load &&load, Store &&store) {
+    for (int base = threadIdx.x; base < count; base += kStagePer * kThreads) {
+        T v[kStagePer];
 #pragma unroll
-        for (int k = 0; k < kPxChunk / kThreads; ++k) {
-            const int64_t p = p0 + k * kThreads;
-            if (p < n) body(Fr, p);
+        for (int j = 0; j < kStagePer; ++j) {
+            const int i = base + j * kThreads;
+            if (i < count) v[j] = load(i);
+        }
+#pragma unroll
+        for (int j = 0; j < kStagePer; ++j) {
+            const int i = base + j * kThreads;
+            if (i < count) store(i, v[j]);
         }
     }
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(kThreads) motion_kernel(const BatchDev *__restrict__ B, const PrepostArgs a) {
-    for_px(B, [&](const FrameDev &F, int64_t p) {
-        if (!F.motion) return;
-        const int y = (int)(p / F.W), x = (int)(p - (int64_t)y * F.W);
-        const uint8_t *c = F.rgb + (int64_t)y * F.rgb_pitch + 3 * x;
-        const uint8_t *q = F.prev_rgb + (int64_t)y * F.prev_pitch + 3 * x;
-        int d2 = 0;
-#pragma unroll
-        for (int ch = 0; ch < 3; ++ch) {
-            const int d = (int)c[ch] - (int)q[ch];
-            d2 += d * d;
-        }
-        F.motion[p] = (float)d2 > a.motion_t2;
-    });
+// ---------------------------------------------------------------------------
+// The motion mask and its closing work on bit-packed rows: bit i of word j of row y is pixel
+// (32 j + i, y), a row of Wp = ceil(W / 32) words, the bits past W zero. One warp takes a 32 x 32
+// tile (the occlusion tiles): 32 rows of one word each.
+constexpr int kMaxCloseR = 16;
+constexpr int kPPWarps = kThreads / 32;
+struct MotionFrame {
+    const uint8_t *rgb, *prev;
+    uint32_t *raw;     // the raw mask, bit-packed; NULL: afterimage removal is off for the frame
+    uint32_t *dil;     // its dilation, bit-packed
+    uint8_t *mask;     // the closing, one byte a pixel
+    int64_t pitch, ppitch;
+    int32_t W, H, Wp;
+};
+
+__device__ __forceinline__ void motion_frames(const BatchDev *B, int32_t *s_pre, MotionFrame *s_f) {
+    const int nf = B->n_frames;
+    for (int i = threadIdx.x; i <= nf; i += kThreads) s_pre[i] = B->oc_pre[i];
+    for (int i = threadIdx.x; i < nf; i += kThreads) {
+        const FrameDev &F = B->f[i];
+        const int Wp = (F.W + 31) / 32;
+        uint32_t *raw = reinterpret_cast<uint32_t *>(F.motion_tmp);
+        s_f[i] = MotionFrame{F.rgb, F.prev_rgb, raw, raw ? raw + (int64_t)Wp * F.H : nullptr, F.motion,
+                             F.rgb_pitch, F.prev_pitch, F.W, F.H, Wp};
+    }
 }
 
+__global__ void __launch_bounds__(kThreads) motion_kernel(const BatchDev *__restrict__ B, const PrepostArgs a) {
+    __shared__ int32_t s_pre[kMaxBatch + 1];
+    __shared__ MotionFrame s_f[kMaxBatch];
+    motion_frames(B, s_pre, s_f);
+    __syncthreads();
+    const int nf = B->n_frames;
+    const int total = s_pre[nf];
+    const int lane = threadIdx.x & 31;
+    for (int item = blockIdx.x * kPPWarps + (threadIdx.x >> 5); item < total; item += gridDim.x * kPPWarps) {
+        const int fi = find_segment(s_pre, nf, item);
+        const MotionFrame &F = s_f[fi];
+        if (!F.raw) continue;   // the same for every lane of the warp
+        const int t = item - s_pre[fi];
+        const int tx = t % F.Wp, y0 = (t / F.Wp) * 32;
+        // lane = 4 consecutive columns (group g = lane & 7) of one of 4 rows (lane >> 3); 8 steps of 4
+        // rows. A group inside the image on word-aligned rows reads 3 words of each frame; the 8
+        // groups' nibbles of a row meet in one word by 3 shuffles.
+        const int g = lane & 7, rr = lane >> 3;
+        const int x = 32 * tx + 4 * g;
+        const bool words = x + 4 <= F.W && ((((uintptr_t)F.rgb) | ((uintptr_t)F.prev) | F.pitch | F.ppitch) & 3) == 0;
+#pragma unroll 4
+        for (int step = 0; step < 8; ++step) {
+            const int y = y0 + 4 * step + rr;
+            uint32_t bits = 0u;   // bit k: pixel x + k moved
+            if (y < F.H && x < F.W) {
+                if (words) {   // 12 bytes at 3 x, a multiple of 4
+                    const uint32_t *c = reinterpret_cast<const uint32_t *>(F.rgb + (int64_t)y * F.pitch + 3 * x);
+                    const uint32_t *q = reinterpret_cast<const uint32_t *>(F.prev + (int64_t)y * F.ppitch + 3 * x);
+                    const uint32_t c0 = c[0], c1 = c[1], c2 = c[2], q0 = q[0], q1 = q[1], q2 = q[2];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const uint32_t d = __vabsdiffu4(rgb_of(c0, c1, c2, k), rgb_of(q0, q1, q2, k));
+                        const uint32_t d2 = __dp4a(d, d & 0x00FFFFFFu, 0u);   // squared RGB distance, exact
+                        if ((float)d2 > a.motion_t2) bits |= 1u << k;
+                    }
+                } else {
+                    for (int k = 0; k < 4 && x + k < F.W; ++k) {
+                        const uint8_t *c = F.rgb + (int64_t)y * F.pitch + 3 * (x + k);
+                        const uint8_t *q = F.prev + (int64_t)y * F.ppitch + 3 * (x + k);
+                        int d2 = 0;
+#pragma unroll
+                        for (int ch = 0; ch < 3; ++ch) {
+                            const int d = (int)c[ch] - (int)q[ch];
+                            d2 += d * d;
+                        }
+                        if ((float)d2 > a.motion_t2) bits |= 1u << k;
+                    }
+                }
+            }
+            uint32_t word = bits << (4 * g);
+            word |= __shfl_xor_sync(0xffffffffu, word, 1);
+            word |= __shfl_xor_sync(0xffffffffu, word, 2);
+            word |= __shfl_xor_sync(0xffffffffu, word, 4);
+            if (g == 0 && y < F.H) F.raw[(int64_t)y * F.Wp + tx] = word;
+        }
+    }
+}
+
+// Dilation (src: the raw mask, out: its packed dilation) or erosion (src: the dilation, out: the byte
+// mask) with a square (2c+1)^2 element. Lane r of a warp takes row y0 + r of the tile's word column tx:
+// the rows y0 - c .. y0 + 31 + c are first dilated (eroded) along the row, 2c funnel shifts a word with
+// its neighbour words, then the lane combines the 2c + 1 rows of its window. Outside the image the
+// dilation sees no motion and the erosion motion (the bits past W of the erosion's input are set).
 __global__ void __launch_bounds__(kThreads) morph_kernel(const BatchDev *__restrict__ B, const PrepostArgs a,
                                                          int dilate) {
+    __shared__ int32_t s_pre[kMaxBatch + 1];
+    __shared__ MotionFrame s_f[kMaxBatch];
+    __shared__ uint32_t s_h[kPPWarps][32 + 2 * kMaxCloseR];
+    motion_frames(B, s_pre, s_f);
+    __syncthreads();
     const int c = a.close_radius;
-    for_px(B, [&](const FrameDev &F, int64_t p) {
-        if (!F.motion) return;
-        const uint8_t *src = dilate ? F.motion : F.motion_tmp;
-        uint8_t *dst = dilate ? F.motion_tmp : F.motion;
-        const int y = (int)(p / F.W), x = (int)(p - (int64_t)y * F.W);
-        uint8_t m = dilate ? 0 : 1;
-        for (int dy = -c; dy <= c; ++dy) {
-            const int qy = y + dy;
-            if (qy < 0 || qy >= F.H) continue;
-            for (int dx = -c; dx <= c; ++dx) {
-                const int qx = x + dx;
-                if (qx < 0 || qx >= F.W) continue;
-                const uint8_t v = src[(int64_t)qy * F.W + qx];
-                if (dilate) m |= v;
-                else m &= v;
+    const uint32_t fill = dilate ? 0u : ~0u;
+    const int nf = B->n_frames;
+    const int total = s_pre[nf];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t *const h = s_h[warp];
+    for (int item = blockIdx.x * kPPWarps + warp; item < total; item += gridDim.x * kPPWarps) {
+        const int fi = find_segment(s_pre, nf, item);
+        const MotionFrame &F = s_f[fi];
+        if (!F.raw) continue;   // the same for every lane of the warp
+        const int t = item - s_pre[fi];
+        const int tx = t % F.Wp, y0 = (t / F.Wp) * 32;
+        const uint32_t *src = dilate ? F.raw : F.dil;
+        // the erosion's input has the bits past W set (outside: motion)
+        const int tailbits = F.W - 32 * (F.Wp - 1);
+        const uint32_t tail = dilate || tailbits == 32 ? 0u : ~0u << tailbits;
+        auto word = [&](int y, int j) -> uint32_t {
+            if (y < 0 || y >= F.H || j < 0 || j >= F.Wp) return fill;
+            const uint32_t v = src[(int64_t)y * F.Wp + j];
+            return j == F.Wp - 1 ? (v | tail) : v;
+        };
+        for (int k = lane; k < 32 + 2 * c; k += 32) {   // rows y0 - c + k
+            const int y = y0 - c + k;
+            const uint32_t w = word(y, tx), l = word(y, tx - 1), r = word(y, tx + 1);
+            uint32_t v = w;
+            for (int s = 1; s <= c; ++s) {
+                const uint32_t lo = __funnelshift_l(l, w, s), hi = __funnelshift_r(w, r, s);   // pixels x - s, x + s
+                v = dilate ? (v | lo | hi) : (v & lo & hi);
+            }
+            h[k] = v;
+        }
+        __syncwarp();
+        const int y = y0 + lane;
+        uint32_t v = h[lane];
+        for (int s = 1; s <= 2 * c; ++s) v = dilate ? (v | h[lane + s]) : (v & h[lane + s]);
+        __syncwarp();   // h is rewritten by the warp's next tile
+        if (y >= F.H) continue;
+        if (dilate) {
+            F.dil[(int64_t)y * F.Wp + tx] = v;
+        } else {
+            const int x0 = 32 * tx, n = min(32, F.W - x0);
+            uint8_t *row = F.mask + (int64_t)y * F.W + x0;
+            if ((((uintptr_t)row) & 3) == 0) {
+                int i = 0;
+                for (; i + 4 <= n; i += 4) {
+                    const uint32_t nib = (v >> i) & 0xFu;
+                    *reinterpret_cast<uint32_t *>(row + i) =
+                        (nib & 1u) | ((nib & 2u) << 7) | ((nib & 4u) << 14) | ((nib & 8u) << 21);
+                }
+                for (; i < n; ++i) row[i] = (v >> i) & 1u;
+            } else {
+                for (int i = 0; i < n; ++i) row[i] = (v >> i) & 1u;
             }
         }
-        dst[p] = m;
-    });
+    }
 }
 
+// ---------------------------------------------------------------------------
 // Tiles of 32 x 32 output pixels; the tile plus a rho halo is staged as depth
 // (0 where empty) and an observation flag, then row sums and column sums.
 constexpr int kMaxOccR = 16;
+struct OccFrame {
+    const uint32_t *src;   // merged z-buffer
+    uint32_t *dst;         // kept z-buffer
+    int64_t zpitch;
+    int32_t W, H, tiles_x;
+};
+
 __global__ void __launch_bounds__(kThreads) occlusion_kernel(const BatchDev *__restrict__ B, const PrepostArgs a) {
     constexpr int T = kOccTile, S = T + 2 * kMaxOccR;
     __shared__ float sd[S * S];
     __shared__ uint8_t sc[S * S];
     __shared__ float hs[S * T];
     __shared__ int16_t hc[S * T];
+    __shared__ int32_t s_pre[kMaxBatch + 1];
+    __shared__ OccFrame s_f[kMaxBatch];
     const int rho = a.occ_radius, sw = T + 2 * rho;
     const int nf = B->n_frames;
-    const int total = B->oc_pre[nf];
+    for (int i = threadIdx.x; i <= nf; i += kThreads) s_pre[i] = B->oc_pre[i];
+    for (int i = threadIdx.x; i < nf; i += kThreads) {
+        const FrameDev &F = B->f[i];
+        s_f[i] = OccFrame{F.zbuf_raw, F.zbuf, F.zpitch, F.W, F.H, (F.W + T - 1) / T};
+    }
+    __syncthreads();
+    const int total = s_pre[nf];
     for (int item = blockIdx.x; item < total; item += gridDim.x) {
-        const int fi = find_segment(B->oc_pre, nf, item);
-        const FrameDev &F = B->f[fi];
-        const int tiles_x = (F.W + T - 1) / T;
-        const int t = item - B->oc_pre[fi];
-        const int x0 = (t % tiles_x) * T, y0 = (t / tiles_x) * T;
-        __syncthreads();
-        for (int i = threadIdx.x; i < sw * sw; i += kThreads) {
+        const int fi = find_segment(s_pre, nf, item);
+        const OccFrame &F = s_f[fi];
+        const int t = item - s_pre[fi];
+        const int x0 = (t % F.tiles_x) * T, y0 = (t / F.tiles_x) * T;
+        stage<uint32_t>(sw * sw, [&](int i) -> uint32_t {
             const int sy = i / sw, sx = i - sy * sw;
             const int gx = x0 - rho + sx, gy = y0 - rho + sy;
-            uint32_t z = kEmpty;
-            if (gx >= 0 && gx < F.W && gy >= 0 && gy < F.H) z = F.zbuf_raw[(int64_t)gy * F.zpitch + gx];
+            return (gx >= 0 && gx < F.W && gy >= 0 && gy < F.H) ? F.src[(int64_t)gy * F.zpitch + gx] : kEmpty;
+        }, [&](int i, uint32_t z) {
             sd[i] = z != kEmpty ? __uint_as_float(z) : 0.0f;
             sc[i] = z != kEmpty;
-        }
+        });
         __syncthreads();
-        for (int i = threadIdx.x; i < sw * T; i += kThreads) {
-            const int r = i / T, x = i - r * T;
-            float s = 0.0f;
-            int n = 0;
+        // row sums: a thread takes 4 consecutive columns of a staged row, its 4 window sums (over dx
+        // in order) fed from a window of 4 staged values that slides along the row
+        for (int i = threadIdx.x; i < sw * (T / 4); i += kThreads) {
+            const int r = i / (T / 4), x = 4 * (i - r * (T / 4));
+            const float *d = sd + r * sw + x;
+            const uint8_t *cc = sc + r * sw + x;
+            float v0 = d[0], v1 = d[1], v2 = d[2], v3 = d[3];
+            int c0 = cc[0], c1 = cc[1], c2 = cc[2], c3 = cc[3];
+            float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;   // adding 0 for an empty cell changes nothing
+            int n0 = 0, n1 = 0, n2 = 0, n3 = 0;
             for (int dx = 0; dx <= 2 * rho; ++dx) {
-                s = __fadd_rn(s, sd[r * sw + x + dx]);   // adding 0 for an empty cell changes nothing
-                n += sc[r * sw + x + dx];
+                s0 = __fadd_rn(s0, v0); s1 = __fadd_rn(s1, v1); s2 = __fadd_rn(s2, v2); s3 = __fadd_rn(s3, v3);
+                n0 += c0; n1 += c1; n2 += c2; n3 += c3;
+                v0 = v1; v1 = v2; v2 = v3;
+                c0 = c1; c1 = c2; c2 = c3;
+                if (dx < 2 * rho) {
+                    v3 = d[dx + 4];
+                    c3 = cc[dx + 4];
+                }
             }
-            hs[i] = s;
-            hc[i] = (int16_t)n;
+            float *hrow = hs + r * T + x;
+            int16_t *crow = hc + r * T + x;
+            hrow[0] = s0; hrow[1] = s1; hrow[2] = s2; hrow[3] = s3;
+            crow[0] = (int16_t)n0; crow[1] = (int16_t)n1; crow[2] = (int16_t)n2; crow[3] = (int16_t)n3;
         }
         __syncthreads();
-        for (int i = threadIdx.x; i < T * T; i += kThreads) {
-            const int y = i / T, x = i - y * T;
-            const int gx = x0 + x, gy = y0 + y;
-            if (gx >= F.W || gy >= F.H) continue;
-            const uint32_t z = F.zbuf_raw[(int64_t)gy * F.zpitch + gx];
-            uint32_t out = z;
-            if (z != kEmpty) {
-                float s = 0.0f;
-                int n = 0;
-                for (int dy = 0; dy <= 2 * rho; ++dy) {
-                    s = __fadd_rn(s, hs[(y + dy) * T + x]);
-                    n += hc[(y + dy) * T + x];
+        // column sums (over dy in order) of the row sums and the decision: a thread takes 4
+        // consecutive rows of a column, likewise with a sliding window of 4 row sums
+        for (int i = threadIdx.x; i < T * (T / 4); i += kThreads) {
+            const int x = i % T, y = 4 * (i / T);
+            const float *hcol = hs + y * T + x;
+            const int16_t *ccol = hc + y * T + x;
+            float v0 = hcol[0], v1 = hcol[T], v2 = hcol[2 * T], v3 = hcol[3 * T];
+            int c0 = ccol[0], c1 = ccol[T], c2 = ccol[2 * T], c3 = ccol[3 * T];
+            float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
+            int n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+            for (int dy = 0; dy <= 2 * rho; ++dy) {
+                s0 = __fadd_rn(s0, v0); s1 = __fadd_rn(s1, v1); s2 = __fadd_rn(s2, v2); s3 = __fadd_rn(s3, v3);
+                n0 += c0; n1 += c1; n2 += c2; n3 += c3;
+                v0 = v1; v1 = v2; v2 = v3;
+                c0 = c1; c1 = c2; c2 = c3;
+                if (dy < 2 * rho) {
+                    v3 = hcol[(dy + 4) * T];
+                    c3 = ccol[(dy + 4) * T];
                 }
-                const float avg = __fdiv_rn(s, (float)n);
-                if (__uint_as_float(z) > __fadd_rn(avg, a.occ_margin)) out = kEmpty;
             }
-            F.zbuf[(int64_t)gy * F.zpitch + gx] = out;
+            const float sum[4] = {s0, s1, s2, s3};
+            const int cnt[4] = {n0, n1, n2, n3};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int gx = x0 + x, gy = y0 + y + k;
+                if (gx >= F.W || gy >= F.H) continue;
+                const int o = (y + k + rho) * sw + x + rho;   // the pixel's own staged cell
+                uint32_t out = kEmpty;
+                if (sc[o]) {
+                    const float z = sd[o];
+                    const float avg = __fdiv_rn(sum[k], (float)cnt[k]);
+                    out = z > __fadd_rn(avg, a.occ_margin) ? kEmpty : __float_as_uint(z);
+                }
+                F.dst[(int64_t)gy * F.zpitch + gx] = out;
+            }
         }
+        __syncthreads();   // the staged tile and sums are rewritten by the next tile
     }
 }
 
+// ---------------------------------------------------------------------------
+struct ContourFrame {
+    const float *depth;
+    const uint8_t *valid;
+    float *out_depth;
+    uint8_t *out_valid;
+    int32_t W, H;
+};
+
 __global__ void __launch_bounds__(kThreads) contour_kernel(const BatchDev *__restrict__ B, const PrepostArgs a) {
-    for_px(B, [&](const FrameDev &F, int64_t p) {
-        const int y = (int)(p / F.W), x = (int)(p - (int64_t)y * F.W);
-        const uint8_t v = F.flt_valid[p];
-        const float d = F.flt_depth[p];
-        bool drop = false;
-        if (v) {
-            const float lim = __fmul_rn(a.contour_t, d);
-            const int qx[4] = {x - 1, x + 1, x, x}, qy[4] = {y, y, y - 1, y + 1};
+    __shared__ int32_t s_pre[kMaxBatch + 1];
+    __shared__ ContourFrame s_f[kMaxBatch];
+    const int nf = B->n_frames;
+    for (int i = threadIdx.x; i <= nf; i += kThreads) s_pre[i] = B->px_pre[i];
+    for (int i = threadIdx.x; i < nf; i += kThreads) {
+        const FrameDev &F = B->f[i];
+        s_f[i] = ContourFrame{F.flt_depth, F.flt_valid, F.out_depth, F.out_valid, F.W, F.H};
+    }
+    __syncthreads();
+    const int total = s_pre[nf];
+    for (int item = blockIdx.x; item < total; item += gridDim.x) {
+        const int fi = find_segment(s_pre, nf, item);
+        const ContourFrame &F = s_f[fi];
+        const int n = F.W * F.H;
+        const int p0 = (item - s_pre[fi]) * kPxChunk + threadIdx.x * kPxPerThread;
+        if (p0 >= n) continue;
+        int y, x;
+        px_row_col(p0, F.W, y, x);
+        // every load of the 4 pixels and their neighbours first
+        float d[kPxPerThread], nd[kPxPerThread][4];
+        uint8_t v[kPxPerThread], nv[kPxPerThread][4];
+        int yk = y, xk = x;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                if (qx[k] < 0 || qx[k] >= F.W || qy[k] < 0 || qy[k] >= F.H) continue;
-                const int64_t q = (int64_t)qy[k] * F.W + qx[k];
-                if (F.flt_valid[q] && fabsf(__fadd_rn(F.flt_depth[q], -d)) > lim) drop = true;
+        for (int k = 0; k < kPxPerThread; ++k) {
+            const int p = p0 + k;
+            v[k] = 0;
+            d[k] = 0.0f;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                nv[k][j] = 0;
+                nd[k][j] = 0.0f;
+            }
+            if (p < n) {
+                v[k] = F.valid[p];
+                d[k] = F.depth[p];
+                const int qx[4] = {xk - 1, xk + 1, xk, xk}, qy[4] = {yk, yk, yk - 1, yk + 1};
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (qx[j] >= 0 && qx[j] < F.W && qy[j] >= 0 && qy[j] < F.H) {
+                        const int q = qy[j] * F.W + qx[j];
+                        nv[k][j] = F.valid[q];
+                        nd[k][j] = F.depth[q];
+                    }
+            }
+            if (++xk == F.W) {
+                xk = 0;
+                ++yk;
             }
         }
-        F.out_valid[p] = v && !drop;
-        F.out_depth[p] = drop ? 0.0f : d;
-    });
+#pragma unroll
+        for (int k = 0; k < kPxPerThread; ++k) {
+            const int p = p0 + k;
+            if (p >= n) break;
+            bool drop = false;
+            if (v[k]) {
+                const float lim = __fmul_rn(a.contour_t, d[k]);
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (nv[k][j] && fabsf(__fadd_rn(nd[k][j], -d[k])) > lim) drop = true;
+            }
+            F.out_valid[p] = v[k] && !drop;
+            F.out_depth[p] = drop ? 0.0f : d[k];
+        }
+    }
 }
 
 cudaError_t launch_motion(const BatchDev *b, const PrepostArgs &a, int grid, cudaStream_t s) {
@@ -169,6 +416,7 @@ cudaError_t launch_motion(const BatchDev *b, const PrepostArgs &a, int grid, cud
 }
 
 cudaError_t launch_morph(const BatchDev *b, const PrepostArgs &a, bool dilate, int grid, cudaStream_t s) {
+    if (a.close_radius < 0 || a.close_radius > kMaxCloseR) return cudaErrorInvalidValue;
     morph_kernel<<<grid, kThreads, 0, s>>>(b, a, dilate ? 1 : 0);
     return cudaGetLastError();
 }

@@ -484,7 +484,8 @@ Layout layout_of(const densify_params &p, const densify_frame *f, bool allow_zpo
     L.has_motion = p.motion_threshold > 0.0f && f->prev_rgb;
     if (L.has_motion) {
         L.motion = take(npx);
-        L.motion_tmp = take(npx);
+        // two bit-packed masks (32 pixels a word, rows of ceil(W / 32) words): the raw and the dilated one
+        L.motion_tmp = take(std::max<int64_t>(npx, 2 * 4 * ((W + 31) / 32) * H));
         if (host) L.prev = take((uint64_t)npx * 3);
     }
     if (p.contour_threshold > 0.0f) {

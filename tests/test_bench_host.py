@@ -172,3 +172,51 @@ def test_single_stage_work_counts_observed_taps():
 
     assert bench.step_work(Buf([(8, 10)]), View, single_radius=4)["taps1"] == 81
     assert bench.step_work(Buf([(0, 0)]), View, single_radius=4)["taps1"] == 25
+
+
+def test_prepost_config_leg_runs_the_oracle_with_the_same_options():
+    """The pre/post-filter workload's CPU leg: the oracle runs with the workload's preprocessing and
+    post-filter options and each view's previous frame, so the oracle's own outputs for those options
+    score exact masks and no error, and outputs without the options do not."""
+    import numpy as np
+
+    import bench
+    import oracle
+    import scene
+    oracle.build()
+    cfg = bench.EXTRA_CONFIGS["1080p_3scan_two_stage_prepost_fp32"]
+    views = [scene.make_view(606 + i, res="qvga", scene_kind="room", n_scans=3, beams=64, az_steps=512)
+             for i in range(2)]
+    outs, plain = [], []
+    for i, v in enumerate(views):
+        o = oracle.densify_view(v, num_stages=2, stages=cfg["stages"], emit_points=False,
+                                prev_rgb=bench.moved_frame(v, i), **cfg["prepost"])
+        outs.append({"depth": o["depth"].astype(np.float32), "valid": o["valid"]})
+        p = oracle.densify_view(v, num_stages=2, stages=cfg["stages"], emit_points=False)
+        plain.append({"depth": p["depth"].astype(np.float32), "valid": p["valid"]})
+    e = bench.config_cpu_leg("prepost", cfg, views, outs, 2)["error_vs_oracle"]
+    assert e["all_masks_exact"] and e["max_rel"] < 1e-7 and "masks_note" in e
+    e = bench.config_cpu_leg("prepost", cfg, views, plain, 2)["error_vs_oracle"]
+    assert not e["all_masks_exact"]
+
+
+def test_prepost_work_adds_the_preprocessing_kernels():
+    import numpy as np
+    import torch
+
+    import bench
+
+    class Buf:
+        W, H = 20, 16
+        zbuf = torch.from_numpy(np.full((16, 20), 0x7F800000, np.uint32).view(np.int32))
+
+        def n_points(self):
+            return 0
+
+    class View:
+        scans = []
+
+    w = bench.step_work(Buf(), View, single_radius=2, prepost=dict(occlusion_radius=5, motion_threshold=40.0,
+                                                                   contour_threshold=0.05))
+    assert (w["motion_mask"], w["motion_dilate"], w["occlusion"], w["contour"]) == (7 * 320, 2 * 320, 8 * 320, 10 * 320)
+    assert "occlusion" not in bench.step_work(Buf(), View, single_radius=2)
