@@ -237,15 +237,17 @@ struct OccFrame {
     int32_t W, H, tiles_x;
 };
 
+// RHO > 0: the window radius fixed at compile time (the sliding sums unrolled); 0: a.occ_radius.
+template <int RHO>
 __global__ void __launch_bounds__(kThreads) occlusion_kernel(const BatchDev *__restrict__ B, const PrepostArgs a) {
-    constexpr int T = kOccTile, S = T + 2 * kMaxOccR;
+    constexpr int T = kOccTile, S = T + 2 * (RHO > 0 ? RHO : kMaxOccR);
     __shared__ float sd[S * S];
     __shared__ uint8_t sc[S * S];
     __shared__ float hs[S * T];
     __shared__ int16_t hc[S * T];
     __shared__ int32_t s_pre[kMaxBatch + 1];
     __shared__ OccFrame s_f[kMaxBatch];
-    const int rho = a.occ_radius, sw = T + 2 * rho;
+    const int rho = RHO > 0 ? RHO : a.occ_radius, sw = T + 2 * rho;
     const int nf = B->n_frames;
     for (int i = threadIdx.x; i <= nf; i += kThreads) s_pre[i] = B->oc_pre[i];
     for (int i = threadIdx.x; i < nf; i += kThreads) {
@@ -278,6 +280,7 @@ __global__ void __launch_bounds__(kThreads) occlusion_kernel(const BatchDev *__r
             int c0 = cc[0], c1 = cc[1], c2 = cc[2], c3 = cc[3];
             float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;   // adding 0 for an empty cell changes nothing
             int n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+#pragma unroll
             for (int dx = 0; dx <= 2 * rho; ++dx) {
                 s0 = __fadd_rn(s0, v0); s1 = __fadd_rn(s1, v1); s2 = __fadd_rn(s2, v2); s3 = __fadd_rn(s3, v3);
                 n0 += c0; n1 += c1; n2 += c2; n3 += c3;
@@ -304,6 +307,7 @@ __global__ void __launch_bounds__(kThreads) occlusion_kernel(const BatchDev *__r
             int c0 = ccol[0], c1 = ccol[T], c2 = ccol[2 * T], c3 = ccol[3 * T];
             float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;
             int n0 = 0, n1 = 0, n2 = 0, n3 = 0;
+#pragma unroll
             for (int dy = 0; dy <= 2 * rho; ++dy) {
                 s0 = __fadd_rn(s0, v0); s1 = __fadd_rn(s1, v1); s2 = __fadd_rn(s2, v2); s3 = __fadd_rn(s3, v3);
                 n0 += c0; n1 += c1; n2 += c2; n3 += c3;
@@ -362,6 +366,60 @@ __global__ void __launch_bounds__(kThreads) contour_kernel(const BatchDev *__res
         if (p0 >= n) continue;
         int y, x;
         px_row_col(p0, F.W, y, x);
+        // 4 pixels of one row, rows of a width divisible by 4 and aligned arrays: the 4 pixels and the
+        // rows above and below by 16- and 4-byte loads, the left and right neighbours by single loads
+        const bool vec = (F.W & 3) == 0 && x + 4 <= F.W &&
+                         ((((uintptr_t)F.depth) | ((uintptr_t)F.out_depth)) & 15) == 0 &&
+                         ((((uintptr_t)F.valid) | ((uintptr_t)F.out_valid)) & 3) == 0;
+        if (vec) {
+            const float4 dc = *reinterpret_cast<const float4 *>(F.depth + p0);
+            const uint32_t vc = *reinterpret_cast<const uint32_t *>(F.valid + p0);
+            float4 du = make_float4(0.f, 0.f, 0.f, 0.f), dd = du;
+            uint32_t vu = 0u, vd = 0u;
+            if (y > 0) {
+                du = *reinterpret_cast<const float4 *>(F.depth + p0 - F.W);
+                vu = *reinterpret_cast<const uint32_t *>(F.valid + p0 - F.W);
+            }
+            if (y + 1 < F.H) {
+                dd = *reinterpret_cast<const float4 *>(F.depth + p0 + F.W);
+                vd = *reinterpret_cast<const uint32_t *>(F.valid + p0 + F.W);
+            }
+            float dl = 0.0f, dr = 0.0f;
+            uint8_t vl = 0, vr = 0;
+            if (x > 0) {
+                dl = F.depth[p0 - 1];
+                vl = F.valid[p0 - 1];
+            }
+            if (x + 4 < F.W) {
+                dr = F.depth[p0 + 4];
+                vr = F.valid[p0 + 4];
+            }
+            const float d[6] = {dl, dc.x, dc.y, dc.z, dc.w, dr};   // the row, with the left and right neighbour
+            const uint8_t v[6] = {vl, (uint8_t)(vc & 1u), (uint8_t)((vc >> 8) & 1u), (uint8_t)((vc >> 16) & 1u),
+                                  (uint8_t)((vc >> 24) & 1u), vr};
+            const float up[4] = {du.x, du.y, du.z, du.w}, dn[4] = {dd.x, dd.y, dd.z, dd.w};
+            float od[4];
+            uint32_t ov = 0u;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const float c = d[k + 1];
+                bool keep = v[k + 1] != 0;
+                if (keep) {
+                    const float lim = __fmul_rn(a.contour_t, c);
+                    // left, right, above, below (the order of the per-pixel form; any step drops)
+                    if (v[k] && fabsf(__fadd_rn(d[k], -c)) > lim) keep = false;
+                    if (v[k + 2] && fabsf(__fadd_rn(d[k + 2], -c)) > lim) keep = false;
+                    if (((vu >> (8 * k)) & 1u) && fabsf(__fadd_rn(up[k], -c)) > lim) keep = false;
+                    if (((vd >> (8 * k)) & 1u) && fabsf(__fadd_rn(dn[k], -c)) > lim) keep = false;
+                }
+                const bool drop = v[k + 1] && !keep;
+                od[k] = drop ? 0.0f : c;
+                ov |= (uint32_t)(v[k + 1] && keep) << (8 * k);
+            }
+            *reinterpret_cast<float4 *>(F.out_depth + p0) = make_float4(od[0], od[1], od[2], od[3]);
+            *reinterpret_cast<uint32_t *>(F.out_valid + p0) = ov;
+            continue;
+        }
         // every load of the 4 pixels and their neighbours first
         float d[kPxPerThread], nd[kPxPerThread][4];
         uint8_t v[kPxPerThread], nv[kPxPerThread][4];
@@ -423,7 +481,17 @@ cudaError_t launch_morph(const BatchDev *b, const PrepostArgs &a, bool dilate, i
 
 cudaError_t launch_occlusion(const BatchDev *b, const PrepostArgs &a, int grid, cudaStream_t s) {
     if (a.occ_radius < 1 || a.occ_radius > kMaxOccR) return cudaErrorInvalidValue;
-    occlusion_kernel<<<grid, kThreads, 0, s>>>(b, a);
+    switch (a.occ_radius) {
+        case 1: occlusion_kernel<1><<<grid, kThreads, 0, s>>>(b, a); break;
+        case 2: occlusion_kernel<2><<<grid, kThreads, 0, s>>>(b, a); break;
+        case 3: occlusion_kernel<3><<<grid, kThreads, 0, s>>>(b, a); break;
+        case 4: occlusion_kernel<4><<<grid, kThreads, 0, s>>>(b, a); break;
+        case 5: occlusion_kernel<5><<<grid, kThreads, 0, s>>>(b, a); break;
+        case 6: occlusion_kernel<6><<<grid, kThreads, 0, s>>>(b, a); break;
+        case 7: occlusion_kernel<7><<<grid, kThreads, 0, s>>>(b, a); break;
+        case 8: occlusion_kernel<8><<<grid, kThreads, 0, s>>>(b, a); break;
+        default: occlusion_kernel<0><<<grid, kThreads, 0, s>>>(b, a); break;
+    }
     return cudaGetLastError();
 }
 
@@ -436,7 +504,7 @@ int occupancy_prepost(KernelId k) {
     int n = 0;
     if (k == K_MOTION) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, motion_kernel, kThreads, 0);
     else if (k == K_DILATE || k == K_ERODE) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, morph_kernel, kThreads, 0);
-    else if (k == K_OCCLUSION) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, occlusion_kernel, kThreads, 0);
+    else if (k == K_OCCLUSION) cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, occlusion_kernel<0>, kThreads, 0);
     else cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, contour_kernel, kThreads, 0);
     return n > 0 ? n : 1;
 }
