@@ -932,15 +932,17 @@ densify_status issue_kernels(densify_ctx *c, Slot &sl, cudaStream_t s, bool reco
 // write whose points go straight into page-locked host memory runs at the host link's rate, about
 // a millisecond for eight 1080p frames; with the persistent grid on every SM it would hold them all
 // that long, and the next batch's kernels (on another slot's stream) could not start. When every
-// frame of the first batch writes its points that way, the compaction write gets a quarter of the
-// SMs, which still outpace the link, and the rest run the next batch.
+// frame of the first batch writes its points that way, the compaction write gets an eighth of its
+// persistent grid (one block on every second SM), which still keeps the link busy, and the rest run
+// the next batch (measured on eight 1080p frames, three batches in flight: 6.6k frames/s end to end
+// at an eighth, 6.3k at a quarter, 6.1k at a half, 6.2k at a sixteenth).
 void settle_grids(densify_ctx *c, const std::vector<uint64_t> &tk) {
     if (c->grids_fixed) return;
     c->grids_fixed = true;
     // (only a context with its own streams overlaps its slots' batches)
     bool host_points = c->p.emit_points && c->own_stream && c->slots.size() > 1 && !tk.empty();
     for (uint64_t t : tk) host_points &= c->frames[t].L.points_direct != nullptr;
-    if (host_points) c->grid[K_BP_WRITE] = std::max(1, c->grid[K_BP_WRITE] / 4);
+    if (host_points) c->grid[K_BP_WRITE] = std::max(1, c->grid[K_BP_WRITE] / 8);
 }
 
 // Capture a slot's kernel sequence (its own device descriptor) into a graph, instantiate it and
