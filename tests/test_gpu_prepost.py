@@ -98,3 +98,41 @@ def test_all_three_together(view):
     assert np.array_equal(g["zbuf"].reshape(-1), o["zbuf"].reshape(-1))
     assert np.array_equal(g["motion"], o["motion"])
     assert (g["valid"] != o["valid"]).mean() < 1e-4
+
+
+@pytest.mark.parametrize("res", [(1281, 721), (97, 250), (33, 17), (31, 40), (1, 1)])
+@pytest.mark.parametrize("close_radius", [0, 2, 7])
+def test_ragged_sizes(res, close_radius):
+    """Widths that are not multiples of 32 or of 4 (the closing's bit-packed rows end in a partial
+    word; the motion and contour kernels take their per-pixel paths), tiles cut by the image
+    border, and the largest closing radii against the frame: motion mask and z-buffer bit-exact,
+    the contour step exact on the GPU's own filtered map."""
+    import torch
+    import oracle
+    W, H = res
+    rng = np.random.default_rng(W * 13 + H + close_radius)
+    sc = scene.make_scene(6, "room")
+    f = 1400.0 * max(W, 8) / 1920.0
+    cam = scene.make_camera(W, H, f, f, W / 2.0, H / 2.0, (0.0, 0.0, 1.5))
+    rgb, gt = scene.render_rgb(sc, cam, rng)
+    scans = []
+    for s in range(3):
+        pose = scene.make_lidar_pose(cam, (0.1 * s, 0.05, 0.02), 2.0 * s)
+        scans.append(scene.Scan(scene.lidar_sweep(sc, pose, 48, 700 + s, rng), pose))
+    v = scene.View(cam, rgb, scans, gt)
+    prev = rgb.copy()
+    prev[H // 3:H // 3 + max(1, H // 4), W // 3:W // 3 + max(1, W // 4)] = rng.integers(0, 256, 3, dtype=np.uint8)
+    prev[0, 0] = 255 - prev[0, 0]   # a changed pixel at the corner (the closing's border)
+    kw = dict(occlusion_radius=3, occlusion_margin=0.2, motion_threshold=30.0, motion_close_radius=close_radius)
+    g = _run(v, torch, prev=prev, **kw)
+    o = oracle.densify_view(v, num_stages=2, stages=STAGES, prev_rgb=prev, **kw)
+    assert np.array_equal(g["motion"], o["motion"])
+    assert np.array_equal(g["zbuf"].reshape(-1), o["zbuf"].reshape(-1))
+    assert np.array_equal(g["valid"], o["valid"])
+    m = o["valid"].astype(bool)
+    np.testing.assert_allclose(g["depth"][m], o["depth"][m], rtol=1e-4)
+    t = 0.05
+    gc = _run(v, torch, prev=prev, contour_threshold=t, **kw)
+    d, vmask, _ = oracle.contour(g["depth"], g["valid"], t)
+    assert np.array_equal(gc["valid"], vmask)
+    assert np.array_equal(gc["depth"], d)
