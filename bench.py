@@ -207,10 +207,10 @@ def make_config_views(n_qvga=16, seed_qvga=1000, seed_uneven=1003):
 
 
 EXTRA_CONFIGS = {
-    # BASELINE configs 0 / 2: one viewpoint at 320x240, one 32x256 sweep, single-stage 9x9 window
+    # one viewpoint at 320x240, one 32x256 sweep, single-stage 9x9 window (FP32, and FP16 guide and weights)
     "qvga_1scan_single_stage_fp32": dict(views="qvga", stages=QVGA_STAGES, precision=0, batch=32),
     "qvga_1scan_single_stage_fp16": dict(views="qvga", stages=QVGA_STAGES, precision=1, batch=32),
-    # config 3: 12 uneven views in one batched, graph-captured launch sequence, FP16, autotuned
+    # 12 uneven views (4 x 1080p, 4 x 720p, 4 x 540p) in one batched, graph-captured launch sequence, FP16, autotuned
     "uneven_12view_two_stage_fp16": dict(views="uneven", stages=STAGES, precision=1, batch=12),
     # the 1080p three-scan views with the single-stage alternative: one 15x15 window at full resolution
     "1080p_3scan_single_stage_15x15_fp32": dict(views="main", stages=((7, 5.0, 20.0),), precision=0, batch=4),
