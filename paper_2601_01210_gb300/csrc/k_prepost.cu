@@ -240,14 +240,17 @@ struct OccFrame {
 // RHO > 0: the window radius fixed at compile time (the sliding sums unrolled); 0: a.occ_radius.
 template <int RHO>
 __global__ void __launch_bounds__(kThreads) occlusion_kernel(const BatchDev *__restrict__ B, const PrepostArgs a) {
-    constexpr int T = kOccTile, S = T + 2 * (RHO > 0 ? RHO : kMaxOccR);
-    __shared__ float sd[S * S];
-    __shared__ uint8_t sc[S * S];
+    constexpr int T = kOccTile, RMAX = RHO > 0 ? RHO : kMaxOccR;
+    constexpr int S = T + 2 * RMAX;                  // staged rows
+    constexpr int SW = T + 2 * ((RMAX + 3) / 4 * 4);   // staged row stride (columns from x0 - lead)
+    __shared__ float sd[S * SW];
+    __shared__ uint8_t sc[S * SW];
     __shared__ float hs[S * T];
     __shared__ int16_t hc[S * T];
     __shared__ int32_t s_pre[kMaxBatch + 1];
     __shared__ OccFrame s_f[kMaxBatch];
     const int rho = RHO > 0 ? RHO : a.occ_radius, sw = T + 2 * rho;
+    const int lead = (rho + 3) & ~3, off = lead - rho, gpr = (T + 2 * lead) / 4;   // groups of 4 words a row
     const int nf = B->n_frames;
     for (int i = threadIdx.x; i <= nf; i += kThreads) s_pre[i] = B->oc_pre[i];
     for (int i = threadIdx.x; i < nf; i += kThreads) {
@@ -261,21 +264,29 @@ __global__ void __launch_bounds__(kThreads) occlusion_kernel(const BatchDev *__r
         const OccFrame &F = s_f[fi];
         const int t = item - s_pre[fi];
         const int x0 = (t % F.tiles_x) * T, y0 = (t / F.tiles_x) * T;
-        stage<uint32_t>(sw * sw, [&](int i) -> uint32_t {
-            const int sy = i / sw, sx = i - sy * sw;
-            const int gx = x0 - rho + sx, gy = y0 - rho + sy;
-            return (gx >= 0 && gx < F.W && gy >= 0 && gy < F.H) ? F.src[(int64_t)gy * F.zpitch + gx] : kEmpty;
-        }, [&](int i, uint32_t z) {
-            sd[i] = z != kEmpty ? __uint_as_float(z) : 0.0f;
-            sc[i] = z != kEmpty;
+        // rows y0 - rho .. y0 + 31 + rho, columns x0 - lead .. x0 + 31 + lead (lead = rho rounded up
+        // to 4) in aligned groups of 4 words: one 16-byte load a group; a group lies either inside
+        // the row's zpitch words (the cells past W hold the empty pattern) or outside it
+        stage<uint4>(sw * gpr, [&](int i) -> uint4 {
+            const int sy = i / gpr, gx = x0 - lead + 4 * (i - sy * gpr), gy = y0 - rho + sy;
+            if (gy < 0 || gy >= F.H || gx < 0 || gx >= F.zpitch) return make_uint4(kEmpty, kEmpty, kEmpty, kEmpty);
+            return *reinterpret_cast<const uint4 *>(F.src + (int64_t)gy * F.zpitch + gx);
+        }, [&](int i, uint4 z) {
+            const int sy = i / gpr, c = 4 * (i - sy * gpr);
+            const uint32_t w[4] = {z.x, z.y, z.z, z.w};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                sd[sy * SW + c + k] = w[k] != kEmpty ? __uint_as_float(w[k]) : 0.0f;
+                sc[sy * SW + c + k] = w[k] != kEmpty;
+            }
         });
         __syncthreads();
         // row sums: a thread takes 4 consecutive columns of a staged row, its 4 window sums (over dx
         // in order) fed from a window of 4 staged values that slides along the row
         for (int i = threadIdx.x; i < sw * (T / 4); i += kThreads) {
             const int r = i / (T / 4), x = 4 * (i - r * (T / 4));
-            const float *d = sd + r * sw + x;
-            const uint8_t *cc = sc + r * sw + x;
+            const float *d = sd + r * SW + off + x;
+            const uint8_t *cc = sc + r * SW + off + x;
             float v0 = d[0], v1 = d[1], v2 = d[2], v3 = d[3];
             int c0 = cc[0], c1 = cc[1], c2 = cc[2], c3 = cc[3];
             float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f, s3 = 0.0f;   // adding 0 for an empty cell changes nothing
@@ -324,7 +335,7 @@ __global__ void __launch_bounds__(kThreads) occlusion_kernel(const BatchDev *__r
             for (int k = 0; k < 4; ++k) {
                 const int gx = x0 + x, gy = y0 + y + k;
                 if (gx >= F.W || gy >= F.H) continue;
-                const int o = (y + k + rho) * sw + x + rho;   // the pixel's own staged cell
+                const int o = (y + k + rho) * SW + off + x + rho;   // the pixel's own staged cell
                 uint32_t out = kEmpty;
                 if (sc[o]) {
                     const float z = sd[o];
