@@ -980,6 +980,9 @@ def main():
     if world > 1:
         import torch
         import torch.distributed as dist
+        # a multi-rank run times the headline workload and its end-to-end form only: the serving loop, the
+        # other workloads and the FP16 form are single-GPU measurements that would hold every rank's GPU
+        a.no_serve = a.no_configs = a.no_fp16 = True
         # views are generated before the first CUDA call (spawn pool), then the group starts
         dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     ours_arm(a, rank, world, local_rank)
