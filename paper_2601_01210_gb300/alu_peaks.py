@@ -1,11 +1,11 @@
 """Measured instruction rates of the filter kernels' arithmetic on the current GPU.
 
 Runs the microbenchmark in ``peaks/alu_peaks.cu`` (libalupeaks.so): FP32 FMA,
-two-lane FP32 FMA, ex2.approx.ftz.f32, ex2.approx.f16x2 and the mixed loop of
-the paired expanded filter form (3 two-lane FMA + 2 ex2 + 2 two-lane FMA per
-pair of taps). Each rate is given per second and per SM per clock (the SM
-clock sampled by nvidia-smi while the kernels run), and the tap peaks of the
-filter forms follow from them:
+two-lane FP32 FMA, ex2.approx.ftz.f32, ex2.approx.f16x2, dp4a and the mixed
+loop of the paired expanded filter form (2 dp4a + 1 two-lane FMA + 2 ex2 + 2
+two-lane FMA per pair of taps). Each rate is given per second and per SM per
+clock (the SM clock sampled by nvidia-smi while the kernels run), and the tap
+peaks of the filter forms follow from them:
 
   taps/s = SMs x clock x min(issue bound, FMA-pipe bound, ex2 bound)
 
@@ -14,6 +14,12 @@ filter forms follow from them:
   * FMA-pipe bound: the measured FMA (or two-lane FMA) rate divided by the
     form's FMA instructions per tap;
   * ex2 bound: the measured ex2 rate divided by the form's ex2 per tap.
+
+dp4a issues to the same pipe as the two-lane FMA: the paired form's FMA-pipe
+bound adds the two instructions' times per tap (two-lane FMA per tap / its
+rate + dp4a per tap / its rate). On the GB300 the mixed loop of the paired
+form runs at 96 % of that bound and at 71 % of the bound the two pipes would
+give if they were apart.
 
 Usage: ``python -m paper_2601_01210_gb300.alu_peaks [--out FILE]``.
 """
@@ -31,13 +37,15 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libalupeaks.so")
 
 OPS = {"ffma": 0, "ffma2": 1, "ex2_f32": 2, "ex2_f16x2": 3, "tap_paired": 4, "red_shared_f32": 5, "hfma2": 6,
-       "tap_fp16": 7}
+       "tap_fp16": 7, "dp4a": 8}
 ISSUE_PER_SM_CLK = 128.0   # 4 schedulers x one 32-lane warp instruction per clock
-# per tap of each filter form: (FP32 FMA-pipe thread-instructions, of which two-lane, ex2 thread-instructions)
+# per tap of each filter form: FP32 FMA-pipe thread-instructions (fma), two-lane FMA (fma2), ex2 and
+# dp4a thread-instructions
 FORMS = {
     "fp32": {"fma": 9.0, "fma2": 0.0, "ex2": 1.0},                 # difference form: 3 sub, 3 fma, 1 fma, 2 fma
     "fp32_expanded": {"fma": 5.0, "fma2": 0.0, "ex2": 1.0},        # 3 fma exponent, 2 fma sums
-    "fp32_expanded_pairs": {"fma": 0.0, "fma2": 2.5, "ex2": 1.0},  # per tap: 1.5 + 1 two-lane fma
+    # per tap: one dp4a (colour dot product), half a two-lane fma (exponent), one two-lane fma (sums)
+    "fp32_expanded_pairs": {"fma": 0.0, "fma2": 1.5, "ex2": 1.0, "dp4a": 1.0},
     # sparse (a warp walks the observed positions of its block's footprint; per evaluated pixel and
     # position): row offset, squared distance, 4 fma exponent, 2 sums, half the column terms of the
     # two pixels a lane owns; window test (max, compare); half of the position's loads and loop work
@@ -108,17 +116,21 @@ def tap_peaks(rates_per_sm_clk):
                        "bounds_taps_per_sm_clk": {"measured_tap_loop": round(rates_per_sm_clk["tap_fp16"], 3)},
                        "thread_instructions_per_tap": None}
     for form, k in FORMS.items():
-        instr = k["fma"] + k["fma2"] + k["ex2"] + k.get("lds", 0.0) + k.get("red", 0.0) + k.get("other", 0.0)
+        instr = (k["fma"] + k["fma2"] + k["ex2"] + k.get("dp4a", 0.0) + k.get("lds", 0.0) + k.get("red", 0.0) +
+                 k.get("other", 0.0))
         bounds = {"issue": ISSUE_PER_SM_CLK / instr,
                   "ex2": rates_per_sm_clk["ex2_f32"] / k["ex2"]}
+        if k.get("dp4a") and "dp4a" not in rates_per_sm_clk:
+            continue
         if k.get("red"):
             if "red_shared_f32" not in rates_per_sm_clk:
                 continue
             bounds["smem_atomic"] = rates_per_sm_clk["red_shared_f32"] / k["red"]
         if k["fma"]:
             bounds["fma_pipe"] = rates_per_sm_clk["ffma"] / k["fma"]
-        if k["fma2"]:
-            bounds["fma_pipe"] = rates_per_sm_clk["ffma2"] / k["fma2"]
+        if k["fma2"]:   # with the form's dp4a on the same pipe
+            bounds["fma_pipe"] = 1.0 / (k["fma2"] / rates_per_sm_clk["ffma2"] +
+                                        k.get("dp4a", 0.0) / rates_per_sm_clk.get("dp4a", 1.0))
         binding = min(bounds, key=bounds.get)
         out[form] = {"taps_per_sm_clk": bounds[binding], "binds": binding,
                      "bounds_taps_per_sm_clk": {b: round(v, 3) for b, v in bounds.items()},

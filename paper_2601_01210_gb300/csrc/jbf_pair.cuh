@@ -4,24 +4,34 @@
 // shared memory; the full-resolution stages only (restored first-stage result
 // or z-buffer as depth, RGB bytes as guide).
 //
-// Expanded form (same arithmetic as the scalar one in jbf_tma.cuh): with the
-// centred colours c' = c - 128 (exact in FP32), the colour term of a tap is
+// Expanded form: with the centred colours c' = c - 128 (one signed byte per
+// channel), the colour term of a tap is
 //   -kc |c'_p - c'_q|^2 = 2 kc c'_p . c'_q - kc |c'_p|^2 - kc |c'_q|^2,
 // so the weight of neighbour q at offset (dx - R, dy - R) is
-//   2^(2 kc c'_p . c'_q - kc |c'_p|^2 + ex_sy[dy]) * F_q * ex_sx[dx],
-// F_q = 2^(-kc |c'_q|^2) computed once per staged neighbour (0 when q holds no
-// observation), and the depth enters as G_q = F_q * depth_q. Per tap: three
-// FMAs for the exponent, one ex2, one FMA each into numerator and weight sum.
+//   2^(2 kc c'_p . c'_q - kc |c'_p|^2) * F_q * S(dx) * S(dy),
+// with F_q = 2^(-kc |c'_q|^2) computed once per staged neighbour (0 when q
+// holds no observation), S(d) = 2^(-kp (d - R)^2) the separable spatial
+// factor, and the depth entering as G_q = F_q * depth_q.
+//
+// The dot product c'_p . c'_q is one dp4a of the packed signed bytes, exact in
+// integers. Started from the bit pattern of 1.5 * 2^23, the dp4a result read
+// as a float is exactly 1.5 * 2^23 + c'_p . c'_q, and one FMA gives the
+// exponent: f * 2kc + C_p, C_p = -kc |c'_p|^2 - 2kc * 1.5 * 2^23 rounded once.
+// The FMA cancels the large terms exactly; the rounding of C_p moves every
+// exponent of pixel p by the same amount, which cancels in Eq. (1)'s quotient.
+// The row factor S(dy) scales each staged row's partial sums. A tap costs one
+// dp4a, one FMA, one ex2 and one FMA each into the numerator and weight sum.
 //
 // Column pairs: a thread owns output columns x0 + lane and x0 + 32 + lane of a
 // 64-column tile, rows rbase .. rbase + KP - 1. Staged slot s of a row holds
 // the records of staged columns s and s + 32 side by side, so the neighbour at
-// tap dx of both pixels sits in one slot (lane + dx) and every arithmetic step
-// above runs once for the two pixels as a two-lane FP32 instruction
+// tap dx of both pixels sits in one slot (lane + dx) and every floating-point
+// step runs once for the two pixels as a two-lane FP32 instruction
 // (__ffma2_rn / __fmul2_rn / __fadd2_rn, each lane rounded as its scalar
-// counterpart): slot records are
-//   sc = {r', r'', g', g''},  sb = {b', b'', F', F''},  sg = {G', G''}
-// (' for the first staged column of the slot, '' for the second).
+// counterpart). A slot's records (24 bytes):
+//   sc = (colour word of column s, colour word of column s + 32), each the
+//        packed signed bytes (r', g', b', 0);
+//   fg = (F of column s, F of column s + 32, G of column s, G of column s + 32).
 //
 // A tile takes two steps: pair_convert writes the slot records and
 // observation bitmaps from the raw boxes (every thread of the CTA), then
@@ -38,12 +48,21 @@ namespace dz {
 
 __device__ __forceinline__ float2 f2(float lo, float hi) { return make_float2(lo, hi); }
 
+// Bit pattern of 1.5 * 2^23: a float whose last mantissa bit weighs 1, with 2^22 of room on either side.
+constexpr int kDotBias = 0x4B400000;
+constexpr float kDotBiasF = 12582912.0f;
+
+// Colour bytes r, g, b (0..255) as the packed signed bytes of c - 128 (byte b xor 0x80 = b - 128).
+__device__ __forceinline__ uint32_t pack_centred(uint32_t r, uint32_t g, uint32_t b) {
+    return (r | (g << 8) | (b << 16)) ^ 0x00808080u;
+}
+
 // One set of slot records and observation bitmaps in shared memory (bit i of
 // obs0 / obs1: the first / second staged column of slot i holds an observation;
 // each bitmap ends in a zero guard word).
 struct PairRecords {
-    float4 *sc, *sb;
-    float2 *sg;
+    float4 *fg;
+    uint2 *sc;
     uint32_t *obs0, *obs1;
 };
 
@@ -80,11 +99,6 @@ __device__ __forceinline__ void pair_convert(const StageArgs &a, int x0, int y0,
     auto rgb_at = [&](int sy, int sx) { return rgbraw + sy * G::RGB_BX + 3 * sx - 3 * R + G::RGB_LEAD; };
     // a tile whose halo lies inside the image needs no bounds checks on its staged positions
     const bool interior = x0 >= R && x0 + G::TW + R <= gw && y0 >= R && y0 + G::TH + R <= gh;
-    // bytes b, b' as exact floats minus 128: 2^23 + b has b in its low mantissa bits
-    auto bytes2 = [](uint32_t b, uint32_t b2) {
-        return __fadd2_rn(f2(__uint_as_float(0x4B000000u | b), __uint_as_float(0x4B000000u | b2)),
-                          f2(-8388736.0f, -8388736.0f));
-    };
     const float kc = a.kc;
 #pragma unroll 1
     for (int j0 = 0; j0 < NCONV; j0 += CH) {
@@ -120,14 +134,18 @@ __device__ __forceinline__ void pair_convert(const StageArgs &a, int x0, int y0,
             const int i = t + (j0 + j) * NCT;
             const bool o0 = (om0 >> j) & 1u, o1 = (om1 >> j) & 1u;
             if (i < SH * SP) {
-                // centred colours (exact); an unobserved record keeps its colour with F = G = 0
-                const float2 r = bytes2(r0[j], r1[j]), g = bytes2(g0[j], g1[j]), b = bytes2(b0[j], b1[j]);
-                const float2 e = __fmul2_rn(f2(-kc, -kc), __ffma2_rn(r, r, __ffma2_rn(g, g, __fmul2_rn(b, b))));
+                // centred colours; |c'|^2 by dp4a (exact integer below 2^16, read as a float from
+                // 2^23 + n); an unobserved record keeps its colour with F = G = 0
+                const uint32_t c0 = pack_centred(r0[j], g0[j], b0[j]), c1 = pack_centred(r1[j], g1[j], b1[j]);
+                const float2 n2 = __fadd2_rn(f2(__int_as_float(__dp4a((int)c0, (int)c0, 0x4B000000)),
+                                                __int_as_float(__dp4a((int)c1, (int)c1, 0x4B000000))),
+                                             f2(-8388608.0f, -8388608.0f));
+                const float2 e = __fmul2_rn(f2(-kc, -kc), n2);
                 const float f0 = o0 ? ex2_approx(e.x) : 0.0f, f1 = o1 ? ex2_approx(e.y) : 0.0f;
                 const float2 fd = __fmul2_rn(f2(f0, f1), f2(d0[j], d1[j]));
-                st.sc[i] = make_float4(r.x, r.y, g.x, g.y);
-                st.sb[i] = make_float4(b.x, b.y, f0, f1);
-                st.sg[i] = f2(o0 ? fd.x : 0.0f, o1 ? fd.y : 0.0f);   // an empty z-buffer cell holds +inf
+                st.sc[i] = make_uint2(c0, c1);
+                // an empty z-buffer cell holds +inf: G = 0 where unobserved
+                st.fg[i] = make_float4(f0, f1, o0 ? fd.x : 0.0f, o1 ? fd.y : 0.0f);
             }
             const uint32_t w0 = __ballot_sync(0xffffffffu, o0), w1 = __ballot_sync(0xffffffffu, o1);
             if (lane == 0) {
@@ -178,45 +196,52 @@ __device__ __forceinline__ void pair_filter(float *out_depth, uint8_t *out_valid
 #pragma unroll
     for (int k = 0; k < KP; ++k) num[k] = den[k] = f2(0.0f, 0.0f);
     if (__any_sync(0xffffffffu, any_val)) {
-        const float kc2 = 2.0f * kc;
-        float2 ar[KP], ag[KP], ab[KP], cp[KP];   // 2 kc c'_p per channel, -kc |c'_p|^2
+        const float kc2 = 2.0f * kc, bias = -kc2 * kDotBiasF;
+        uint2 cq[KP];     // packed centred colours of the thread's two pixels in row k
+        float2 cp[KP];    // C_p of both: -kc |c'_p|^2 + bias (one rounding, the same for every tap of p)
 #pragma unroll
         for (int k = 0; k < KP; ++k) {
-            const int o = (rbase + k + R) * SP + lane + R;
-            const float4 c = st.sc[o], b = st.sb[o];
-            ar[k] = f2(kc2 * c.x, kc2 * c.y);
-            ag[k] = f2(kc2 * c.z, kc2 * c.w);
-            ab[k] = f2(kc2 * b.x, kc2 * b.y);
-            cp[k] = f2(-kc * fmaf(c.x, c.x, fmaf(c.z, c.z, b.x * b.x)), -kc * fmaf(c.y, c.y, fmaf(c.w, c.w, b.y * b.y)));
+            cq[k] = st.sc[(rbase + k + R) * SP + lane + R];
+            cp[k] = f2(fmaf(-kc, (float)__dp4a((int)cq[k].x, (int)cq[k].x, 0), bias),
+                       fmaf(-kc, (float)__dp4a((int)cq[k].y, (int)cq[k].y, 0), bias));
         }
 #pragma unroll
         for (int iy = 0; iy < KP + 2 * R; ++iy) {
             // a staged row no lane's window observes adds exact zeros (F = G = 0): skip it
             if (!((rows_warp >> iy) & 1u)) continue;
-            float2 dd[KP];
-#pragma unroll
-            for (int k = 0; k < KP; ++k) {
-                const int dy = iy - k;
-                dd[k] = (dy >= 0 && dy < T) ? __fadd2_rn(cp[k], f2(a.ex_sy[dy], a.ex_sy[dy])) : f2(0.0f, 0.0f);
-            }
+            float2 rn[KP], rd[KP];   // the row's partial sums of pixel k, before its factor S(dy)
 #pragma unroll
             for (int dx = 0; dx < T; ++dx) {
                 const int o = (rbase + iy) * SP + lane + dx;
-                const float4 qc = st.sc[o], qb = st.sb[o];
-                const float2 qg = st.sg[o];
+                const uint2 qc = st.sc[o];
+                const float4 q = st.fg[o];
                 const float2 ex = f2(a.ex_sx[dx], a.ex_sx[dx]);
-                const float2 fx = __fmul2_rn(f2(qb.z, qb.w), ex), gx = __fmul2_rn(qg, ex);
+                const float2 fx = __fmul2_rn(f2(q.x, q.y), ex), gx = __fmul2_rn(f2(q.z, q.w), ex);
 #pragma unroll
                 for (int k = 0; k < KP; ++k) {
                     const int dy = iy - k;
                     if (dy >= 0 && dy < T) {
-                        const float2 e = __ffma2_rn(
-                            ar[k], f2(qc.x, qc.y),
-                            __ffma2_rn(ag[k], f2(qc.z, qc.w), __ffma2_rn(ab[k], f2(qb.x, qb.y), dd[k])));
+                        const float2 f = f2(__int_as_float(__dp4a((int)cq[k].x, (int)qc.x, kDotBias)),
+                                            __int_as_float(__dp4a((int)cq[k].y, (int)qc.y, kDotBias)));
+                        const float2 e = __ffma2_rn(f, f2(kc2, kc2), cp[k]);
                         const float2 w = f2(ex2_approx(e.x), ex2_approx(e.y));
-                        num[k] = __ffma2_rn(w, gx, num[k]);
-                        den[k] = __ffma2_rn(w, fx, den[k]);
+                        if (dx == 0) {
+                            rn[k] = __fmul2_rn(w, gx);
+                            rd[k] = __fmul2_rn(w, fx);
+                        } else {
+                            rn[k] = __ffma2_rn(w, gx, rn[k]);
+                            rd[k] = __ffma2_rn(w, fx, rd[k]);
+                        }
                     }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+                const int dy = iy - k;
+                if (dy >= 0 && dy < T) {
+                    const float2 ey = f2(a.ex_sx[dy], a.ex_sx[dy]);   // S(dy): the factor is symmetric
+                    num[k] = __ffma2_rn(ey, rn[k], num[k]);
+                    den[k] = __ffma2_rn(ey, rd[k], den[k]);
                 }
             }
         }
@@ -309,9 +334,8 @@ __device__ __forceinline__ bool pair_tile(float *out_depth, uint8_t *out_valid, 
                                           AfterConversion &&after_conversion) {
     using G = TmaGeom<SRC, R, KP, NW, FORM_EXP_PAIRS>;
     PairRecords st;
-    st.sc = reinterpret_cast<float4 *>(smem + G::OFF_STAGED);
-    st.sb = st.sc + G::SH * G::SP;
-    st.sg = reinterpret_cast<float2 *>(smem + G::OFF_G);
+    st.fg = reinterpret_cast<float4 *>(smem + G::OFF_STAGED);
+    st.sc = reinterpret_cast<uint2 *>(smem + G::OFF_G);
     st.obs0 = reinterpret_cast<uint32_t *>(smem + G::OFF_OBS);
     st.obs1 = st.obs0 + G::OBS_ONE / 4;
     if (!bad) pair_convert<SRC, R, G, G::NT>(a, x0, y0, gw, gh, rgbraw, rawb, st, threadIdx.x);

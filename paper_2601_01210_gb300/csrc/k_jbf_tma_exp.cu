@@ -9,10 +9,10 @@ namespace dz {
 // (source, radius, rows per thread, form, warps per CTA); the first listed
 // variant of a (source, radius) is the default before autotuning
 #define DZ_TMA_EXP_CASES(X)              \
+    X(SRC_UP, 2, 6, FORM_EXP_PAIRS, 8)   \
     X(SRC_UP, 2, 4, FORM_EXP_PAIRS, 8)   \
-    X(SRC_UP, 2, 2, FORM_EXP_PAIRS, 8)   \
+    X(SRC_UP, 2, 6, FORM_EXP_PAIRS, 4)   \
     X(SRC_UP, 2, 4, FORM_EXP_PAIRS, 4)   \
-    X(SRC_UP, 2, 4, FORM_EXP_PAIRS, 16)  \
     X(SRC_UP, 2, 8, FORM_EXP_PAIRS, 4)   \
     X(SRC_UP, 2, 8, FORM_EXP, 16)        \
     X(SRC_UP, 2, 8, FORM_EXP, 8)         \

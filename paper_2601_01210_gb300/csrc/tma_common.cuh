@@ -117,12 +117,13 @@ struct TmaGeom {
                                                       : RGB_BX * RGB_BY + Z_BX * Z_BY * 4;
     // sparse form: staged rows per warp in the record pass (warp w scans rows w, w + NW, ...)
     static constexpr int RPW = (SH + NW - 1) / NW;
-    // staged records: float4 per position (two float4 per slot in the paired form, two per
-    // position in the sparse form)
+    // staged records: float4 per position (per slot in the paired form: F and G of both columns;
+    // two per position in the sparse form)
     static constexpr int STAGED = SPARSE ? 2 * SH * SW * 16
-                                  : PAIRS ? 2 * SH * SP * 16
+                                  : PAIRS ? SH * SP * 16
                                   : SRC == SRC_COARSE && !EXP ? 0 : SH * SW * 16;
-    // expanded forms: F_q times depth (float per position, float2 per slot)
+    // scalar expanded form: F_q times depth (float per position); paired form: both columns'
+    // packed colour words (uint2 per slot)
     static constexpr int STAGED_G = PAIRS ? SH * SP * 8 : EXP ? ceil_to(SH * SW * 4, 16) : 0;
     // sparse form: one observation mask (uint64) per staged row
     static constexpr int ROWS = SPARSE ? ceil_to(SH * 8, 16) : 0;

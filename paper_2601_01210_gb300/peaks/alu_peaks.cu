@@ -1,13 +1,15 @@
 // Instruction-rate microbenchmark of the arithmetic the filter kernels issue:
 // FP32 FMA (fma.rn.f32), two-lane FP32 FMA (fma.rn.f32x2), the exponent
-// (ex2.approx.ftz.f32, ex2.approx.f16x2) and the mixed loop of one filter tap
-// pair in the paired expanded form (three two-lane FMA for the exponents of two
-// output pixels, one ex2 per pixel, two two-lane FMA into numerator and weight
-// sum: 3.5 instructions a tap), FP32 adds into shared memory (the scatter
-// form's accumulation), half2 FMA (fma.rn.f16x2) and the FP16 form's tap pair
-// (half2 colour differences, squared distance and exponent for two output
-// rows, one ex2.approx.f16x2, the weights widened to FP32 and accumulated). Its measured rates are the peaks the filter
-// rooflines divide by.
+// (ex2.approx.ftz.f32, ex2.approx.f16x2), the four-byte integer dot product
+// (dp4a.s32.s32) and the mixed loop of one filter tap pair in the paired
+// expanded form (per output pixel one dp4a of the packed colours, then one
+// two-lane FMA for the two pixels' exponents, one ex2 per pixel and two
+// two-lane FMA into numerator and weight sum: 3.5 instructions a tap), FP32
+// adds into shared memory (the scatter form's accumulation), half2 FMA
+// (fma.rn.f16x2) and the FP16 form's tap pair (half2 colour differences,
+// squared distance and exponent for two output rows, one ex2.approx.f16x2, the
+// weights widened to FP32 and accumulated). Its measured rates are the peaks
+// the filter rooflines divide by.
 //
 // Every thread runs kChains independent dependency chains, unrolled, so that
 // issue (not latency) limits the rate once enough warps are resident; each
@@ -27,7 +29,7 @@ constexpr int kUnroll = 16;
 
 enum Op {
     OP_FFMA = 0, OP_FFMA2 = 1, OP_EX2 = 2, OP_EX2_H2 = 3, OP_TAP_PAIRED = 4, OP_RED_SHARED = 5, OP_HFMA2 = 6,
-    OP_TAP_FP16 = 7, OP_COUNT = 8
+    OP_TAP_FP16 = 7, OP_DP4A = 8, OP_COUNT = 9
 };
 
 __device__ __forceinline__ float ex2f(float x) {
@@ -96,6 +98,19 @@ __global__ void __launch_bounds__(kThreads, 6) rate_kernel(float *__restrict__ o
         }
 #pragma unroll
         for (int c = 0; c < kChains; ++c) sink += __uint_as_float(a[c] & 0x3FFFFFFFu);
+    } else if (OP == OP_DP4A) {
+        int a[kChains];
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) a[c] = (int)(0x01020304u * (uint32_t)(c + 1)) ^ tid;
+        const int m = (int)(0x7F01FF80u ^ (uint32_t)(s * 3.0f));
+        for (int i = 0; i < iters; ++i) {
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+                for (int c = 0; c < kChains; ++c) a[c] = __dp4a(a[c], m, a[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < kChains; ++c) sink += (float)(a[c] & 0xFF);
     } else if (OP == OP_HFMA2) {
         __half2 a[kChains];
 #pragma unroll
@@ -160,29 +175,32 @@ __global__ void __launch_bounds__(kThreads, 6) rate_kernel(float *__restrict__ o
         for (int c = 0; c < kChains; ++c) sink += acc[c][threadIdx.x];
     } else {   // OP_TAP_PAIRED: kChains / 2 independent tap pairs per thread
         constexpr int P = kChains / 2;
-        float2 e[P], num[P], den[P];
+        int q0[P], q1[P];
+        float2 num[P], den[P];
 #pragma unroll
         for (int c = 0; c < P; ++c) {
-            e[c] = make_float2(-1.0f - 0.1f * c, -2.0f + 1e-7f * tid);
+            q0[c] = 0x4B400000 + c + (tid & 15);
+            q1[c] = 0x4B400000 - c;
             num[c] = den[c] = make_float2(0.0f, 0.0f);
         }
-        const float2 kr = make_float2(0.5f, 0.4f), kg = make_float2(0.3f, 0.2f), kb = make_float2(0.1f, 0.15f);
-        const float2 br = make_float2(-0.2f * s, -0.1f), g = make_float2(1.5f, 2.5f), f = make_float2(0.75f, 0.5f);
+        const int cp0 = (int)(0x00102030u ^ (uint32_t)s), cp1 = 0x00F0E0D0;
+        const float2 kc2 = make_float2(1e-3f, 1e-3f), bias = make_float2(-12582.9f * s, -12582.8f);
+        const float2 g = make_float2(1.5f, 2.5f), f = make_float2(0.75f, 0.5f);
         for (int i = 0; i < iters; ++i) {
 #pragma unroll
             for (int u = 0; u < kUnroll; ++u) {
 #pragma unroll
                 for (int c = 0; c < P; ++c) {
-                    // exponent of two output pixels at one tap: three two-lane FMA
-                    float2 x = __ffma2_rn(e[c], kr, br);
-                    x = __ffma2_rn(x, kg, kb);
-                    x = __ffma2_rn(x, kb, kr);
+                    // colour dot products of two output pixels at one tap, read as biased floats
+                    q0[c] = __dp4a(cp0, q0[c], 0x4B400000);
+                    q1[c] = __dp4a(cp1, q1[c], 0x4B400000);
+                    // both exponents: one two-lane FMA
+                    const float2 x = __ffma2_rn(make_float2(__int_as_float(q0[c]), __int_as_float(q1[c])), kc2, bias);
                     // one ex2 per pixel
                     const float2 w = make_float2(ex2f(x.x), ex2f(x.y));
                     // numerator and weight sum: two two-lane FMA
                     num[c] = __ffma2_rn(w, g, num[c]);
                     den[c] = __ffma2_rn(w, f, den[c]);
-                    e[c] = x;
                 }
             }
         }
@@ -201,6 +219,7 @@ double units_per_iteration(int op) {
     case OP_EX2:
     case OP_EX2_H2:
     case OP_RED_SHARED:
+    case OP_DP4A:
     case OP_HFMA2: return (double)kUnroll * kChains;
     case OP_TAP_FP16: return (double)kUnroll * (kChains / 2) * 2;   // two taps per pair
     case OP_TAP_PAIRED: return (double)kUnroll * (kChains / 2) * 2;   // two taps per pair
@@ -218,6 +237,7 @@ cudaError_t launch(int op, int blocks, int iters, float *out, cudaStream_t st) {
     case OP_RED_SHARED: rate_kernel<OP_RED_SHARED><<<blocks, kThreads, 0, st>>>(out, iters, 1.0f); break;
     case OP_HFMA2: rate_kernel<OP_HFMA2><<<blocks, kThreads, 0, st>>>(out, iters, 1.0f); break;
     case OP_TAP_FP16: rate_kernel<OP_TAP_FP16><<<blocks, kThreads, 0, st>>>(out, iters, 1.0f); break;
+    case OP_DP4A: rate_kernel<OP_DP4A><<<blocks, kThreads, 0, st>>>(out, iters, 1.0f); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -105,15 +105,23 @@ def test_tap_peaks_take_the_binding_bound():
     """The filter forms' tap peaks are the least of the issue, FMA-pipe and ex2 bounds of the
     measured per-SM-per-clock rates."""
     from paper_2601_01210_gb300 import alu_peaks
-    rates = {"ffma": 128.0, "ffma2": 64.0, "ex2_f32": 32.0, "ex2_f16x2": 32.0, "tap_paired": 20.0}
+    rates = {"ffma": 128.0, "ffma2": 64.0, "ex2_f32": 32.0, "ex2_f16x2": 32.0, "tap_paired": 20.0, "dp4a": 64.0}
     p = alu_peaks.tap_peaks(rates)
-    # paired: issue 128 / 3.5 = 36.6, two-lane FMA 64 / 2.5 = 25.6, ex2 32 / 1 = 32
+    # paired: issue 128 / 3.5 = 36.6; FMA pipe shared by 1.5 two-lane FMA and 1 dp4a a tap:
+    # 1 / (1.5 / 64 + 1 / 64) = 25.6; ex2 32 / 1 = 32
     assert p["fp32_expanded_pairs"]["binds"] == "fma_pipe"
     assert abs(p["fp32_expanded_pairs"]["taps_per_sm_clk"] - 25.6) < 1e-9
+    assert p["fp32_expanded_pairs"]["thread_instructions_per_tap"] == 3.5
     # expanded: issue 128 / 6 = 21.3, FMA 128 / 5 = 25.6, ex2 32
     assert p["fp32_expanded"]["binds"] == "issue"
+    rates["dp4a"] = 1e9
+    assert abs(alu_peaks.tap_peaks(rates)["fp32_expanded_pairs"]["bounds_taps_per_sm_clk"]["fma_pipe"] -
+               64.0 / 1.5) < 1e-3
     rates["ex2_f32"] = 16.0
     assert alu_peaks.tap_peaks(rates)["fp32_expanded_pairs"]["binds"] == "ex2"
+    # without a measured dp4a rate the paired form has no peak
+    del rates["dp4a"]
+    assert "fp32_expanded_pairs" not in alu_peaks.tap_peaks(rates)
 
 
 def test_alu_microbenchmark_library_builds():

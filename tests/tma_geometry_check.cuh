@@ -51,6 +51,8 @@ int check(const char *name) {
     if (G::OFF_STAGED % 16 || G::OFF_G % 16 || G::OFF_OBS % 4 || G::OFF_BAR % 8) rep.fail("layout alignment", G::OFF_STAGED, G::OFF_G, G::OFF_OBS);
     if (G::SMEM > 232448) rep.fail("shared memory", G::SMEM, 232448, 0);
     if (G::NCONV * G::NT < G::SH * G::SP) rep.fail("conversion coverage", G::NCONV, G::NT, G::SH * G::SP);
+    if (PAIRS && (G::STAGED < G::SH * G::SP * 16 || G::STAGED_G < G::SH * G::SP * 8))
+        rep.fail("paired records", G::STAGED, G::STAGED_G, G::SH * G::SP);
     if (G::SPARSE) {
         constexpr int FW = 8 + 2 * R;
         if (G::TW != 32 || G::TH % 8 || G::SW > 64) rep.fail("sparse tile / row mask", G::TW, G::TH, G::SW);
