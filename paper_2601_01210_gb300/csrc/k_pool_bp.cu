@@ -2,6 +2,7 @@
 // back-projection of the dense depth to coloured points with a deterministic
 // row-major compaction (Sec. 2: coloured point clouds in a common frame).
 #include "desc.cuh"
+#include "tma_common.cuh"
 
 namespace dz {
 
@@ -33,6 +34,7 @@ struct PoolFrame {
     int64_t rgb_pitch, zpitch, cpitch;
     int32_t W, H, Wc, Hc, segs;
     int32_t zrestore;
+    int32_t bulk_ok;   // z-buffer and colour rows start on 16-byte boundaries (bulk-copy path)
 };
 
 __device__ __forceinline__ bool pool_words_ok(const PoolFrame &F) {
@@ -110,13 +112,79 @@ __device__ __forceinline__ void pool_one(const PoolFrame &F, int I, int J, int f
     }
 }
 
+// Pooled pixel (I, J), f = 3, from a work item's rows staged in shared memory: zs holds the three
+// rows' z-buffer words and cs their colour bytes (row strides kPoolSegPx words and 3 kPoolSegPx
+// bytes), both starting at full-resolution column 3 (I - i); i is the pixel's index in the item.
+// The same sums in the same order as pool_one.
+constexpr int kPoolSegPx = 3 * kPoolPerChunk;                      // full-resolution columns of an item
+constexpr int kPoolZBytes = 3 * kPoolSegPx * 4;                    // three rows of z-buffer words
+constexpr int kPoolCBytes = 3 * kPoolSegPx * 3 + 16;               // three rows of colour bytes, read 2 past
+constexpr int kPoolBuf = kPoolZBytes + kPoolCBytes;               // one buffer (a multiple of 16 bytes)
+static_assert(kPoolZBytes % 16 == 0 && kPoolBuf % 16 == 0 && (3 * kPoolSegPx) % 16 == 0, "bulk copy alignment");
+
+__device__ __forceinline__ void pool_staged(const PoolFrame &F, int I, int J, int i, const uint32_t *zs,
+                                            const uint8_t *cs, float &cnt_out) {
+    const int x0 = I * 3, y0 = J * 3;
+    const int o = (9 * i) & 3;          // first colour byte inside its word (9 I and 9 i agree mod 4)
+    const int wb = 9 * i - o;
+    uint32_t z[3][3], c[3][3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const uint32_t *cw = reinterpret_cast<const uint32_t *>(cs + r * 3 * kPoolSegPx + wb);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            z[r][j] = zs[r * kPoolSegPx + 3 * i + j];
+            c[r][j] = cw[j];
+        }
+    }
+    float s = 0.0f, cnt = 0.0f;
+    uint32_t rs = 0u, gs = 0u, bs = 0u;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (z[r][j] != kEmpty) {
+                s = __fadd_rn(s, __uint_as_float(z[r][j]));
+                cnt += 1.0f;
+                if (F.zrestore) F.zbuf[(int64_t)(y0 + r) * F.zpitch + x0 + j] = kEmpty;   // the clean pool's invariant
+            }
+        }
+        const uint32_t a0 = __funnelshift_r(c[r][0], c[r][1], 8 * o);
+        const uint32_t a1 = __funnelshift_r(c[r][1], c[r][2], 8 * o);
+        const uint32_t a2 = c[r][2] >> (8 * o);
+        rs = __dp4a(__byte_perm(a0, a1, 0x0630), 0x00010101u, rs);   // c0 + c3 + c6
+        gs = __dp4a(__byte_perm(a0, a1, 0x0741), 0x00010101u, gs);   // c1 + c4 + c7
+        bs = __dp4a(__byte_perm(a0, a1, 0x0052), 0x00000101u, bs) + (a2 & 0xFFu);   // c2 + c5 + c8
+    }
+    pool_store(F, I, J, (float)rs, (float)gs, (float)bs, cnt, s, 1.0f / 9.0f);
+    cnt_out = cnt;
+}
+
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
 // With a TMA first-stage filter (tl_th[0] > 0) every warp also flags the first-stage tiles that
 // its observed pooled pixels reach (one ballot; a row segment of 32 pooled pixels grown by the
 // radius spans at most two tiles across and two down), so no mark kernel runs before that filter.
+//
+// For f = 3 a work item's three full-resolution rows reach shared memory by 1-D bulk copies
+// (cp.async.bulk, one per row for the z-buffer words and one for the colour bytes), issued by
+// thread 0 one item ahead into the other of two buffers: the next item's copies run while the
+// block pools the current one from shared memory. An item is staged when its rows lie inside the
+// image, its pooled pixels are whole 3 x 3 blocks, its row segments are a multiple of 16 columns
+// and its frame's rows start on 16-byte boundaries; other items take the per-thread loads of
+// pool_one. A wait that gives up (about 2 s) sets bit 0 of the batch status word; the block then
+// waits (bounded) for its own copies in flight and leaves.
 __global__ void __launch_bounds__(kThreads) pool_kernel(const BatchDev *__restrict__ B, int f) {
     __shared__ int32_t s_pre[kMaxBatch + 1];   // pooling chunk prefix, searched per work item
     __shared__ PoolFrame s_f[kMaxBatch];
     __shared__ int32_t s_geo[3];               // the first filter's tile width, height and radius
+    __shared__ __align__(128) uint8_t s_buf[2][kPoolBuf];
+    __shared__ __align__(8) uint64_t s_bar[2];
     const int nf = B->n_frames;
     for (int i = threadIdx.x; i <= nf; i += kThreads) s_pre[i] = B->pool_pre[i];
     for (int i = threadIdx.x; i < nf; i += kThreads) {
@@ -136,30 +204,93 @@ __global__ void __launch_bounds__(kThreads) pool_kernel(const BatchDev *__restri
         P.Hc = F.Hc;
         P.segs = (F.Wc + kPoolPerChunk - 1) / kPoolPerChunk;
         P.zrestore = F.zrestore;
+        P.bulk_ok = ((((uintptr_t)F.zbuf) | ((uintptr_t)F.rgb)) & 15u) == 0 && (F.zpitch & 3) == 0 &&
+                    (F.rgb_pitch & 15) == 0;
     }
     if (threadIdx.x == 0) {
         s_geo[0] = B->tl_tw[0];
         s_geo[1] = B->tl_th[0];
         s_geo[2] = B->tl_r[0];
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        mbar_fence_init();
     }
     __syncthreads();
     const int total = s_pre[nf];
     const int lane = threadIdx.x & 31;
     const int mtw = s_geo[0], mth = s_geo[1], mr = s_geo[2];
     const bool marks = mth > 0;
-    for (int item = blockIdx.x; item < total; item += gridDim.x) {
-        const int fi = find_segment(s_pre, nf, item);
+
+    // item -> frame, coarse row J, first pooled pixel I0, pooled pixels m, and whether it is staged
+    auto locate = [&](int item, int &fi, int &J, int &I0, int &m) -> bool {
+        fi = find_segment(s_pre, nf, item);
         const PoolFrame &F = s_f[fi];
         const int t = item - s_pre[fi];
-        const int J = t / F.segs;
-        const int I = (t - J * F.segs) * kPoolPerChunk + threadIdx.x;
+        J = t / F.segs;
+        I0 = (t - J * F.segs) * kPoolPerChunk;
+        m = min(kPoolPerChunk, F.Wc - I0);
+        const int n = min(kPoolSegPx, F.W - 3 * I0);   // full-resolution columns of the segment
+        return f == 3 && F.bulk_ok && 3 * J + 3 <= F.H && n == 3 * m && (n & 15) == 0;
+    };
+    // thread 0: the copies of a staged item into buffer b (rows y0 .. y0 + 2, columns 3 I0 .. + n)
+    auto issue = [&](int fi, int J, int I0, int m, int b) {
+        const PoolFrame &F = s_f[fi];
+        const int n = 3 * m, x0 = 3 * I0;
+        uint32_t *zs = reinterpret_cast<uint32_t *>(s_buf[b]);
+        uint8_t *cs = s_buf[b] + kPoolZBytes;
+        mbar_expect_tx(&s_bar[b], (uint32_t)(3 * 7 * n));
+        for (int r = 0; r < 3; ++r) {
+            const int64_t y = 3 * J + r;
+            bulk_copy(zs + r * kPoolSegPx, F.zbuf + y * F.zpitch + x0, (uint32_t)(4 * n), &s_bar[b]);
+            bulk_copy(cs + r * 3 * kPoolSegPx, F.rgb + y * F.rgb_pitch + 3 * (int64_t)x0, (uint32_t)(3 * n), &s_bar[b]);
+        }
+    };
+    uint32_t phase = 0u, inflight = 0u;   // per buffer: wait parity; copies issued and not yet waited for
+    int fi, J, I0, m;
+    if (threadIdx.x == 0 && (int)blockIdx.x < total && locate(blockIdx.x, fi, J, I0, m)) {
+        issue(fi, J, I0, m, 0);
+        inflight |= 1u;
+    }
+    int b = 0;
+    for (int item = blockIdx.x; item < total; item += gridDim.x, b ^= 1) {
+        const int next = item + gridDim.x;
+        if (threadIdx.x == 0 && next < total) {   // buffer b ^ 1 was freed by the previous item's barrier
+            int nfi, nJ, nI0, nm;
+            if (locate(next, nfi, nJ, nI0, nm)) {
+                issue(nfi, nJ, nI0, nm, b ^ 1);
+                inflight |= 1u << (b ^ 1);
+            }
+        }
+        const bool staged = locate(item, fi, J, I0, m);
+        const PoolFrame &F = s_f[fi];
+        const int I = I0 + threadIdx.x;
         float cnt = 0.0f;
-        if (I < F.Wc) pool_one(F, I, J, f, cnt);
+        bool ok = true;
+        if (staged) {
+            ok = mbar_wait_bounded(&s_bar[b], (phase >> b) & 1u);
+            if (ok) {
+                phase ^= 1u << b;
+                inflight &= ~(1u << b);
+                if ((int)threadIdx.x < m)
+                    pool_staged(F, I, J, threadIdx.x, reinterpret_cast<const uint32_t *>(s_buf[b]),
+                                s_buf[b] + kPoolZBytes, cnt);
+            }
+        } else if (I < F.Wc) {
+            pool_one(F, I, J, f, cnt);
+        }
         if (marks) {
-            const uint32_t m = __ballot_sync(0xffffffffu, cnt > 0.0f);
-            const int I0 = I - lane;
-            if (m)
-                mark_reach(F.tflags, mtw, mth, mr, 1, F.Wc, F.Hc, I0 + __ffs(m) - 1, I0 + 31 - __clz(m), J, J, lane);
+            const uint32_t mk = __ballot_sync(0xffffffffu, cnt > 0.0f);
+            const int Ib = I - lane;
+            if (mk)
+                mark_reach(F.tflags, mtw, mth, mr, 1, F.Wc, F.Hc, Ib + __ffs(mk) - 1, Ib + 31 - __clz(mk), J, J, lane);
+        }
+        if (__syncthreads_or(!ok)) {   // buffer b is free again once every thread is past this barrier
+            if (threadIdx.x == 0) {
+                atomicOr(B->status, 1);
+                for (int bb = 0; bb < 2; ++bb)
+                    if ((inflight >> bb) & 1u) mbar_wait_bounded(&s_bar[bb], (phase >> bb) & 1u);
+            }
+            return;
         }
     }
 }
