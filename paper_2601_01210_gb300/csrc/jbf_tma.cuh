@@ -72,11 +72,17 @@ __device__ __forceinline__ __half2 h2exp2_approx(__half2 x) {
     return h2bits(y);
 }
 
-// Resident CTAs per SM the compiler is asked to fit (registers): 16 warps per SM, 32 for the
-// paired form at two rows per thread, whose state fits 64 registers, and 8 for the paired form
+// Resident CTAs per SM the compiler is asked to fit (registers): 16 warps per SM; 32 for the
+// paired form at two rows per thread, whose state fits 64 registers; 24 for the scalar expanded
+// form at two rows per thread, whose state fits 80 (the pooled first stage's 32 x 16 tiles: three
+// CTAs of 8 warps ran 70 us against 75 us at two CTAs on 8 1080p frames); 8 for the paired form
 // at eight rows per thread, whose state needs more than 128.
 constexpr int tma_min_ctas(int form, int kp, int nw) {
-    return (form == FORM_EXP_PAIRS && kp == 2 ? 32 : form == FORM_EXP_PAIRS && kp == 8 ? 8 : 16) / nw;
+    return (form == FORM_EXP_PAIRS && kp == 2   ? 32
+            : form == FORM_EXP && kp == 2       ? 24
+            : form == FORM_EXP_PAIRS && kp == 8 ? 8
+                                                : 16) /
+           nw;
 }
 
 // FP16 form: bound on the relative error of a weight (2^(e) with e = -kc |dc|^2 + spatial term

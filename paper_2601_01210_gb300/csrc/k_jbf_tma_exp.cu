@@ -19,8 +19,8 @@ namespace dz {
     X(SRC_UP, 2, 4, FORM_EXP, 8)         \
     X(SRC_UP, 1, 8, FORM_EXP, 8)         \
     X(SRC_UP, 3, 4, FORM_EXP, 8)         \
-    X(SRC_COARSE, 4, 4, FORM_EXP, 8)     \
     X(SRC_COARSE, 4, 2, FORM_EXP, 8)     \
+    X(SRC_COARSE, 4, 4, FORM_EXP, 8)     \
     X(SRC_COARSE, 4, 2, FORM_EXP, 4)     \
     X(SRC_COARSE, 2, 4, FORM_EXP, 8)     \
     X(SRC_ZBUF, 2, 4, FORM_EXP_PAIRS, 4) \
