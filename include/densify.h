@@ -140,15 +140,16 @@ typedef struct densify_stage {
  *                 FP32 tolerance) where log2(e) / (2 sigma_c^2) * 3 * 128^2 +
  *                 log2(e) / (2 sigma_p^2) * 2 r^2 <= 100, else the difference
  *                 form; at radius 2 of a full-resolution stage also on pairs of
- *                 output columns in two-lane FP32 instructions (same rounding
- *                 as the scalar expanded form). For a single stage on the
- *                 z-buffer the autotuner also weighs Algorithm 1's scatter
- *                 form: every observed neighbour adds its weighted depth and
- *                 weight into the sums of the pixels its window reaches (same
- *                 weights up to a per-pixel factor that cancels; the sums are
- *                 added in a fixed order, so results repeat exactly). 1: the plain kernels everywhere (difference form,
- *                 for comparison). 2: the TMA kernels in the difference form
- *                 only (the same bits as 1).
+ *                 output columns in two-lane FP32 instructions, the colour
+ *                 dot product taken exactly by dp4a on the colour bytes (one
+ *                 rounding of the exponent instead of three, within the same
+ *                 tolerance). For a single stage on the z-buffer the sparse
+ *                 form runs first: a warp walks only the observed positions
+ *                 of its 8 x 8 block's footprint and sums in registers (same
+ *                 weights up to a per-pixel factor that cancels). 1: the plain
+ *                 kernels everywhere (difference form, for comparison). 2: the
+ *                 TMA kernels in the difference form only (the same bits as
+ *                 1).
  *   autotune      1: on the first batch, time every kernel that can run each
  *                 filter stage (TMA-staged at each instantiated tile height,
  *                 and the plain kernel) on that batch and keep the fastest for
