@@ -13,8 +13,9 @@ is not available). Metric: dense 1080p frames per second.
           before every step, CUDA events on the launching stream around the
           step's work, summed over K steps.
   e2e     the same frames through the C ABI with pinned HOST buffers:
-          host->device copies of points and RGB and device->host copies of
-          depth, mask and points inside the timed region (wall clock).
+          host->device copies of points and RGB, and the coloured points and
+          their count written by the GPU into pinned host memory, inside the
+          timed region (wall clock).
 
 --impl reference times the FP64 CPU oracle (the method's plain definition)
 on the host cores, on a bounded sample of the same workload.
@@ -109,7 +110,7 @@ def make_mixed_views(n, seed0):
 
 def serve_measure(views, dev, seconds, autotune=1):
     """Frames/s and p50/p99 latency of the serving loop at the paper's load (16 viewpoints x 30 fps,
-    Poisson-jittered, ``seconds`` long) and at a saturating load, in three modes: single-frame
+    Poisson-jittered, ``seconds`` long) and at two saturating loads, in three modes: single-frame
     launches in FP32, continuous batching in FP32 and continuous batching in FP16 (so that the
     effect of batching and the effect of precision are measured apart). Each context owns its
     streams (two batches in flight overlap on the GPU). The loop is a host Python busy-poll, so
@@ -125,7 +126,10 @@ def serve_measure(views, dev, seconds, autotune=1):
         "batched_fp32": dict(max_batch=16, batches_in_flight=2, precision=0),
         "batched_fp16": dict(max_batch=16, batches_in_flight=2, precision=1),
     }
-    loads = {"paper_rate_30fps": (30.0, seconds), "saturating_1000fps": (1000.0, 2.0)}
+    # the paper's rate, a load above the single-frame form's capacity, and one above every form's
+    # capacity (its frames/s is the form's serving capacity; its latencies are queueing)
+    loads = {"paper_rate_30fps": (30.0, seconds), "saturating_1000fps": (1000.0, 2.0),
+             "capacity_4000fps": (4000.0, 2.0)}
     out = {}
     for mname, extra in modes.items():
         params = dict(num_stages=2, stages=STAGES, max_inflight=32, launch_policy=0, autotune=autotune,

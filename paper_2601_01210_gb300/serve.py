@@ -4,9 +4,11 @@ real time, continuous batching.
 Each viewpoint produces frames at ``fps`` with Poisson-jittered arrival times
 (exponential inter-arrival gaps of mean 1/fps). The loop
 
-  1. admits every frame whose arrival time has passed with densify_submit;
-     a frame refused with DENSIFY_E_AGAIN (all slots admitted or the scratch
-     arena full) stays in the backlog and is retried on the next turn,
+  1. admits every frame whose arrival time has passed with densify_submit,
+     in arrival order over the viewpoints (each viewpoint's frames wait in
+     its own queue, so a turn costs the same whatever the backlog); a frame
+     refused with DENSIFY_E_AGAIN (all slots admitted or the scratch arena
+     full) stays queued and is retried on the next turn,
   2. calls densify_flush(ctx, 0), which sends the queued frames to the GPU as
      one batch as soon as a launch slot is free (frames that arrived while the
      GPU was busy go out together),
@@ -23,6 +25,7 @@ from __future__ import annotations
 
 import heapq
 import time
+from collections import deque
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -80,38 +83,39 @@ class ServeLoop:
 
     def run(self, arrivals, duration_s: float, drain_s: float = 5.0) -> ServeStats:
         st = ServeStats(offered=len(arrivals))
-        backlog = []                  # heap of (arrival time, seq, view)
+        waiting = [deque() for _ in self.frames]   # per viewpoint: arrival times not yet admitted
         outstanding = {}              # ticket -> (arrival time, view, slot)
         busy = [[False] * self.ring for _ in self.frames]
         next_slot = [0] * len(self.frames)
+        backlog = 0
         i = 0
-        seq = 0
         t0 = self.clock()
         end = duration_s + drain_s
         while True:
             now = self.clock() - t0
             while i < len(arrivals) and arrivals[i][0] <= now:
-                heapq.heappush(backlog, (arrivals[i][0], seq, arrivals[i][1]))
-                seq += 1
+                waiting[arrivals[i][1]].append(arrivals[i][0])
+                backlog += 1
                 i += 1
-            # admit in arrival order
-            kept = []
-            while backlog:
-                ta, s, v = heapq.heappop(backlog)
+            # admit in arrival order over the viewpoints whose next output slot is free (a viewpoint's
+            # later frames wait behind its first); E_AGAIN ends admission for this turn. The heap holds
+            # one entry per viewpoint, so a turn costs O(viewpoints), whatever the backlog.
+            heads = [(q[0], v) for v, q in enumerate(waiting) if q and not busy[v][next_slot[v]]]
+            heapq.heapify(heads)
+            while heads:
+                ta, v = heapq.heappop(heads)
                 slot = next_slot[v]
-                if busy[v][slot]:
-                    kept.append((ta, s, v))
-                    continue
                 status, ticket = self.d.try_submit(self.frames[v][slot])
                 if status == DENSIFY_E_AGAIN:
                     st.refused_again += 1
-                    kept.append((ta, s, v))
                     break
+                waiting[v].popleft()
+                backlog -= 1
                 busy[v][slot] = True
                 next_slot[v] = (slot + 1) % self.ring
                 outstanding[ticket] = (ta, v, slot)
-            for k in kept:
-                heapq.heappush(backlog, k)
+                if waiting[v] and not busy[v][next_slot[v]]:
+                    heapq.heappush(heads, (waiting[v][0], v))
             self.d.flush(0)
             done = []
             for ticket, (ta, v, slot) in outstanding.items():
