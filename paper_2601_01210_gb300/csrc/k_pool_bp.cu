@@ -14,10 +14,11 @@ namespace dz {
 // block's in-image pixels as the coarse guide. Sums run in row-major order.
 // ---------------------------------------------------------------------------
 // A work item is one coarse row J and a segment of 256 coarse pixels; one
-// thread per coarse pixel. For f = 3, a block inside the image and
-// word-aligned rows, the thread issues all 18 word loads of its block first:
-// per row the 3 z-buffer words and the 3 aligned RGB words covering the row's
-// 9 colour bytes (byte offset 9I, rounded down to a word). The colour bytes are
+// thread per coarse pixel. For f = 3 the thread reads 18 words of its block:
+// per row the 3 z-buffer words and the 3 aligned words covering the row's 9
+// colour bytes (byte offset 9I, rounded down to a word), from the item's rows
+// staged in shared memory by bulk copies (pool_kernel), or from global memory
+// (all 18 loads issued first) for items at a ragged edge. The colour bytes are
 // shifted into place, each channel's 3 bytes gathered by a byte permute and
 // summed by dp4a: integer sums, exactly the FP32 sums of the bytes. Blocks at
 // the image border, other factors and layouts use plain loads.
