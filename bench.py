@@ -41,7 +41,7 @@ METRIC = "1080p dense-depth frames/s (3 merged LiDAR scans, two-stage JBF r=4@1/
 UNIT = "frames/s"
 # issue slots of one filter tap in each arithmetic form: the last-resort peak model, used only when
 # neither the committed nor a live measurement of the instruction rates is available
-TAP_INSTR = {"fp32": 10.0, "fp32_expanded": 6.0, "fp32_expanded_pairs": 3.5}
+TAP_INSTR = {"fp32": 10.0, "fp32_expanded": 6.0, "fp32_expanded_pairs": 3.5, "fp32_sparse": 15.0, "fp16_sparse": 18.5}
 ALU_PEAKS = os.path.join(ROOT, "profiles", "alu_peaks.json")
 STAGES = ((4, 5.0, 20.0), (2, 5.0, 20.0))
 L2_FLUSH_BYTES = 256 << 20

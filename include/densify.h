@@ -146,7 +146,8 @@ typedef struct densify_stage {
  *                 tolerance). For a single stage on the z-buffer the sparse
  *                 form runs first: a warp walks only the observed positions
  *                 of its 8 x 8 block's footprint and sums in registers (same
- *                 weights up to a per-pixel factor that cancels). 1: the plain
+ *                 weights up to a per-pixel factor that cancels; in FP16, with
+ *                 half2 weights and FP32 sums). 1: the plain
  *                 kernels everywhere (difference form, for comparison). 2: the
  *                 TMA kernels in the difference form only (the same bits as
  *                 1).

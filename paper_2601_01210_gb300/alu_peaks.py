@@ -50,6 +50,12 @@ FORMS = {
     # position): row offset, squared distance, 4 fma exponent, 2 sums, half the column terms of the
     # two pixels a lane owns; window test (max, compare); half of the position's loads and loop work
     "fp32_sparse": {"fma": 9.0, "fma2": 0.0, "ex2": 1.0, "other": 5.0},
+    # the sparse form with FP16 weights (per evaluated pixel and position, half of a lane's pair):
+    # FP32 row offset, window test, squared distance and its kp product, the sums (num, weight,
+    # squared-depth term); half of the pair's half2 differences, squares and exponent (7 half2
+    # instructions) and of its ex2.approx.f16x2; packing and widening, the position's loads and
+    # loop work
+    "fp16_sparse": {"fma": 9.0, "fma2": 0.0, "ex2": 0.0, "ex2_h2": 0.5, "hfma2": 3.5, "other": 5.5},
 }
 
 
@@ -116,18 +122,22 @@ def tap_peaks(rates_per_sm_clk):
                        "bounds_taps_per_sm_clk": {"measured_tap_loop": round(rates_per_sm_clk["tap_fp16"], 3)},
                        "thread_instructions_per_tap": None}
     for form, k in FORMS.items():
-        instr = (k["fma"] + k["fma2"] + k["ex2"] + k.get("dp4a", 0.0) + k.get("lds", 0.0) + k.get("red", 0.0) +
-                 k.get("other", 0.0))
-        bounds = {"issue": ISSUE_PER_SM_CLK / instr,
-                  "ex2": rates_per_sm_clk["ex2_f32"] / k["ex2"]}
+        instr = (k["fma"] + k["fma2"] + k["ex2"] + k.get("ex2_h2", 0.0) + k.get("hfma2", 0.0) + k.get("dp4a", 0.0) +
+                 k.get("lds", 0.0) + k.get("red", 0.0) + k.get("other", 0.0))
+        bounds = {"issue": ISSUE_PER_SM_CLK / instr}
+        if k["ex2"]:
+            bounds["ex2"] = rates_per_sm_clk["ex2_f32"] / k["ex2"]
+        if k.get("ex2_h2"):
+            bounds["ex2"] = rates_per_sm_clk["ex2_f16x2"] / k["ex2_h2"]
         if k.get("dp4a") and "dp4a" not in rates_per_sm_clk:
             continue
         if k.get("red"):
             if "red_shared_f32" not in rates_per_sm_clk:
                 continue
             bounds["smem_atomic"] = rates_per_sm_clk["red_shared_f32"] / k["red"]
-        if k["fma"]:
-            bounds["fma_pipe"] = rates_per_sm_clk["ffma"] / k["fma"]
+        if k["fma"]:   # with the form's half2 FMAs on the same pipe
+            bounds["fma_pipe"] = 1.0 / (k["fma"] / rates_per_sm_clk["ffma"] +
+                                        k.get("hfma2", 0.0) / rates_per_sm_clk.get("hfma2", 1.0))
         if k["fma2"]:   # with the form's dp4a on the same pipe
             bounds["fma_pipe"] = 1.0 / (k["fma2"] / rates_per_sm_clk["ffma2"] +
                                         k.get("dp4a", 0.0) / rates_per_sm_clk.get("dp4a", 1.0))

@@ -63,15 +63,6 @@ __device__ __forceinline__ bool half_record(const uint4 &q, float &r, float &g, 
     return r < 65000.0f;
 }
 
-__device__ __forceinline__ __half2 h2bits(uint32_t u) { return *reinterpret_cast<const __half2 *>(&u); }
-__device__ __forceinline__ uint32_t h2u(__half2 h) { return *reinterpret_cast<const uint32_t *>(&h); }
-
-__device__ __forceinline__ __half2 h2exp2_approx(__half2 x) {
-    uint32_t y;
-    asm("ex2.approx.f16x2 %0, %1;" : "=r"(y) : "r"(h2u(x)));
-    return h2bits(y);
-}
-
 // Resident CTAs per SM the compiler is asked to fit (registers): 16 warps per SM; 32 for the
 // paired form at two rows per thread, whose state fits 64 registers; 24 for the scalar expanded
 // form at two rows per thread, whose state fits 80 (the pooled first stage's 32 x 16 tiles: three
@@ -85,13 +76,6 @@ constexpr int tma_min_ctas(int form, int kp, int nw) {
            nw;
 }
 
-// FP16 form: bound on the relative error of a weight (2^(e) with e = -kc |dc|^2 + spatial term
-// evaluated in half precision: roundings of kc, of the squared distance and of e, about 2^-10.4 of
-// |e| each, for |e| <= 24, plus the ex2.approx.f16 error), and the weighted standard deviation of a
-// window's depths, as a fraction of the pixel's depth, above which the pixel is recomputed in FP32
-// (kHalfWeightErr * kHalfStdFrac = 5e-4, half the 1e-3 relative bar).
-constexpr float kHalfWeightErr = 0.02f;
-constexpr float kHalfStdFrac = 5e-4f / kHalfWeightErr;
 
 // A frame's outputs as the filter writes them, copied into shared memory once per CTA: the outputs
 // of a tile then wait on no read of the frame descriptor.
@@ -338,7 +322,7 @@ __global__ void __launch_bounds__(NW * 32, tma_min_ctas(FORM, KP, NW)) jbf_tma_k
                     out_valid[o] = v;
                 }
             };
-            if (sparse_tile<R, KP, NW>(a, x0, y0, gw, gh, rawA(buf), rawB(buf), smem, bad, [&]() {
+            if (sparse_tile<R, KP, NW, FORM == FORM_SPARSE_FP16>(a, x0, y0, gw, gh, rawA(buf), rawB(buf), smem, bad, [&]() {
                     if (threadIdx.x == 0 && n1 < total) advance();   // off the path of the CTA's barriers
                 }, store)) {
                 leave();

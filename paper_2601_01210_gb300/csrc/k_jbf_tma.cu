@@ -49,14 +49,14 @@ bool jbf_tma_info(int src, int r, TmaVariant v, int form, TmaKernelInfo *out) {
 }
 
 cudaError_t jbf_tma_prepare(int src, int r, TmaVariant v, int form) {
-    return form == TMA_FORM_SPARSE ? jbf_tma_sp_prepare(src, r, v, form)
+    return form >= TMA_FORM_SPARSE ? jbf_tma_sp_prepare(src, r, v, form)
            : form >= TMA_FORM_EXP   ? jbf_tma_exp_prepare(src, r, v, form)
                                     : base_prepare(src, r, v, form);
 }
 
 cudaError_t launch_jbf_tma(int src, int r, TmaVariant v, int form, const BatchDev *b, const StageArgs &a, int grid,
                            cudaStream_t s) {
-    return form == TMA_FORM_SPARSE ? jbf_tma_sp_launch(src, r, v, form, b, a, grid, s)
+    return form >= TMA_FORM_SPARSE ? jbf_tma_sp_launch(src, r, v, form, b, a, grid, s)
            : form >= TMA_FORM_EXP   ? jbf_tma_exp_launch(src, r, v, form, b, a, grid, s)
                                     : base_launch(src, r, v, form, b, a, grid, s);
 }
@@ -70,7 +70,7 @@ cudaError_t launch_tile_mark(int src, const BatchDev *b, int stage, int th, int 
 }
 
 int occupancy_jbf_tma(int src, int r, TmaVariant v, int form) {
-    const int n = form == TMA_FORM_SPARSE ? jbf_tma_sp_occupancy(src, r, v, form)
+    const int n = form >= TMA_FORM_SPARSE ? jbf_tma_sp_occupancy(src, r, v, form)
                   : form >= TMA_FORM_EXP   ? jbf_tma_exp_occupancy(src, r, v, form)
                                            : base_occupancy(src, r, v, form);
     return n > 0 ? n : 1;

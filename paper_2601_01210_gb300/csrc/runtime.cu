@@ -285,7 +285,7 @@ std::vector<FilterSel> filter_candidates(const densify_params &p, int kind, int 
             s.kind = kind;
             s.radius = r;
             s.tma = true;
-            s.half = form == TMA_FORM_FP16;
+            s.half = form == TMA_FORM_FP16 || form == TMA_FORM_SPARSE_FP16;
             s.form = form;
             s.src = src;
             s.kp = vs[i].kp;
@@ -298,6 +298,8 @@ std::vector<FilterSel> filter_candidates(const densify_params &p, int kind, int 
     };
     if (allowed) {
         if (half) {
+            // the single stage on the z-buffer: the sparse form first, as in FP32
+            if (kind == 0) add_tma(TMA_FORM_SPARSE_FP16);
             add_tma(TMA_FORM_FP16);
         } else {
             // expanded FP32 form first where its weights stay in range (colours centred at 128)
@@ -693,7 +695,7 @@ void cache_store(const std::string &key, const std::string &val) {
 }
 
 std::string cand_name(const FilterSel &f) {
-    static const char *forms[] = {"fp32", "fp16", "exp", "exp_pairs", "sparse"};
+    static const char *forms[] = {"fp32", "fp16", "exp", "exp_pairs", "sparse", "sparse_fp16"};
     return std::string(f.tma ? "tma" : "plain") + ":kp" + std::to_string(f.kp) + ":nw" + std::to_string(f.nw) +
            (f.tma ? std::string(":") + forms[f.form] : std::string());
 }
@@ -1572,7 +1574,8 @@ int32_t densify_describe(densify_ctx *c, char *buf, int32_t cap) {
                       "{\"kernel\": \"%s\", \"kp\": %d, \"warps\": %d, \"tile\": [%d, %d], \"fp16\": %s, "
                       "\"form\": \"%s\", \"ctas_per_sm\": %d%s",
                       f.tma ? "tma" : "plain", f.kp, f.nw, f.tile_w, f.tile_h, f.half ? "true" : "false",
-                      f.half                          ? "fp16"
+                      f.form == TMA_FORM_SPARSE_FP16 ? "fp16_sparse"
+                      : f.half                        ? "fp16"
                       : f.form == TMA_FORM_SPARSE    ? "fp32_sparse"
                       : f.form == TMA_FORM_EXP_PAIRS ? "fp32_expanded_pairs"
                       : f.form == TMA_FORM_EXP        ? "fp32_expanded"

@@ -3,6 +3,8 @@
 // the tile geometry that the kernels and the host's tensor-map boxes agree on.
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include <cstdint>
 
 #include "desc.cuh"
@@ -71,21 +73,42 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *m, int
 
 __device__ __forceinline__ int floor_div3(int a) { return a >= 0 ? a / 3 : -((2 - a) / 3); }
 
+// half2 <-> its 32 bits, and ex2.approx.f16x2 (the FP16 forms' weights)
+__device__ __forceinline__ __half2 h2bits(uint32_t u) { return *reinterpret_cast<const __half2 *>(&u); }
+__device__ __forceinline__ uint32_t h2u(__half2 h) { return *reinterpret_cast<const uint32_t *>(&h); }
+
+__device__ __forceinline__ __half2 h2exp2_approx(__half2 x) {
+    uint32_t y;
+    asm("ex2.approx.f16x2 %0, %1;" : "=r"(y) : "r"(h2u(x)));
+    return h2bits(y);
+}
+
+// FP16 form: bound on the relative error of a weight (2^(e) with e = -kc |dc|^2 + spatial term
+// evaluated in half precision: roundings of kc, of the squared distance and of e, about 2^-10.4 of
+// |e| each, for |e| <= 24, plus the ex2.approx.f16 error), and the weighted standard deviation of a
+// window's depths, as a fraction of the pixel's depth, above which the pixel is recomputed in FP32
+// (kHalfWeightErr * kHalfStdFrac = 5e-4, half the 1e-3 relative bar).
+constexpr float kHalfWeightErr = 0.02f;
+constexpr float kHalfStdFrac = 5e-4f / kHalfWeightErr;
+
+
 constexpr int ceil_to(int x, int m) { return (x + m - 1) / m * m; }
 
 // Tile geometry shared by the kernel and the host (tensor-map boxes).
 // Arithmetic forms of the kernels (the host's TMA_FORM_* values).
-enum { FORM_FP32 = 0, FORM_FP16 = 1, FORM_EXP = 2, FORM_EXP_PAIRS = 3, FORM_SPARSE = 4 };
+enum { FORM_FP32 = 0, FORM_FP16 = 1, FORM_EXP = 2, FORM_EXP_PAIRS = 3, FORM_SPARSE = 4, FORM_SPARSE_FP16 = 5 };
 
 // Tile geometry shared by the kernels and the host (tensor-map boxes). The
 // paired form filters 64-column tiles, a thread taking columns c and c + 32;
 // its staged records are slots of SP = 32 + 2R per staged row, slot s holding
-// staged columns s and s + 32 side by side. The sparse form (jbf_sparse.cuh)
-// keeps a 32-byte record per staged position (written for the observed ones)
+// staged columns s and s + 32 side by side. The sparse forms (jbf_sparse.cuh,
+// FP32 and FP16 weights) keep a 32-byte record per staged position (written for
+// the observed ones)
 // and one 64-bit observation mask per staged row.
 template <int SRC, int R, int KP, int NW_ = 8, int FORM = FORM_FP32>
 struct TmaGeom {
-    static constexpr bool EXP = FORM == FORM_EXP, PAIRS = FORM == FORM_EXP_PAIRS, SPARSE = FORM == FORM_SPARSE;
+    static constexpr bool EXP = FORM == FORM_EXP, PAIRS = FORM == FORM_EXP_PAIRS;
+    static constexpr bool SPARSE = FORM == FORM_SPARSE || FORM == FORM_SPARSE_FP16;
     static constexpr int TW = PAIRS ? 64 : 32, NW = NW_, TH = NW * KP, SW = TW + 2 * R, SH = TH + 2 * R;
     static constexpr int SP = PAIRS ? 32 + 2 * R : SW;   // staged records per staged row
     // RGB bytes: box starts at byte 3*x0 - RGB_LEAD (x0 is a multiple of 32, so 3*x0 of 16)

@@ -32,10 +32,11 @@ struct TmaKernelInfo {
 // squared colour distance expanded into a dot product (weights kept in range
 // only while kc * 3 * 128^2 + kp * 2 R^2 <= kExpRange, see jbf_tma.cuh), the
 // expanded form on pairs of output columns in packed two-lane FP32 arithmetic
-// (64-column tiles, see jbf_pair.cuh), and the sparse form on the same weights (a warp
-// walks only the observed positions of its block's footprint; the single stage on the
-// z-buffer, see jbf_sparse.cuh).
-enum { TMA_FORM_FP32 = 0, TMA_FORM_FP16 = 1, TMA_FORM_EXP = 2, TMA_FORM_EXP_PAIRS = 3, TMA_FORM_SPARSE = 4 };
+// (64-column tiles, see jbf_pair.cuh), and the sparse forms (a warp walks only the
+// observed positions of its block's footprint; the single stage on the z-buffer, see
+// jbf_sparse.cuh) with the expanded FP32 weights or with FP16 guide and weights.
+enum { TMA_FORM_FP32 = 0, TMA_FORM_FP16 = 1, TMA_FORM_EXP = 2, TMA_FORM_EXP_PAIRS = 3, TMA_FORM_SPARSE = 4,
+       TMA_FORM_SPARSE_FP16 = 5 };
 constexpr double kExpRange = 100.0;
 
 // Instantiated variants of (source, radius, form).

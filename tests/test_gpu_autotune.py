@@ -65,7 +65,7 @@ def test_tuned_equals_untuned_and_cache_is_reused(tmp_path, monkeypatch, precisi
 
 
 _FORM_TAG = {"fp32": "fp32", "fp16": "fp16", "fp32_expanded": "exp", "fp32_expanded_pairs": "exp_pairs",
-             "fp32_sparse": "sparse"}
+             "fp32_sparse": "sparse", "fp16_sparse": "sparse_fp16"}
 
 
 @pytest.mark.parametrize("stage", [0, 1])

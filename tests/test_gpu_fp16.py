@@ -69,6 +69,51 @@ def test_fp16_qvga_single_stage():
         _check(g, o, f"qvga 9x9 seed {seed}")
 
 
+@pytest.mark.parametrize("radius,sigma_p", [(4, 3.0), (7, 5.0), (2, 5.0)])
+def test_fp16_single_stage_every_candidate(tmp_path, monkeypatch, radius, sigma_p):
+    """Each FP16 kernel the tuner may pick for a single stage (the sparse form with FP16 weights and
+    the gather form with FP16 weights), forced through a tuning-cache entry, holds the FP16 bar against
+    the oracle (two 320x240 views and a 960x540 view in one batch: ragged tiles of every kind)."""
+    import torch
+    import oracle
+    from paper_2601_01210_gb300 import Densifier, build
+    from paper_2601_01210_gb300.frames import FrameBuffers
+    build.build()
+    st = ((radius, sigma_p, 20.0),)
+    views = [scene.make_workload("qvga_1scan", 1003), scene.make_workload("qvga_1scan", 1011),
+             scene.make_batch_view(80, "540p", 0, 2)]
+
+    def run(**params):
+        with Densifier(dict(num_stages=1, stages=st, precision=1, launch_policy=1, max_batch=8, **params)) as d:
+            bufs = [FrameBuffers(v.camera, v.rgb, [(s.xyz, s.lidar_to_world) for s in v.scans], debug=True,
+                                 num_stages=1) for v in views]
+            ts = [d.submit(b.frame) for b in bufs]
+            d.flush()
+            for t in ts:
+                assert d.poll(t, -1) == 0
+            torch.cuda.synchronize()
+            return [b.results() for b in bufs], d.describe()
+
+    _, desc = run()
+    oracles = [oracle.densify_view(v, num_stages=1, stages=st) for v in views]
+    px = sum(v.rgb.shape[0] * v.rgb.shape[1] for v in views)
+    key = f"kind=0,r={radius},half=1,px=2^{px.bit_length() - 1}"
+    tag = {"fp16": "fp16", "fp16_sparse": "sparse_fp16"}
+    tried = set()
+    for c in desc["stages"][0]["candidates"]:
+        name = f"tma:kp{c['kp']}:nw{c['warps']}:{tag[c['form']]}"
+        cache = tmp_path / f"{radius}_{name.replace(':', '_')}.txt"
+        cache.write_text(f"{key} {name}\n")
+        monkeypatch.setenv("DENSIFY_TUNE_CACHE", str(cache))
+        got, d = run(autotune=1)
+        ch = d["stages"][0]["chosen"]
+        assert (ch["kp"], ch["warps"], ch["form"]) == (c["kp"], c["warps"], c["form"])
+        for g, o, v in zip(got, oracles, views):
+            _check(g, o, f"{name} {v.name}")
+        tried.add(c["form"])
+    assert tried == {"fp16", "fp16_sparse"}
+
+
 def test_fp16_uneven_views_two_stage():
     import torch
     import oracle
